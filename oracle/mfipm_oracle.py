@@ -1,0 +1,414 @@
+"""CPU oracle for the matrix-free primal-dual IPM of l1-regularised least squares.
+
+TEST INFRASTRUCTURE ONLY.  Nothing in the product path may import, call or run
+this module: only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline
+leg of ``bench.py`` use it.  It shares no code with the CUDA path.
+
+What it computes (all float64, plain numpy; scipy only for Cholesky and the
+library DCT):
+
+* the problem  min tau*||x||_1 + 1/2||Ax-b||^2  via the split x = u - v,
+  z = [u; v] >= 0 and the QP  min tau*1^T z + 1/2||F^T z - b||^2,
+  F^T = [A, -A]                                      (Sec. 1, Eqs. uvDef, lintechni, wrightBPDN)
+* its dual slack  s = c + F F^T z,  c = [tau - A^T b; tau + A^T b]
+                                                      (Sec. 3, Eq. dualquadraticBPDN)
+* the residuals f_z = s - c - F F^T z, f_s = sigma*mu*e - Z S e, mu = z^T s/(2n)
+                                                      (Sec. 3, Eq. fzfs)
+* the Newton direction from the reduced system
+  (Theta^-1 + F F^T) dz = f_z + Z^-1 f_s,  ds = Z^-1 f_s - Theta^-1 dz,
+  Theta = S^-1 Z                                      (Sec. 3, Eqs. redNewtonA, redNewtonB)
+  solved EXACTLY: Cholesky of the 2n x 2n matrix, or of the m x m matrix
+  I + A (Theta_u + Theta_v) A^T through the Sherman-Morrison-Woodbury identity
+  (the paper's own direct-solver variant of the IPM, Sec. 5.7)
+* the single-centrality-corrector primal-dual IPM loop  (Sec. 5.1, Algorithm
+  "Single-Corrector Primal-Dual Matrix-Free IPM", parameters sigma1=0.1,
+  sigma2=0.5, sigma3=0.8, alpha_bar=0.5, alpha_tilde=0.1)
+* the paper's preconditioner P and a plain PCG on the 2n system
+                                                      (Sec. 4, Eqs. eq:ne2_H, eq:ne2_P)
+  used by the pins (Theorem thm:ne2_prec) and to count PCG work; the oracle's
+  solve itself never uses PCG.
+* certificates: the prox (KKT) residual of the l1 problem and an l1 duality-gap
+  certificate.
+
+Readings where the paper is silent or ambiguous (each also listed in the design doc):
+  R1 objective has the 1/2 factor (the QP of Eq. wrightBPDN) although Eq.
+     formulationsnoisy1 prints it without;
+  R2 rho = ||A||_F^2 / n (the Frobenius-closest multiple of I to A^T A; equals
+     the printed m/n when A A^T = I);
+  R3 z0 = s0 = 1;
+  R4 step to the boundary alpha = min(1, eta*min_{dz_i<0} -z_i/dz_i),
+     eta = 0.995 (Algorithm asks for the largest alpha keeping z > 0, which is
+     not attained);
+  R5 separate primal and dual step lengths as in the Algorithm;
+  R6 corrector: right-hand side from Eq. fzfs at the trial point with sigma3 and
+     the trial point's mu; the matrix Theta and Z^-1 stay those of the current
+     iterate; the combined direction is stepped from the current iterate;
+  R7 termination on the relative duality gap  z^T s / (1 + |P(z)|) <= tol
+     (Sec. 5.1 "Duality Gap", Sec. 5.4 "tol");
+  R8 sigma = sigma2 on iterations k != 1 whose previous step had
+     alpha_P <= alpha_bar or alpha_D <= alpha_bar, else sigma1.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+from typing import Callable, Optional
+
+import numpy as np
+import scipy.fft
+import scipy.linalg
+
+# Paper parameters (Sec. 5.1, after the Algorithm; Sec. 5.4).
+SIGMA1, SIGMA2, SIGMA3 = 0.1, 0.5, 0.8
+ALPHA_BAR, ALPHA_TILDE = 0.5, 0.1
+MAXITERS = 100
+MXITERPCG = 200
+
+
+# --------------------------------------------------------------------------------------
+# Operators
+# --------------------------------------------------------------------------------------
+def dct_matrix_rows(n: int, rows) -> np.ndarray:
+    """Rows of the orthonormal n x n DCT-II matrix, from its definition
+    C[j,k] = alpha_j cos(pi j (2k+1) / (2n)), alpha_0 = sqrt(1/n), alpha_j = sqrt(2/n)
+    (Sec. 2: partial DCT with orthonormal rows, Eq. eq:orthonormality)."""
+    rows = np.asarray(rows, dtype=np.int64)
+    j = rows[:, None].astype(np.float64)
+    k = np.arange(n, dtype=np.float64)[None, :]
+    alpha = np.where(rows == 0, math.sqrt(1.0 / n), math.sqrt(2.0 / n))[:, None]
+    # (j*(2k+1)) mod 4n keeps the cosine argument small and exact in float64
+    arg = np.mod(rows[:, None] * (2 * np.arange(n, dtype=np.int64)[None, :] + 1), 4 * n)
+    return alpha * np.cos(np.pi * arg.astype(np.float64) / (2.0 * n))
+
+
+def dct_rows_apply(x: np.ndarray, rows: np.ndarray) -> np.ndarray:
+    """A x for the partial DCT via the library DCT (large-n certificates only)."""
+    return scipy.fft.dct(np.asarray(x, dtype=np.float64), type=2, norm="ortho")[rows]
+
+
+def dct_rows_apply_t(y: np.ndarray, rows: np.ndarray, n: int) -> np.ndarray:
+    full = np.zeros(n)
+    full[rows] = y
+    return scipy.fft.idct(full, type=2, norm="ortho")
+
+
+class Operator:
+    """A as the two products x -> A x and y -> A^T y (Sec. 1: A used only as an operator)."""
+
+    def __init__(self, m: int, n: int, mv: Callable, rmv: Callable, dense: Optional[np.ndarray] = None):
+        self.m, self.n, self.mv, self.rmv, self.dense = m, n, mv, rmv, dense
+
+    @staticmethod
+    def from_dense(A: np.ndarray) -> "Operator":
+        A = np.asarray(A, dtype=np.float64)
+        return Operator(A.shape[0], A.shape[1], lambda x: A @ x, lambda y: A.T @ y, A)
+
+    @staticmethod
+    def from_dct_rows(n: int, rows, explicit: bool = True) -> "Operator":
+        rows = np.asarray(rows, dtype=np.int64)
+        if explicit:
+            return Operator.from_dense(dct_matrix_rows(n, rows))
+        return Operator(len(rows), n, lambda x: dct_rows_apply(x, rows),
+                        lambda y: dct_rows_apply_t(y, rows, n))
+
+
+# --------------------------------------------------------------------------------------
+# Problem quantities (Sec. 1 and Sec. 3)
+# --------------------------------------------------------------------------------------
+def soft_threshold(y: np.ndarray, tau: float) -> np.ndarray:
+    return np.sign(y) * np.maximum(np.abs(y) - tau, 0.0)
+
+
+def objective(op: Operator, b, tau, x) -> float:
+    """tau*||x||_1 + 1/2||Ax-b||^2 (reading R1)."""
+    r = op.mv(x) - b
+    return tau * float(np.abs(x).sum()) + 0.5 * float(r @ r)
+
+
+def c_vector(op: Operator, b, tau) -> np.ndarray:
+    """c = [tau*1 - A^T b; tau*1 + A^T b]  (Sec. 3, below Eq. dualquadraticBPDN)."""
+    atb = op.rmv(b)
+    return np.concatenate([tau - atb, tau + atb])
+
+
+def FFt_apply(op: Operator, z: np.ndarray) -> np.ndarray:
+    """F F^T z with F^T = [A, -A]  (Sec. 1, Eq. wrightBPDN; block form Eq. eq:ne2_H)."""
+    n = op.n
+    t = op.rmv(op.mv(z[:n] - z[n:]))
+    return np.concatenate([t, -t])
+
+
+def primal_value(op: Operator, b, tau, z) -> float:
+    """P(z) = tau*1^T z + 1/2||F^T z - b||^2  (Eq. wrightBPDN)."""
+    n = op.n
+    r = op.mv(z[:n] - z[n:]) - b
+    return tau * float(z.sum()) + 0.5 * float(r @ r)
+
+
+def residuals(op: Operator, b, tau, z, s, c):
+    """f_z = s - c - F F^T z and mu = z^T s / (2n)  (Sec. 3, Eq. fzfs)."""
+    fz = s - c - FFt_apply(op, z)
+    mu = float(z @ s) / z.size
+    return fz, mu
+
+
+def complementarity_rhs(z, s, sigma, mu):
+    """f_s = sigma*mu*e - Z S e  (Eq. fzfs); it vanishes on the central path z o s = mu e
+    when sigma = 1 (Sec. 4: the IPM perturbs z_j s_j = mu)."""
+    return sigma * mu - z * s
+
+
+def newton_rhs(fz, fs, z):
+    """Right-hand side of the reduced Newton system  f_z + Z^-1 f_s  (Eq. redNewtonA)."""
+    return fz + fs / z
+
+
+def recover_ds(fs, z, d, dz):
+    """ds = Z^-1 f_s - Theta^-1 dz,  Theta^-1 = Z^-1 S = d  (Eq. redNewtonB)."""
+    return fs / z - d * dz
+
+
+# --------------------------------------------------------------------------------------
+# Exact solves of (Theta^-1 + F F^T) dz = r   (Sec. 5.7 direct variant)
+# --------------------------------------------------------------------------------------
+def newton_matrix(op: Operator, d: np.ndarray) -> np.ndarray:
+    """H = Theta^-1 + F F^T as an explicit 2n x 2n matrix (Eq. eq:ne2_matrix / eq:ne2_H)."""
+    A = op.dense
+    K = A.T @ A
+    H = np.block([[K, -K], [-K, K]])
+    H[np.diag_indices_from(H)] += d
+    return H
+
+
+def solve_full_cholesky(op: Operator, d, r):
+    H = newton_matrix(op, d)
+    cf = scipy.linalg.cho_factor(H, lower=True, check_finite=False)
+    return scipy.linalg.cho_solve(cf, r, check_finite=False)
+
+
+def solve_woodbury(op: Operator, d, r):
+    """(D + F F^T)^-1 r = D^-1 r - D^-1 F (I_m + F^T D^-1 F)^-1 F^T D^-1 r,
+    F^T D^-1 F = A (Theta_u + Theta_v) A^T; Cholesky of the m x m matrix."""
+    A = op.dense
+    n = op.n
+    theta = 1.0 / d
+    th_sum = theta[:n] + theta[n:]
+    M = (A * th_sum[None, :]) @ A.T
+    M[np.diag_indices_from(M)] += 1.0
+    Dr = theta * r
+    t = A @ (Dr[:n] - Dr[n:])
+    cf = scipy.linalg.cho_factor(M, lower=True, check_finite=False)
+    y = scipy.linalg.cho_solve(cf, t, check_finite=False)
+    aty = A.T @ y
+    return Dr - theta * np.concatenate([aty, -aty])
+
+
+def solve_newton_direct(op: Operator, d, r, method: str = "auto"):
+    if method == "auto":
+        method = "cholesky" if 2 * op.n <= 2048 else "woodbury"
+    return solve_full_cholesky(op, d, r) if method == "cholesky" else solve_woodbury(op, d, r)
+
+
+# --------------------------------------------------------------------------------------
+# The paper's preconditioner and PCG (Sec. 4)
+# --------------------------------------------------------------------------------------
+def rho_of(op: Operator) -> float:
+    """rho: the scalar of the Frobenius-closest rho*I to A^T A (reading R2):
+    rho = ||A||_F^2 / n  (= m/n when A A^T = I, Eq. eq:ne2_P)."""
+    if op.dense is not None:
+        return float((op.dense ** 2).sum()) / op.n
+    return op.m / op.n
+
+
+def precond_matrix(d: np.ndarray, rho: float) -> np.ndarray:
+    """P = [[Theta_u^-1 + rho I, -rho I], [-rho I, Theta_v^-1 + rho I]]  (Eq. eq:ne2_P)."""
+    n = d.size // 2
+    I = np.eye(n)
+    return np.block([[np.diag(d[:n]) + rho * I, -rho * I], [-rho * I, np.diag(d[n:]) + rho * I]])
+
+
+def precond_apply(d: np.ndarray, rho: float, r: np.ndarray) -> np.ndarray:
+    """P^-1 r, one 2x2 block per index i (blocks [[du+rho, -rho], [-rho, dv+rho]])."""
+    n = d.size // 2
+    du, dv, ru, rv = d[:n], d[n:], r[:n], r[n:]
+    det = (du + rho) * (dv + rho) - rho * rho
+    return np.concatenate([((dv + rho) * ru + rho * rv) / det, (rho * ru + (du + rho) * rv) / det])
+
+
+def H_apply(op: Operator, d, p):
+    """H p = Theta^-1 p + F F^T p  (Eq. eq:ne2_matrix)."""
+    return d * p + FFt_apply(op, p)
+
+
+def pcg(op: Operator, d, rhs, rho, tol, maxiter=MXITERPCG):
+    """Textbook preconditioned conjugate gradients on H dz = rhs from dz = 0 (Sec. 4).
+    Stops when sqrt(r^T P^-1 r) <= tol * sqrt(rhs^T P^-1 rhs).  Returns (dz, iterations)."""
+    x = np.zeros_like(rhs)
+    r = rhs.copy()
+    zz = precond_apply(d, rho, r)
+    p = zz.copy()
+    rz = float(r @ zz)
+    rz0 = rz
+    it = 0
+    while it < maxiter and rz > tol * tol * rz0:
+        q = H_apply(op, d, p)
+        alpha = rz / float(p @ q)
+        x += alpha * p
+        r -= alpha * q
+        zz = precond_apply(d, rho, r)
+        rz_new = float(r @ zz)
+        p = zz + (rz_new / rz) * p
+        rz = rz_new
+        it += 1
+    return x, it
+
+
+# --------------------------------------------------------------------------------------
+# Step lengths and the IPM (Sec. 5.1)
+# --------------------------------------------------------------------------------------
+def step_to_boundary(v: np.ndarray, dv: np.ndarray, eta: float) -> float:
+    """alpha = min(1, eta * min_{dv_i < 0} (-v_i / dv_i)); 1 if no component decreases (R4)."""
+    neg = dv < 0
+    if not neg.any():
+        return 1.0
+    return min(1.0, eta * float(np.min(-v[neg] / dv[neg])))
+
+
+@dataclasses.dataclass
+class OracleParams:
+    tol: float = 1e-12
+    max_iter: int = MAXITERS
+    sigma1: float = SIGMA1
+    sigma2: float = SIGMA2
+    sigma3: float = SIGMA3
+    alpha_bar: float = ALPHA_BAR
+    alpha_tilde: float = ALPHA_TILDE
+    eta: float = 0.995
+    equal_steps: bool = False
+    solver: str = "auto"        # "auto" | "cholesky" | "woodbury" | "pcg"
+    tol_pcg: float = 1e-2       # only for solver="pcg"
+
+
+@dataclasses.dataclass
+class OracleResult:
+    x: np.ndarray
+    z: np.ndarray
+    s: np.ndarray
+    iters: int
+    correctors: int
+    pcg_iters: int
+    rel_gap: float
+    dual_res: float
+    converged: bool
+    history: list
+
+
+def ipm(op: Operator, b, tau, params: Optional[OracleParams] = None) -> OracleResult:
+    """Single-corrector primal-dual IPM (Sec. 5.1, Algorithm) with the Newton systems of
+    Eq. redNewton solved exactly (Sec. 5.7), in float64."""
+    p = params or OracleParams()
+    n = op.n
+    N2 = 2 * n
+    c = c_vector(op, b, tau)
+    cnorm = float(np.linalg.norm(c))
+    rho = rho_of(op)
+    z = np.ones(N2)                       # R3
+    s = np.ones(N2)
+    aP_prev = aD_prev = 1.0
+    corr = 0
+    pcg_total = 0
+    hist = []
+
+    def solve(d, r):
+        nonlocal pcg_total
+        if p.solver == "pcg":
+            dz, it = pcg(op, d, r, rho, p.tol_pcg)
+            pcg_total += it
+            return dz
+        return solve_newton_direct(op, d, r, p.solver)
+
+    def steps(dz, ds):
+        aP = step_to_boundary(z, dz, p.eta)
+        aD = step_to_boundary(s, ds, p.eta)
+        if p.equal_steps:
+            aP = aD = min(aP, aD)
+        return aP, aD
+
+    converged = False
+    k = 0
+    rel_gap = dual_res = float("inf")
+    for k in range(1, p.max_iter + 1):
+        fz, mu = residuals(op, b, tau, z, s, c)
+        P = primal_value(op, b, tau, z)
+        rel_gap = float(z @ s) / (1.0 + abs(P))
+        dual_res = float(np.linalg.norm(fz)) / (1.0 + cnorm)
+        hist.append(dict(k=k, mu=mu, rel_gap=rel_gap, dual_res=dual_res, alpha_p=aP_prev, alpha_d=aD_prev))
+        if rel_gap <= p.tol:                                                     # R7
+            converged = True
+            break
+        if k != 1 and (aP_prev <= p.alpha_bar or aD_prev <= p.alpha_bar):        # R8
+            sigma = p.sigma2
+        else:
+            sigma = p.sigma1
+        # predictor
+        fs = complementarity_rhs(z, s, sigma, mu)
+        d = s / z
+        dz = solve(d, newton_rhs(fz, fs, z))
+        ds = recover_ds(fs, z, d, dz)
+        aP, aD = steps(dz, ds)
+        # corrector (R6)
+        if aP <= p.alpha_tilde or aD <= p.alpha_tilde:
+            corr += 1
+            zt = z + aP * dz
+            st = s + aD * ds
+            fzt, mut = residuals(op, b, tau, zt, st, c)
+            fst = complementarity_rhs(zt, st, p.sigma3, mut)
+            dz2 = solve(d, newton_rhs(fzt, fst, z))
+            ds2 = recover_ds(fst, z, d, dz2)
+            dz = dz + dz2
+            ds = ds + ds2
+            aP, aD = steps(dz, ds)
+        z = z + aP * dz
+        s = s + aD * ds
+        aP_prev, aD_prev = aP, aD
+    else:
+        k = p.max_iter
+    x = z[:n] - z[n:]
+    return OracleResult(x, z, s, k, corr, pcg_total, rel_gap, dual_res, converged, hist)
+
+
+# --------------------------------------------------------------------------------------
+# Certificates
+# --------------------------------------------------------------------------------------
+def gradient(op: Operator, b, x):
+    """g(x) = A^T (A x - b)."""
+    return op.rmv(op.mv(x) - b)
+
+
+def kkt_rel(op: Operator, b, tau, x) -> float:
+    """||x - S_tau(x - g(x))||_2 / (1 + ||x||_2): zero exactly at the minimiser."""
+    g = gradient(op, b, x)
+    return float(np.linalg.norm(x - soft_threshold(x - g, tau))) / (1.0 + float(np.linalg.norm(x)))
+
+
+def optimality_violation(op: Operator, b, tau, x, support_tol: float):
+    """Largest violation of the l1 optimality conditions: g_i = -tau*sign(x_i) where
+    |x_i| > support_tol, |g_i| <= tau elsewhere.  Returns (on-support, off-support)."""
+    g = gradient(op, b, x)
+    on = np.abs(x) > support_tol
+    v_on = float(np.max(np.abs(g[on] + tau * np.sign(x[on])))) if on.any() else 0.0
+    v_off = float(np.max(np.maximum(np.abs(g[~on]) - tau, 0.0))) if (~on).any() else 0.0
+    return v_on, v_off
+
+
+def dual_gap_certificate(op: Operator, b, tau, x):
+    """Duality gap of the l1 problem at a dual-feasible point built from x:
+    nu = (A x - b) * min(1, tau / ||A^T(Ax-b)||_inf), D(nu) = -1/2||nu||^2 - b^T nu,
+    and 0 <= P(x) - P* <= P(x) - D(nu).  Returns (P(x), D(nu))."""
+    r = op.mv(x) - b
+    g = op.rmv(r)
+    gi = float(np.abs(g).max())
+    nu = r * (min(1.0, tau / gi) if gi > 0 else 1.0)
+    P = tau * float(np.abs(x).sum()) + 0.5 * float(r @ r)
+    D = -0.5 * float(nu @ nu) - float(b @ nu)
+    return P, D

@@ -1,0 +1,183 @@
+"""Seeded synthetic inputs for the l1-regularised least-squares problems.
+
+This module only draws random problem data; it contains none of the solver's
+arithmetic.  Both the CPU oracle (``oracle/``) and the CUDA path (tests,
+``bench.py``) take their inputs from here, so the two sides always see the
+same problems.
+
+Problem:  min_x  tau*||x||_1 + 1/2*||A x - b||_2^2            (Sec. 1, Eq. formulationsnoisy1;
+                                                              the 1/2 form of Eq. wrightBPDN)
+with b = A x_hat + e,  e_i ~ N(0, sigma^2)                    (Eq. incomplsysnoisy)
+
+Operators:
+  * dense Gaussian ensemble, i.i.d. N(0, 1/m) entries         (Sec. 2, Table tbl:RIP; Table sparcocollect "gausspike")
+  * partial orthonormal DCT-II: m distinct rows of the n x n orthonormal DCT-II matrix,
+    chosen uniformly without replacement and sorted           (Sec. 2, Eq. eq:orthonormality; Sec. 5.8)
+  * the dense ensemble quantised to bf16 with one per-tensor scale: the problem's matrix is
+    exactly  a_scale * bf16(A / a_scale)
+
+The named workloads mirror the five benchmark configurations of this project
+(sizes in the docstrings of ``WORKLOADS``).  Random streams: numpy PCG64 seeded
+with the SeedSequence ``[seed, j]`` for problem ``j`` of a workload.
+"""
+from __future__ import annotations
+
+import dataclasses
+from typing import Optional
+
+import numpy as np
+import scipy.fft
+
+__all__ = [
+    "Problem", "dense_problem", "dct_problem", "bf16_dense_problems", "WORKLOADS",
+    "make_workload", "bf16_round", "dct_apply", "dct_apply_t",
+]
+
+
+@dataclasses.dataclass
+class Problem:
+    """One seeded l1-LS instance.  ``A`` (dense, row-major m x n float64) or
+    ``rows`` (partial DCT, sorted int64 row indices) describes the operator."""
+    kind: str                      # "dense" | "dct"
+    m: int
+    n: int
+    b: np.ndarray                  # (m,) float64
+    tau: float
+    x_hat: np.ndarray              # (n,) float64, the sparse signal b was made from
+    A: Optional[np.ndarray] = None     # dense: (m, n) float64 (already the exact problem matrix)
+    rows: Optional[np.ndarray] = None  # dct: (m,) int64 ascending
+    a_bf16: Optional[np.ndarray] = None  # bf16-quantised dense: (m, n) uint16 bit patterns
+    a_scale: float = 1.0
+    seed: tuple = ()
+
+
+def _rng(seed: int, j: int = 0) -> np.random.Generator:
+    return np.random.Generator(np.random.PCG64(np.random.SeedSequence([int(seed), int(j)])))
+
+
+def dct_apply(x: np.ndarray, rows: np.ndarray) -> np.ndarray:
+    """A x for the partial orthonormal DCT-II (library DCT; used only to synthesise b)."""
+    return scipy.fft.dct(x, type=2, norm="ortho")[rows]
+
+
+def dct_apply_t(y: np.ndarray, rows: np.ndarray, n: int) -> np.ndarray:
+    """A^T y for the partial orthonormal DCT-II (library inverse DCT)."""
+    full = np.zeros(n)
+    full[rows] = y
+    return scipy.fft.idct(full, type=2, norm="ortho")
+
+
+def _sparse_signal(rng, n, k, values):
+    x = np.zeros(n)
+    pos = rng.choice(n, size=k, replace=False)
+    if values == "pm1":
+        x[pos] = rng.choice(np.array([-1.0, 1.0]), size=k)
+    else:
+        x[pos] = rng.standard_normal(k)
+    return x
+
+
+def dense_problem(m: int, n: int, k: int, seed: int, j: int = 0, sigma: float = 1e-3,
+                  tau_frac: float = 0.01, values: str = "pm1") -> Problem:
+    """Gaussian A with N(0,1/m) entries, k-sparse x_hat (+-1 or N(0,1) values at uniform
+    positions), b = A x_hat + N(0, sigma^2), tau = tau_frac*||A^T b||_inf."""
+    rng = _rng(seed, j)
+    A = rng.standard_normal((m, n)) / np.sqrt(m)
+    x_hat = _sparse_signal(rng, n, k, values)
+    b = A @ x_hat + sigma * rng.standard_normal(m)
+    tau = tau_frac * float(np.abs(A.T @ b).max())
+    return Problem("dense", m, n, b, tau, x_hat, A=A, seed=(seed, j))
+
+
+def dct_problem(n: int, m: int, k: int, seed: int, j: int = 0, sigma: float = 1e-3,
+                tau_frac: float = 0.01, values: str = "normal") -> Problem:
+    """Partial orthonormal DCT-II with m of n rows (uniform, without replacement, sorted)."""
+    rng = _rng(seed, j)
+    rows = np.sort(rng.choice(n, size=m, replace=False)).astype(np.int64)
+    x_hat = _sparse_signal(rng, n, k, values)
+    b = dct_apply(x_hat, rows) + sigma * rng.standard_normal(m)
+    tau = tau_frac * float(np.abs(dct_apply_t(b, rows, n)).max())
+    return Problem("dct", m, n, b, tau, x_hat, rows=rows, seed=(seed, j))
+
+
+def bf16_round(a: np.ndarray) -> np.ndarray:
+    """Round float64 -> bfloat16 (round to nearest even) and return the uint16 bit patterns."""
+    f = np.ascontiguousarray(a, dtype=np.float32).view(np.uint32)
+    lsb = (f >> 16) & 1
+    rounded = (f + 0x7FFF + lsb) >> 16
+    return rounded.astype(np.uint16)
+
+
+def bf16_to_f64(bits: np.ndarray) -> np.ndarray:
+    return (bits.astype(np.uint32) << 16).view(np.float32).astype(np.float64)
+
+
+def bf16_dense_problems(m: int, n: int, k: int, nrhs: int, seed: int, sigma: float = 1e-3,
+                        tau_frac: float = 0.01):
+    """One shared Gaussian A stored as bf16 with a per-tensor scale (a_scale = 1/sqrt(m)),
+    and ``nrhs`` right-hand sides from k-sparse +-1 signals.  The problem matrix is exactly
+    a_scale * bf16(A/a_scale); b and tau are computed with that exact matrix."""
+    rng = _rng(seed, 0)
+    a_scale = 1.0 / np.sqrt(m)
+    bits = bf16_round(rng.standard_normal((m, n)))
+    A = a_scale * bf16_to_f64(bits)
+    probs = []
+    for j in range(nrhs):
+        r = _rng(seed, 1 + j)
+        x_hat = _sparse_signal(r, n, k, "pm1")
+        b = A @ x_hat + sigma * r.standard_normal(m)
+        tau = tau_frac * float(np.abs(A.T @ b).max())
+        probs.append(Problem("dense", m, n, b, tau, x_hat, A=A, a_bf16=bits, a_scale=a_scale,
+                             seed=(seed, j)))
+    return probs
+
+
+# The five benchmark workloads (sizes and distributions of this project's configurations).
+WORKLOADS = {
+    # Gaussian 256 x 1024 (the shape of Sparco "gausspike", Table sparcocollect), k=20 +-1 spikes
+    "dense_fp64_256x1024": dict(kind="dense", m=256, n=1024, k=20, values="pm1", seed=1001, count=1),
+    # partial DCT n=65536, m=16384, k=655 N(0,1) values
+    "dct_65536": dict(kind="dct", n=65536, m=16384, k=655, values="normal", seed=1002, count=1),
+    # 256 partial-DCT problems, n uniform in {2^12..2^16}, m=n/4, k uniform in [n/100, n/20]
+    "dct_batch_256": dict(kind="dct_batch", count=256, seed=1003),
+    # shared bf16 Gaussian 4096 x 16384, 64 right-hand sides, k=164 +-1 spikes
+    "bf16_4096x16384_64rhs": dict(kind="bf16", m=4096, n=16384, k=164, nrhs=64, seed=1004),
+    # 32 partial-DCT problems n=2^20, m=2^18, k=n/100 N(0,1)
+    "dct_adjoint_32x1M": dict(kind="dct", n=1 << 20, m=1 << 18, k=(1 << 20) // 100, values="normal",
+                              seed=1005, count=32),
+}
+
+
+def batch_sizes(count: int, seed: int):
+    """(n, m, k) for each problem of the uneven partial-DCT batch."""
+    rng = _rng(seed, 10**6)
+    ns = rng.choice(np.array([4096, 8192, 16384, 32768, 65536]), size=count)
+    out = []
+    for n in ns:
+        n = int(n)
+        k = int(rng.integers(n // 100, n // 20 + 1))
+        out.append((n, n // 4, k))
+    return out
+
+
+def make_workload(name: str, count: Optional[int] = None, scale_n: Optional[int] = None):
+    """Return the list of Problems of a named workload.  ``count`` truncates the batch;
+    ``scale_n`` (DCT only) replaces n by a smaller power of two with the same m/n and k/n
+    ratios, for oracle-sized cases."""
+    w = WORKLOADS[name]
+    if w["kind"] == "dense":
+        return [dense_problem(w["m"], w["n"], w["k"], w["seed"], j, values=w["values"])
+                for j in range(count or w["count"])]
+    if w["kind"] == "dct":
+        n, m, k = w["n"], w["m"], w["k"]
+        if scale_n:
+            m = m * scale_n // n
+            k = max(1, k * scale_n // n)
+            n = scale_n
+        return [dct_problem(n, m, k, w["seed"], j, values=w["values"]) for j in range(count or w["count"])]
+    if w["kind"] == "dct_batch":
+        sizes = batch_sizes(w["count"], w["seed"])[: (count or w["count"])]
+        return [dct_problem(n, m, k, w["seed"], j) for j, (n, m, k) in enumerate(sizes)]
+    if w["kind"] == "bf16":
+        return bf16_dense_problems(w["m"], w["n"], w["k"], count or w["nrhs"], w["seed"])
+    raise KeyError(name)
