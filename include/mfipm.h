@@ -1,0 +1,175 @@
+/*
+ * mfipm.h -- C ABI of the GB300 matrix-free primal-dual interior-point solver for
+ *
+ *     min_x  tau*||x||_1 + 1/2*||A x - b||_2^2                         (1)
+ *
+ * solved through the split x = u - v, z = [u; v] >= 0 and the quadratic program
+ * min tau*1^T z + 1/2*||F^T z - b||^2, F^T = [A, -A]   (arXiv:1208.5435, Sec. 1,
+ * Eqs. uvDef, lintechni, wrightBPDN).  Each Newton system of the primal-dual IPM
+ * (Sec. 3, Eqs. sepregaugeq, fzfs, redNewtonA/B) is solved by preconditioned
+ * conjugate gradients that touch A only through A*x and A^T*y, with the block
+ * preconditioner P of Sec. 4, Eq. eq:ne2_P.  The outer loop is the single-corrector
+ * IPM of Sec. 5.1 (Algorithm; sigma1=0.1, sigma2=0.5, sigma3=0.8, alpha_bar=0.5,
+ * alpha_tilde=0.1).
+ *
+ * Conventions for every entry point:
+ *   - Pointers named in a comment as DEVICE point to GPU memory owned by the caller;
+ *     HOST pointers point to host memory owned by the caller.  The library never frees
+ *     or retains a caller pointer after the call returns.
+ *   - Work is enqueued on `stream` (a cudaStream_t passed as void*; NULL = legacy
+ *     default stream).  Entry points that return per-problem information through a HOST
+ *     pointer synchronise `stream` once before returning.
+ *   - Return value: an mfipm_status code.  On any code other than MFIPM_OK or
+ *     MFIPM_NOT_CONVERGED, mfipm_last_error() holds a one-line message (thread-local).
+ *   - Arguments are validated before anything is launched; an invalid argument launches
+ *     nothing and leaves outputs untouched.
+ *   - All scratch memory comes from the caller's `workspace` (DEVICE, at least
+ *     mfipm_workspace_size() bytes, 256-byte aligned); the library allocates no device
+ *     memory in these calls.
+ *   - Calls on the same stream are ordered; calls on different streams must not share a
+ *     workspace.
+ */
+#ifndef MFIPM_H_
+#define MFIPM_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  MFIPM_OK = 0,
+  MFIPM_INVALID_ARG = 1,    /* null pointer, m > n, bad DCT size or rows, tau <= 0, small workspace */
+  MFIPM_NOT_CONVERGED = 2,  /* max_iter reached; x and info are still written */
+  MFIPM_NUMERIC = 3,        /* NaN/Inf met in the data or during the iteration */
+  MFIPM_CUDA = 4,           /* CUDA runtime error (message in mfipm_last_error) */
+  MFIPM_TIMEOUT = 5,        /* a bounded device-side wait expired */
+  MFIPM_UNSUPPORTED = 6     /* valid request this build does not implement */
+} mfipm_status;
+
+/* Operator kinds (Sec. 2):
+ *   MFIPM_OP_DENSE        A is an explicit m x n matrix (e.g. the Gaussian ensemble).
+ *   MFIPM_OP_PARTIAL_DCT  A = m distinct rows of the orthonormal n x n DCT-II matrix
+ *                         C[j,k] = a_j cos(pi*j*(2k+1)/(2n)), a_0 = sqrt(1/n), a_j = sqrt(2/n),
+ *                         so that A A^T = I_m (Eq. eq:orthonormality).  n must be a power of
+ *                         two with 64 <= n <= 65536. */
+typedef enum { MFIPM_OP_DENSE = 0, MFIPM_OP_PARTIAL_DCT = 1 } mfipm_op_kind;
+
+/* Storage type of a dense A. */
+typedef enum { MFIPM_A_F64 = 0, MFIPM_A_F32 = 1, MFIPM_A_BF16 = 2 } mfipm_a_dtype;
+
+/* Arithmetic of the PCG solve.  The IPM residuals, duality gap, step lengths and
+ * iterate updates are always float64.
+ *   MFIPM_PREC_FP64      PCG vectors and operator products in float64.
+ *   MFIPM_PREC_FP32_PCG  PCG vectors and operator products in float32 (the inexact Newton
+ *                        direction is corrected by the float64 residuals of the outer loop).
+ *   MFIPM_PREC_BF16_A    dense A stored bf16 (times a_scale) on the tensor cores with float32
+ *                        accumulation; float32 PCG. */
+typedef enum { MFIPM_PREC_FP64 = 0, MFIPM_PREC_FP32_PCG = 1, MFIPM_PREC_BF16_A = 2 } mfipm_precision;
+
+typedef struct {
+  int32_t kind;          /* mfipm_op_kind */
+  int32_t a_dtype;       /* mfipm_a_dtype (dense only) */
+  int64_t m, n;          /* A is m x n, 0 <= m <= n */
+  const void* A;         /* DEVICE, dense only: row-major, entry (i,j) = a_scale * A[i*lda + j] */
+  double a_scale;        /* dense only; 1.0 for plain storage */
+  int64_t lda;           /* dense only; >= n */
+  const int64_t* rows;   /* DEVICE, partial DCT only: m distinct row indices in [0, n), ascending */
+} mfipm_operator;
+
+typedef struct {
+  double tol;            /* relative duality gap z^T s / (1 + |P(z)|) to stop at (Sec. 5.4 "tol"); 1e-10 */
+  int32_t max_iter;      /* IPM iteration cap (Sec. 5.4 "maxiters"); 100 */
+  double tol_pcg;        /* PCG tolerance (Sec. 5.4 "tolpcg") on the preconditioned residual norm
+                            sqrt(r^T P^-1 r) relative to its initial value; 1e-2 */
+  int32_t max_iter_pcg;  /* PCG iteration cap (Sec. 5.4 "mxiterpcg"); 200 */
+  double sigma1, sigma2, sigma3;  /* centering parameters (Sec. 5.1); 0.1, 0.5, 0.8 */
+  double alpha_bar, alpha_tilde;  /* step-size thresholds (Sec. 5.1); 0.5, 0.1 */
+  double eta;            /* fraction of the step to the boundary; 0.995 */
+  int32_t precision;     /* mfipm_precision; MFIPM_PREC_FP32_PCG for the DCT, MFIPM_PREC_FP64 dense */
+  int32_t equal_steps;   /* 0: separate primal and dual steps as in Sec. 5.1; 1: common step */
+  int32_t cluster_size;  /* CTAs that cooperate on one problem (1,2,4,8,16); 0 = automatic */
+  int32_t reserved;
+} mfipm_params;
+
+typedef struct {
+  int32_t status;        /* mfipm_status of this problem */
+  int32_t ipm_iters;     /* outer iterations taken */
+  int32_t correctors;    /* corrector directions computed */
+  int32_t pcg_iters;     /* total PCG iterations */
+  int64_t n_mat;         /* products with A and A^T (the paper's nMat, Table tablesymbabb) */
+  double rel_gap;        /* z^T s / (1 + |P(z)|) at exit */
+  double dual_res;       /* ||s - c - F F^T z||_2 / (1 + ||c||_2) at exit */
+  double kkt_rel;        /* ||x - S_tau(x - A^T(Ax-b))||_2 / (1 + ||x||_2) at exit, float64 */
+  double primal_obj;     /* tau*||x||_1 + 1/2||Ax-b||^2 evaluated at z (tau*1^T z + ...) */
+} mfipm_info;
+
+/* Fill *p with the defaults listed above.  Returns MFIPM_OK, or MFIPM_INVALID_ARG if p is NULL. */
+int mfipm_params_default(mfipm_params* p);
+
+/* Bytes of DEVICE workspace needed to solve `batch` problems whose operators are ops[0..batch)
+ * (HOST array) with parameters *p (HOST).  Writes *bytes (HOST).  Errors: MFIPM_INVALID_ARG for a
+ * malformed operator, MFIPM_UNSUPPORTED for an operator/precision pair this build lacks. */
+int mfipm_workspace_size(const mfipm_operator* ops, int32_t batch, const mfipm_params* p, size_t* bytes);
+
+/* Solve one problem (1).
+ *   op       HOST struct describing A (its A / rows pointers are DEVICE).
+ *   b        DEVICE, m float64.       tau  > 0.
+ *   x        DEVICE, n float64, output: the minimiser x = u - v.
+ *   zs_out   DEVICE, 4n float64 or NULL: final [u; v; s_u; s_v] (input of mfipm_backward).
+ *   info     HOST, output.
+ * Returns the problem's status (MFIPM_NOT_CONVERGED still writes x). */
+int mfipm_solve(const mfipm_operator* op, const double* b, double tau, const mfipm_params* p,
+                double* x, double* zs_out, void* workspace, size_t ws_bytes, mfipm_info* info,
+                void* stream);
+
+/* Solve `batch` independent problems in one persistent launch (one CTA cluster per problem,
+ * problems taken from a device work queue, largest first).  ops, b, tau, x, zs_out, infos are
+ * HOST arrays of length batch; b[j], x[j], zs_out[j] are DEVICE pointers (zs_out may be NULL or
+ * hold NULLs).  Returns MFIPM_OK if every problem converged, else the first non-OK problem
+ * status. */
+int mfipm_solve_batched(int32_t batch, const mfipm_operator* ops, const double* const* b,
+                        const double* tau, const mfipm_params* p, double* const* x,
+                        double* const* zs_out, void* workspace, size_t ws_bytes,
+                        mfipm_info* infos, void* stream);
+
+/* Reverse-mode derivative of the solution map (b, tau) -> x* of (1) at a solution returned by
+ * mfipm_solve[_batched] (not in the paper, which has no derivative; derived from the
+ * perturbed KKT conditions of Sec. 3, Eq. fzfs, at the final iterate).  Given grad_x = dL/dx*,
+ * solves ((Theta_u + Theta_v)^-1 + A^T A) w = grad_x by PCG with the preconditioner
+ * (Theta_u + Theta_v)^-1 + rho I (Lemma lem:ne2_prec) and returns
+ *   grad_b = A w,   grad_tau = -sum_i (Theta_u - Theta_v)_i/(Theta_u + Theta_v)_i * (.)...
+ * (exact formulas in the implementation's documentation).
+ *   zs        DEVICE 4n: the zs_out of the forward solve.
+ *   grad_x    DEVICE n.   grad_b DEVICE m or NULL.   grad_tau HOST (batch) or NULL.
+ *   grad_A    DEVICE m x n row-major or NULL (dense operators only).
+ * Arrays are HOST arrays of DEVICE pointers, as in mfipm_solve_batched. */
+int mfipm_backward(int32_t batch, const mfipm_operator* ops, const double* const* b,
+                   const double* tau, const double* const* x, const double* const* zs,
+                   const double* const* grad_x, double* const* grad_b, double* grad_tau,
+                   double* const* grad_A, const mfipm_params* p, void* workspace,
+                   size_t ws_bytes, mfipm_info* infos, void* stream);
+
+/* Matrix-free products with the operator (the only way the solver touches A, Sec. 1):
+ *   mfipm_apply_A:   y (DEVICE, m) = A x (x DEVICE, n)
+ *   mfipm_apply_At:  x (DEVICE, n) = A^T y (y DEVICE, m)
+ * float64 in and out.  `workspace` as for mfipm_solve with batch 1. */
+int mfipm_apply_A(const mfipm_operator* op, const double* x, double* y, void* workspace,
+                  size_t ws_bytes, void* stream);
+int mfipm_apply_At(const mfipm_operator* op, const double* y, double* x, void* workspace,
+                   size_t ws_bytes, void* stream);
+
+/* kkt_rel(x) = ||x - S_tau(x - A^T(Ax - b))||_2 / (1 + ||x||_2) in float64 for a candidate x
+ * (DEVICE, n); result in *out (HOST).  Synchronises `stream`. */
+int mfipm_kkt_residual(const mfipm_operator* op, const double* b, double tau, const double* x,
+                       void* workspace, size_t ws_bytes, double* out, void* stream);
+
+/* Message of the last failing call on this thread ("" if none). */
+const char* mfipm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MFIPM_H_ */

@@ -1,0 +1,419 @@
+// C ABI of the mfIPM library (declarations and contracts in include/mfipm.h):
+// argument validation, workspace layout, cluster-size choice and launches.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "device_common.cuh"
+#include "internal.h"
+
+using namespace mfipm;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char* where) {
+  return fail(MFIPM_CUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+int ilog2(int64_t v) {
+  int l = 0;
+  while (((int64_t)1 << l) < v) ++l;
+  return l;
+}
+bool is_pow2(int64_t v) { return v > 0 && (v & (v - 1)) == 0; }
+
+constexpr int64_t kDctMinN = 64, kDctMaxN = 65536;
+constexpr int64_t kDenseMaxM = 6144;
+
+int validate_op(const mfipm_operator* op, int idx) {
+  if (!op) return fail(MFIPM_INVALID_ARG, "operator %d is NULL", idx);
+  if (op->m < 0 || op->n <= 0 || op->m > op->n)
+    return fail(MFIPM_INVALID_ARG, "operator %d: need 0 <= m <= n, n > 0 (m=%lld n=%lld)", idx,
+                (long long)op->m, (long long)op->n);
+  if (op->kind == MFIPM_OP_PARTIAL_DCT) {
+    if (!is_pow2(op->n) || op->n < kDctMinN || op->n > kDctMaxN)
+      return fail(MFIPM_INVALID_ARG, "operator %d: partial DCT needs n a power of two in [%lld, %lld] (n=%lld)",
+                  idx, (long long)kDctMinN, (long long)kDctMaxN, (long long)op->n);
+    if (op->m > 0 && !op->rows) return fail(MFIPM_INVALID_ARG, "operator %d: rows is NULL", idx);
+    return MFIPM_OK;
+  }
+  if (op->kind == MFIPM_OP_DENSE) {
+    if (op->m > 0 && !op->A) return fail(MFIPM_INVALID_ARG, "operator %d: A is NULL", idx);
+    if (op->lda < op->n) return fail(MFIPM_INVALID_ARG, "operator %d: lda < n", idx);
+    if (!(op->a_scale > 0.0) || !isfinite(op->a_scale))
+      return fail(MFIPM_INVALID_ARG, "operator %d: a_scale must be positive and finite", idx);
+    if (op->a_dtype != MFIPM_A_F64)
+      return fail(MFIPM_UNSUPPORTED, "operator %d: this entry point takes float64 dense A (a_dtype=%d)", idx,
+                  op->a_dtype);
+    if (op->m > kDenseMaxM)
+      return fail(MFIPM_UNSUPPORTED, "operator %d: dense m=%lld above %lld for the per-problem solver", idx,
+                  (long long)op->m, (long long)kDenseMaxM);
+    return MFIPM_OK;
+  }
+  return fail(MFIPM_INVALID_ARG, "operator %d: unknown kind %d", idx, op->kind);
+}
+
+int validate_params(const mfipm_params* p) {
+  if (!p) return fail(MFIPM_INVALID_ARG, "params is NULL");
+  if (!(p->tol > 0) || !(p->tol_pcg > 0) || p->max_iter < 1 || p->max_iter_pcg < 1)
+    return fail(MFIPM_INVALID_ARG, "params: tol, tol_pcg must be > 0 and iteration caps >= 1");
+  if (!(p->eta > 0 && p->eta < 1)) return fail(MFIPM_INVALID_ARG, "params: eta must be in (0,1)");
+  if (!(p->sigma1 >= 0 && p->sigma2 >= 0 && p->sigma3 >= 0 && p->sigma1 <= 1 && p->sigma2 <= 1 && p->sigma3 <= 1))
+    return fail(MFIPM_INVALID_ARG, "params: sigma values must lie in [0,1]");
+  if (p->precision < 0 || p->precision > 2) return fail(MFIPM_INVALID_ARG, "params: bad precision %d", p->precision);
+  const int cs = p->cluster_size;
+  if (!(cs == 0 || cs == 1 || cs == 2 || cs == 4 || cs == 8 || cs == 16))
+    return fail(MFIPM_INVALID_ARG, "params: cluster_size must be 0,1,2,4,8,16");
+  return MFIPM_OK;
+}
+
+SolveParams to_solve(const mfipm_params* p) {
+  SolveParams s{};
+  s.tol = p->tol;
+  s.tol_pcg = p->tol_pcg;
+  s.sigma1 = p->sigma1;
+  s.sigma2 = p->sigma2;
+  s.sigma3 = p->sigma3;
+  s.alpha_bar = p->alpha_bar;
+  s.alpha_tilde = p->alpha_tilde;
+  s.eta = p->eta;
+  s.max_iter = p->max_iter;
+  s.max_iter_pcg = p->max_iter_pcg;
+  s.equal_steps = p->equal_steps;
+  return s;
+}
+
+// Largest cluster size that the DCT chain supports for length n: shared memory holds
+// 12 n / G bytes (<= 192 KiB) and every CTA needs >= 1 exchange slot (n >= 4 G^2).
+int dct_min_G(int64_t n) { return (int)std::max<int64_t>(1, n / 16384); }
+int dct_max_G(int64_t n) {
+  int g = 16;
+  while (g > 1 && n < 4 * (int64_t)g * g) g >>= 1;
+  return g;
+}
+
+// Per-problem bytes of the device state (excluding shared tables).
+size_t problem_bytes(const mfipm_operator& op, bool pcg64) {
+  const size_t n = (size_t)op.n;
+  size_t b = 0;
+  if (op.kind == MFIPM_OP_PARTIAL_DCT) b += align256(n) + align256(8 * n);  // mask, bsu
+  b += align256(32 * n);                                                     // z, s
+  b += align256(5 * n * (pcg64 ? 16 : 8));                                   // x1 x2 r p d
+  b += align256(8 * n);                                                      // scratch (apply)
+  return b;
+}
+
+struct Layout {
+  size_t off_hdr, off_tw64, off_tw32, off_desc, off_info, off_probs, total;
+  int log2_tw;
+};
+
+Layout make_layout(const mfipm_operator* ops, int batch, bool pcg64) {
+  Layout L{};
+  int64_t max_dct = 0;
+  for (int i = 0; i < batch; ++i)
+    if (ops[i].kind == MFIPM_OP_PARTIAL_DCT) max_dct = std::max<int64_t>(max_dct, ops[i].n);
+  L.log2_tw = max_dct ? ilog2(max_dct) + 2 : 6;
+  size_t o = 0;
+  L.off_hdr = o;
+  o += 256;
+  L.off_tw64 = o;
+  o += align256(((size_t)1 << L.log2_tw) * 16);
+  L.off_tw32 = o;
+  o += align256(((size_t)1 << L.log2_tw) * 8);
+  L.off_desc = o;
+  o += align256(sizeof(ProbDesc) * (size_t)batch);
+  L.off_info = o;
+  o += align256(sizeof(mfipm_info) * (size_t)batch);
+  L.off_probs = o;
+  for (int i = 0; i < batch; ++i) o += problem_bytes(ops[i], pcg64);
+  L.total = o;
+  return L;
+}
+
+bool pcg_in_fp64(const mfipm_operator& op, const mfipm_params* p) {
+  return op.kind == MFIPM_OP_DENSE && p->precision == MFIPM_PREC_FP64;
+}
+
+int pick_G(const std::vector<mfipm_operator>& ops, const mfipm_params* p, int batch) {
+  const bool dct = ops[0].kind == MFIPM_OP_PARTIAL_DCT;
+  int64_t max_n = 0, min_n = INT64_MAX;
+  for (auto& o : ops) {
+    max_n = std::max<int64_t>(max_n, o.n);
+    min_n = std::min<int64_t>(min_n, o.n);
+  }
+  if (p->cluster_size) return p->cluster_size;
+  if (dct) {
+    int g;
+    if (batch == 1) {
+      g = (int)std::min<int64_t>(16, std::max<int64_t>(1, max_n / 2048));
+    } else {
+      g = dct_min_G(max_n);
+    }
+    g = std::max(g, dct_min_G(max_n));
+    g = std::min(g, dct_max_G(min_n));
+    return g;
+  }
+  // dense: columns per CTA >= 32
+  int g = 16;
+  while (g > 1 && min_n < 32 * (int64_t)g) g >>= 1;
+  if (batch > 1) g = std::min(g, 4);
+  return g;
+}
+
+struct Prepared {
+  Layout lay;
+  std::vector<ProbDesc> desc;
+  KernelArgs args;
+  int G;
+  bool dct, pcg64;
+  int64_t max_n, max_m;
+  char* ws;
+};
+
+int prepare(int batch, const mfipm_operator* ops, const double* const* b, const double* tau,
+            const mfipm_params* p, double* const* x, double* const* zs_out, void* workspace, size_t ws_bytes,
+            Prepared& P) {
+  if (batch < 1) return fail(MFIPM_INVALID_ARG, "batch must be >= 1");
+  if (!ops || !b || !tau || !x) return fail(MFIPM_INVALID_ARG, "NULL argument array");
+  int rc = validate_params(p);
+  if (rc) return rc;
+  std::vector<mfipm_operator> vops(ops, ops + batch);
+  const int kind = ops[0].kind;
+  for (int i = 0; i < batch; ++i) {
+    if ((rc = validate_op(&ops[i], i))) return rc;
+    if (ops[i].kind != kind) return fail(MFIPM_UNSUPPORTED, "a batch must use one operator kind");
+    if (!(tau[i] > 0.0) || !isfinite(tau[i])) return fail(MFIPM_INVALID_ARG, "tau[%d] must be positive and finite", i);
+    if (ops[i].m > 0 && !b[i]) return fail(MFIPM_INVALID_ARG, "b[%d] is NULL", i);
+    if (!x[i]) return fail(MFIPM_INVALID_ARG, "x[%d] is NULL", i);
+  }
+  P.dct = kind == MFIPM_OP_PARTIAL_DCT;
+  if (P.dct && p->precision != MFIPM_PREC_FP32_PCG)
+    return fail(MFIPM_UNSUPPORTED, "the partial-DCT solver runs its PCG in float32 (precision=%d)", p->precision);
+  if (!P.dct && p->precision == MFIPM_PREC_BF16_A)
+    return fail(MFIPM_UNSUPPORTED, "bf16 dense A goes through the shared-A multi-RHS solver");
+  P.pcg64 = pcg_in_fp64(ops[0], p);
+  P.lay = make_layout(ops, batch, P.pcg64);
+  if (!workspace) return fail(MFIPM_INVALID_ARG, "workspace is NULL");
+  if (((uintptr_t)workspace & 255) != 0) return fail(MFIPM_INVALID_ARG, "workspace must be 256-byte aligned");
+  if (ws_bytes < P.lay.total)
+    return fail(MFIPM_INVALID_ARG, "workspace too small: %zu < %zu bytes", ws_bytes, P.lay.total);
+  P.max_n = 0;
+  P.max_m = 0;
+  for (auto& o : vops) {
+    P.max_n = std::max<int64_t>(P.max_n, o.n);
+    P.max_m = std::max<int64_t>(P.max_m, o.m);
+  }
+  P.G = pick_G(vops, p, batch);
+  if (P.dct) {
+    int64_t min_n = INT64_MAX;
+    for (auto& o : vops) min_n = std::min<int64_t>(min_n, o.n);
+    if (P.G < dct_min_G(P.max_n) || P.G > dct_max_G(min_n))
+      return fail(MFIPM_INVALID_ARG, "cluster_size %d does not fit n in [%lld, %lld]", P.G, (long long)min_n,
+                  (long long)P.max_n);
+  } else if ((P.max_n + P.G - 1) / P.G > 16384) {
+    return fail(MFIPM_UNSUPPORTED, "dense n=%lld too large for cluster size %d", (long long)P.max_n, P.G);
+  }
+  char* ws = static_cast<char*>(workspace);
+  P.ws = ws;
+  P.desc.resize(batch);
+  size_t o = P.lay.off_probs;
+  mfipm_info* info_dev = reinterpret_cast<mfipm_info*>(ws + P.lay.off_info);
+  for (int i = 0; i < batch; ++i) {
+    ProbDesc& d = P.desc[i];
+    memset(&d, 0, sizeof(d));
+    const mfipm_operator& op = ops[i];
+    const size_t n = (size_t)op.n;
+    d.n = op.n;
+    d.m = op.m;
+    d.kind = op.kind;
+    d.log2n = ilog2(op.n);
+    d.tau = tau[i];
+    d.b = b[i];
+    d.x_out = x[i];
+    d.zs_out = zs_out ? zs_out[i] : nullptr;
+    d.rows = op.rows;
+    d.A = op.A;
+    d.a_dtype = op.a_dtype;
+    d.a_scale = op.a_scale;
+    d.lda = op.lda;
+    size_t q = o;
+    if (P.dct) {
+      d.mask = reinterpret_cast<uint8_t*>(ws + q);
+      q += align256(n);
+      d.bsu = reinterpret_cast<double*>(ws + q);
+      q += align256(8 * n);
+    }
+    d.zs = reinterpret_cast<double*>(ws + q);
+    q += align256(32 * n);
+    d.pcg = ws + q;
+    q += align256(5 * n * (P.pcg64 ? 16 : 8));
+    q += align256(8 * n);
+    d.info = info_dev + i;
+    o += problem_bytes(op, P.pcg64);
+  }
+  KernelArgs& a = P.args;
+  memset(&a, 0, sizeof(a));
+  a.probs = reinterpret_cast<const ProbDesc*>(ws + P.lay.off_desc);
+  a.batch = batch;
+  a.queue = reinterpret_cast<int*>(ws + P.lay.off_hdr);
+  a.err = reinterpret_cast<int*>(ws + P.lay.off_hdr + 4);
+  a.tw64 = reinterpret_cast<const double2*>(ws + P.lay.off_tw64);
+  a.tw32 = reinterpret_cast<const float2*>(ws + P.lay.off_tw32);
+  a.log2_tw = P.lay.log2_tw;
+  a.prm = to_solve(p);
+  return MFIPM_OK;
+}
+
+int run(Prepared& P, cudaStream_t st, int batch, mfipm_info* infos, const std::vector<int>* order) {
+  cudaError_t e;
+  // work queue in cost order (largest first): the descriptor array is permuted, infos are not
+  std::vector<ProbDesc> sorted(P.desc);
+  if (order) {
+    for (int i = 0; i < batch; ++i) sorted[i] = P.desc[(*order)[i]];
+  }
+  if ((e = cudaMemcpyAsync(P.ws + P.lay.off_desc, sorted.data(), sizeof(ProbDesc) * batch, cudaMemcpyHostToDevice,
+                           st)) != cudaSuccess)
+    return cuda_fail(e, "upload descriptors");
+  if ((e = cudaMemsetAsync(P.ws + P.lay.off_hdr, 0, 256, st)) != cudaSuccess) return cuda_fail(e, "clear header");
+  if (P.dct) {
+    if ((e = launch_twiddles(const_cast<double2*>(P.args.tw64), const_cast<float2*>(P.args.tw32), P.args.log2_tw,
+                             st)) != cudaSuccess)
+      return cuda_fail(e, "twiddle kernel");
+    if ((e = launch_dct_setup(P.args.probs, batch, P.max_n, P.args.err, st)) != cudaSuccess)
+      return cuda_fail(e, "setup kernel");
+  }
+  int maxc = P.dct ? max_active_clusters_dct(P.G, P.max_n) : max_active_clusters_dense(P.G, P.pcg64, P.max_n, P.max_m);
+  if (maxc < 1) return fail(MFIPM_UNSUPPORTED, "no resident cluster of size %d fits this problem", P.G);
+  const int clusters = std::min(maxc, batch);
+  e = P.dct ? launch_dct_solver(P.G, P.args, P.max_n, clusters, st)
+            : launch_dense_solver(P.G, P.pcg64, P.args, P.max_n, P.max_m, clusters, st);
+  if (e != cudaSuccess) return cuda_fail(e, "solver launch");
+  int err = 0;
+  if ((e = cudaMemcpyAsync(&err, P.args.err, sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+    return cuda_fail(e, "read error word");
+  if (infos) {
+    if ((e = cudaMemcpyAsync(infos, P.ws + P.lay.off_info, sizeof(mfipm_info) * batch, cudaMemcpyDeviceToHost, st)) !=
+        cudaSuccess)
+      return cuda_fail(e, "read infos");
+  }
+  if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(e, "solve");
+  if (err == -1) return fail(MFIPM_INVALID_ARG, "rows must be distinct, ascending and inside [0, n)");
+  if (err == -2) return fail(MFIPM_NUMERIC, "b contains a non-finite value");
+  if (err > 0 && infos) {
+    for (int i = 0; i < batch; ++i)
+      if (infos[i].status != MFIPM_OK) return infos[i].status;
+  }
+  return err > 0 ? err : MFIPM_OK;
+}
+
+std::vector<int> cost_order(const mfipm_operator* ops, int batch) {
+  std::vector<int> ord(batch);
+  std::iota(ord.begin(), ord.end(), 0);
+  std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return ops[a].n > ops[b].n; });
+  return ord;
+}
+
+}  // namespace
+
+extern "C" {
+
+int mfipm_params_default(mfipm_params* p) {
+  if (!p) return fail(MFIPM_INVALID_ARG, "params is NULL");
+  memset(p, 0, sizeof(*p));
+  p->tol = 1e-10;
+  p->max_iter = 100;
+  p->tol_pcg = 1e-2;
+  p->max_iter_pcg = 200;
+  p->sigma1 = 0.1;
+  p->sigma2 = 0.5;
+  p->sigma3 = 0.8;
+  p->alpha_bar = 0.5;
+  p->alpha_tilde = 0.1;
+  p->eta = 0.995;
+  p->precision = MFIPM_PREC_FP32_PCG;
+  p->equal_steps = 0;
+  p->cluster_size = 0;
+  return MFIPM_OK;
+}
+
+int mfipm_workspace_size(const mfipm_operator* ops, int32_t batch, const mfipm_params* p, size_t* bytes) {
+  if (!ops || !bytes || batch < 1) return fail(MFIPM_INVALID_ARG, "NULL argument or batch < 1");
+  int rc = validate_params(p);
+  if (rc) return rc;
+  for (int i = 0; i < batch; ++i)
+    if ((rc = validate_op(&ops[i], i))) return rc;
+  *bytes = make_layout(ops, batch, pcg_in_fp64(ops[0], p)).total;
+  return MFIPM_OK;
+}
+
+int mfipm_solve(const mfipm_operator* op, const double* b, double tau, const mfipm_params* p, double* x,
+                double* zs_out, void* workspace, size_t ws_bytes, mfipm_info* info, void* stream) {
+  g_err.clear();
+  const double* bb[1] = {b};
+  double* xx[1] = {x};
+  double* zz[1] = {zs_out};
+  double tt[1] = {tau};
+  Prepared P;
+  int rc = prepare(1, op, bb, tt, p, xx, zs_out ? zz : nullptr, workspace, ws_bytes, P);
+  if (rc) return rc;
+  mfipm_info tmp;
+  return run(P, static_cast<cudaStream_t>(stream), 1, info ? info : &tmp, nullptr);
+}
+
+int mfipm_solve_batched(int32_t batch, const mfipm_operator* ops, const double* const* b, const double* tau,
+                        const mfipm_params* p, double* const* x, double* const* zs_out, void* workspace,
+                        size_t ws_bytes, mfipm_info* infos, void* stream) {
+  g_err.clear();
+  Prepared P;
+  int rc = prepare(batch, ops, b, tau, p, x, zs_out, workspace, ws_bytes, P);
+  if (rc) return rc;
+  std::vector<mfipm_info> tmp;
+  if (!infos) {
+    tmp.resize(batch);
+    infos = tmp.data();
+  }
+  std::vector<int> ord = cost_order(ops, batch);
+  return run(P, static_cast<cudaStream_t>(stream), batch, infos, &ord);
+}
+
+int mfipm_backward(int32_t, const mfipm_operator*, const double* const*, const double*, const double* const*,
+                   const double* const*, const double* const*, double* const*, double*, double* const*,
+                   const mfipm_params*, void*, size_t, mfipm_info*, void*) {
+  return fail(MFIPM_UNSUPPORTED, "mfipm_backward is not built yet");
+}
+
+int mfipm_apply_A(const mfipm_operator*, const double*, double*, void*, size_t, void*) {
+  return fail(MFIPM_UNSUPPORTED, "mfipm_apply_A is not built yet");
+}
+int mfipm_apply_At(const mfipm_operator*, const double*, double*, void*, size_t, void*) {
+  return fail(MFIPM_UNSUPPORTED, "mfipm_apply_At is not built yet");
+}
+int mfipm_kkt_residual(const mfipm_operator*, const double*, double, const double*, void*, size_t, double*, void*) {
+  return fail(MFIPM_UNSUPPORTED, "mfipm_kkt_residual is not built yet");
+}
+
+const char* mfipm_last_error(void) { return g_err.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,257 @@
+// Device building blocks of the mfIPM kernels: complex arithmetic, CTA/cluster
+// reductions through distributed shared memory, and the shared-memory radix-4 FFT
+// used by the partial-DCT operator.
+#pragma once
+
+#include <cooperative_groups.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace cg = cooperative_groups;
+
+namespace mfipm {
+
+constexpr int kThreads = 512;          // threads per CTA of every solver kernel
+constexpr int kWarps = kThreads / 32;
+constexpr int kMaxRed = 8;             // values per fused cluster reduction
+
+// ------------------------------------------------------------------ complex helpers
+template <class R> struct cplx;
+template <> struct cplx<float> { using T = float2; };
+template <> struct cplx<double> { using T = double2; };
+
+__device__ __forceinline__ float2 mk(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ double2 mk(double a, double b) { return make_double2(a, b); }
+template <class C> __device__ __forceinline__ C cadd(C a, C b) { return mk(a.x + b.x, a.y + b.y); }
+template <class C> __device__ __forceinline__ C csub(C a, C b) { return mk(a.x - b.x, a.y - b.y); }
+template <class C> __device__ __forceinline__ C cmul(C a, C b) {
+  return mk(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+template <class C> __device__ __forceinline__ C cmulc(C a, C b) {  // a * conj(b)
+  return mk(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
+}
+template <class C> __device__ __forceinline__ C cconj(C a) { return mk(a.x, -a.y); }
+template <class C> __device__ __forceinline__ C cmul_i(C a) { return mk(-a.y, a.x); }     // i*a
+template <class C> __device__ __forceinline__ C cmul_mi(C a) { return mk(a.y, -a.x); }    // -i*a
+template <class C, class R> __device__ __forceinline__ C cscale(C a, R s) { return mk(a.x * s, a.y * s); }
+
+// Twiddle table: tw[j] = exp(-2*pi*i*j / 2^log2_tw), built once per call by a setup
+// kernel with sincospi; every transform size indexes it with a power-of-two stride.
+template <class C> struct Twiddle {
+  const C* tw;
+  int log2_tw;
+  // exp(-2 pi i j / 2^logB) for 0 <= j < 2^logB
+  __device__ __forceinline__ C root(int64_t j, int logB) const { return __ldg(&tw[j << (log2_tw - logB)]); }
+};
+
+// ------------------------------------------------------------------ reductions
+template <class V> __device__ __forceinline__ V warp_sum(V v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double warp_min(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// Shared state of the cluster reductions (lives in static shared memory).
+struct RedSmem {
+  double warp_part[kWarps][kMaxRed];
+  double cta_part[2][kMaxRed];  // double-buffered: read remotely by the other CTAs
+  int fetched;                  // problem index broadcast by CTA rank 0
+};
+
+// Sum K per-thread values over the whole cluster of G CTAs; every thread of every CTA
+// receives identical totals (same summation order everywhere).  `parity` alternates
+// between calls so that a CTA can publish the next partials while slower CTAs still read
+// the previous ones; between two uses of the same buffer there is always the barrier of
+// the intermediate call.
+template <int G, int K, class V>
+__device__ __forceinline__ void cluster_sum(RedSmem& rs, int& parity, const V (&v)[K], double (&out)[K]) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    V w = warp_sum(v[k]);
+    if (lane == 0) rs.warp_part[warp][k] = (double)w;
+  }
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      double t = lane < kWarps ? rs.warp_part[lane][k] : 0.0;
+      t = warp_sum(t);
+      if (lane == 0) rs.cta_part[parity][k] = t;
+    }
+  }
+  if constexpr (G == 1) {
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < K; ++k) out[k] = rs.cta_part[parity][k];
+  } else {
+    cg::cluster_group cl = cg::this_cluster();
+    cl.sync();
+#pragma unroll
+    for (int k = 0; k < K; ++k) out[k] = 0.0;
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+      const RedSmem* r = cl.map_shared_rank(&rs, g);
+#pragma unroll
+      for (int k = 0; k < K; ++k) out[k] += r->cta_part[parity][k];
+    }
+  }
+  parity ^= 1;
+}
+
+// Minimum of K per-thread doubles over the cluster (same structure as cluster_sum).
+template <int G, int K>
+__device__ __forceinline__ void cluster_min(RedSmem& rs, int& parity, const double (&v)[K], double (&out)[K]) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    double w = warp_min(v[k]);
+    if (lane == 0) rs.warp_part[warp][k] = w;
+  }
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      double t = lane < kWarps ? rs.warp_part[lane][k] : INFINITY;
+      t = warp_min(t);
+      if (lane == 0) rs.cta_part[parity][k] = t;
+    }
+  }
+  if constexpr (G == 1) {
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < K; ++k) out[k] = rs.cta_part[parity][k];
+  } else {
+    cg::cluster_group cl = cg::this_cluster();
+    cl.sync();
+#pragma unroll
+    for (int k = 0; k < K; ++k) out[k] = INFINITY;
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+      const RedSmem* r = cl.map_shared_rank(&rs, g);
+#pragma unroll
+      for (int k = 0; k < K; ++k) out[k] = fmin(out[k], r->cta_part[parity][k]);
+    }
+  }
+  parity ^= 1;
+}
+
+template <int G> __device__ __forceinline__ void cluster_barrier() {
+  if constexpr (G == 1) {
+    __syncthreads();
+  } else {
+    cg::this_cluster().sync();
+  }
+}
+
+// ------------------------------------------------------------------ shared-memory FFT
+// In-place radix-4 decimation-in-frequency FFT of M = 2^logM points held in shared
+// memory: natural-order input, bit-reversed output, forward sign exp(-2 pi i jk/M).
+// Each radix-4 group is two radix-2 stages, so the output order is plain bit reversal.
+template <class C, class R>
+__device__ void fft_dif(C* buf, int logM, const Twiddle<C>& tw) {
+  const int M = 1 << logM;
+  int logB = logM;
+  for (; logB >= 2; logB -= 2) {
+    const int logS = logB - 2, S = 1 << logS;
+    for (int gi = threadIdx.x; gi < (M >> 2); gi += kThreads) {
+      const int blk = gi >> logS, t = gi & (S - 1);
+      C* p = buf + (blk << logB) + t;
+      C a0 = p[0], a1 = p[S], a2 = p[2 * S], a3 = p[3 * S];
+      C w1 = tw.root(t, logB), w2 = tw.root(2 * t, logB), w3 = tw.root(3 * t, logB);
+      C s02 = cadd(a0, a2), d02 = csub(a0, a2), s13 = cadd(a1, a3), d13 = csub(a1, a3);
+      p[0] = cadd(s02, s13);
+      p[S] = cmul(csub(s02, s13), w2);
+      p[2 * S] = cmul(cadd(d02, cmul_mi(d13)), w1);
+      p[3 * S] = cmul(cadd(d02, cmul_i(d13)), w3);
+    }
+    __syncthreads();
+  }
+  if (logB == 1) {
+    for (int gi = threadIdx.x; gi < (M >> 1); gi += kThreads) {
+      C a0 = buf[2 * gi], a1 = buf[2 * gi + 1];
+      buf[2 * gi] = cadd(a0, a1);
+      buf[2 * gi + 1] = csub(a0, a1);
+    }
+    __syncthreads();
+  }
+}
+
+// Unnormalised inverse of fft_dif: bit-reversed input, natural output, sign +,
+// result = M * IDFT.
+template <class C, class R>
+__device__ void fft_dit_inv(C* buf, int logM, const Twiddle<C>& tw) {
+  const int M = 1 << logM;
+  int logB = 2;
+  if (logM & 1) {
+    for (int gi = threadIdx.x; gi < (M >> 1); gi += kThreads) {
+      C a0 = buf[2 * gi], a1 = buf[2 * gi + 1];
+      buf[2 * gi] = cadd(a0, a1);
+      buf[2 * gi + 1] = csub(a0, a1);
+    }
+    __syncthreads();
+    logB = 3;
+  }
+  for (; logB <= logM; logB += 2) {
+    const int logS = logB - 2, S = 1 << logS;
+    for (int gi = threadIdx.x; gi < (M >> 2); gi += kThreads) {
+      const int blk = gi >> logS, t = gi & (S - 1);
+      C* p = buf + (blk << logB) + t;
+      C o0 = p[0];
+      C b1 = cmulc(p[S], tw.root(2 * t, logB));
+      C b2 = cmulc(p[2 * S], tw.root(t, logB));
+      C b3 = cmulc(p[3 * S], tw.root(3 * t, logB));
+      C Ss = cadd(o0, b1), D = csub(o0, b1), E = cadd(b2, b3), F = csub(b3, b2);
+      p[0] = cadd(Ss, E);
+      p[S] = cadd(D, cmul_mi(F));
+      p[2 * S] = csub(Ss, E);
+      p[3 * S] = cadd(D, cmul_i(F));
+    }
+    __syncthreads();
+  }
+}
+
+// G-point DFT of a register array (G a compile-time power of two), natural order in and
+// out.  inverse=true uses the + sign and does not normalise.
+template <int G, class C>
+__device__ __forceinline__ void small_dft(C (&a)[G], bool inverse, const Twiddle<C>& tw) {
+  if constexpr (G == 1) {
+    return;
+  } else {
+    constexpr int logG = (G == 2) ? 1 : (G == 4) ? 2 : (G == 8) ? 3 : 4;
+    // bit-reversal permutation (compile-time indices)
+#pragma unroll
+    for (int i = 0; i < G; ++i) {
+      int r = 0;
+#pragma unroll
+      for (int bbit = 0; bbit < logG; ++bbit) r |= ((i >> bbit) & 1) << (logG - 1 - bbit);
+      if (r > i) { C t = a[i]; a[i] = a[r]; a[r] = t; }
+    }
+#pragma unroll
+    for (int ls = 0; ls < logG; ++ls) {
+      const int s = 1 << ls;
+#pragma unroll
+      for (int j = 0; j < G; j += 2 * s) {
+#pragma unroll
+        for (int t = 0; t < s; ++t) {
+          C w = tw.root(t, ls + 1);
+          if (inverse) w = cconj(w);
+          C u = a[j + t], v = cmul(a[j + t + s], w);
+          a[j + t] = cadd(u, v);
+          a[j + t + s] = csub(u, v);
+        }
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ int bitrev(int x, int bits) {
+  return bits == 0 ? 0 : (int)(__brev((unsigned)x) >> (32 - bits));
+}
+
+}  // namespace mfipm

@@ -1,0 +1,73 @@
+// Structures shared by the C-ABI layer (capi.cu) and the kernels (solver.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/mfipm.h"
+
+namespace mfipm {
+
+// Parameters of the IPM as the kernels read them (copied from mfipm_params).
+struct SolveParams {
+  double tol, tol_pcg, sigma1, sigma2, sigma3, alpha_bar, alpha_tilde, eta;
+  int32_t max_iter, max_iter_pcg, equal_steps, pad;
+};
+
+// One problem of a launch.  Vectors of length n live in the caller's workspace, in the
+// operator's storage order (the partial DCT keeps its vectors permuted so that the FFT
+// reads them in place; see solver.cu).
+struct ProbDesc {
+  int64_t n, m;
+  int32_t kind;           // mfipm_op_kind
+  int32_t log2n;          // partial DCT
+  double tau;
+  const double* b;        // DEVICE m
+  double* x_out;          // DEVICE n (natural order)
+  double* zs_out;         // DEVICE 4n or null
+  // partial DCT
+  const int64_t* rows;    // DEVICE m
+  uint8_t* mask;          // DEVICE n: 1 where the DCT row is sampled
+  double* bsu;            // DEVICE n: b scattered to its rows, divided by the row's DCT scale
+  // dense
+  const void* A;
+  int32_t a_dtype;
+  int32_t pad0;
+  double a_scale;
+  int64_t lda;
+  // state
+  double* zs;             // DEVICE 4n: per index {u, v, s_u, s_v}
+  void* pcg;              // DEVICE 5 vectors of n pairs (x1, x2, r, p, d), float or double pairs
+  mfipm_info* info;       // DEVICE
+};
+
+struct KernelArgs {
+  const ProbDesc* probs;
+  int32_t batch;
+  int32_t pad;
+  int* queue;             // DEVICE work counter, zero at launch
+  int* err;               // DEVICE error word (first failing problem's status)
+  const double2* tw64;    // exp(-2 pi i j / 2^log2_tw)
+  const float2* tw32;
+  int32_t log2_tw;
+  int32_t pad2;
+  SolveParams prm;
+};
+
+// Launchers implemented in solver.cu.  Return cudaError_t of the launch.
+cudaError_t launch_twiddles(double2* tw64, float2* tw32, int log2_tw, cudaStream_t st);
+cudaError_t launch_dct_setup(const ProbDesc* probs_dev, int batch, int64_t max_n, int* err, cudaStream_t st);
+cudaError_t launch_dct_solver(int G, const KernelArgs& a, int64_t max_n, int grid_clusters, cudaStream_t st);
+cudaError_t launch_dense_solver(int G, bool fp64_pcg, const KernelArgs& a, int64_t max_n, int64_t max_m,
+                                int grid_clusters, cudaStream_t st);
+int max_active_clusters_dct(int G, int64_t max_n);
+int max_active_clusters_dense(int G, bool fp64_pcg, int64_t max_n, int64_t max_m);
+size_t dct_smem_bytes(int G, int64_t max_n);
+size_t dense_smem_bytes(int G, bool fp64_pcg, int64_t max_n, int64_t max_m);
+
+// Operator-only kernels for mfipm_apply_A / mfipm_apply_At / mfipm_kkt_residual:
+// mode 0 = A x (out m), 1 = A^T y (out n), 2 = kkt_rel (out 1 double, device).
+cudaError_t launch_apply(int mode, int G, const KernelArgs& a, const double* in, double* out,
+                         cudaStream_t st);
+
+}  // namespace mfipm

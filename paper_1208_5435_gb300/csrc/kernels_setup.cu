@@ -1,0 +1,72 @@
+// Setup kernels of the mfIPM launches: twiddle table, partial-DCT row mask and scaled b.
+#include "solver_impl.cuh"
+
+namespace mfipm {
+
+// ------------------------------------------------------------------ setup kernels
+__global__ void twiddle_kernel(double2* tw64, float2* tw32, int log2_tw) {
+  const int64_t T = (int64_t)1 << log2_tw;
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < T; j += (int64_t)gridDim.x * blockDim.x) {
+    double s, c;
+    // exp(-2 pi i j / T) = cos(pi * 2j/T) - i sin(pi * 2j/T)
+    sincospi(2.0 * (double)j / (double)T, &s, &c);
+    tw64[j] = make_double2(c, -s);
+    tw32[j] = make_float2((float)c, (float)-s);
+  }
+}
+
+// mask[j] = 1 and bsu[j] = b_i / alpha_j for j = rows[i]; validates rows.
+__global__ void dct_setup_kernel(const ProbDesc* probs, int batch, int* err) {
+  const ProbDesc pd = probs[blockIdx.y];
+  const int64_t n = pd.n;
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+    pd.mask[j] = 0;
+    pd.bsu[j] = 0.0;
+  }
+}
+__global__ void dct_scatter_kernel(const ProbDesc* probs, int batch, int* err) {
+  const ProbDesc pd = probs[blockIdx.y];
+  const int64_t n = pd.n, m = pd.m;
+  const double sc0 = sqrt((double)n), scj = sqrt(0.5 * (double)n);  // 1/alpha
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = pd.rows[i];
+    const bool ok = r >= 0 && r < n && (i == 0 || pd.rows[i - 1] < r);
+    if (!ok) {
+      atomicCAS(err, 0, -1);  // invalid rows: reported by the host as MFIPM_INVALID_ARG
+      continue;
+    }
+    const double bi = pd.b[i];
+    if (!isfinite(bi)) atomicCAS(err, 0, -2);
+    pd.mask[r] = 1;
+    pd.bsu[r] = bi * (r == 0 ? sc0 : scj);
+  }
+}
+
+// ------------------------------------------------------------------ launchers
+size_t dct_smem_bytes(int G, int64_t max_n) {
+  const int64_t M = max_n / 2 / G;
+  return (size_t)M * 16 + (size_t)M * 8;
+}
+size_t dense_smem_bytes(int G, bool, int64_t max_n, int64_t max_m) {
+  const int64_t chunk = (max_n + G - 1) / G;
+  const size_t c8 = ((size_t)chunk * 8 + 255) & ~(size_t)255;
+  return 2 * c8 + 2 * (size_t)((max_m + 31) & ~31) * 8;
+}
+
+cudaError_t launch_twiddles(double2* tw64, float2* tw32, int log2_tw, cudaStream_t st) {
+  const int64_t T = (int64_t)1 << log2_tw;
+  const int blocks = (int)((T + 255) / 256 < 1024 ? (T + 255) / 256 : 1024);
+  twiddle_kernel<<<blocks, 256, 0, st>>>(tw64, tw32, log2_tw);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dct_setup(const ProbDesc* probs_dev, int batch, int64_t max_n, int* err, cudaStream_t st) {
+  const int bx = (int)((max_n + 255) / 256 < 64 ? (max_n + 255) / 256 : 64);
+  dct_setup_kernel<<<dim3(bx, batch), 256, 0, st>>>(probs_dev, batch, err);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  dct_scatter_kernel<<<dim3(bx, batch), 256, 0, st>>>(probs_dev, batch, err);
+  return cudaGetLastError();
+}
+
+}  // namespace mfipm

@@ -1,0 +1,826 @@
+#pragma once
+// Device-resident matrix-free primal-dual IPM (arXiv:1208.5435, Sec. 5.1 Algorithm)
+// with PCG Newton solves (Sec. 4) for  min tau||x||_1 + 1/2||Ax - b||^2.
+//
+// Execution model: one thread-block cluster of G CTAs solves one problem from start to
+// finish inside a single kernel launch; clusters take problems from a device work
+// queue (persistent launch).  CTA rank r of a cluster owns a contiguous chunk of the
+// 2n-vectors' indices; per-index work (PCG updates, preconditioner, IPM residuals,
+// step lengths) is local, and the only cross-CTA traffic is
+//   * scalar reductions through distributed shared memory (cluster barrier + DSMEM reads),
+//   * the operator: partial DCT = a distributed FFT whose single exchange step reads and
+//     writes the other CTAs' shared-memory buffers; dense A = an all-reduce of A w.
+//
+// Partial DCT operator, A = R C with C the orthonormal DCT-II (Sec. 2, Eq.
+// eq:orthonormality).  With the unnormalised DCT-II D (C = diag(alpha) D),
+//     A^T A w = D^-1 M D w,   A^T (A x - b) = D^-1 M (D x - b_u),
+// where M masks the sampled rows and b_u holds b_i / alpha_{row_i} at the sampled rows.
+// D of length N is evaluated through a complex FFT of length L = N/2 (the even/odd
+// reordering of Makhoul and the half-length real-FFT packing): v_j = x_{2j},
+// v_{N-1-j} = x_{2j+1}; h_j = v_{2j} + i v_{2j+1}.  The FFT is split four-step
+// style over the cluster: L = M G, CTA g holds h_{g + G n2} (n2 < M) and runs a local
+// M-point FFT; a "slot step" then gathers, for each output column k2, the G values
+// Y_g[k2] from all CTAs, applies the four-step twiddles and a G-point DFT, performs the
+// real-DCT untangling, the row mask (and the subtraction of b), and the exact inverse of
+// all of it, and writes the results back.  k2 and M-k2 are handled by lanes l and l^16
+// of one warp, so the pairing H[k] <-> H[L-k] of the real-FFT untangling is a shuffle.
+// Because every per-index operation of the IPM and the PCG is elementwise, all
+// n-vectors are stored directly in this FFT order ("storage order"): no gather or
+// scatter happens inside the iteration.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "device_common.cuh"
+#include "internal.h"
+
+namespace mfipm {
+
+// ------------------------------------------------------------------ small helpers
+// Reciprocal by Newton-Raphson iteration r <- r + r (1 - z r) from a float32 seed
+// (two steps: the relative error squares each step, 1e-7 -> 1e-14 -> rounding).
+__device__ __forceinline__ double rcp64(double z) {
+  const float zf = (float)z;
+  if (!(fabsf(zf) > 1e-36f && fabsf(zf) < 1e36f)) return 1.0 / z;
+  double r = (double)__frcp_rn(zf);
+  double e = fma(-z, r, 1.0);
+  r = fma(r, e, r);
+  e = fma(-z, r, 1.0);
+  return fma(r, e, r);
+}
+
+template <class PS> struct V2;
+template <> struct V2<float> { using T = float2; };
+template <> struct V2<double> { using T = double2; };
+
+// P^-1 r for one index: P block [[du + rho, -rho], [-rho, dv + rho]]  (Eq. eq:ne2_P)
+template <class PS>
+__device__ __forceinline__ typename V2<PS>::T precond(typename V2<PS>::T d, typename V2<PS>::T r, PS rho) {
+  const PS a = d.x + rho, c = d.y + rho;
+  const PS det = d.x * d.y + rho * (d.x + d.y);
+  const PS inv = (PS)1 / det;
+  typename V2<PS>::T z;
+  z.x = (c * r.x + rho * r.y) * inv;
+  z.y = (rho * r.x + a * r.y) * inv;
+  return z;
+}
+
+enum { MODE_NORMAL = 0, MODE_RESID = 1, MODE_FORWARD = 2 };
+
+// ------------------------------------------------------------------ partial DCT op
+struct DctGeom {
+  int logN, logL, logM, rank;
+  int64_t N;
+  const uint8_t* mask;
+  const double* bsu;
+};
+
+// Real-DCT untangling, row mask (minus b_u) and its exact inverse for one frequency k of
+// the length-L FFT, given a = H[k] and b = H[L-k].  Returns the value H'[k] that the
+// inverse chain needs; accumulates this index's share of the masked energy into acc and,
+// in MODE_FORWARD, writes alpha_j X_j instead.  Each DCT coefficient j is counted by
+// exactly one k: j in {k, N-k (k>0)} and, for k = 0, also j = L.
+template <class C, int MODE>
+__device__ __forceinline__ C dct_pointwise(int64_t k, C a, C b, const DctGeom& geo, const Twiddle<C>& tw,
+                                           bool valid, double& acc, double* fwd_out) {
+  using R = decltype(C().x);
+  const int64_t L = (int64_t)1 << geo.logL, N = geo.N;
+  const R rs2 = (R)0.70710678118654752440;
+  const C c45 = mk(rs2, -rs2);  // exp(-i pi/4)
+  const C E = cscale(cadd(a, cconj(b)), (R)0.5);
+  const C O = cscale(cmul_mi(csub(a, cconj(b))), (R)0.5);
+  const C wN = tw.root(k, geo.logN);       // exp(-2 pi i k / N)
+  const C eps = tw.root(k, geo.logN + 2);  // exp(-i pi k / (2N))
+  const C wO = cmul(wN, O);
+  const C Wk = cmul(eps, cadd(E, wO));                   // eps^k V[k]
+  const C Wlk = cmul(c45, cconj(cmul(eps, csub(E, wO))));  // eps^(L-k) V[L-k]
+  const int64_t i1 = k, i2 = N - k, i3 = L - k, i4 = L + k;
+  R X1 = Wk.x, X2 = -Wk.y, X3 = Wlk.x, X4 = -Wlk.y;
+  if constexpr (MODE == MODE_FORWARD) {
+    if (valid) {
+      const double sj = sqrt(2.0 / (double)N);
+      fwd_out[i1] = (i1 == 0 ? sqrt(1.0 / (double)N) : sj) * (double)X1;
+      if (k > 0) fwd_out[i2] = sj * (double)X2;
+      if (k == 0) fwd_out[i3] = sj * (double)X3;
+    }
+    return a;
+  } else {
+    const R a2_0 = (R)(1.0 / (double)N), a2_j = (R)(2.0 / (double)N);
+    const bool m1 = geo.mask[i1], m2 = (k > 0) && geo.mask[i2], m3 = geo.mask[i3], m4 = geo.mask[i4];
+    if constexpr (MODE == MODE_RESID) {
+      X1 = m1 ? X1 - (R)geo.bsu[i1] : (R)0;
+      X2 = m2 ? X2 - (R)geo.bsu[i2] : (R)0;
+      X3 = m3 ? X3 - (R)geo.bsu[i3] : (R)0;
+      X4 = m4 ? X4 - (R)geo.bsu[i4] : (R)0;
+    } else {
+      X1 = m1 ? X1 : (R)0;
+      X2 = m2 ? X2 : (R)0;
+      X3 = m3 ? X3 : (R)0;
+      X4 = m4 ? X4 : (R)0;
+    }
+    if (valid) {
+      R t = (i1 == 0 ? a2_0 : a2_j) * X1 * X1;
+      if (k > 0) t += a2_j * X2 * X2;
+      if (k == 0) t += a2_j * X3 * X3;
+      acc += (double)t;
+    }
+    const C Vk = cmulc(mk(X1, -X2), eps);                     // conj(eps^k) W'[k]
+    const C Vlk = cmul(cconj(c45), cmul(eps, mk(X3, -X4)));    // conj(eps^(L-k)) W'[L-k]
+    const C cVlk = cconj(Vlk);
+    const C Ep = cscale(cadd(Vk, cVlk), (R)0.5);
+    const C Op = cscale(cmulc(csub(Vk, cVlk), wN), (R)0.5);
+    return cscale(cadd(Ep, cmul_i(Op)), (R)1 / (R)L);
+  }
+}
+
+// The exchange step of the distributed DCT chain (see the file comment).  Returns this
+// CTA's share of sum_j alpha_j^2 X'_j^2 (||A w||^2 or ||A x - b||^2).  MODE_FORWARD
+// writes alpha_j X_j (the full orthonormal DCT-II) to fwd_out[j] and stops there.
+template <int G, class C, int MODE>
+__device__ __noinline__ double dct_slot_step(C* buf, const DctGeom& geo, const Twiddle<C>& tw, double* fwd_out) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int M = 1 << geo.logM;
+  const int spc = (M >> 1) / G;  // slots per CTA (>= 1 by the host's choice of G)
+  double acc = 0.0;
+  cg::cluster_group cl = cg::this_cluster();
+  for (int base = warp * 16; base < spc; base += kWarps * 16) {
+    const int sl = base + (lane & 15);
+    const bool valid = sl < spc;
+    const int s = geo.rank * spc + (valid ? sl : 0);
+    // lanes l and l^16 hold columns k2 and M - k2 (slot 0: columns 0 and M/2, each
+    // paired with itself)
+    const int k2 = (lane < 16) ? s : (s == 0 ? (M >> 1) : M - s);
+    const bool self0 = (k2 == 0), selfh = (k2 == (M >> 1));
+    const int pos = bitrev(k2, geo.logM);
+    C Z[G];
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+      C y;
+      if constexpr (G == 1) {
+        y = buf[pos];
+      } else {
+        y = cl.map_shared_rank(buf, g)[pos];
+      }
+      Z[g] = (g == 0) ? y : cmul(y, tw.root((int64_t)g * k2, geo.logL));
+    }
+    small_dft<G>(Z, false, tw);  // Z[k1] = H[k2 + M k1]
+    // column 0: H[M k1] pairs with H[M ((G - k1) mod G)] of the same column
+    if (self0) {
+      C T[G];
+#pragma unroll
+      for (int k1 = 0; k1 < G; ++k1) T[k1] = Z[k1];
+#pragma unroll
+      for (int k1 = 0; k1 < G; ++k1)
+        Z[k1] = dct_pointwise<C, MODE>((int64_t)M * k1, T[k1], T[(G - k1) % G], geo, tw, valid, acc, fwd_out);
+    }
+    // other columns: H[k2 + M k1] pairs with H[(M - k2) + M (G-1-k1)], held by lane^16
+    // (column M/2 pairs with itself the same way); update k1 and G-1-k1 together so
+    // that no value is overwritten before the partner has read it
+#pragma unroll
+    for (int j = 0; j < (G + 1) / 2; ++j) {
+      const int kA = j, kB = G - 1 - j;
+      C bA, bB;
+      bA.x = __shfl_xor_sync(0xffffffffu, Z[kB].x, 16);
+      bA.y = __shfl_xor_sync(0xffffffffu, Z[kB].y, 16);
+      bB.x = __shfl_xor_sync(0xffffffffu, Z[kA].x, 16);
+      bB.y = __shfl_xor_sync(0xffffffffu, Z[kA].y, 16);
+      if (selfh) {
+        bA = Z[kB];
+        bB = Z[kA];
+      }
+      if (!self0) {
+        const C nA = dct_pointwise<C, MODE>((int64_t)k2 + (int64_t)M * kA, Z[kA], bA, geo, tw, valid, acc, fwd_out);
+        if (kB != kA) {
+          const C nB = dct_pointwise<C, MODE>((int64_t)k2 + (int64_t)M * kB, Z[kB], bB, geo, tw, valid, acc, fwd_out);
+          Z[kB] = nB;
+        }
+        Z[kA] = nA;
+      }
+    }
+    if constexpr (MODE != MODE_FORWARD) {
+      small_dft<G>(Z, true, tw);
+      if (valid) {
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+          const C y = (g == 0) ? Z[g] : cmulc(Z[g], tw.root((int64_t)g * k2, geo.logL));
+          if constexpr (G == 1) {
+            buf[pos] = y;
+          } else {
+            cl.map_shared_rank(buf, g)[pos] = y;
+          }
+        }
+      }
+    }
+  }
+  return acc;
+}
+
+// buf (this CTA's chunk, storage order, as complex pairs) := D^-1 M (D buf - b_u) or
+// D^-1 M D buf.  Returns this CTA's share of the masked coefficient energy.
+template <int G, class C, int MODE>
+__device__ double dct_chain(C* buf, const DctGeom& geo, const Twiddle<C>& tw, double* fwd_out = nullptr) {
+  using R = decltype(C().x);
+  fft_dif<C, R>(buf, geo.logM, tw);
+  cluster_barrier<G>();
+  const double acc = dct_slot_step<G, C, MODE>(buf, geo, tw, fwd_out);
+  cluster_barrier<G>();
+  if constexpr (MODE != MODE_FORWARD) fft_dit_inv<C, R>(buf, geo.logM, tw);
+  return acc;
+}
+
+// natural index of storage position q (global over the cluster)
+__device__ __forceinline__ int64_t dct_natural_index(int64_t q, int logM, int G) {
+  const int64_t M = (int64_t)1 << logM;
+  const int64_t g = q / (2 * M), n2 = (q % (2 * M)) >> 1, part = q & 1;
+  const int64_t j = g + (int64_t)G * n2;
+  const int64_t N = 2 * M * G;
+  const int64_t i = 2 * j + part;
+  return i < N / 2 ? 2 * i : 2 * N - 1 - 2 * i;
+}
+
+template <int G> struct DctOp {
+  DctGeom geo;
+  double2* buf64;
+  float2* buf32;
+  Twiddle<double2> tw64;
+  Twiddle<float2> tw32;
+  int64_t chunk, gbase;
+  double rho;
+  int rank;
+
+  __device__ void init(const ProbDesc& pd, const KernelArgs& a, unsigned char* smem, int rank_) {
+    rank = rank_;
+    geo.N = pd.n;
+    geo.logN = pd.log2n;
+    geo.logL = pd.log2n - 1;
+    geo.logM = geo.logL - (G == 1 ? 0 : G == 2 ? 1 : G == 4 ? 2 : G == 8 ? 3 : 4);
+    geo.rank = rank_;
+    geo.mask = pd.mask;
+    geo.bsu = pd.bsu;
+    const int64_t M = (int64_t)1 << geo.logM;
+    buf64 = reinterpret_cast<double2*>(smem);
+    buf32 = reinterpret_cast<float2*>(smem + (size_t)16 * M);
+    tw64 = Twiddle<double2>{a.tw64, a.log2_tw};
+    tw32 = Twiddle<float2>{a.tw32, a.log2_tw};
+    chunk = 2 * M;
+    gbase = (int64_t)rank_ * chunk;
+    rho = (double)pd.m / (double)pd.n;  // A A^T = I: rho = m/n (Eq. eq:ne2_P)
+  }
+  __device__ __forceinline__ bool valid(int64_t) const { return true; }
+  __device__ __forceinline__ double* r64() const { return reinterpret_cast<double*>(buf64); }
+  template <class PS> __device__ __forceinline__ PS* wbuf() const { return reinterpret_cast<PS*>(buf32); }
+  // r64() := A^T (A r64() - b); returns share of ||A x - b||^2
+  __device__ double resid() { return dct_chain<G, double2, MODE_RESID>(buf64, geo, tw64); }
+  // r32() := A^T A r32(); returns share of ||A w||^2
+  template <class PS> __device__ double normal(PS*) { return dct_chain<G, float2, MODE_NORMAL>(buf32, geo, tw32); }
+  __device__ int64_t natural(int64_t q) const { return dct_natural_index(gbase + q, geo.logM, G); }
+  template <int GG> __device__ void setup(RedSmem&, int&) {}
+};
+
+// ------------------------------------------------------------------ dense op
+// CTA rank r owns columns [r*chunk, (r+1)*chunk) of A (row-major m x n, float64).
+// A w is summed over the cluster through DSMEM (an all-reduce of m values).
+template <int G> struct DenseOp {
+  const double* A;
+  double a_scale;
+  int64_t lda, m, n, chunk, gbase;
+  double* buf64;
+  void* bufP;
+  double* tpart;  // m: this CTA's partial A w
+  double* tfull;  // m: reduced A w (identical in every CTA)
+  const double* b;
+  double rho;
+  int rank;
+
+  __device__ void init(const ProbDesc& pd, const KernelArgs&, unsigned char* smem, int rank_) {
+    rank = rank_;
+    A = static_cast<const double*>(pd.A);
+    a_scale = pd.a_scale;
+    lda = pd.lda;
+    m = pd.m;
+    n = pd.n;
+    chunk = (n + G - 1) / G;
+    gbase = (int64_t)rank * chunk;
+    const size_t c8 = ((size_t)chunk * 8 + 255) & ~(size_t)255;
+    buf64 = reinterpret_cast<double*>(smem);
+    bufP = smem + c8;
+    tpart = reinterpret_cast<double*>(smem + 2 * c8);
+    tfull = tpart + ((m + 31) & ~31);
+    b = pd.b;
+  }
+  __device__ __forceinline__ bool valid(int64_t q) const { return gbase + q < n; }
+  __device__ __forceinline__ double* r64() const { return buf64; }
+  template <class PS> __device__ __forceinline__ PS* wbuf() const { return reinterpret_cast<PS*>(bufP); }
+  __device__ __forceinline__ int64_t natural(int64_t q) const { return gbase + q; }
+
+  template <class PS, int MODE> __device__ double chain(PS* v) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t cols = min(chunk, n - gbase);
+    // t_part = A[:, own] v
+    for (int64_t i = warp; i < m; i += kWarps) {
+      const double* Ai = A + i * lda + gbase;
+      double s = 0.0;
+      for (int64_t j = lane; j < cols; j += 32) s += __ldg(&Ai[j]) * (double)v[j];
+      s = warp_sum(s);
+      if (lane == 0) tpart[i] = s * a_scale;
+    }
+    cluster_barrier<G>();
+    double acc = 0.0;
+    cg::cluster_group cl = cg::this_cluster();
+    for (int64_t i = threadIdx.x; i < m; i += kThreads) {
+      double t = 0.0;
+#pragma unroll
+      for (int g = 0; g < G; ++g) {
+        if constexpr (G == 1) t += tpart[i]; else t += cl.map_shared_rank(tpart, g)[i];
+      }
+      if (MODE == MODE_RESID) t -= b[i];
+      tfull[i] = t;
+      if (rank == 0) acc += t * t;
+    }
+    __syncthreads();
+    // v = A[:, own]^T t
+    for (int64_t j = threadIdx.x; j < cols; j += kThreads) {
+      const double* Aj = A + gbase + j;
+      double s0 = 0.0, s1 = 0.0;
+      int64_t i = 0;
+      for (; i + 1 < m; i += 2) {
+        s0 += __ldg(&Aj[i * lda]) * tfull[i];
+        s1 += __ldg(&Aj[(i + 1) * lda]) * tfull[i + 1];
+      }
+      if (i < m) s0 += __ldg(&Aj[i * lda]) * tfull[i];
+      v[j] = (PS)((s0 + s1) * a_scale);
+    }
+    __syncthreads();
+    return acc;
+  }
+  __device__ double resid() { return chain<double, MODE_RESID>(buf64); }
+  template <class PS> __device__ double normal(PS* v) { return chain<PS, MODE_NORMAL>(v); }
+
+  // rho = ||A||_F^2 / n: the Frobenius-closest multiple of I to A^T A (equals m/n when
+  // A A^T = I, Eq. eq:ne2_P)
+  template <int GG> __device__ void setup(RedSmem& rs, int& par) {
+    const int64_t cols = min(chunk, n - gbase);
+    double s = 0.0;
+    for (int64_t idx = threadIdx.x; idx < m * cols; idx += kThreads) {
+      const int64_t i = idx / cols, j = idx % cols;
+      const double a = __ldg(&A[i * lda + gbase + j]) * a_scale;
+      s += a * a;
+    }
+    double v[1] = {s}, out[1];
+    cluster_sum<GG, 1>(rs, par, v, out);
+    rho = out[0] / (double)n;
+  }
+};
+
+// ------------------------------------------------------------------ the IPM driver
+struct IpmScalars {
+  double mu, sigma, alpha_p, alpha_d;       // predictor
+  double mu_t, alpha_p1, alpha_d1;          // corrector trial point
+  bool corr;
+};
+
+// dz and ds of one index from the PCG solution(s) (Eq. redNewtonB):
+//   predictor ds1 = Z^-1 f_s - Theta^-1 dz1 = sigma mu / z - s - (s / z) dz1
+//   corrector ds2 = Z^-1 f_s~ - Theta^-1 dz2, f_s~ = sigma3 mu~ - z~ s~ at the trial point
+//             z~ = z + alpha_p1 dz1, s~ = s + alpha_d1 ds1 (reading: Theta, Z of the current point)
+struct Dir {
+  double dz, ds;
+};
+__device__ __forceinline__ Dir direction(double z, double s, double rz, double dz1, double dz2,
+                                         const IpmScalars& sc, double sigma3) {
+  const double d = s * rz;
+  const double ds1 = fma(sc.sigma * sc.mu, rz, -s) - d * dz1;
+  Dir r{dz1, ds1};
+  if (sc.corr) {
+    const double zt = fma(sc.alpha_p1, dz1, z);
+    const double st = fma(sc.alpha_d1, ds1, s);
+    const double fst = fma(-zt, st, sigma3 * sc.mu_t);
+    const double ds2 = fst * rz - d * dz2;
+    r.dz = dz1 + dz2;
+    r.ds = ds1 + ds2;
+  }
+  return r;
+}
+
+template <int G, class Op, class PS>
+__device__ void solve_one(const ProbDesc& pd, const KernelArgs& a, Op& op, RedSmem& rs, int& par) {
+  using P2 = typename V2<PS>::T;
+  const SolveParams& prm = a.prm;
+  const int tid = threadIdx.x;
+  const int64_t n = pd.n;
+  const double tau = pd.tau;
+  const int64_t chunk = op.chunk, gb = op.gbase;
+  double2* zs = reinterpret_cast<double2*>(pd.zs);
+  P2* X1 = reinterpret_cast<P2*>(pd.pcg);
+  P2* X2 = X1 + n;
+  P2* Rv = X2 + n;
+  P2* Pv = Rv + n;
+  P2* Dv = Pv + n;
+  double* g64 = op.r64();
+  mfipm_info info{};
+  int64_t nmat = 0;
+
+  op.template setup<G>(rs, par);
+  const PS rho = (PS)op.rho;
+
+  // ||c||^2 = sum 2 tau^2 + 2 (A^T b)_i^2 with A^T b = -A^T (A 0 - b)  (c: Sec. 3)
+  for (int64_t q = tid; q < chunk; q += kThreads) g64[q] = 0.0;
+  __syncthreads();
+  double bb = op.resid();
+  ++nmat;
+  double atb2 = 0.0;
+  for (int64_t q = tid; q < chunk; q += kThreads)
+    if (op.valid(q)) atb2 += g64[q] * g64[q];
+  double cn;
+  {
+    double v[2] = {atb2, bb}, out[2];
+    cluster_sum<G, 2>(rs, par, v, out);
+    cn = sqrt(2.0 * (double)n * tau * tau + 2.0 * out[0]);
+  }
+
+  IpmScalars sc{};
+  sc.alpha_p = sc.alpha_d = 1.0;
+  double prev_ap = 1.0, prev_ad = 1.0;
+  int status = MFIPM_NOT_CONVERGED;
+  double rel_gap = INFINITY, P_obj = 0.0;
+  int it = 0;
+  int pcg_total = 0;
+
+  // PCG on (Theta^-1 + F F^T) dz = rhs (Sec. 4).  On entry r = rhs and p = P^-1 r are
+  // stored, the operator input w = p_u - p_v is in the shared buffer, and rz, pdp are this
+  // thread's partials of r.P^-1 r and p.(Theta^-1 p).  Result in Xo (float or double pairs).
+  auto pcg = [&](P2* Xo, double rz_part, double pdp_part) {
+    double rz0 = 0.0, rz = 0.0;
+    int k = 0;
+    PS* w = op.template wbuf<PS>();
+    double pdp_acc = pdp_part;
+    for (;;) {
+      const double aw2 = op.normal(w);
+      ++nmat;
+      ++nmat;
+      double tot[2];
+      {
+        double v[2] = {pdp_acc + aw2, k == 0 ? rz_part : 0.0};
+        cluster_sum<G, 2>(rs, par, v, tot);
+      }
+      if (k == 0) {
+        rz0 = rz = tot[1];
+        if (!(rz0 > 0.0) || !isfinite(rz0)) {  // zero right-hand side: dz = 0
+          for (int64_t q = tid; q < chunk; q += kThreads) {
+            P2 zero;
+            zero.x = (PS)0;
+            zero.y = (PS)0;
+            if (op.valid(q)) Xo[gb + q] = zero;
+          }
+          break;
+        }
+      }
+      const double pq = tot[0];
+      const PS alpha = (PS)(rz / pq);
+      double rzn_part = 0.0;
+      for (int64_t q = tid; q < chunk; q += kThreads) {
+        if (!op.valid(q)) continue;
+        const int64_t gi = gb + q;
+        const P2 p = Pv[gi], d = Dv[gi];
+        P2 r = Rv[gi];
+        P2 x;
+        if (k == 0) { x.x = (PS)0; x.y = (PS)0; } else { x = Xo[gi]; }
+        const PS y = w[q];
+        const PS qu = d.x * p.x + y, qv = d.y * p.y - y;
+        x.x += alpha * p.x;
+        x.y += alpha * p.y;
+        r.x -= alpha * qu;
+        r.y -= alpha * qv;
+        const P2 zz = precond<PS>(d, r, rho);
+        rzn_part += (double)(r.x * zz.x + r.y * zz.y);
+        Xo[gi] = x;
+        Rv[gi] = r;
+      }
+      ++k;
+      double rzn;
+      {
+        double v[1] = {rzn_part}, out[1];
+        cluster_sum<G, 1>(rs, par, v, out);
+        rzn = out[0];
+      }
+      if (!(rzn > prm.tol_pcg * prm.tol_pcg * rz0) || k >= prm.max_iter_pcg || !isfinite(rzn)) break;
+      const PS beta = (PS)(rzn / rz);
+      rz = rzn;
+      double pdp = 0.0;
+      for (int64_t q = tid; q < chunk; q += kThreads) {
+        if (!op.valid(q)) { w[q] = (PS)0; continue; }
+        const int64_t gi = gb + q;
+        const P2 d = Dv[gi], r = Rv[gi];
+        P2 p = Pv[gi];
+        const P2 zz = precond<PS>(d, r, rho);
+        p.x = zz.x + beta * p.x;
+        p.y = zz.y + beta * p.y;
+        Pv[gi] = p;
+        w[q] = p.x - p.y;
+        pdp += (double)(d.x * p.x * p.x + d.y * p.y * p.y);
+      }
+      __syncthreads();
+      pdp_acc = pdp;
+    }
+    pcg_total += k;
+  };
+
+  // PCG initialisation from a float64 right-hand side (rhs_fn(q) -> double2)
+  auto pcg_init = [&](auto rhs_fn, bool write_d, double& rz_part, double& pdp_part) {
+    PS* w = op.template wbuf<PS>();
+    rz_part = 0.0;
+    pdp_part = 0.0;
+    for (int64_t q = tid; q < chunk; q += kThreads) {
+      if (!op.valid(q)) { w[q] = (PS)0; continue; }
+      const int64_t gi = gb + q;
+      P2 d;
+      double2 rhs;
+      if (write_d) {
+        const double2 z = zs[2 * gi], s = zs[2 * gi + 1];
+        const double ru = rcp64(z.x), rv = rcp64(z.y);
+        d.x = (PS)(s.x * ru);
+        d.y = (PS)(s.y * rv);
+        Dv[gi] = d;
+        rhs = rhs_fn(q, z, s, ru, rv);
+      } else {
+        d = Dv[gi];
+        const double2 z = zs[2 * gi], s = zs[2 * gi + 1];
+        rhs = rhs_fn(q, z, s, rcp64(z.x), rcp64(z.y));
+      }
+      P2 r;
+      r.x = (PS)rhs.x;
+      r.y = (PS)rhs.y;
+      const P2 p = precond<PS>(d, r, rho);
+      Rv[gi] = r;
+      Pv[gi] = p;
+      w[q] = p.x - p.y;
+      rz_part += (double)(r.x * p.x + r.y * p.y);
+      pdp_part += (double)(d.x * p.x * p.x + d.y * p.y * p.y);
+    }
+    __syncthreads();
+  };
+
+  // step lengths alpha = min(1, eta * min_{dv<0} -v/dv) for z and s (reading R4)
+  auto step_lengths = [&](double& ap, double& ad) {
+    double mp = INFINITY, md = INFINITY;
+    for (int64_t q = tid; q < chunk; q += kThreads) {
+      if (!op.valid(q)) continue;
+      const int64_t gi = gb + q;
+      const double2 z = zs[2 * gi], s = zs[2 * gi + 1];
+      const P2 x1 = X1[gi];
+      P2 x2;
+      x2.x = (PS)0;
+      x2.y = (PS)0;
+      if (sc.corr) x2 = X2[gi];
+      const Dir du = direction(z.x, s.x, rcp64(z.x), (double)x1.x, (double)x2.x, sc, prm.sigma3);
+      const Dir dv = direction(z.y, s.y, rcp64(z.y), (double)x1.y, (double)x2.y, sc, prm.sigma3);
+      if (du.dz < 0.0) mp = fmin(mp, z.x * rcp64(-du.dz));
+      if (dv.dz < 0.0) mp = fmin(mp, z.y * rcp64(-dv.dz));
+      if (du.ds < 0.0) md = fmin(md, s.x * rcp64(-du.ds));
+      if (dv.ds < 0.0) md = fmin(md, s.y * rcp64(-dv.ds));
+    }
+    double v[2] = {mp, md}, out[2];
+    cluster_min<G, 2>(rs, par, v, out);
+    ap = fmin(1.0, prm.eta * out[0]);
+    ad = fmin(1.0, prm.eta * out[1]);
+    if (prm.equal_steps) ap = ad = fmin(ap, ad);
+  };
+
+  for (it = 1;; ++it) {
+    // ---- update (previous direction) fused with x = u - v for the residual
+    double part[3] = {0.0, 0.0, 0.0};  // z.s, 1^T z, ||x||^2
+    for (int64_t q = tid; q < chunk; q += kThreads) {
+      if (!op.valid(q)) { g64[q] = 0.0; continue; }
+      const int64_t gi = gb + q;
+      double2 z, s;
+      if (it == 1) {
+        z = make_double2(1.0, 1.0);  // reading R3: z0 = s0 = 1
+        s = z;
+      } else {
+        z = zs[2 * gi];
+        s = zs[2 * gi + 1];
+        const P2 x1 = X1[gi];
+        P2 x2;
+        x2.x = (PS)0;
+        x2.y = (PS)0;
+        if (sc.corr) x2 = X2[gi];
+        const Dir du = direction(z.x, s.x, rcp64(z.x), (double)x1.x, (double)x2.x, sc, prm.sigma3);
+        const Dir dv = direction(z.y, s.y, rcp64(z.y), (double)x1.y, (double)x2.y, sc, prm.sigma3);
+        double nu = fma(sc.alpha_p, du.dz, z.x), nv = fma(sc.alpha_p, dv.dz, z.y);
+        double nsu = fma(sc.alpha_d, du.ds, s.x), nsv = fma(sc.alpha_d, dv.ds, s.y);
+        // the step keeps z, s > 0 by construction; guard against a rounding-level crossing
+        if (!(nu > 0.0)) nu = z.x * (1.0 - prm.eta);
+        if (!(nv > 0.0)) nv = z.y * (1.0 - prm.eta);
+        if (!(nsu > 0.0)) nsu = s.x * (1.0 - prm.eta);
+        if (!(nsv > 0.0)) nsv = s.y * (1.0 - prm.eta);
+        z = make_double2(nu, nv);
+        s = make_double2(nsu, nsv);
+      }
+      zs[2 * gi] = z;
+      zs[2 * gi + 1] = s;
+      const double x = z.x - z.y;
+      g64[q] = x;
+      part[0] += z.x * s.x + z.y * s.y;
+      part[1] += z.x + z.y;
+      part[2] += x * x;
+    }
+    __syncthreads();
+    // ---- float64 residual g = A^T (A x - b)  (f_z of Eq. fzfs needs F F^T z + c)
+    const double res2 = op.resid();
+    nmat += 2;
+    double tot[4];
+    {
+      double v[4] = {part[0], part[1], part[2], res2};
+      cluster_sum<G, 4>(rs, par, v, tot);
+    }
+    const double zts = tot[0];
+    sc.mu = zts / (2.0 * (double)n);
+    P_obj = tau * tot[1] + 0.5 * tot[3];
+    rel_gap = zts / (1.0 + fabs(P_obj));
+    if (!isfinite(rel_gap)) { status = MFIPM_NUMERIC; break; }
+    if (rel_gap <= prm.tol) { status = MFIPM_OK; break; }        // reading R7
+    if (it > prm.max_iter) { status = MFIPM_NOT_CONVERGED; break; }
+    // ---- predictor (Algorithm: sigma choice, then PCG)
+    sc.sigma = (it != 1 && (prev_ap <= prm.alpha_bar || prev_ad <= prm.alpha_bar)) ? prm.sigma2 : prm.sigma1;
+    sc.corr = false;
+    const double smu = sc.sigma * sc.mu;
+    double rzp, pdpp;
+    // rhs = f_z + Z^-1 f_s = sigma mu / z - (c + F F^T z) = sigma mu/z - [tau + g; tau - g]
+    pcg_init([&](int64_t q, double2, double2, double ru, double rv) {
+               const double g = g64[q];
+               return make_double2(fma(smu, ru, -(tau + g)), fma(smu, rv, -(tau - g)));
+             }, true, rzp, pdpp);
+    pcg(X1, rzp, pdpp);
+    step_lengths(sc.alpha_p, sc.alpha_d);
+    // ---- corrector (reading R6)
+    if (sc.alpha_p <= prm.alpha_tilde || sc.alpha_d <= prm.alpha_tilde) {
+      ++info.correctors;
+      sc.alpha_p1 = sc.alpha_p;
+      sc.alpha_d1 = sc.alpha_d;
+      double zts_t = 0.0;
+      for (int64_t q = tid; q < chunk; q += kThreads) {
+        if (!op.valid(q)) { g64[q] = 0.0; continue; }
+        const int64_t gi = gb + q;
+        const double2 z = zs[2 * gi], s = zs[2 * gi + 1];
+        const P2 x1 = X1[gi];
+        const Dir du = direction(z.x, s.x, rcp64(z.x), (double)x1.x, 0.0, sc, prm.sigma3);
+        const Dir dv = direction(z.y, s.y, rcp64(z.y), (double)x1.y, 0.0, sc, prm.sigma3);
+        const double zu = fma(sc.alpha_p1, du.dz, z.x), zv = fma(sc.alpha_p1, dv.dz, z.y);
+        const double su = fma(sc.alpha_d1, du.ds, s.x), sv = fma(sc.alpha_d1, dv.ds, s.y);
+        g64[q] = zu - zv;
+        zts_t += zu * su + zv * sv;
+      }
+      __syncthreads();
+      op.resid();
+      nmat += 2;
+      {
+        double v[1] = {zts_t}, out[1];
+        cluster_sum<G, 1>(rs, par, v, out);
+        sc.mu_t = out[0] / (2.0 * (double)n);
+      }
+      const double s3mu = prm.sigma3 * sc.mu_t;
+      // rhs~ = f_z~ + Z^-1 f_s~ with f_z~ = s~ - [tau + g~; tau - g~], f_s~ = sigma3 mu~ - z~ s~
+      pcg_init([&](int64_t q, double2 z, double2 s, double ru, double rv) {
+                 const int64_t gi = gb + q;
+                 const P2 x1 = X1[gi];
+                 const double g = g64[q];
+                 const double dsu = fma(smu, ru, -s.x) - s.x * ru * (double)x1.x;
+                 const double dsv = fma(smu, rv, -s.y) - s.y * rv * (double)x1.y;
+                 const double zu = fma(sc.alpha_p1, (double)x1.x, z.x), zv = fma(sc.alpha_p1, (double)x1.y, z.y);
+                 const double su = fma(sc.alpha_d1, dsu, s.x), sv = fma(sc.alpha_d1, dsv, s.y);
+                 const double fzu = su - (tau + g), fzv = sv - (tau - g);
+                 return make_double2(fma(fma(-zu, su, s3mu), ru, fzu), fma(fma(-zv, sv, s3mu), rv, fzv));
+               }, false, rzp, pdpp);
+      sc.corr = true;
+      pcg(X2, rzp, pdpp);
+      step_lengths(sc.alpha_p, sc.alpha_d);
+    }
+    prev_ap = sc.alpha_p;
+    prev_ad = sc.alpha_d;
+  }
+
+  // ---- exit: certificates and outputs (g64 holds A^T(Ax - b) of the final iterate)
+  double fin[3] = {0.0, 0.0, 0.0};  // ||f_z||^2, kkt^2, ||x||^2
+  for (int64_t q = tid; q < chunk; q += kThreads) {
+    if (!op.valid(q)) continue;
+    const int64_t gi = gb + q;
+    const double2 z = zs[2 * gi], s = zs[2 * gi + 1];
+    const double g = g64[q];
+    const double fzu = s.x - (tau + g), fzv = s.y - (tau - g);
+    const double x = z.x - z.y;
+    const double y = x - g;
+    const double st = copysign(fmax(fabs(y) - tau, 0.0), y);
+    fin[0] += fzu * fzu + fzv * fzv;
+    fin[1] += (x - st) * (x - st);
+    fin[2] += x * x;
+    const int64_t ni = op.natural(q);
+    pd.x_out[ni] = x;
+    if (pd.zs_out) {
+      pd.zs_out[ni] = z.x;
+      pd.zs_out[n + ni] = z.y;
+      pd.zs_out[2 * n + ni] = s.x;
+      pd.zs_out[3 * n + ni] = s.y;
+    }
+  }
+  double ftot[3];
+  cluster_sum<G, 3>(rs, par, fin, ftot);
+  if (op.rank == 0 && tid == 0) {
+    info.status = status;
+    info.ipm_iters = it - 1;
+    info.pcg_iters = pcg_total;
+    info.n_mat = nmat;
+    info.rel_gap = rel_gap;
+    info.dual_res = sqrt(ftot[0]) / (1.0 + cn);
+    info.kkt_rel = sqrt(ftot[1]) / (1.0 + sqrt(ftot[2]));
+    info.primal_obj = P_obj;
+    *pd.info = info;
+    if (status != MFIPM_OK) atomicCAS(a.err, 0, status);
+  }
+}
+
+template <int G, class Op, class PS>
+__global__ void __launch_bounds__(kThreads, 1) ipm_kernel(KernelArgs a) {
+  extern __shared__ __align__(256) unsigned char smem[];
+  __shared__ RedSmem rs;
+  int par = 0;
+  int rank = 0;
+  if constexpr (G > 1) rank = (int)cg::this_cluster().block_rank();
+  for (;;) {
+    if (rank == 0 && threadIdx.x == 0) rs.fetched = atomicAdd(a.queue, 1);
+    cluster_barrier<G>();
+    int pid;
+    if constexpr (G == 1) {
+      pid = rs.fetched;
+    } else {
+      pid = cg::this_cluster().map_shared_rank(&rs, 0)->fetched;
+    }
+    if (pid >= a.batch) break;
+    const ProbDesc pd = a.probs[pid];
+    Op op;
+    op.init(pd, a, smem, rank);
+    solve_one<G, Op, PS>(pd, a, op, rs, par);
+    cluster_barrier<G>();
+  }
+  cluster_barrier<G>();  // no CTA leaves while another may still read its shared memory
+}
+
+template <int G, class Op, class PS>
+inline cudaError_t launch_t(const KernelArgs& a, size_t smem, int grid_clusters, cudaStream_t st) {
+  auto kern = ipm_kernel<G, Op, PS>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  if (G > 8) {
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e != cudaSuccess) return e;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid_clusters * G);
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = G;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, a);
+}
+
+template <int G, class Op, class PS>
+inline int occupancy_t(size_t smem) {
+  auto kern = ipm_kernel<G, Op, PS>;
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
+  if (G > 8 && cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) return 0;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(G);
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = smem;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = G;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int n = 0;
+  if (cudaOccupancyMaxActiveClusters(&n, kern, &cfg) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return n;
+}
+
+
+#define MFIPM_G_SWITCH(G, CALL) \
+  switch (G) {                  \
+    case 1: return CALL(1);     \
+    case 2: return CALL(2);     \
+    case 4: return CALL(4);     \
+    case 8: return CALL(8);     \
+    case 16: return CALL(16);   \
+    default: break;             \
+  }
+
+}  // namespace mfipm

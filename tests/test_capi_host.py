@@ -1,0 +1,94 @@
+"""C-ABI checks that need no GPU: the library loads, exports every declared function,
+has the paper's defaults, sizes workspaces and rejects invalid arguments before any
+launch."""
+import ctypes
+import json
+import os
+
+import pytest
+
+from tests._lib import built_lib, header_functions
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "paper_parameters.json")
+
+
+@pytest.fixture(scope="module")
+def L():
+    return built_lib()
+
+
+def test_exports_every_declared_function(L):
+    names = header_functions()
+    assert "mfipm_solve" in names and "mfipm_solve_batched" in names and "mfipm_backward" in names
+    for name in names:
+        assert hasattr(L, name), name
+    from paper_1208_5435_gb300 import _capi
+    assert set(_capi.SIGNATURES) == set(names)
+
+
+def test_param_defaults_are_the_papers(L):
+    from paper_1208_5435_gb300 import _capi as C
+    p = C.Params()
+    assert L.mfipm_params_default(ctypes.byref(p)) == 0
+    g = json.load(open(GOLDEN))
+    assert (p.sigma1, p.sigma2, p.sigma3) == (g["sigma1"], g["sigma2"], g["sigma3"])
+    assert (p.alpha_bar, p.alpha_tilde) == (g["alpha_bar"], g["alpha_tilde"])
+    assert p.max_iter == g["maxiters"] and p.max_iter_pcg == g["mxiterpcg"]
+    assert g["tolpcg_noisy_range"][0] <= p.tol_pcg <= g["tolpcg_noisy_range"][1]
+    assert g["tol_noisy_range"][0] <= p.tol <= g["tol_noisy_range"][1]
+    assert L.mfipm_params_default(None) == C.MFIPM_INVALID_ARG
+
+
+def _dct_op(C, n, m, rows_ptr=0x1000):
+    op = C.Operator()
+    op.kind, op.a_dtype, op.m, op.n, op.A, op.a_scale, op.lda, op.rows = C.OP_PARTIAL_DCT, 0, m, n, None, 1.0, 0, rows_ptr
+    return op
+
+
+def test_workspace_size_grows_with_batch(L):
+    from paper_1208_5435_gb300 import _capi as C
+    p = C.Params()
+    L.mfipm_params_default(ctypes.byref(p))
+    sizes = []
+    for batch in (1, 2, 8):
+        ops = (C.Operator * batch)(*[_dct_op(C, 4096, 1024) for _ in range(batch)])
+        nb = ctypes.c_size_t()
+        assert L.mfipm_workspace_size(ops, batch, ctypes.byref(p), ctypes.byref(nb)) == 0
+        sizes.append(nb.value)
+    assert sizes[0] >= 4096 * 80 and sizes[0] < sizes[1] < sizes[2]
+
+
+@pytest.mark.parametrize("case", ["n_not_pow2", "m_gt_n", "n_too_big", "tau_nonpositive", "null_ws", "small_ws",
+                                  "bad_cluster", "bad_eta", "dense_bf16_here", "dct_fp64_pcg"])
+def test_invalid_arguments_rejected_before_launch(L, case):
+    from paper_1208_5435_gb300 import _capi as C
+    p = C.Params()
+    L.mfipm_params_default(ctypes.byref(p))
+    op = _dct_op(C, 4096, 1024)
+    tau = 0.1
+    ws, wsb = ctypes.c_void_p(0x10000), 1 << 40
+    if case == "n_not_pow2":
+        op.n = 3000
+    elif case == "m_gt_n":
+        op.m = 5000
+    elif case == "n_too_big":
+        op.n, op.m = 1 << 20, 1 << 18
+    elif case == "tau_nonpositive":
+        tau = 0.0
+    elif case == "null_ws":
+        ws = None
+    elif case == "small_ws":
+        wsb = 1024
+    elif case == "bad_cluster":
+        p.cluster_size = 3
+    elif case == "bad_eta":
+        p.eta = 1.0
+    elif case == "dense_bf16_here":
+        op.kind, op.a_dtype, op.A, op.lda, op.rows = C.OP_DENSE, C.A_BF16, 0x2000, op.n, None
+    elif case == "dct_fp64_pcg":
+        p.precision = C.PREC_FP64
+    info = C.Info()
+    rc = L.mfipm_solve(ctypes.byref(op), ctypes.c_void_p(0x3000), tau, ctypes.byref(p), ctypes.c_void_p(0x4000),
+                       None, ws, wsb, ctypes.byref(info), None)
+    assert rc in (C.MFIPM_INVALID_ARG, C.MFIPM_UNSUPPORTED), (case, rc)
+    assert L.mfipm_last_error() and len(L.mfipm_last_error()) > 5
