@@ -166,6 +166,12 @@ int mfipm_apply_At(const mfipm_operator* op, const double* y, double* x, void* w
 int mfipm_kkt_residual(const mfipm_operator* op, const double* b, double tau, const double* x,
                        void* workspace, size_t ws_bytes, double* out, void* stream);
 
+/* Instrumentation (this thread only): with timing enabled, each solve records CUDA events on
+ * its stream around the persistent solver kernel; mfipm_last_kernel_ms() returns that kernel's
+ * device time of the last solve in milliseconds (-1 if none).  Not in the paper. */
+int mfipm_set_timing(int32_t enable);
+double mfipm_last_kernel_ms(void);
+
 /* Message of the last failing call on this thread ("" if none). */
 const char* mfipm_last_error(void);
 

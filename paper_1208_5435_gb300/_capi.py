@@ -59,6 +59,8 @@ SIGNATURES = {
     "mfipm_kkt_residual": (ctypes.c_int, [ctypes.POINTER(Operator), _P, ctypes.c_double, _P, _P, ctypes.c_size_t,
                                           ctypes.POINTER(ctypes.c_double), _P]),
     "mfipm_last_error": (ctypes.c_char_p, []),
+    "mfipm_set_timing": (ctypes.c_int, [ctypes.c_int32]),
+    "mfipm_last_kernel_ms": (ctypes.c_double, []),
 }
 
 _lib = None

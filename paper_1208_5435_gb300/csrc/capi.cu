@@ -20,6 +20,11 @@ namespace {
 
 thread_local std::string g_err;
 
+// Optional timing of the solver kernel (mfipm_set_timing / mfipm_last_kernel_ms).
+thread_local bool g_timing = false;
+thread_local cudaEvent_t g_ev[2] = {nullptr, nullptr};
+thread_local float g_last_ms = -1.0f;
+
 int fail(int code, const char* fmt, ...) {
   char buf[512];
   va_list ap;
@@ -307,9 +312,15 @@ int run(Prepared& P, cudaStream_t st, int batch, mfipm_info* infos, const std::v
   int maxc = P.dct ? max_active_clusters_dct(P.G, P.max_n) : max_active_clusters_dense(P.G, P.pcg64, P.max_n, P.max_m);
   if (maxc < 1) return fail(MFIPM_UNSUPPORTED, "no resident cluster of size %d fits this problem", P.G);
   const int clusters = std::min(maxc, batch);
+  if (g_timing) {
+    for (auto& ev : g_ev)
+      if (!ev && (e = cudaEventCreate(&ev)) != cudaSuccess) return cuda_fail(e, "timing event");
+    cudaEventRecord(g_ev[0], st);
+  }
   e = P.dct ? launch_dct_solver(P.G, P.args, P.max_n, clusters, st)
             : launch_dense_solver(P.G, P.pcg64, P.args, P.max_n, P.max_m, clusters, st);
   if (e != cudaSuccess) return cuda_fail(e, "solver launch");
+  if (g_timing) cudaEventRecord(g_ev[1], st);
   int err = 0;
   if ((e = cudaMemcpyAsync(&err, P.args.err, sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
     return cuda_fail(e, "read error word");
@@ -319,6 +330,10 @@ int run(Prepared& P, cudaStream_t st, int batch, mfipm_info* infos, const std::v
       return cuda_fail(e, "read infos");
   }
   if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(e, "solve");
+  if (g_timing) {
+    float ms = -1.0f;
+    if (cudaEventElapsedTime(&ms, g_ev[0], g_ev[1]) == cudaSuccess) g_last_ms = ms;
+  }
   if (err == -1) return fail(MFIPM_INVALID_ARG, "rows must be distinct, ascending and inside [0, n)");
   if (err == -2) return fail(MFIPM_NUMERIC, "b contains a non-finite value");
   if (err > 0 && infos) {
@@ -415,5 +430,13 @@ int mfipm_kkt_residual(const mfipm_operator*, const double*, double, const doubl
 }
 
 const char* mfipm_last_error(void) { return g_err.c_str(); }
+
+int mfipm_set_timing(int32_t enable) {
+  g_timing = enable != 0;
+  g_last_ms = -1.0f;
+  return MFIPM_OK;
+}
+
+double mfipm_last_kernel_ms(void) { return (double)g_last_ms; }
 
 }  // extern "C"
