@@ -87,6 +87,8 @@ int validate_params(const mfipm_params* p) {
   if (!(p->sigma1 >= 0 && p->sigma2 >= 0 && p->sigma3 >= 0 && p->sigma1 <= 1 && p->sigma2 <= 1 && p->sigma3 <= 1))
     return fail(MFIPM_INVALID_ARG, "params: sigma values must lie in [0,1]");
   if (p->precision < 0 || p->precision > 2) return fail(MFIPM_INVALID_ARG, "params: bad precision %d", p->precision);
+  if (p->residual != MFIPM_RESID_DF && p->residual != MFIPM_RESID_FP64)
+    return fail(MFIPM_INVALID_ARG, "params: bad residual mode %d", p->residual);
   const int cs = p->cluster_size;
   if (!(cs == 0 || cs == 1 || cs == 2 || cs == 4 || cs == 8 || cs == 16))
     return fail(MFIPM_INVALID_ARG, "params: cluster_size must be 0,1,2,4,8,16");
@@ -106,6 +108,7 @@ SolveParams to_solve(const mfipm_params* p) {
   s.max_iter = p->max_iter;
   s.max_iter_pcg = p->max_iter_pcg;
   s.equal_steps = p->equal_steps;
+  s.resid_fp64 = p->residual == MFIPM_RESID_FP64;
   return s;
 }
 
@@ -122,7 +125,7 @@ int dct_max_G(int64_t n) {
 size_t problem_bytes(const mfipm_operator& op, bool pcg64) {
   const size_t n = (size_t)op.n;
   size_t b = 0;
-  if (op.kind == MFIPM_OP_PARTIAL_DCT) b += align256(n) + align256(8 * n);  // mask, bsu
+  if (op.kind == MFIPM_OP_PARTIAL_DCT) b += align256(n) + 2 * align256(8 * n);  // mask, bsu, bsu_df
   b += align256(32 * n);                                                     // z, s
   b += align256(5 * n * (pcg64 ? 16 : 8));                                   // x1 x2 r p d
   b += align256(8 * n);                                                      // scratch (apply)
@@ -130,7 +133,7 @@ size_t problem_bytes(const mfipm_operator& op, bool pcg64) {
 }
 
 struct Layout {
-  size_t off_hdr, off_tw64, off_tw32, off_desc, off_info, off_probs, total;
+  size_t off_hdr, off_tw64, off_tw32, off_twdf, off_desc, off_info, off_probs, total;
   int log2_tw;
 };
 
@@ -147,6 +150,8 @@ Layout make_layout(const mfipm_operator* ops, int batch, bool pcg64) {
   o += align256(((size_t)1 << L.log2_tw) * 16);
   L.off_tw32 = o;
   o += align256(((size_t)1 << L.log2_tw) * 8);
+  L.off_twdf = o;
+  o += align256(((size_t)1 << L.log2_tw) * 16);
   L.off_desc = o;
   o += align256(sizeof(ProbDesc) * (size_t)batch);
   L.off_info = o;
@@ -269,6 +274,8 @@ int prepare(int batch, const mfipm_operator* ops, const double* const* b, const 
       q += align256(n);
       d.bsu = reinterpret_cast<double*>(ws + q);
       q += align256(8 * n);
+      d.bsu_df = reinterpret_cast<float2*>(ws + q);
+      q += align256(8 * n);
     }
     d.zs = reinterpret_cast<double*>(ws + q);
     q += align256(32 * n);
@@ -286,6 +293,7 @@ int prepare(int batch, const mfipm_operator* ops, const double* const* b, const 
   a.err = reinterpret_cast<int*>(ws + P.lay.off_hdr + 4);
   a.tw64 = reinterpret_cast<const double2*>(ws + P.lay.off_tw64);
   a.tw32 = reinterpret_cast<const float2*>(ws + P.lay.off_tw32);
+  a.twdf = reinterpret_cast<const float4*>(ws + P.lay.off_twdf);
   a.log2_tw = P.lay.log2_tw;
   a.prm = to_solve(p);
   return MFIPM_OK;
@@ -303,8 +311,8 @@ int run(Prepared& P, cudaStream_t st, int batch, mfipm_info* infos, const std::v
     return cuda_fail(e, "upload descriptors");
   if ((e = cudaMemsetAsync(P.ws + P.lay.off_hdr, 0, 256, st)) != cudaSuccess) return cuda_fail(e, "clear header");
   if (P.dct) {
-    if ((e = launch_twiddles(const_cast<double2*>(P.args.tw64), const_cast<float2*>(P.args.tw32), P.args.log2_tw,
-                             st)) != cudaSuccess)
+    if ((e = launch_twiddles(const_cast<double2*>(P.args.tw64), const_cast<float2*>(P.args.tw32),
+                             const_cast<float4*>(P.args.twdf), P.args.log2_tw, st)) != cudaSuccess)
       return cuda_fail(e, "twiddle kernel");
     if ((e = launch_dct_setup(P.args.probs, batch, P.max_n, P.args.err, st)) != cudaSuccess)
       return cuda_fail(e, "setup kernel");

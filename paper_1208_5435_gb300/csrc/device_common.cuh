@@ -15,13 +15,64 @@ constexpr int kThreads = 512;          // threads per CTA of every solver kernel
 constexpr int kWarps = kThreads / 32;
 constexpr int kMaxRed = 8;             // values per fused cluster reduction
 
-// ------------------------------------------------------------------ complex helpers
-template <class R> struct cplx;
-template <> struct cplx<float> { using T = float2; };
-template <> struct cplx<double> { using T = double2; };
+// ------------------------------------------------------------------ double-float
+// A double-float value is the unevaluated sum hi + lo of two float32 numbers with
+// |lo| <= ulp(hi)/2: about 48 significant bits on the float32 pipes.  Built from the
+// error-free transformations TwoSum (Knuth) and Fast2Sum (Dekker) and the FMA-based exact
+// product; addition is the cheap "sloppy" double-double addition of Hida, Li and Bailey,
+// whose absolute error is bounded by about 2^-46 (|a| + |b|) -- what an FFT needs.
+// The _rn intrinsics keep the compiler from contracting or reordering these steps.
+struct df {
+  float hi, lo;
+  __host__ __device__ constexpr df() : hi(0.f), lo(0.f) {}
+  __host__ __device__ constexpr df(float h, float l = 0.f) : hi(h), lo(l) {}
+};
+__device__ __forceinline__ df df_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return df(s, e);
+}
+__device__ __forceinline__ df df_fast_two_sum(float a, float b) {  // needs |a| >= |b|
+  const float s = __fadd_rn(a, b);
+  return df(s, __fsub_rn(b, __fsub_rn(s, a)));
+}
+__device__ __forceinline__ df operator+(df a, df b) {
+  const df s = df_two_sum(a.hi, b.hi);
+  return df_fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
+}
+__device__ __forceinline__ df operator-(df a) { return df(-a.hi, -a.lo); }
+__device__ __forceinline__ df operator-(df a, df b) { return a + (-b); }
+__device__ __forceinline__ df operator*(df a, df b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  return df_fast_two_sum(p, e);
+}
+__device__ __forceinline__ df& operator+=(df& a, df b) { a = a + b; return a; }
+__device__ __forceinline__ df to_df(double x) {
+  const float h = __double2float_rn(x);
+  return df(h, __double2float_rn(x - (double)h));
+}
+__device__ __forceinline__ double to_double(df a) { return (double)a.hi + (double)a.lo; }
+__device__ __forceinline__ double to_double(float a) { return (double)a; }
+__device__ __forceinline__ double to_double(double a) { return a; }
 
+struct dfc {
+  df x, y;
+};
+
+__device__ __forceinline__ float shfl_xor(float v, int m) { return __shfl_xor_sync(0xffffffffu, v, m); }
+__device__ __forceinline__ double shfl_xor(double v, int m) { return __shfl_xor_sync(0xffffffffu, v, m); }
+__device__ __forceinline__ df shfl_xor(df v, int m) {
+  return df(__shfl_xor_sync(0xffffffffu, v.hi, m), __shfl_xor_sync(0xffffffffu, v.lo, m));
+}
+
+// ------------------------------------------------------------------ complex helpers
 __device__ __forceinline__ float2 mk(float a, float b) { return make_float2(a, b); }
 __device__ __forceinline__ double2 mk(double a, double b) { return make_double2(a, b); }
+__device__ __forceinline__ dfc mk(df a, df b) { return dfc{a, b}; }
 template <class C> __device__ __forceinline__ C cadd(C a, C b) { return mk(a.x + b.x, a.y + b.y); }
 template <class C> __device__ __forceinline__ C csub(C a, C b) { return mk(a.x - b.x, a.y - b.y); }
 template <class C> __device__ __forceinline__ C cmul(C a, C b) {
@@ -42,6 +93,14 @@ template <class C> struct Twiddle {
   int log2_tw;
   // exp(-2 pi i j / 2^logB) for 0 <= j < 2^logB
   __device__ __forceinline__ C root(int64_t j, int logB) const { return __ldg(&tw[j << (log2_tw - logB)]); }
+};
+template <> struct Twiddle<dfc> {
+  const float4* tw;  // {re.hi, re.lo, im.hi, im.lo}
+  int log2_tw;
+  __device__ __forceinline__ dfc root(int64_t j, int logB) const {
+    const float4 t = __ldg(&tw[j << (log2_tw - logB)]);
+    return dfc{df(t.x, t.y), df(t.z, t.w)};
+  }
 };
 
 // ------------------------------------------------------------------ reductions

@@ -11,7 +11,7 @@ namespace mfipm {
 // Parameters of the IPM as the kernels read them (copied from mfipm_params).
 struct SolveParams {
   double tol, tol_pcg, sigma1, sigma2, sigma3, alpha_bar, alpha_tilde, eta;
-  int32_t max_iter, max_iter_pcg, equal_steps, pad;
+  int32_t max_iter, max_iter_pcg, equal_steps, resid_fp64;
 };
 
 // One problem of a launch.  Vectors of length n live in the caller's workspace, in the
@@ -29,6 +29,7 @@ struct ProbDesc {
   const int64_t* rows;    // DEVICE m
   uint8_t* mask;          // DEVICE n: 1 where the DCT row is sampled
   double* bsu;            // DEVICE n: b scattered to its rows, divided by the row's DCT scale
+  float2* bsu_df;         // DEVICE n: bsu as double-float (hi, lo)
   // dense
   const void* A;
   int32_t a_dtype;
@@ -49,13 +50,14 @@ struct KernelArgs {
   int* err;               // DEVICE error word (first failing problem's status)
   const double2* tw64;    // exp(-2 pi i j / 2^log2_tw)
   const float2* tw32;
+  const float4* twdf;     // the same roots as double-float {re.hi, re.lo, im.hi, im.lo}
   int32_t log2_tw;
   int32_t pad2;
   SolveParams prm;
 };
 
 // Launchers implemented in solver.cu.  Return cudaError_t of the launch.
-cudaError_t launch_twiddles(double2* tw64, float2* tw32, int log2_tw, cudaStream_t st);
+cudaError_t launch_twiddles(double2* tw64, float2* tw32, float4* twdf, int log2_tw, cudaStream_t st);
 cudaError_t launch_dct_setup(const ProbDesc* probs_dev, int batch, int64_t max_n, int* err, cudaStream_t st);
 cudaError_t launch_dct_solver(int G, const KernelArgs& a, int64_t max_n, int grid_clusters, cudaStream_t st);
 cudaError_t launch_dense_solver(int G, bool fp64_pcg, const KernelArgs& a, int64_t max_n, int64_t max_m,

@@ -4,7 +4,7 @@
 namespace mfipm {
 
 // ------------------------------------------------------------------ setup kernels
-__global__ void twiddle_kernel(double2* tw64, float2* tw32, int log2_tw) {
+__global__ void twiddle_kernel(double2* tw64, float2* tw32, float4* twdf, int log2_tw) {
   const int64_t T = (int64_t)1 << log2_tw;
   for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < T; j += (int64_t)gridDim.x * blockDim.x) {
     double s, c;
@@ -12,6 +12,8 @@ __global__ void twiddle_kernel(double2* tw64, float2* tw32, int log2_tw) {
     sincospi(2.0 * (double)j / (double)T, &s, &c);
     tw64[j] = make_double2(c, -s);
     tw32[j] = make_float2((float)c, (float)-s);
+    const df re = to_df(c), im = to_df(-s);
+    twdf[j] = make_float4(re.hi, re.lo, im.hi, im.lo);
   }
 }
 
@@ -22,6 +24,7 @@ __global__ void dct_setup_kernel(const ProbDesc* probs, int batch, int* err) {
   for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
     pd.mask[j] = 0;
     pd.bsu[j] = 0.0;
+    pd.bsu_df[j] = make_float2(0.f, 0.f);
   }
 }
 __global__ void dct_scatter_kernel(const ProbDesc* probs, int batch, int* err) {
@@ -38,7 +41,10 @@ __global__ void dct_scatter_kernel(const ProbDesc* probs, int batch, int* err) {
     const double bi = pd.b[i];
     if (!isfinite(bi)) atomicCAS(err, 0, -2);
     pd.mask[r] = 1;
-    pd.bsu[r] = bi * (r == 0 ? sc0 : scj);
+    const double v = bi * (r == 0 ? sc0 : scj);
+    pd.bsu[r] = v;
+    const df vd = to_df(v);
+    pd.bsu_df[r] = make_float2(vd.hi, vd.lo);
   }
 }
 
@@ -53,10 +59,10 @@ size_t dense_smem_bytes(int G, bool, int64_t max_n, int64_t max_m) {
   return 2 * c8 + 2 * (size_t)((max_m + 31) & ~31) * 8;
 }
 
-cudaError_t launch_twiddles(double2* tw64, float2* tw32, int log2_tw, cudaStream_t st) {
+cudaError_t launch_twiddles(double2* tw64, float2* tw32, float4* twdf, int log2_tw, cudaStream_t st) {
   const int64_t T = (int64_t)1 << log2_tw;
   const int blocks = (int)((T + 255) / 256 < 1024 ? (T + 255) / 256 : 1024);
-  twiddle_kernel<<<blocks, 256, 0, st>>>(tw64, tw32, log2_tw);
+  twiddle_kernel<<<blocks, 256, 0, st>>>(tw64, tw32, twdf, log2_tw);
   return cudaGetLastError();
 }
 

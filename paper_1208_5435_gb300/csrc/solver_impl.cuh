@@ -72,23 +72,44 @@ struct DctGeom {
   int logN, logL, logM, rank;
   int64_t N;
   const uint8_t* mask;
-  const double* bsu;
+  const double* bsu;      // b scattered to its rows / DCT scale (float64)
+  const float2* bsu_df;   // the same as double-float (hi, lo)
 };
+
+// Constants of the pointwise step in the chain's arithmetic, built once per exchange step.
+template <class R> __device__ __forceinline__ R cst(double v);
+template <> __device__ __forceinline__ float cst<float>(double v) { return (float)v; }
+template <> __device__ __forceinline__ double cst<double>(double v) { return v; }
+template <> __device__ __forceinline__ df cst<df>(double v) { return to_df(v); }
+template <class R> struct PwConst {
+  R half, invL, a2_0, a2_j, rs2, zero;
+  __device__ explicit PwConst(const DctGeom& geo)
+      : half(cst<R>(0.5)),
+        invL(cst<R>(1.0 / (double)((int64_t)1 << geo.logL))),
+        a2_0(cst<R>(1.0 / (double)geo.N)),
+        a2_j(cst<R>(2.0 / (double)geo.N)),
+        rs2(cst<R>(0.70710678118654752440)),
+        zero(cst<R>(0.0)) {}
+};
+__device__ __forceinline__ float load_bsu(const DctGeom&, int64_t, float) { return 0.f; }
+__device__ __forceinline__ double load_bsu(const DctGeom& g, int64_t i, double) { return g.bsu[i]; }
+__device__ __forceinline__ df load_bsu(const DctGeom& g, int64_t i, df) {
+  const float2 v = g.bsu_df[i];
+  return df(v.x, v.y);
+}
 
 // Real-DCT untangling, row mask (minus b_u) and its exact inverse for one frequency k of
 // the length-L FFT, given a = H[k] and b = H[L-k].  Returns the value H'[k] that the
 // inverse chain needs; accumulates this index's share of the masked energy into acc and,
 // in MODE_FORWARD, writes alpha_j X_j instead.  Each DCT coefficient j is counted by
 // exactly one k: j in {k, N-k (k>0)} and, for k = 0, also j = L.
-template <class C, int MODE>
+template <class C, int MODE, class R = decltype(C().x)>
 __device__ __forceinline__ C dct_pointwise(int64_t k, C a, C b, const DctGeom& geo, const Twiddle<C>& tw,
-                                           bool valid, double& acc, double* fwd_out) {
-  using R = decltype(C().x);
+                                           const PwConst<R>& pc, bool valid, R& acc, double* fwd_out) {
   const int64_t L = (int64_t)1 << geo.logL, N = geo.N;
-  const R rs2 = (R)0.70710678118654752440;
-  const C c45 = mk(rs2, -rs2);  // exp(-i pi/4)
-  const C E = cscale(cadd(a, cconj(b)), (R)0.5);
-  const C O = cscale(cmul_mi(csub(a, cconj(b))), (R)0.5);
+  const C c45 = mk(pc.rs2, -pc.rs2);  // exp(-i pi/4)
+  const C E = cscale(cadd(a, cconj(b)), pc.half);
+  const C O = cscale(cmul_mi(csub(a, cconj(b))), pc.half);
   const C wN = tw.root(k, geo.logN);       // exp(-2 pi i k / N)
   const C eps = tw.root(k, geo.logN + 2);  // exp(-i pi k / (2N))
   const C wO = cmul(wN, O);
@@ -99,37 +120,36 @@ __device__ __forceinline__ C dct_pointwise(int64_t k, C a, C b, const DctGeom& g
   if constexpr (MODE == MODE_FORWARD) {
     if (valid) {
       const double sj = sqrt(2.0 / (double)N);
-      fwd_out[i1] = (i1 == 0 ? sqrt(1.0 / (double)N) : sj) * (double)X1;
-      if (k > 0) fwd_out[i2] = sj * (double)X2;
-      if (k == 0) fwd_out[i3] = sj * (double)X3;
+      fwd_out[i1] = (i1 == 0 ? sqrt(1.0 / (double)N) : sj) * to_double(X1);
+      if (k > 0) fwd_out[i2] = sj * to_double(X2);
+      if (k == 0) fwd_out[i3] = sj * to_double(X3);
     }
     return a;
   } else {
-    const R a2_0 = (R)(1.0 / (double)N), a2_j = (R)(2.0 / (double)N);
     const bool m1 = geo.mask[i1], m2 = (k > 0) && geo.mask[i2], m3 = geo.mask[i3], m4 = geo.mask[i4];
     if constexpr (MODE == MODE_RESID) {
-      X1 = m1 ? X1 - (R)geo.bsu[i1] : (R)0;
-      X2 = m2 ? X2 - (R)geo.bsu[i2] : (R)0;
-      X3 = m3 ? X3 - (R)geo.bsu[i3] : (R)0;
-      X4 = m4 ? X4 - (R)geo.bsu[i4] : (R)0;
+      X1 = m1 ? X1 - load_bsu(geo, i1, R()) : pc.zero;
+      X2 = m2 ? X2 - load_bsu(geo, i2, R()) : pc.zero;
+      X3 = m3 ? X3 - load_bsu(geo, i3, R()) : pc.zero;
+      X4 = m4 ? X4 - load_bsu(geo, i4, R()) : pc.zero;
     } else {
-      X1 = m1 ? X1 : (R)0;
-      X2 = m2 ? X2 : (R)0;
-      X3 = m3 ? X3 : (R)0;
-      X4 = m4 ? X4 : (R)0;
+      X1 = m1 ? X1 : pc.zero;
+      X2 = m2 ? X2 : pc.zero;
+      X3 = m3 ? X3 : pc.zero;
+      X4 = m4 ? X4 : pc.zero;
     }
     if (valid) {
-      R t = (i1 == 0 ? a2_0 : a2_j) * X1 * X1;
-      if (k > 0) t += a2_j * X2 * X2;
-      if (k == 0) t += a2_j * X3 * X3;
-      acc += (double)t;
+      R t = (i1 == 0 ? pc.a2_0 : pc.a2_j) * X1 * X1;
+      if (k > 0) t += pc.a2_j * X2 * X2;
+      if (k == 0) t += pc.a2_j * X3 * X3;
+      acc += t;
     }
     const C Vk = cmulc(mk(X1, -X2), eps);                     // conj(eps^k) W'[k]
     const C Vlk = cmul(cconj(c45), cmul(eps, mk(X3, -X4)));    // conj(eps^(L-k)) W'[L-k]
     const C cVlk = cconj(Vlk);
-    const C Ep = cscale(cadd(Vk, cVlk), (R)0.5);
-    const C Op = cscale(cmulc(csub(Vk, cVlk), wN), (R)0.5);
-    return cscale(cadd(Ep, cmul_i(Op)), (R)1 / (R)L);
+    const C Ep = cscale(cadd(Vk, cVlk), pc.half);
+    const C Op = cscale(cmulc(csub(Vk, cVlk), wN), pc.half);
+    return cscale(cadd(Ep, cmul_i(Op)), pc.invL);
   }
 }
 
@@ -141,7 +161,9 @@ __device__ __noinline__ double dct_slot_step(C* buf, const DctGeom& geo, const T
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int M = 1 << geo.logM;
   const int spc = (M >> 1) / G;  // slots per CTA (>= 1 by the host's choice of G)
-  double acc = 0.0;
+  using R = decltype(C().x);
+  const PwConst<R> pc(geo);
+  R acc = pc.zero;
   cg::cluster_group cl = cg::this_cluster();
   for (int base = warp * 16; base < spc; base += kWarps * 16) {
     const int sl = base + (lane & 15);
@@ -171,7 +193,7 @@ __device__ __noinline__ double dct_slot_step(C* buf, const DctGeom& geo, const T
       for (int k1 = 0; k1 < G; ++k1) T[k1] = Z[k1];
 #pragma unroll
       for (int k1 = 0; k1 < G; ++k1)
-        Z[k1] = dct_pointwise<C, MODE>((int64_t)M * k1, T[k1], T[(G - k1) % G], geo, tw, valid, acc, fwd_out);
+        Z[k1] = dct_pointwise<C, MODE>((int64_t)M * k1, T[k1], T[(G - k1) % G], geo, tw, pc, valid, acc, fwd_out);
     }
     // other columns: H[k2 + M k1] pairs with H[(M - k2) + M (G-1-k1)], held by lane^16
     // (column M/2 pairs with itself the same way); update k1 and G-1-k1 together so
@@ -180,18 +202,18 @@ __device__ __noinline__ double dct_slot_step(C* buf, const DctGeom& geo, const T
     for (int j = 0; j < (G + 1) / 2; ++j) {
       const int kA = j, kB = G - 1 - j;
       C bA, bB;
-      bA.x = __shfl_xor_sync(0xffffffffu, Z[kB].x, 16);
-      bA.y = __shfl_xor_sync(0xffffffffu, Z[kB].y, 16);
-      bB.x = __shfl_xor_sync(0xffffffffu, Z[kA].x, 16);
-      bB.y = __shfl_xor_sync(0xffffffffu, Z[kA].y, 16);
+      bA.x = shfl_xor(Z[kB].x, 16);
+      bA.y = shfl_xor(Z[kB].y, 16);
+      bB.x = shfl_xor(Z[kA].x, 16);
+      bB.y = shfl_xor(Z[kA].y, 16);
       if (selfh) {
         bA = Z[kB];
         bB = Z[kA];
       }
       if (!self0) {
-        const C nA = dct_pointwise<C, MODE>((int64_t)k2 + (int64_t)M * kA, Z[kA], bA, geo, tw, valid, acc, fwd_out);
+        const C nA = dct_pointwise<C, MODE>((int64_t)k2 + (int64_t)M * kA, Z[kA], bA, geo, tw, pc, valid, acc, fwd_out);
         if (kB != kA) {
-          const C nB = dct_pointwise<C, MODE>((int64_t)k2 + (int64_t)M * kB, Z[kB], bB, geo, tw, valid, acc, fwd_out);
+          const C nB = dct_pointwise<C, MODE>((int64_t)k2 + (int64_t)M * kB, Z[kB], bB, geo, tw, pc, valid, acc, fwd_out);
           Z[kB] = nB;
         }
         Z[kA] = nA;
@@ -212,7 +234,7 @@ __device__ __noinline__ double dct_slot_step(C* buf, const DctGeom& geo, const T
       }
     }
   }
-  return acc;
+  return to_double(acc);
 }
 
 // buf (this CTA's chunk, storage order, as complex pairs) := D^-1 M (D buf - b_u) or
@@ -244,9 +266,11 @@ template <int G> struct DctOp {
   float2* buf32;
   Twiddle<double2> tw64;
   Twiddle<float2> tw32;
+  Twiddle<dfc> twdf;
   int64_t chunk, gbase;
   double rho;
   int rank;
+  int resid_fp64;
 
   __device__ void init(const ProbDesc& pd, const KernelArgs& a, unsigned char* smem, int rank_) {
     rank = rank_;
@@ -257,11 +281,14 @@ template <int G> struct DctOp {
     geo.rank = rank_;
     geo.mask = pd.mask;
     geo.bsu = pd.bsu;
+    geo.bsu_df = pd.bsu_df;
+    resid_fp64 = a.prm.resid_fp64;
     const int64_t M = (int64_t)1 << geo.logM;
     buf64 = reinterpret_cast<double2*>(smem);
     buf32 = reinterpret_cast<float2*>(smem + (size_t)16 * M);
     tw64 = Twiddle<double2>{a.tw64, a.log2_tw};
     tw32 = Twiddle<float2>{a.tw32, a.log2_tw};
+    twdf = Twiddle<dfc>{a.twdf, a.log2_tw};
     chunk = 2 * M;
     gbase = (int64_t)rank_ * chunk;
     rho = (double)pd.m / (double)pd.n;  // A A^T = I: rho = m/n (Eq. eq:ne2_P)
@@ -269,8 +296,26 @@ template <int G> struct DctOp {
   __device__ __forceinline__ bool valid(int64_t) const { return true; }
   __device__ __forceinline__ double* r64() const { return reinterpret_cast<double*>(buf64); }
   template <class PS> __device__ __forceinline__ PS* wbuf() const { return reinterpret_cast<PS*>(buf32); }
-  // r64() := A^T (A r64() - b); returns share of ||A x - b||^2
-  __device__ double resid() { return dct_chain<G, double2, MODE_RESID>(buf64, geo, tw64); }
+  // r64() := A^T (A r64() - b); returns share of ||A x - b||^2.  Evaluated in double-float
+  // (float32 pipes, ~48-bit significand) unless the float64 residual is selected; the
+  // buffer is converted in place (a double2 and a double-float complex are both 16 bytes).
+  __device__ double resid() {
+    if (resid_fp64) return dct_chain<G, double2, MODE_RESID>(buf64, geo, tw64);
+    dfc* bd = reinterpret_cast<dfc*>(buf64);
+    const int64_t M = chunk >> 1;
+    for (int64_t i = threadIdx.x; i < M; i += kThreads) {
+      const double2 v = buf64[i];
+      bd[i] = dfc{to_df(v.x), to_df(v.y)};
+    }
+    __syncthreads();
+    const double acc = dct_chain<G, dfc, MODE_RESID>(bd, geo, twdf);
+    for (int64_t i = threadIdx.x; i < M; i += kThreads) {
+      const dfc v = bd[i];
+      buf64[i] = make_double2(to_double(v.x), to_double(v.y));
+    }
+    __syncthreads();
+    return acc;
+  }
   // r32() := A^T A r32(); returns share of ||A w||^2
   template <class PS> __device__ double normal(PS*) { return dct_chain<G, float2, MODE_NORMAL>(buf32, geo, tw32); }
   __device__ int64_t natural(int64_t q) const { return dct_natural_index(gbase + q, geo.logM, G); }
@@ -373,29 +418,49 @@ template <int G> struct DenseOp {
 };
 
 // ------------------------------------------------------------------ the IPM driver
+// Precision split of the per-index work.  Kept in float64: the iterate (z, s) and its
+// update, x = u - v, the residual A^T(Ax - b) and the dual-residual terms tau +/- g built
+// from it, and the scalar reductions across the cluster.  Computed in the PCG precision H
+// (float32 for the partial DCT): quantities that only steer the iteration or feed the
+// float32 PCG -- Theta^-1 = s/z, sigma*mu/z, the direction components and the
+// step-to-boundary ratios.  Both uses of a direction (ratio test and update) evaluate it
+// through the same function from the same inputs, so the fraction-to-boundary rule keeps
+// z, s > 0.
 struct IpmScalars {
   double mu, sigma, alpha_p, alpha_d;       // predictor
   double mu_t, alpha_p1, alpha_d1;          // corrector trial point
   bool corr;
 };
 
-// dz and ds of one index from the PCG solution(s) (Eq. redNewtonB):
+template <class H> struct ScH {
+  H smu, ap1, ad1, s3mut;
+  bool corr;
+  __device__ explicit ScH(const IpmScalars& sc, double sigma3)
+      : smu((H)(sc.sigma * sc.mu)), ap1((H)sc.alpha_p1), ad1((H)sc.alpha_d1), s3mut((H)(sigma3 * sc.mu_t)),
+        corr(sc.corr) {}
+};
+
+__device__ __forceinline__ float rcpH(float z) { return __frcp_rn(z); }
+__device__ __forceinline__ double rcpH(double z) { return rcp64(z); }
+
+template <class H> struct Dir {
+  H dz, ds;
+};
+// dz and ds of one index (Eq. redNewtonB):
 //   predictor ds1 = Z^-1 f_s - Theta^-1 dz1 = sigma mu / z - s - (s / z) dz1
 //   corrector ds2 = Z^-1 f_s~ - Theta^-1 dz2, f_s~ = sigma3 mu~ - z~ s~ at the trial point
-//             z~ = z + alpha_p1 dz1, s~ = s + alpha_d1 ds1 (reading: Theta, Z of the current point)
-struct Dir {
-  double dz, ds;
-};
-__device__ __forceinline__ Dir direction(double z, double s, double rz, double dz1, double dz2,
-                                         const IpmScalars& sc, double sigma3) {
-  const double d = s * rz;
-  const double ds1 = fma(sc.sigma * sc.mu, rz, -s) - d * dz1;
-  Dir r{dz1, ds1};
-  if (sc.corr) {
-    const double zt = fma(sc.alpha_p1, dz1, z);
-    const double st = fma(sc.alpha_d1, ds1, s);
-    const double fst = fma(-zt, st, sigma3 * sc.mu_t);
-    const double ds2 = fst * rz - d * dz2;
+//             z~ = z + alpha_p1 dz1, s~ = s + alpha_d1 ds1 (reading: Theta and Z of the current
+//             point); the combined direction is (dz1 + dz2, ds1 + ds2)
+template <class H>
+__device__ __forceinline__ Dir<H> direction(H z, H s, H dz1, H dz2, const ScH<H>& c) {
+  const H rz = rcpH(z);
+  const H d = s * rz;
+  const H ds1 = (c.smu * rz - s) - d * dz1;
+  Dir<H> r{dz1, ds1};
+  if (c.corr) {
+    const H zt = z + c.ap1 * dz1;
+    const H st = s + c.ad1 * ds1;
+    const H ds2 = (c.s3mut - zt * st) * rz - d * dz2;
     r.dz = dz1 + dz2;
     r.ds = ds1 + ds2;
   }
@@ -405,6 +470,7 @@ __device__ __forceinline__ Dir direction(double z, double s, double rz, double d
 template <int G, class Op, class PS>
 __device__ void solve_one(const ProbDesc& pd, const KernelArgs& a, Op& op, RedSmem& rs, int& par) {
   using P2 = typename V2<PS>::T;
+  using H = PS;
   const SolveParams& prm = a.prm;
   const int tid = threadIdx.x;
   const int64_t n = pd.n;
@@ -445,39 +511,37 @@ __device__ void solve_one(const ProbDesc& pd, const KernelArgs& a, Op& op, RedSm
   double rel_gap = INFINITY, P_obj = 0.0;
   int it = 0;
   int pcg_total = 0;
+  PS* w = op.template wbuf<PS>();
 
   // PCG on (Theta^-1 + F F^T) dz = rhs (Sec. 4).  On entry r = rhs and p = P^-1 r are
-  // stored, the operator input w = p_u - p_v is in the shared buffer, and rz, pdp are this
-  // thread's partials of r.P^-1 r and p.(Theta^-1 p).  Result in Xo (float or double pairs).
-  auto pcg = [&](P2* Xo, double rz_part, double pdp_part) {
+  // stored, the operator input w = p_u - p_v is in the shared buffer, and rz_part, pdp_part
+  // are this thread's shares of r.P^-1 r and p.(Theta^-1 p).  Stops when
+  // sqrt(r.P^-1 r) <= tol_pcg * its initial value or after max_iter_pcg iterations.
+  auto pcg = [&](P2* Xo, PS rz_part, PS pdp_part) {
     double rz0 = 0.0, rz = 0.0;
     int k = 0;
-    PS* w = op.template wbuf<PS>();
-    double pdp_acc = pdp_part;
+    PS pdp_acc = pdp_part;
     for (;;) {
       const double aw2 = op.normal(w);
-      ++nmat;
-      ++nmat;
+      nmat += 2;
       double tot[2];
       {
-        double v[2] = {pdp_acc + aw2, k == 0 ? rz_part : 0.0};
+        PS v[2] = {pdp_acc + (PS)aw2, k == 0 ? rz_part : (PS)0};
         cluster_sum<G, 2>(rs, par, v, tot);
       }
       if (k == 0) {
         rz0 = rz = tot[1];
         if (!(rz0 > 0.0) || !isfinite(rz0)) {  // zero right-hand side: dz = 0
-          for (int64_t q = tid; q < chunk; q += kThreads) {
-            P2 zero;
-            zero.x = (PS)0;
-            zero.y = (PS)0;
+          P2 zero;
+          zero.x = (PS)0;
+          zero.y = (PS)0;
+          for (int64_t q = tid; q < chunk; q += kThreads)
             if (op.valid(q)) Xo[gb + q] = zero;
-          }
           break;
         }
       }
-      const double pq = tot[0];
-      const PS alpha = (PS)(rz / pq);
-      double rzn_part = 0.0;
+      const PS alpha = (PS)(rz / tot[0]);
+      PS rzn_part = 0;
       for (int64_t q = tid; q < chunk; q += kThreads) {
         if (!op.valid(q)) continue;
         const int64_t gi = gb + q;
@@ -492,21 +556,22 @@ __device__ void solve_one(const ProbDesc& pd, const KernelArgs& a, Op& op, RedSm
         r.x -= alpha * qu;
         r.y -= alpha * qv;
         const P2 zz = precond<PS>(d, r, rho);
-        rzn_part += (double)(r.x * zz.x + r.y * zz.y);
+        rzn_part += r.x * zz.x + r.y * zz.y;
         Xo[gi] = x;
         Rv[gi] = r;
       }
       ++k;
       double rzn;
       {
-        double v[1] = {rzn_part}, out[1];
+        PS v[1] = {rzn_part};
+        double out[1];
         cluster_sum<G, 1>(rs, par, v, out);
         rzn = out[0];
       }
       if (!(rzn > prm.tol_pcg * prm.tol_pcg * rz0) || k >= prm.max_iter_pcg || !isfinite(rzn)) break;
       const PS beta = (PS)(rzn / rz);
       rz = rzn;
-      double pdp = 0.0;
+      PS pdp = 0;
       for (int64_t q = tid; q < chunk; q += kThreads) {
         if (!op.valid(q)) { w[q] = (PS)0; continue; }
         const int64_t gi = gb + q;
@@ -517,7 +582,7 @@ __device__ void solve_one(const ProbDesc& pd, const KernelArgs& a, Op& op, RedSm
         p.y = zz.y + beta * p.y;
         Pv[gi] = p;
         w[q] = p.x - p.y;
-        pdp += (double)(d.x * p.x * p.x + d.y * p.y * p.y);
+        pdp += d.x * p.x * p.x + d.y * p.y * p.y;
       }
       __syncthreads();
       pdp_acc = pdp;
@@ -525,61 +590,60 @@ __device__ void solve_one(const ProbDesc& pd, const KernelArgs& a, Op& op, RedSm
     pcg_total += k;
   };
 
-  // PCG initialisation from a float64 right-hand side (rhs_fn(q) -> double2)
-  auto pcg_init = [&](auto rhs_fn, bool write_d, double& rz_part, double& pdp_part) {
-    PS* w = op.template wbuf<PS>();
-    rz_part = 0.0;
-    pdp_part = 0.0;
+  // PCG initialisation: r = rhs (from rhs_fn(q, z, s) in precision H), p = P^-1 r, w = p_u - p_v.
+  // Writes Theta^-1 = s/z when write_d.
+  auto pcg_init = [&](auto rhs_fn, bool write_d, PS& rz_part, PS& pdp_part) {
+    rz_part = 0;
+    pdp_part = 0;
     for (int64_t q = tid; q < chunk; q += kThreads) {
       if (!op.valid(q)) { w[q] = (PS)0; continue; }
       const int64_t gi = gb + q;
+      const double2 z = zs[2 * gi], s = zs[2 * gi + 1];
       P2 d;
-      double2 rhs;
       if (write_d) {
-        const double2 z = zs[2 * gi], s = zs[2 * gi + 1];
-        const double ru = rcp64(z.x), rv = rcp64(z.y);
-        d.x = (PS)(s.x * ru);
-        d.y = (PS)(s.y * rv);
+        d.x = (H)s.x * rcpH((H)z.x);
+        d.y = (H)s.y * rcpH((H)z.y);
         Dv[gi] = d;
-        rhs = rhs_fn(q, z, s, ru, rv);
       } else {
         d = Dv[gi];
-        const double2 z = zs[2 * gi], s = zs[2 * gi + 1];
-        rhs = rhs_fn(q, z, s, rcp64(z.x), rcp64(z.y));
       }
-      P2 r;
-      r.x = (PS)rhs.x;
-      r.y = (PS)rhs.y;
+      const P2 r = rhs_fn(q, gi, z, s);
       const P2 p = precond<PS>(d, r, rho);
       Rv[gi] = r;
       Pv[gi] = p;
       w[q] = p.x - p.y;
-      rz_part += (double)(r.x * p.x + r.y * p.y);
-      pdp_part += (double)(d.x * p.x * p.x + d.y * p.y * p.y);
+      rz_part += r.x * p.x + r.y * p.y;
+      pdp_part += d.x * p.x * p.x + d.y * p.y * p.y;
     }
     __syncthreads();
   };
 
+  auto load_dir = [&](int64_t gi, const double2& z, const double2& s, const ScH<H>& c, Dir<H>& du, Dir<H>& dv) {
+    const P2 x1 = X1[gi];
+    P2 x2;
+    x2.x = (PS)0;
+    x2.y = (PS)0;
+    if (c.corr) x2 = X2[gi];
+    du = direction<H>((H)z.x, (H)s.x, x1.x, x2.x, c);
+    dv = direction<H>((H)z.y, (H)s.y, x1.y, x2.y, c);
+  };
+
   // step lengths alpha = min(1, eta * min_{dv<0} -v/dv) for z and s (reading R4)
   auto step_lengths = [&](double& ap, double& ad) {
-    double mp = INFINITY, md = INFINITY;
+    const ScH<H> c(sc, prm.sigma3);
+    H mp = (H)INFINITY, md = (H)INFINITY;
     for (int64_t q = tid; q < chunk; q += kThreads) {
       if (!op.valid(q)) continue;
       const int64_t gi = gb + q;
       const double2 z = zs[2 * gi], s = zs[2 * gi + 1];
-      const P2 x1 = X1[gi];
-      P2 x2;
-      x2.x = (PS)0;
-      x2.y = (PS)0;
-      if (sc.corr) x2 = X2[gi];
-      const Dir du = direction(z.x, s.x, rcp64(z.x), (double)x1.x, (double)x2.x, sc, prm.sigma3);
-      const Dir dv = direction(z.y, s.y, rcp64(z.y), (double)x1.y, (double)x2.y, sc, prm.sigma3);
-      if (du.dz < 0.0) mp = fmin(mp, z.x * rcp64(-du.dz));
-      if (dv.dz < 0.0) mp = fmin(mp, z.y * rcp64(-dv.dz));
-      if (du.ds < 0.0) md = fmin(md, s.x * rcp64(-du.ds));
-      if (dv.ds < 0.0) md = fmin(md, s.y * rcp64(-dv.ds));
+      Dir<H> du, dv;
+      load_dir(gi, z, s, c, du, dv);
+      if (du.dz < (H)0) mp = fmin(mp, (H)z.x * rcpH(-du.dz));
+      if (dv.dz < (H)0) mp = fmin(mp, (H)z.y * rcpH(-dv.dz));
+      if (du.ds < (H)0) md = fmin(md, (H)s.x * rcpH(-du.ds));
+      if (dv.ds < (H)0) md = fmin(md, (H)s.y * rcpH(-dv.ds));
     }
-    double v[2] = {mp, md}, out[2];
+    double v[2] = {(double)mp, (double)md}, out[2];
     cluster_min<G, 2>(rs, par, v, out);
     ap = fmin(1.0, prm.eta * out[0]);
     ad = fmin(1.0, prm.eta * out[1]);
@@ -588,41 +652,46 @@ __device__ void solve_one(const ProbDesc& pd, const KernelArgs& a, Op& op, RedSm
 
   for (it = 1;; ++it) {
     // ---- update (previous direction) fused with x = u - v for the residual
-    double part[3] = {0.0, 0.0, 0.0};  // z.s, 1^T z, ||x||^2
-    for (int64_t q = tid; q < chunk; q += kThreads) {
-      if (!op.valid(q)) { g64[q] = 0.0; continue; }
-      const int64_t gi = gb + q;
-      double2 z, s;
-      if (it == 1) {
-        z = make_double2(1.0, 1.0);  // reading R3: z0 = s0 = 1
-        s = z;
-      } else {
-        z = zs[2 * gi];
-        s = zs[2 * gi + 1];
-        const P2 x1 = X1[gi];
-        P2 x2;
-        x2.x = (PS)0;
-        x2.y = (PS)0;
-        if (sc.corr) x2 = X2[gi];
-        const Dir du = direction(z.x, s.x, rcp64(z.x), (double)x1.x, (double)x2.x, sc, prm.sigma3);
-        const Dir dv = direction(z.y, s.y, rcp64(z.y), (double)x1.y, (double)x2.y, sc, prm.sigma3);
-        double nu = fma(sc.alpha_p, du.dz, z.x), nv = fma(sc.alpha_p, dv.dz, z.y);
-        double nsu = fma(sc.alpha_d, du.ds, s.x), nsv = fma(sc.alpha_d, dv.ds, s.y);
-        // the step keeps z, s > 0 by construction; guard against a rounding-level crossing
-        if (!(nu > 0.0)) nu = z.x * (1.0 - prm.eta);
-        if (!(nv > 0.0)) nv = z.y * (1.0 - prm.eta);
-        if (!(nsu > 0.0)) nsu = s.x * (1.0 - prm.eta);
-        if (!(nsv > 0.0)) nsv = s.y * (1.0 - prm.eta);
-        z = make_double2(nu, nv);
-        s = make_double2(nsu, nsv);
+    H part[3] = {0, 0, 0};  // z.s, 1^T z, ||x||^2
+    {
+      const ScH<H> c(sc, prm.sigma3);
+      const H apH = (H)sc.alpha_p, adH = (H)sc.alpha_d;
+      for (int64_t q = tid; q < chunk; q += kThreads) {
+        if (!op.valid(q)) { g64[q] = 0.0; continue; }
+        const int64_t gi = gb + q;
+        double2 z, s;
+        H zu, zv, su, sv;
+        if (it == 1) {
+          z = make_double2(1.0, 1.0);  // reading R3: z0 = s0 = 1
+          s = z;
+          zu = zv = su = sv = (H)1;
+        } else {
+          z = zs[2 * gi];
+          s = zs[2 * gi + 1];
+          Dir<H> du, dv;
+          load_dir(gi, z, s, c, du, dv);
+          double nu = fma(sc.alpha_p, (double)du.dz, z.x), nv = fma(sc.alpha_p, (double)dv.dz, z.y);
+          double nsu = fma(sc.alpha_d, (double)du.ds, s.x), nsv = fma(sc.alpha_d, (double)dv.ds, s.y);
+          // the step keeps z, s > 0 by construction; guard against a rounding-level crossing
+          if (!(nu > 0.0)) nu = z.x * (1.0 - prm.eta);
+          if (!(nv > 0.0)) nv = z.y * (1.0 - prm.eta);
+          if (!(nsu > 0.0)) nsu = s.x * (1.0 - prm.eta);
+          if (!(nsv > 0.0)) nsv = s.y * (1.0 - prm.eta);
+          zu = (H)z.x + apH * du.dz;
+          zv = (H)z.y + apH * dv.dz;
+          su = (H)s.x + adH * du.ds;
+          sv = (H)s.y + adH * dv.ds;
+          z = make_double2(nu, nv);
+          s = make_double2(nsu, nsv);
+        }
+        zs[2 * gi] = z;
+        zs[2 * gi + 1] = s;
+        g64[q] = z.x - z.y;
+        const H xh = zu - zv;
+        part[0] += zu * su + zv * sv;
+        part[1] += zu + zv;
+        part[2] += xh * xh;
       }
-      zs[2 * gi] = z;
-      zs[2 * gi + 1] = s;
-      const double x = z.x - z.y;
-      g64[q] = x;
-      part[0] += z.x * s.x + z.y * s.y;
-      part[1] += z.x + z.y;
-      part[2] += x * x;
     }
     __syncthreads();
     // ---- float64 residual g = A^T (A x - b)  (f_z of Eq. fzfs needs F F^T z + c)
@@ -630,7 +699,7 @@ __device__ void solve_one(const ProbDesc& pd, const KernelArgs& a, Op& op, RedSm
     nmat += 2;
     double tot[4];
     {
-      double v[4] = {part[0], part[1], part[2], res2};
+      double v[4] = {(double)part[0], (double)part[1], (double)part[2], res2};
       cluster_sum<G, 4>(rs, par, v, tot);
     }
     const double zts = tot[0];
@@ -643,13 +712,18 @@ __device__ void solve_one(const ProbDesc& pd, const KernelArgs& a, Op& op, RedSm
     // ---- predictor (Algorithm: sigma choice, then PCG)
     sc.sigma = (it != 1 && (prev_ap <= prm.alpha_bar || prev_ad <= prm.alpha_bar)) ? prm.sigma2 : prm.sigma1;
     sc.corr = false;
-    const double smu = sc.sigma * sc.mu;
-    double rzp, pdpp;
-    // rhs = f_z + Z^-1 f_s = sigma mu / z - (c + F F^T z) = sigma mu/z - [tau + g; tau - g]
-    pcg_init([&](int64_t q, double2, double2, double ru, double rv) {
-               const double g = g64[q];
-               return make_double2(fma(smu, ru, -(tau + g)), fma(smu, rv, -(tau - g)));
-             }, true, rzp, pdpp);
+    PS rzp, pdpp;
+    {
+      const H smuH = (H)(sc.sigma * sc.mu);
+      // rhs = f_z + Z^-1 f_s = sigma mu / z - (c + F F^T z) = sigma mu / z - [tau + g; tau - g]
+      pcg_init([&](int64_t q, int64_t, const double2& z, const double2&) {
+                 const double g = g64[q];
+                 P2 r;
+                 r.x = smuH * rcpH((H)z.x) - (H)(tau + g);
+                 r.y = smuH * rcpH((H)z.y) - (H)(tau - g);
+                 return r;
+               }, true, rzp, pdpp);
+    }
     pcg(X1, rzp, pdpp);
     step_lengths(sc.alpha_p, sc.alpha_d);
     // ---- corrector (reading R6)
@@ -657,40 +731,48 @@ __device__ void solve_one(const ProbDesc& pd, const KernelArgs& a, Op& op, RedSm
       ++info.correctors;
       sc.alpha_p1 = sc.alpha_p;
       sc.alpha_d1 = sc.alpha_d;
-      double zts_t = 0.0;
-      for (int64_t q = tid; q < chunk; q += kThreads) {
-        if (!op.valid(q)) { g64[q] = 0.0; continue; }
-        const int64_t gi = gb + q;
-        const double2 z = zs[2 * gi], s = zs[2 * gi + 1];
-        const P2 x1 = X1[gi];
-        const Dir du = direction(z.x, s.x, rcp64(z.x), (double)x1.x, 0.0, sc, prm.sigma3);
-        const Dir dv = direction(z.y, s.y, rcp64(z.y), (double)x1.y, 0.0, sc, prm.sigma3);
-        const double zu = fma(sc.alpha_p1, du.dz, z.x), zv = fma(sc.alpha_p1, dv.dz, z.y);
-        const double su = fma(sc.alpha_d1, du.ds, s.x), sv = fma(sc.alpha_d1, dv.ds, s.y);
-        g64[q] = zu - zv;
-        zts_t += zu * su + zv * sv;
+      H zts_t = 0;
+      {
+        const ScH<H> c(sc, prm.sigma3);  // corr == false: predictor direction only
+        for (int64_t q = tid; q < chunk; q += kThreads) {
+          if (!op.valid(q)) { g64[q] = 0.0; continue; }
+          const int64_t gi = gb + q;
+          const double2 z = zs[2 * gi], s = zs[2 * gi + 1];
+          Dir<H> du, dv;
+          load_dir(gi, z, s, c, du, dv);
+          g64[q] = fma(sc.alpha_p1, (double)du.dz, z.x) - fma(sc.alpha_p1, (double)dv.dz, z.y);
+          const H zu = (H)z.x + c.ap1 * du.dz, zv = (H)z.y + c.ap1 * dv.dz;
+          const H su = (H)s.x + c.ad1 * du.ds, sv = (H)s.y + c.ad1 * dv.ds;
+          zts_t += zu * su + zv * sv;
+        }
       }
       __syncthreads();
       op.resid();
       nmat += 2;
       {
-        double v[1] = {zts_t}, out[1];
+        PS v[1] = {zts_t};
+        double out[1];
         cluster_sum<G, 1>(rs, par, v, out);
         sc.mu_t = out[0] / (2.0 * (double)n);
       }
-      const double s3mu = prm.sigma3 * sc.mu_t;
-      // rhs~ = f_z~ + Z^-1 f_s~ with f_z~ = s~ - [tau + g~; tau - g~], f_s~ = sigma3 mu~ - z~ s~
-      pcg_init([&](int64_t q, double2 z, double2 s, double ru, double rv) {
-                 const int64_t gi = gb + q;
-                 const P2 x1 = X1[gi];
-                 const double g = g64[q];
-                 const double dsu = fma(smu, ru, -s.x) - s.x * ru * (double)x1.x;
-                 const double dsv = fma(smu, rv, -s.y) - s.y * rv * (double)x1.y;
-                 const double zu = fma(sc.alpha_p1, (double)x1.x, z.x), zv = fma(sc.alpha_p1, (double)x1.y, z.y);
-                 const double su = fma(sc.alpha_d1, dsu, s.x), sv = fma(sc.alpha_d1, dsv, s.y);
-                 const double fzu = su - (tau + g), fzv = sv - (tau - g);
-                 return make_double2(fma(fma(-zu, su, s3mu), ru, fzu), fma(fma(-zv, sv, s3mu), rv, fzv));
-               }, false, rzp, pdpp);
+      {
+        const ScH<H> c(sc, prm.sigma3);
+        // rhs~ = f_z~ + Z^-1 f_s~ with f_z~ = s~ - [tau + g~; tau - g~] (float64),
+        // f_s~ = sigma3 mu~ - z~ s~
+        pcg_init([&](int64_t q, int64_t gi, const double2& z, const double2& s) {
+                   const double g = g64[q];
+                   Dir<H> du, dv;
+                   load_dir(gi, z, s, c, du, dv);
+                   const H zu = (H)z.x + c.ap1 * du.dz, zv = (H)z.y + c.ap1 * dv.dz;
+                   const H su = (H)s.x + c.ad1 * du.ds, sv = (H)s.y + c.ad1 * dv.ds;
+                   const double fzu = fma(sc.alpha_d1, (double)du.ds, s.x) - (tau + g);
+                   const double fzv = fma(sc.alpha_d1, (double)dv.ds, s.y) - (tau - g);
+                   P2 r;
+                   r.x = (H)fzu + (c.s3mut - zu * su) * rcpH((H)z.x);
+                   r.y = (H)fzv + (c.s3mut - zv * sv) * rcpH((H)z.y);
+                   return r;
+                 }, false, rzp, pdpp);
+      }
       sc.corr = true;
       pcg(X2, rzp, pdpp);
       step_lengths(sc.alpha_p, sc.alpha_d);
