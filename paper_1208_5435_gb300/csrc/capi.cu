@@ -146,12 +146,12 @@ Layout make_layout(const mfipm_operator* ops, int batch, bool pcg64) {
   size_t o = 0;
   L.off_hdr = o;
   o += 256;
-  L.off_tw64 = o;
-  o += align256(((size_t)1 << L.log2_tw) * 16);
+  L.off_tw64 = o;  // level-ordered tables: 2^(log2_tw+1) entries each
+  o += align256(((size_t)2 << L.log2_tw) * 16);
   L.off_tw32 = o;
-  o += align256(((size_t)1 << L.log2_tw) * 8);
+  o += align256(((size_t)2 << L.log2_tw) * 8);
   L.off_twdf = o;
-  o += align256(((size_t)1 << L.log2_tw) * 16);
+  o += align256(((size_t)2 << L.log2_tw) * 16);
   L.off_desc = o;
   o += align256(sizeof(ProbDesc) * (size_t)batch);
   L.off_info = o;
@@ -290,7 +290,7 @@ int prepare(int batch, const mfipm_operator* ops, const double* const* b, const 
   a.probs = reinterpret_cast<const ProbDesc*>(ws + P.lay.off_desc);
   a.batch = batch;
   a.queue = reinterpret_cast<int*>(ws + P.lay.off_hdr);
-  a.err = reinterpret_cast<int*>(ws + P.lay.off_hdr + 4);
+  a.err = reinterpret_cast<int*>(ws + P.lay.off_hdr + 64);  // queue counters occupy bytes 0..7
   a.tw64 = reinterpret_cast<const double2*>(ws + P.lay.off_tw64);
   a.tw32 = reinterpret_cast<const float2*>(ws + P.lay.off_tw32);
   a.twdf = reinterpret_cast<const float4*>(ws + P.lay.off_twdf);
@@ -317,9 +317,20 @@ int run(Prepared& P, cudaStream_t st, int batch, mfipm_info* infos, const std::v
     if ((e = launch_dct_setup(P.args.probs, batch, P.max_n, P.args.err, st)) != cudaSuccess)
       return cuda_fail(e, "setup kernel");
   }
+  // problems small enough for one CTA's shared memory go to the per-CTA phase of the kernel
+  // (the queue order puts every cluster problem before them)
+  int nbig = batch;
+  if (P.G == 1) {
+    nbig = 0;
+  } else if (P.dct) {
+    const int64_t small_max = std::min<int64_t>(16384, P.max_n / P.G);
+    nbig = 0;
+    for (int i = 0; i < batch; ++i) nbig += sorted[i].n > small_max;
+  }
+  P.args.nbig = nbig;
   int maxc = P.dct ? max_active_clusters_dct(P.G, P.max_n) : max_active_clusters_dense(P.G, P.pcg64, P.max_n, P.max_m);
   if (maxc < 1) return fail(MFIPM_UNSUPPORTED, "no resident cluster of size %d fits this problem", P.G);
-  const int clusters = std::min(maxc, batch);
+  const int clusters = std::min(maxc, std::max(nbig, (batch + P.G - 1) / P.G));
   if (g_timing) {
     for (auto& ev : g_ev)
       if (!ev && (e = cudaEventCreate(&ev)) != cudaSuccess) return cuda_fail(e, "timing event");

@@ -86,19 +86,21 @@ template <class C> __device__ __forceinline__ C cmul_i(C a) { return mk(-a.y, a.
 template <class C> __device__ __forceinline__ C cmul_mi(C a) { return mk(a.y, -a.x); }    // -i*a
 template <class C, class R> __device__ __forceinline__ C cscale(C a, R s) { return mk(a.x * s, a.y * s); }
 
-// Twiddle table: tw[j] = exp(-2*pi*i*j / 2^log2_tw), built once per call by a setup
-// kernel with sincospi; every transform size indexes it with a power-of-two stride.
+// Twiddle tables, level-ordered: tw[2^l + j] = exp(-2 pi i j / 2^l) for 0 <= j < 2^l and
+// 1 <= l <= log2_tw (built once per call by a setup kernel with sincospi).  Roots of one
+// order sit contiguously, so the lanes of a warp that need consecutive j read consecutive
+// entries (one cache line serves 8-16 lanes).
 template <class C> struct Twiddle {
   const C* tw;
   int log2_tw;
   // exp(-2 pi i j / 2^logB) for 0 <= j < 2^logB
-  __device__ __forceinline__ C root(int64_t j, int logB) const { return __ldg(&tw[j << (log2_tw - logB)]); }
+  __device__ __forceinline__ C root(int64_t j, int logB) const { return __ldg(&tw[((int64_t)1 << logB) + j]); }
 };
 template <> struct Twiddle<dfc> {
   const float4* tw;  // {re.hi, re.lo, im.hi, im.lo}
   int log2_tw;
   __device__ __forceinline__ dfc root(int64_t j, int logB) const {
-    const float4 t = __ldg(&tw[j << (log2_tw - logB)]);
+    const float4 t = __ldg(&tw[((int64_t)1 << logB) + j]);
     return dfc{df(t.x, t.y), df(t.z, t.w)};
   }
 };
@@ -119,84 +121,68 @@ __device__ __forceinline__ double warp_min(double v) {
 struct RedSmem {
   double warp_part[kWarps][kMaxRed];
   double cta_part[2][kMaxRed];  // double-buffered: read remotely by the other CTAs
+  double sd[8];                 // scalars derived by thread 0 from the last reduction
+  float sf[8];
+  int flag;
   int fetched;                  // problem index broadcast by CTA rank 0
 };
 
-// Sum K per-thread values over the whole cluster of G CTAs; every thread of every CTA
-// receives identical totals (same summation order everywhere).  `parity` alternates
-// between calls so that a CTA can publish the next partials while slower CTAs still read
-// the previous ones; between two uses of the same buffer there is always the barrier of
-// the intermediate call.
-template <int G, int K, class V>
-__device__ __forceinline__ void cluster_sum(RedSmem& rs, int& parity, const V (&v)[K], double (&out)[K]) {
+// Reduce K per-thread values over the cluster of G CTAs (sum, or min when kMin).  Thread 0
+// of every CTA receives identical totals (the G partials are combined in rank order) and
+// runs fin(totals), which stores derived scalars in rs.sd / rs.sf / rs.flag; the function
+// ends with a CTA barrier, after which every thread may read them.  `parity` alternates so
+// that a CTA can publish new partials while a slower CTA still reads the previous ones;
+// between two uses of one buffer lies the cluster barrier of the call in between.
+template <int G, int K, bool kMin = false, class V, class Fin>
+__device__ __forceinline__ void cluster_reduce(RedSmem& rs, int& parity, const V (&v)[K], Fin&& fin) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
   for (int k = 0; k < K; ++k) {
-    V w = warp_sum(v[k]);
+    V w = v[k];
+    if constexpr (kMin) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) w = fmin(w, __shfl_xor_sync(0xffffffffu, w, o));
+    } else {
+      w = warp_sum(w);
+    }
     if (lane == 0) rs.warp_part[warp][k] = (double)w;
   }
   __syncthreads();
+  double mine[K];
   if (warp == 0) {
 #pragma unroll
     for (int k = 0; k < K; ++k) {
-      double t = lane < kWarps ? rs.warp_part[lane][k] : 0.0;
-      t = warp_sum(t);
-      if (lane == 0) rs.cta_part[parity][k] = t;
+      double t = lane < kWarps ? rs.warp_part[lane][k] : (kMin ? INFINITY : 0.0);
+      if constexpr (kMin) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) t = fmin(t, __shfl_xor_sync(0xffffffffu, t, o));
+      } else {
+        t = warp_sum(t);
+      }
+      mine[k] = t;
+      if (G > 1 && lane == 0) rs.cta_part[parity][k] = t;
     }
   }
-  if constexpr (G == 1) {
-    __syncthreads();
+  if constexpr (G > 1) cg::this_cluster().sync();
+  if (threadIdx.x == 0) {
+    double tot[K];
+    if constexpr (G == 1) {
 #pragma unroll
-    for (int k = 0; k < K; ++k) out[k] = rs.cta_part[parity][k];
-  } else {
-    cg::cluster_group cl = cg::this_cluster();
-    cl.sync();
+      for (int k = 0; k < K; ++k) tot[k] = mine[k];
+    } else {
+      cg::cluster_group cl = cg::this_cluster();
 #pragma unroll
-    for (int k = 0; k < K; ++k) out[k] = 0.0;
+      for (int k = 0; k < K; ++k) tot[k] = kMin ? INFINITY : 0.0;
 #pragma unroll
-    for (int g = 0; g < G; ++g) {
-      const RedSmem* r = cl.map_shared_rank(&rs, g);
+      for (int g = 0; g < G; ++g) {
+        const RedSmem* r = cl.map_shared_rank(&rs, g);
 #pragma unroll
-      for (int k = 0; k < K; ++k) out[k] += r->cta_part[parity][k];
+        for (int k = 0; k < K; ++k) tot[k] = kMin ? fmin(tot[k], r->cta_part[parity][k]) : tot[k] + r->cta_part[parity][k];
+      }
     }
-  }
-  parity ^= 1;
-}
-
-// Minimum of K per-thread doubles over the cluster (same structure as cluster_sum).
-template <int G, int K>
-__device__ __forceinline__ void cluster_min(RedSmem& rs, int& parity, const double (&v)[K], double (&out)[K]) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-  for (int k = 0; k < K; ++k) {
-    double w = warp_min(v[k]);
-    if (lane == 0) rs.warp_part[warp][k] = w;
+    fin(tot);
   }
   __syncthreads();
-  if (warp == 0) {
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-      double t = lane < kWarps ? rs.warp_part[lane][k] : INFINITY;
-      t = warp_min(t);
-      if (lane == 0) rs.cta_part[parity][k] = t;
-    }
-  }
-  if constexpr (G == 1) {
-    __syncthreads();
-#pragma unroll
-    for (int k = 0; k < K; ++k) out[k] = rs.cta_part[parity][k];
-  } else {
-    cg::cluster_group cl = cg::this_cluster();
-    cl.sync();
-#pragma unroll
-    for (int k = 0; k < K; ++k) out[k] = INFINITY;
-#pragma unroll
-    for (int g = 0; g < G; ++g) {
-      const RedSmem* r = cl.map_shared_rank(&rs, g);
-#pragma unroll
-      for (int k = 0; k < K; ++k) out[k] = fmin(out[k], r->cta_part[parity][k]);
-    }
-  }
   parity ^= 1;
 }
 

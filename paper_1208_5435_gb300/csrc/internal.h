@@ -45,8 +45,8 @@ struct ProbDesc {
 struct KernelArgs {
   const ProbDesc* probs;
   int32_t batch;
-  int32_t pad;
-  int* queue;             // DEVICE work counter, zero at launch
+  int32_t nbig;           // problems [0, nbig) are solved by a whole cluster, the rest by one CTA each
+  int* queue;             // DEVICE work counters (cluster queue, CTA queue), zero at launch
   int* err;               // DEVICE error word (first failing problem's status)
   const double2* tw64;    // exp(-2 pi i j / 2^log2_tw)
   const float2* tw32;

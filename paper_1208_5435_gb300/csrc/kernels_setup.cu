@@ -5,15 +5,19 @@ namespace mfipm {
 
 // ------------------------------------------------------------------ setup kernels
 __global__ void twiddle_kernel(double2* tw64, float2* tw32, float4* twdf, int log2_tw) {
-  const int64_t T = (int64_t)1 << log2_tw;
-  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < T; j += (int64_t)gridDim.x * blockDim.x) {
+  // level-ordered: entry 2^l + j holds exp(-2 pi i j / 2^l), 1 <= l <= log2_tw, j < 2^l
+  const int64_t T = (int64_t)2 << log2_tw;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < T; e += (int64_t)gridDim.x * blockDim.x) {
+    if (e < 2) continue;
+    const int l = 63 - __clzll((unsigned long long)e);
+    const int64_t j = e - ((int64_t)1 << l);
     double s, c;
-    // exp(-2 pi i j / T) = cos(pi * 2j/T) - i sin(pi * 2j/T)
-    sincospi(2.0 * (double)j / (double)T, &s, &c);
-    tw64[j] = make_double2(c, -s);
-    tw32[j] = make_float2((float)c, (float)-s);
+    // exp(-2 pi i j / 2^l) = cos(pi * 2j/2^l) - i sin(pi * 2j/2^l)
+    sincospi(2.0 * (double)j / (double)((int64_t)1 << l), &s, &c);
+    tw64[e] = make_double2(c, -s);
+    tw32[e] = make_float2((float)c, (float)-s);
     const df re = to_df(c), im = to_df(-s);
-    twdf[j] = make_float4(re.hi, re.lo, im.hi, im.lo);
+    twdf[e] = make_float4(re.hi, re.lo, im.hi, im.lo);
   }
 }
 
@@ -60,7 +64,7 @@ size_t dense_smem_bytes(int G, bool, int64_t max_n, int64_t max_m) {
 }
 
 cudaError_t launch_twiddles(double2* tw64, float2* tw32, float4* twdf, int log2_tw, cudaStream_t st) {
-  const int64_t T = (int64_t)1 << log2_tw;
+  const int64_t T = (int64_t)2 << log2_tw;
   const int blocks = (int)((T + 255) / 256 < 1024 ? (T + 255) / 256 : 1024);
   twiddle_kernel<<<blocks, 256, 0, st>>>(tw64, tw32, twdf, log2_tw);
   return cudaGetLastError();

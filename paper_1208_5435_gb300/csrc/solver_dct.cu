@@ -5,7 +5,7 @@ namespace mfipm {
 
 cudaError_t launch_dct_solver(int G, const KernelArgs& a, int64_t max_n, int grid_clusters, cudaStream_t st) {
   const size_t smem = dct_smem_bytes(G, max_n);
-#define L_(g) launch_t<g, DctOp<g>, float>(a, smem, grid_clusters, st)
+#define L_(g) launch_t<g, DctOp<g>, DctOp<1>, float>(a, smem, grid_clusters, st)
   MFIPM_G_SWITCH(G, L_)
 #undef L_
   return cudaErrorInvalidValue;
@@ -13,7 +13,7 @@ cudaError_t launch_dct_solver(int G, const KernelArgs& a, int64_t max_n, int gri
 
 int max_active_clusters_dct(int G, int64_t max_n) {
   const size_t smem = dct_smem_bytes(G, max_n);
-#define O_(g) occupancy_t<g, DctOp<g>, float>(smem)
+#define O_(g) occupancy_t<g, DctOp<g>, DctOp<1>, float>(smem)
   MFIPM_G_SWITCH(G, O_)
 #undef O_
   return 0;

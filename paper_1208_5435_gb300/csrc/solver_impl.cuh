@@ -411,9 +411,9 @@ template <int G> struct DenseOp {
       const double a = __ldg(&A[i * lda + gbase + j]) * a_scale;
       s += a * a;
     }
-    double v[1] = {s}, out[1];
-    cluster_sum<GG, 1>(rs, par, v, out);
-    rho = out[0] / (double)n;
+    double v[1] = {s};
+    cluster_reduce<GG, 1>(rs, par, v, [&](const double (&t)[1]) { rs.sd[0] = t[0] / (double)n; });
+    rho = rs.sd[0];
   }
 };
 
@@ -426,18 +426,9 @@ template <int G> struct DenseOp {
 // step-to-boundary ratios.  Both uses of a direction (ratio test and update) evaluate it
 // through the same function from the same inputs, so the fraction-to-boundary rule keeps
 // z, s > 0.
-struct IpmScalars {
-  double mu, sigma, alpha_p, alpha_d;       // predictor
-  double mu_t, alpha_p1, alpha_d1;          // corrector trial point
-  bool corr;
-};
-
 template <class H> struct ScH {
   H smu, ap1, ad1, s3mut;
   bool corr;
-  __device__ explicit ScH(const IpmScalars& sc, double sigma3)
-      : smu((H)(sc.sigma * sc.mu)), ap1((H)sc.alpha_p1), ad1((H)sc.alpha_d1), s3mut((H)(sigma3 * sc.mu_t)),
-        corr(sc.corr) {}
 };
 
 __device__ __forceinline__ float rcpH(float z) { return __frcp_rn(z); }
@@ -467,8 +458,29 @@ __device__ __forceinline__ Dir<H> direction(H z, H s, H dz1, H dz2, const ScH<H>
   return r;
 }
 
+// Scalars of one solve, written by thread 0 inside cluster_reduce and read by every
+// thread after its closing barrier (identical in all CTAs of the cluster).
+template <class H> struct IpmShared {
+  double mu, sigma, alpha_p, alpha_d, mu_t, alpha_p1, alpha_d1, prev_ap, prev_ad;
+  double rel_gap, P_obj, cn, rz0, rz;
+  H smu, ap1, ad1, s3mut, apH, adH, alpha, beta;
+  int corr, corr_next, stop, pcg_stop, correctors;
+};
+
+template <class H>
+__device__ __forceinline__ ScH<H> steering(const IpmShared<H>& sh, bool corr) {
+  ScH<H> c;
+  c.smu = sh.smu;
+  c.ap1 = sh.ap1;
+  c.ad1 = sh.ad1;
+  c.s3mut = sh.s3mut;
+  c.corr = corr;
+  return c;
+}
+
 template <int G, class Op, class PS>
-__device__ void solve_one(const ProbDesc& pd, const KernelArgs& a, Op& op, RedSmem& rs, int& par) {
+__device__ void solve_one(const ProbDesc& pd, const KernelArgs& a, Op& op, RedSmem& rs, IpmShared<PS>& sh,
+                          int& par) {
   using P2 = typename V2<PS>::T;
   using H = PS;
   const SolveParams& prm = a.prm;
@@ -476,15 +488,16 @@ __device__ void solve_one(const ProbDesc& pd, const KernelArgs& a, Op& op, RedSm
   const int64_t n = pd.n;
   const double tau = pd.tau;
   const int64_t chunk = op.chunk, gb = op.gbase;
-  double2* zs = reinterpret_cast<double2*>(pd.zs);
-  P2* X1 = reinterpret_cast<P2*>(pd.pcg);
-  P2* X2 = X1 + n;
-  P2* Rv = X2 + n;
-  P2* Pv = Rv + n;
-  P2* Dv = Pv + n;
-  double* g64 = op.r64();
-  mfipm_info info{};
+  double2* __restrict__ zs = reinterpret_cast<double2*>(pd.zs);
+  P2* __restrict__ X1 = reinterpret_cast<P2*>(pd.pcg);
+  P2* __restrict__ X2 = X1 + n;
+  P2* __restrict__ Rv = X2 + n;
+  P2* __restrict__ Pv = Rv + n;
+  P2* __restrict__ Dv = Pv + n;
+  double* __restrict__ g64 = op.r64();
+  PS* __restrict__ w = op.template wbuf<PS>();
   int64_t nmat = 0;
+  int pcg_total = 0, it = 0;
 
   op.template setup<G>(rs, par);
   const PS rho = (PS)op.rho;
@@ -492,63 +505,65 @@ __device__ void solve_one(const ProbDesc& pd, const KernelArgs& a, Op& op, RedSm
   // ||c||^2 = sum 2 tau^2 + 2 (A^T b)_i^2 with A^T b = -A^T (A 0 - b)  (c: Sec. 3)
   for (int64_t q = tid; q < chunk; q += kThreads) g64[q] = 0.0;
   __syncthreads();
-  double bb = op.resid();
-  ++nmat;
-  double atb2 = 0.0;
-  for (int64_t q = tid; q < chunk; q += kThreads)
-    if (op.valid(q)) atb2 += g64[q] * g64[q];
-  double cn;
   {
-    double v[2] = {atb2, bb}, out[2];
-    cluster_sum<G, 2>(rs, par, v, out);
-    cn = sqrt(2.0 * (double)n * tau * tau + 2.0 * out[0]);
+    const double bb = op.resid();
+    ++nmat;
+    double atb2 = 0.0;
+    for (int64_t q = tid; q < chunk; q += kThreads)
+      if (op.valid(q)) atb2 += g64[q] * g64[q];
+    double v[2] = {atb2, bb};
+    cluster_reduce<G, 2>(rs, par, v, [&](const double (&t)[2]) {
+      sh.cn = sqrt(2.0 * (double)n * tau * tau + 2.0 * t[0]);
+      sh.alpha_p = sh.alpha_d = 1.0;
+      sh.prev_ap = sh.prev_ad = 1.0;
+      sh.apH = sh.adH = (H)1;
+      sh.corr = sh.corr_next = 0;
+      sh.correctors = 0;
+      sh.stop = 0;
+      sh.rel_gap = INFINITY;
+      sh.P_obj = 0.0;
+    });
   }
-
-  IpmScalars sc{};
-  sc.alpha_p = sc.alpha_d = 1.0;
-  double prev_ap = 1.0, prev_ad = 1.0;
-  int status = MFIPM_NOT_CONVERGED;
-  double rel_gap = INFINITY, P_obj = 0.0;
-  int it = 0;
-  int pcg_total = 0;
-  PS* w = op.template wbuf<PS>();
 
   // PCG on (Theta^-1 + F F^T) dz = rhs (Sec. 4).  On entry r = rhs and p = P^-1 r are
   // stored, the operator input w = p_u - p_v is in the shared buffer, and rz_part, pdp_part
   // are this thread's shares of r.P^-1 r and p.(Theta^-1 p).  Stops when
   // sqrt(r.P^-1 r) <= tol_pcg * its initial value or after max_iter_pcg iterations.
-  auto pcg = [&](P2* Xo, PS rz_part, PS pdp_part) {
-    double rz0 = 0.0, rz = 0.0;
+  auto pcg = [&](P2* __restrict__ Xo, PS rz_part, PS pdp_part) {
     int k = 0;
     PS pdp_acc = pdp_part;
     for (;;) {
       const double aw2 = op.normal(w);
       nmat += 2;
-      double tot[2];
       {
         PS v[2] = {pdp_acc + (PS)aw2, k == 0 ? rz_part : (PS)0};
-        cluster_sum<G, 2>(rs, par, v, tot);
+        cluster_reduce<G, 2>(rs, par, v, [&](const double (&t)[2]) {
+          if (k == 0) {
+            sh.rz0 = sh.rz = t[1];
+            sh.pcg_stop = !(t[1] > 0.0) || !isfinite(t[1]);
+          }
+          sh.alpha = (PS)(sh.rz / t[0]);
+        });
       }
-      if (k == 0) {
-        rz0 = rz = tot[1];
-        if (!(rz0 > 0.0) || !isfinite(rz0)) {  // zero right-hand side: dz = 0
-          P2 zero;
-          zero.x = (PS)0;
-          zero.y = (PS)0;
-          for (int64_t q = tid; q < chunk; q += kThreads)
-            if (op.valid(q)) Xo[gb + q] = zero;
-          break;
-        }
+      if (sh.pcg_stop) {  // zero right-hand side: dz = 0
+        P2 zero;
+        zero.x = (PS)0;
+        zero.y = (PS)0;
+        for (int64_t q = tid; q < chunk; q += kThreads)
+          if (op.valid(q)) Xo[gb + q] = zero;
+        break;
       }
-      const PS alpha = (PS)(rz / tot[0]);
+      const PS alpha = sh.alpha;
       PS rzn_part = 0;
+      const bool first = (k == 0);
+#pragma unroll 4
       for (int64_t q = tid; q < chunk; q += kThreads) {
         if (!op.valid(q)) continue;
         const int64_t gi = gb + q;
         const P2 p = Pv[gi], d = Dv[gi];
         P2 r = Rv[gi];
         P2 x;
-        if (k == 0) { x.x = (PS)0; x.y = (PS)0; } else { x = Xo[gi]; }
+        if (first) { x.x = (PS)0; x.y = (PS)0; } else { x = Xo[gi]; }
         const PS y = w[q];
         const PS qu = d.x * p.x + y, qv = d.y * p.y - y;
         x.x += alpha * p.x;
@@ -561,17 +576,19 @@ __device__ void solve_one(const ProbDesc& pd, const KernelArgs& a, Op& op, RedSm
         Rv[gi] = r;
       }
       ++k;
-      double rzn;
       {
         PS v[1] = {rzn_part};
-        double out[1];
-        cluster_sum<G, 1>(rs, par, v, out);
-        rzn = out[0];
+        cluster_reduce<G, 1>(rs, par, v, [&](const double (&t)[1]) {
+          const double rzn = t[0];
+          sh.pcg_stop = !(rzn > prm.tol_pcg * prm.tol_pcg * sh.rz0) || k >= prm.max_iter_pcg || !isfinite(rzn);
+          sh.beta = (PS)(rzn / sh.rz);
+          sh.rz = rzn;
+        });
       }
-      if (!(rzn > prm.tol_pcg * prm.tol_pcg * rz0) || k >= prm.max_iter_pcg || !isfinite(rzn)) break;
-      const PS beta = (PS)(rzn / rz);
-      rz = rzn;
+      if (sh.pcg_stop) break;
+      const PS beta = sh.beta;
       PS pdp = 0;
+#pragma unroll 4
       for (int64_t q = tid; q < chunk; q += kThreads) {
         if (!op.valid(q)) { w[q] = (PS)0; continue; }
         const int64_t gi = gb + q;
@@ -590,11 +607,12 @@ __device__ void solve_one(const ProbDesc& pd, const KernelArgs& a, Op& op, RedSm
     pcg_total += k;
   };
 
-  // PCG initialisation: r = rhs (from rhs_fn(q, z, s) in precision H), p = P^-1 r, w = p_u - p_v.
-  // Writes Theta^-1 = s/z when write_d.
+  // PCG initialisation: r = rhs (from rhs_fn(q, gi, z, s) in precision H), p = P^-1 r,
+  // w = p_u - p_v.  Writes Theta^-1 = s/z when write_d.
   auto pcg_init = [&](auto rhs_fn, bool write_d, PS& rz_part, PS& pdp_part) {
     rz_part = 0;
     pdp_part = 0;
+#pragma unroll 2
     for (int64_t q = tid; q < chunk; q += kThreads) {
       if (!op.valid(q)) { w[q] = (PS)0; continue; }
       const int64_t gi = gb + q;
@@ -628,10 +646,12 @@ __device__ void solve_one(const ProbDesc& pd, const KernelArgs& a, Op& op, RedSm
     dv = direction<H>((H)z.y, (H)s.y, x1.y, x2.y, c);
   };
 
-  // step lengths alpha = min(1, eta * min_{dv<0} -v/dv) for z and s (reading R4)
-  auto step_lengths = [&](double& ap, double& ad) {
-    const ScH<H> c(sc, prm.sigma3);
+  // step lengths alpha = min(1, eta * min_{dv<0} -v/dv) for z and s (reading R4); then the
+  // corrector test of the Algorithm (alpha_P or alpha_D <= alpha_tilde)
+  auto step_lengths = [&](bool corr) {
+    const ScH<H> c = steering(sh, corr);
     H mp = (H)INFINITY, md = (H)INFINITY;
+#pragma unroll 2
     for (int64_t q = tid; q < chunk; q += kThreads) {
       if (!op.valid(q)) continue;
       const int64_t gi = gb + q;
@@ -643,19 +663,38 @@ __device__ void solve_one(const ProbDesc& pd, const KernelArgs& a, Op& op, RedSm
       if (du.ds < (H)0) md = fmin(md, (H)s.x * rcpH(-du.ds));
       if (dv.ds < (H)0) md = fmin(md, (H)s.y * rcpH(-dv.ds));
     }
-    double v[2] = {(double)mp, (double)md}, out[2];
-    cluster_min<G, 2>(rs, par, v, out);
-    ap = fmin(1.0, prm.eta * out[0]);
-    ad = fmin(1.0, prm.eta * out[1]);
-    if (prm.equal_steps) ap = ad = fmin(ap, ad);
+    H v[2] = {mp, md};
+    cluster_reduce<G, 2, true>(rs, par, v, [&](const double (&t)[2]) {
+      double ap = fmin(1.0, prm.eta * t[0]);
+      double ad = fmin(1.0, prm.eta * t[1]);
+      if (prm.equal_steps) ap = ad = fmin(ap, ad);
+      sh.alpha_p = ap;
+      sh.alpha_d = ad;
+      sh.apH = (H)ap;
+      sh.adH = (H)ad;
+      sh.corr_next = corr ? 0 : (ap <= prm.alpha_tilde || ad <= prm.alpha_tilde);
+      if (sh.corr_next) {
+        sh.alpha_p1 = ap;
+        sh.alpha_d1 = ad;
+        sh.ap1 = (H)ap;
+        sh.ad1 = (H)ad;
+        ++sh.correctors;
+      }
+      sh.corr = corr;
+      sh.prev_ap = ap;
+      sh.prev_ad = ad;
+    });
   };
 
   for (it = 1;; ++it) {
     // ---- update (previous direction) fused with x = u - v for the residual
     H part[3] = {0, 0, 0};  // z.s, 1^T z, ||x||^2
     {
-      const ScH<H> c(sc, prm.sigma3);
-      const H apH = (H)sc.alpha_p, adH = (H)sc.alpha_d;
+      const ScH<H> c = steering(sh, sh.corr != 0);
+      const double ap = sh.alpha_p, ad = sh.alpha_d;
+      const H apH = sh.apH, adH = sh.adH;
+      const double keep = 1.0 - prm.eta;
+#pragma unroll 2
       for (int64_t q = tid; q < chunk; q += kThreads) {
         if (!op.valid(q)) { g64[q] = 0.0; continue; }
         const int64_t gi = gb + q;
@@ -670,13 +709,13 @@ __device__ void solve_one(const ProbDesc& pd, const KernelArgs& a, Op& op, RedSm
           s = zs[2 * gi + 1];
           Dir<H> du, dv;
           load_dir(gi, z, s, c, du, dv);
-          double nu = fma(sc.alpha_p, (double)du.dz, z.x), nv = fma(sc.alpha_p, (double)dv.dz, z.y);
-          double nsu = fma(sc.alpha_d, (double)du.ds, s.x), nsv = fma(sc.alpha_d, (double)dv.ds, s.y);
+          double nu = fma(ap, (double)du.dz, z.x), nv = fma(ap, (double)dv.dz, z.y);
+          double nsu = fma(ad, (double)du.ds, s.x), nsv = fma(ad, (double)dv.ds, s.y);
           // the step keeps z, s > 0 by construction; guard against a rounding-level crossing
-          if (!(nu > 0.0)) nu = z.x * (1.0 - prm.eta);
-          if (!(nv > 0.0)) nv = z.y * (1.0 - prm.eta);
-          if (!(nsu > 0.0)) nsu = s.x * (1.0 - prm.eta);
-          if (!(nsv > 0.0)) nsv = s.y * (1.0 - prm.eta);
+          if (!(nu > 0.0)) nu = z.x * keep;
+          if (!(nv > 0.0)) nv = z.y * keep;
+          if (!(nsu > 0.0)) nsu = s.x * keep;
+          if (!(nsv > 0.0)) nsv = s.y * keep;
           zu = (H)z.x + apH * du.dz;
           zv = (H)z.y + apH * dv.dz;
           su = (H)s.x + adH * du.ds;
@@ -697,24 +736,27 @@ __device__ void solve_one(const ProbDesc& pd, const KernelArgs& a, Op& op, RedSm
     // ---- float64 residual g = A^T (A x - b)  (f_z of Eq. fzfs needs F F^T z + c)
     const double res2 = op.resid();
     nmat += 2;
-    double tot[4];
     {
       double v[4] = {(double)part[0], (double)part[1], (double)part[2], res2};
-      cluster_sum<G, 4>(rs, par, v, tot);
+      const int itc = it;
+      cluster_reduce<G, 4>(rs, par, v, [&](const double (&t)[4]) {
+        sh.mu = t[0] / (2.0 * (double)n);
+        sh.P_obj = tau * t[1] + 0.5 * t[3];
+        sh.rel_gap = t[0] / (1.0 + fabs(sh.P_obj));
+        sh.corr = 0;
+        if (!isfinite(sh.rel_gap)) sh.stop = MFIPM_NUMERIC;
+        else if (sh.rel_gap <= prm.tol) sh.stop = -1;                       // converged (reading R7)
+        else if (itc > prm.max_iter) sh.stop = MFIPM_NOT_CONVERGED;
+        // predictor centering (Algorithm; reading R8)
+        sh.sigma = (itc != 1 && (sh.prev_ap <= prm.alpha_bar || sh.prev_ad <= prm.alpha_bar)) ? prm.sigma2 : prm.sigma1;
+        sh.smu = (H)(sh.sigma * sh.mu);
+      });
     }
-    const double zts = tot[0];
-    sc.mu = zts / (2.0 * (double)n);
-    P_obj = tau * tot[1] + 0.5 * tot[3];
-    rel_gap = zts / (1.0 + fabs(P_obj));
-    if (!isfinite(rel_gap)) { status = MFIPM_NUMERIC; break; }
-    if (rel_gap <= prm.tol) { status = MFIPM_OK; break; }        // reading R7
-    if (it > prm.max_iter) { status = MFIPM_NOT_CONVERGED; break; }
-    // ---- predictor (Algorithm: sigma choice, then PCG)
-    sc.sigma = (it != 1 && (prev_ap <= prm.alpha_bar || prev_ad <= prm.alpha_bar)) ? prm.sigma2 : prm.sigma1;
-    sc.corr = false;
+    if (sh.stop) break;
+    // ---- predictor
     PS rzp, pdpp;
     {
-      const H smuH = (H)(sc.sigma * sc.mu);
+      const H smuH = sh.smu;
       // rhs = f_z + Z^-1 f_s = sigma mu / z - (c + F F^T z) = sigma mu / z - [tau + g; tau - g]
       pcg_init([&](int64_t q, int64_t, const double2& z, const double2&) {
                  const double g = g64[q];
@@ -725,22 +767,21 @@ __device__ void solve_one(const ProbDesc& pd, const KernelArgs& a, Op& op, RedSm
                }, true, rzp, pdpp);
     }
     pcg(X1, rzp, pdpp);
-    step_lengths(sc.alpha_p, sc.alpha_d);
+    step_lengths(false);
     // ---- corrector (reading R6)
-    if (sc.alpha_p <= prm.alpha_tilde || sc.alpha_d <= prm.alpha_tilde) {
-      ++info.correctors;
-      sc.alpha_p1 = sc.alpha_p;
-      sc.alpha_d1 = sc.alpha_d;
+    if (sh.corr_next) {
       H zts_t = 0;
       {
-        const ScH<H> c(sc, prm.sigma3);  // corr == false: predictor direction only
+        const ScH<H> c = steering(sh, false);  // predictor direction only
+        const double ap1 = sh.alpha_p1;
+#pragma unroll 2
         for (int64_t q = tid; q < chunk; q += kThreads) {
           if (!op.valid(q)) { g64[q] = 0.0; continue; }
           const int64_t gi = gb + q;
           const double2 z = zs[2 * gi], s = zs[2 * gi + 1];
           Dir<H> du, dv;
           load_dir(gi, z, s, c, du, dv);
-          g64[q] = fma(sc.alpha_p1, (double)du.dz, z.x) - fma(sc.alpha_p1, (double)dv.dz, z.y);
+          g64[q] = fma(ap1, (double)du.dz, z.x) - fma(ap1, (double)dv.dz, z.y);
           const H zu = (H)z.x + c.ap1 * du.dz, zv = (H)z.y + c.ap1 * dv.dz;
           const H su = (H)s.x + c.ad1 * du.ds, sv = (H)s.y + c.ad1 * dv.ds;
           zts_t += zu * su + zv * sv;
@@ -751,12 +792,14 @@ __device__ void solve_one(const ProbDesc& pd, const KernelArgs& a, Op& op, RedSm
       nmat += 2;
       {
         PS v[1] = {zts_t};
-        double out[1];
-        cluster_sum<G, 1>(rs, par, v, out);
-        sc.mu_t = out[0] / (2.0 * (double)n);
+        cluster_reduce<G, 1>(rs, par, v, [&](const double (&t)[1]) {
+          sh.mu_t = t[0] / (2.0 * (double)n);
+          sh.s3mut = (H)(prm.sigma3 * sh.mu_t);
+        });
       }
       {
-        const ScH<H> c(sc, prm.sigma3);
+        const ScH<H> c = steering(sh, false);
+        const double ad1 = sh.alpha_d1;
         // rhs~ = f_z~ + Z^-1 f_s~ with f_z~ = s~ - [tau + g~; tau - g~] (float64),
         // f_s~ = sigma3 mu~ - z~ s~
         pcg_init([&](int64_t q, int64_t gi, const double2& z, const double2& s) {
@@ -765,20 +808,17 @@ __device__ void solve_one(const ProbDesc& pd, const KernelArgs& a, Op& op, RedSm
                    load_dir(gi, z, s, c, du, dv);
                    const H zu = (H)z.x + c.ap1 * du.dz, zv = (H)z.y + c.ap1 * dv.dz;
                    const H su = (H)s.x + c.ad1 * du.ds, sv = (H)s.y + c.ad1 * dv.ds;
-                   const double fzu = fma(sc.alpha_d1, (double)du.ds, s.x) - (tau + g);
-                   const double fzv = fma(sc.alpha_d1, (double)dv.ds, s.y) - (tau - g);
+                   const double fzu = fma(ad1, (double)du.ds, s.x) - (tau + g);
+                   const double fzv = fma(ad1, (double)dv.ds, s.y) - (tau - g);
                    P2 r;
                    r.x = (H)fzu + (c.s3mut - zu * su) * rcpH((H)z.x);
                    r.y = (H)fzv + (c.s3mut - zv * sv) * rcpH((H)z.y);
                    return r;
                  }, false, rzp, pdpp);
       }
-      sc.corr = true;
       pcg(X2, rzp, pdpp);
-      step_lengths(sc.alpha_p, sc.alpha_d);
+      step_lengths(true);
     }
-    prev_ap = sc.alpha_p;
-    prev_ad = sc.alpha_d;
   }
 
   // ---- exit: certificates and outputs (g64 holds A^T(Ax - b) of the final iterate)
@@ -804,26 +844,36 @@ __device__ void solve_one(const ProbDesc& pd, const KernelArgs& a, Op& op, RedSm
       pd.zs_out[3 * n + ni] = s.y;
     }
   }
-  double ftot[3];
-  cluster_sum<G, 3>(rs, par, fin, ftot);
-  if (op.rank == 0 && tid == 0) {
-    info.status = status;
-    info.ipm_iters = it - 1;
-    info.pcg_iters = pcg_total;
-    info.n_mat = nmat;
-    info.rel_gap = rel_gap;
-    info.dual_res = sqrt(ftot[0]) / (1.0 + cn);
-    info.kkt_rel = sqrt(ftot[1]) / (1.0 + sqrt(ftot[2]));
-    info.primal_obj = P_obj;
-    *pd.info = info;
-    if (status != MFIPM_OK) atomicCAS(a.err, 0, status);
-  }
+  const int its = it;
+  cluster_reduce<G, 3>(rs, par, fin, [&](const double (&t)[3]) {
+    if (op.rank == 0) {
+      mfipm_info info{};
+      info.status = sh.stop == -1 ? MFIPM_OK : sh.stop;
+      info.ipm_iters = its - 1;
+      info.correctors = sh.correctors;
+      info.pcg_iters = pcg_total;
+      info.n_mat = nmat;
+      info.rel_gap = sh.rel_gap;
+      info.dual_res = sqrt(t[0]) / (1.0 + sh.cn);
+      info.kkt_rel = sqrt(t[1]) / (1.0 + sqrt(t[2]));
+      info.primal_obj = sh.P_obj;
+      *pd.info = info;
+      if (info.status != MFIPM_OK) atomicCAS(a.err, 0, info.status);
+    }
+  });
 }
 
-template <int G, class Op, class PS>
+// Persistent solver kernel.  Phase 1: whole clusters take problems [0, nbig) from queue[0]
+// (the problems whose vectors need the shared memory of G CTAs).  Phase 2: every CTA on its
+// own takes problems [nbig, batch) from queue[1] and solves them with no cross-CTA traffic
+// (one problem per CTA uses the SMs more efficiently than a cluster per problem).  There is
+// no grid-wide barrier between the phases: a cluster that runs out of large problems
+// starts on small ones while others finish theirs.
+template <int G, class Op, class Op1, class PS>
 __global__ void __launch_bounds__(kThreads, 1) ipm_kernel(KernelArgs a) {
   extern __shared__ __align__(256) unsigned char smem[];
   __shared__ RedSmem rs;
+  __shared__ IpmShared<PS> sh;
   int par = 0;
   int rank = 0;
   if constexpr (G > 1) rank = (int)cg::this_cluster().block_rank();
@@ -836,19 +886,31 @@ __global__ void __launch_bounds__(kThreads, 1) ipm_kernel(KernelArgs a) {
     } else {
       pid = cg::this_cluster().map_shared_rank(&rs, 0)->fetched;
     }
-    if (pid >= a.batch) break;
+    if (pid >= a.nbig) break;
     const ProbDesc pd = a.probs[pid];
     Op op;
     op.init(pd, a, smem, rank);
-    solve_one<G, Op, PS>(pd, a, op, rs, par);
+    solve_one<G, Op, PS>(pd, a, op, rs, sh, par);
     cluster_barrier<G>();
+  }
+  cluster_barrier<G>();  // every CTA has read rank 0's last fetch before it is reused
+  for (;;) {
+    if (threadIdx.x == 0) rs.fetched = a.nbig + atomicAdd(a.queue + 1, 1);
+    __syncthreads();
+    const int pid = rs.fetched;
+    if (pid >= a.batch) break;
+    const ProbDesc pd = a.probs[pid];
+    Op1 op;
+    op.init(pd, a, smem, 0);
+    solve_one<1, Op1, PS>(pd, a, op, rs, sh, par);
+    __syncthreads();
   }
   cluster_barrier<G>();  // no CTA leaves while another may still read its shared memory
 }
 
-template <int G, class Op, class PS>
+template <int G, class Op, class Op1, class PS>
 inline cudaError_t launch_t(const KernelArgs& a, size_t smem, int grid_clusters, cudaStream_t st) {
-  auto kern = ipm_kernel<G, Op, PS>;
+  auto kern = ipm_kernel<G, Op, Op1, PS>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   if (G > 8) {
@@ -870,9 +932,9 @@ inline cudaError_t launch_t(const KernelArgs& a, size_t smem, int grid_clusters,
   return cudaLaunchKernelEx(&cfg, kern, a);
 }
 
-template <int G, class Op, class PS>
+template <int G, class Op, class Op1, class PS>
 inline int occupancy_t(size_t smem) {
-  auto kern = ipm_kernel<G, Op, PS>;
+  auto kern = ipm_kernel<G, Op, Op1, PS>;
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
   if (G > 8 && cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) return 0;
   cudaLaunchConfig_t cfg = {};
