@@ -69,15 +69,16 @@ typedef enum { MFIPM_A_F64 = 0, MFIPM_A_F32 = 1, MFIPM_A_BF16 = 2 } mfipm_a_dtyp
  *                        accumulation; float32 PCG. */
 typedef enum { MFIPM_PREC_FP64 = 0, MFIPM_PREC_FP32_PCG = 1, MFIPM_PREC_BF16_A = 2 } mfipm_precision;
 
-/* Arithmetic of the partial-DCT residual A^T(Ax - b) of the outer loop (the FFT chain that
- * corrects the inexact float32 Newton directions).
- *   MFIPM_RESID_DF    double-float: each value is a sum of two float32 words (about 48
- *                     significant bits, relative error of the transform ~1e-13), evaluated on
- *                     the float32 pipes.  GB300 runs float64 at 1/64 of the float32 rate.
- *   MFIPM_RESID_FP64  native float64.
- * The iterate (z, s), x = u - v and the dual-residual terms tau +/- g are float64 in both
- * modes; dense operators always use float64. */
-typedef enum { MFIPM_RESID_DF = 0, MFIPM_RESID_FP64 = 1 } mfipm_residual;
+/* Arithmetic of the outer IPM loop of the partial-DCT solver: the iterate (z, s) and its
+ * update, x = u - v, the residual A^T(Ax - b) (the FFT chain that corrects the inexact
+ * float32 Newton directions) and the dual-residual terms tau +/- g.
+ *   MFIPM_OUTER_DF    double-float: every value is the sum of two float32 words (about 48
+ *                     significant bits; relative rounding ~1e-14), computed on the float32
+ *                     pipes.  GB300 runs float64 at 1/64 of its float32 rate.
+ *   MFIPM_OUTER_FP64  native float64.
+ * Scalar reductions (gap, mu, step lengths) are float64 in both modes, and the outputs
+ * (x, zs_out, info) are float64.  Dense operators always use MFIPM_OUTER_FP64. */
+typedef enum { MFIPM_OUTER_DF = 0, MFIPM_OUTER_FP64 = 1 } mfipm_outer;
 
 typedef struct {
   int32_t kind;          /* mfipm_op_kind */
@@ -101,7 +102,7 @@ typedef struct {
   int32_t precision;     /* mfipm_precision; MFIPM_PREC_FP32_PCG for the DCT, MFIPM_PREC_FP64 dense */
   int32_t equal_steps;   /* 0: separate primal and dual steps as in Sec. 5.1; 1: common step */
   int32_t cluster_size;  /* CTAs that cooperate on one problem (1,2,4,8,16); 0 = automatic */
-  int32_t residual;      /* mfipm_residual; MFIPM_RESID_DF */
+  int32_t outer;         /* mfipm_outer; MFIPM_OUTER_DF */
 } mfipm_params;
 
 typedef struct {

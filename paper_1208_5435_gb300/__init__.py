@@ -35,7 +35,7 @@ class SolverParams:
     precision: Optional[int] = None   # None: FP32 PCG for the DCT, FP64 for dense A
     equal_steps: int = 0
     cluster_size: int = 0
-    residual: int = 0                 # 0: double-float partial-DCT residual, 1: native float64
+    outer: int = 0                    # partial DCT outer loop: 0 double-float, 1 native float64
 
     def to_c(self, default_precision: int) -> C.Params:
         p = C.Params()

@@ -12,7 +12,7 @@ STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "NOT_CONVERGED", 3: "NUMERIC", 4: 
 OP_DENSE, OP_PARTIAL_DCT = 0, 1
 A_F64, A_F32, A_BF16 = 0, 1, 2
 PREC_FP64, PREC_FP32_PCG, PREC_BF16_A = 0, 1, 2
-RESID_DF, RESID_FP64 = 0, 1
+OUTER_DF, OUTER_FP64 = 0, 1
 
 
 class Operator(ctypes.Structure):
@@ -26,7 +26,7 @@ class Params(ctypes.Structure):
                 ("max_iter_pcg", ctypes.c_int32), ("sigma1", ctypes.c_double), ("sigma2", ctypes.c_double),
                 ("sigma3", ctypes.c_double), ("alpha_bar", ctypes.c_double), ("alpha_tilde", ctypes.c_double),
                 ("eta", ctypes.c_double), ("precision", ctypes.c_int32), ("equal_steps", ctypes.c_int32),
-                ("cluster_size", ctypes.c_int32), ("residual", ctypes.c_int32)]
+                ("cluster_size", ctypes.c_int32), ("outer", ctypes.c_int32)]
 
 
 class Info(ctypes.Structure):

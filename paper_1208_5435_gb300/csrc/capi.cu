@@ -87,8 +87,8 @@ int validate_params(const mfipm_params* p) {
   if (!(p->sigma1 >= 0 && p->sigma2 >= 0 && p->sigma3 >= 0 && p->sigma1 <= 1 && p->sigma2 <= 1 && p->sigma3 <= 1))
     return fail(MFIPM_INVALID_ARG, "params: sigma values must lie in [0,1]");
   if (p->precision < 0 || p->precision > 2) return fail(MFIPM_INVALID_ARG, "params: bad precision %d", p->precision);
-  if (p->residual != MFIPM_RESID_DF && p->residual != MFIPM_RESID_FP64)
-    return fail(MFIPM_INVALID_ARG, "params: bad residual mode %d", p->residual);
+  if (p->outer != MFIPM_OUTER_DF && p->outer != MFIPM_OUTER_FP64)
+    return fail(MFIPM_INVALID_ARG, "params: bad outer-loop arithmetic %d", p->outer);
   const int cs = p->cluster_size;
   if (!(cs == 0 || cs == 1 || cs == 2 || cs == 4 || cs == 8 || cs == 16))
     return fail(MFIPM_INVALID_ARG, "params: cluster_size must be 0,1,2,4,8,16");
@@ -108,7 +108,7 @@ SolveParams to_solve(const mfipm_params* p) {
   s.max_iter = p->max_iter;
   s.max_iter_pcg = p->max_iter_pcg;
   s.equal_steps = p->equal_steps;
-  s.resid_fp64 = p->residual == MFIPM_RESID_FP64;
+  s.resid_fp64 = p->outer == MFIPM_OUTER_FP64;
   return s;
 }
 
@@ -328,7 +328,9 @@ int run(Prepared& P, cudaStream_t st, int batch, mfipm_info* infos, const std::v
     for (int i = 0; i < batch; ++i) nbig += sorted[i].n > small_max;
   }
   P.args.nbig = nbig;
-  int maxc = P.dct ? max_active_clusters_dct(P.G, P.max_n) : max_active_clusters_dense(P.G, P.pcg64, P.max_n, P.max_m);
+  const bool f64 = P.args.prm.resid_fp64 != 0;
+  int maxc = P.dct ? (f64 ? max_active_clusters_dct_f64(P.G, P.max_n) : max_active_clusters_dct_df(P.G, P.max_n))
+                   : max_active_clusters_dense(P.G, P.pcg64, P.max_n, P.max_m);
   if (maxc < 1) return fail(MFIPM_UNSUPPORTED, "no resident cluster of size %d fits this problem", P.G);
   const int clusters = std::min(maxc, std::max(nbig, (batch + P.G - 1) / P.G));
   if (g_timing) {
@@ -336,7 +338,8 @@ int run(Prepared& P, cudaStream_t st, int batch, mfipm_info* infos, const std::v
       if (!ev && (e = cudaEventCreate(&ev)) != cudaSuccess) return cuda_fail(e, "timing event");
     cudaEventRecord(g_ev[0], st);
   }
-  e = P.dct ? launch_dct_solver(P.G, P.args, P.max_n, clusters, st)
+  e = P.dct ? (f64 ? launch_dct_solver_f64(P.G, P.args, P.max_n, clusters, st)
+                   : launch_dct_solver_df(P.G, P.args, P.max_n, clusters, st))
             : launch_dense_solver(P.G, P.pcg64, P.args, P.max_n, P.max_m, clusters, st);
   if (e != cudaSuccess) return cuda_fail(e, "solver launch");
   if (g_timing) cudaEventRecord(g_ev[1], st);

@@ -59,10 +59,12 @@ struct KernelArgs {
 // Launchers implemented in solver.cu.  Return cudaError_t of the launch.
 cudaError_t launch_twiddles(double2* tw64, float2* tw32, float4* twdf, int log2_tw, cudaStream_t st);
 cudaError_t launch_dct_setup(const ProbDesc* probs_dev, int batch, int64_t max_n, int* err, cudaStream_t st);
-cudaError_t launch_dct_solver(int G, const KernelArgs& a, int64_t max_n, int grid_clusters, cudaStream_t st);
+cudaError_t launch_dct_solver_df(int G, const KernelArgs& a, int64_t max_n, int grid_clusters, cudaStream_t st);
+cudaError_t launch_dct_solver_f64(int G, const KernelArgs& a, int64_t max_n, int grid_clusters, cudaStream_t st);
 cudaError_t launch_dense_solver(int G, bool fp64_pcg, const KernelArgs& a, int64_t max_n, int64_t max_m,
                                 int grid_clusters, cudaStream_t st);
-int max_active_clusters_dct(int G, int64_t max_n);
+int max_active_clusters_dct_df(int G, int64_t max_n);
+int max_active_clusters_dct_f64(int G, int64_t max_n);
 int max_active_clusters_dense(int G, bool fp64_pcg, int64_t max_n, int64_t max_m);
 size_t dct_smem_bytes(int G, int64_t max_n);
 size_t dense_smem_bytes(int G, bool fp64_pcg, int64_t max_n, int64_t max_m);

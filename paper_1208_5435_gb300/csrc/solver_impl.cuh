@@ -31,6 +31,8 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "device_common.cuh"
 #include "internal.h"
 
@@ -270,7 +272,6 @@ template <int G> struct DctOp {
   int64_t chunk, gbase;
   double rho;
   int rank;
-  int resid_fp64;
 
   __device__ void init(const ProbDesc& pd, const KernelArgs& a, unsigned char* smem, int rank_) {
     rank = rank_;
@@ -282,7 +283,6 @@ template <int G> struct DctOp {
     geo.mask = pd.mask;
     geo.bsu = pd.bsu;
     geo.bsu_df = pd.bsu_df;
-    resid_fp64 = a.prm.resid_fp64;
     const int64_t M = (int64_t)1 << geo.logM;
     buf64 = reinterpret_cast<double2*>(smem);
     buf32 = reinterpret_cast<float2*>(smem + (size_t)16 * M);
@@ -294,29 +294,18 @@ template <int G> struct DctOp {
     rho = (double)pd.m / (double)pd.n;  // A A^T = I: rho = m/n (Eq. eq:ne2_P)
   }
   __device__ __forceinline__ bool valid(int64_t) const { return true; }
-  __device__ __forceinline__ double* r64() const { return reinterpret_cast<double*>(buf64); }
+  // residual buffer: this CTA's chunk of x (in) / A^T(Ax - b) (out), one value per storage
+  // position, as float64 or as double-float (both 16 bytes per complex pair)
+  template <class T> __device__ __forceinline__ T* rbuf() const { return reinterpret_cast<T*>(buf64); }
   template <class PS> __device__ __forceinline__ PS* wbuf() const { return reinterpret_cast<PS*>(buf32); }
-  // r64() := A^T (A r64() - b); returns share of ||A x - b||^2.  Evaluated in double-float
-  // (float32 pipes, ~48-bit significand) unless the float64 residual is selected; the
-  // buffer is converted in place (a double2 and a double-float complex are both 16 bytes).
-  __device__ double resid() {
-    if (resid_fp64) return dct_chain<G, double2, MODE_RESID>(buf64, geo, tw64);
-    dfc* bd = reinterpret_cast<dfc*>(buf64);
-    const int64_t M = chunk >> 1;
-    for (int64_t i = threadIdx.x; i < M; i += kThreads) {
-      const double2 v = buf64[i];
-      bd[i] = dfc{to_df(v.x), to_df(v.y)};
+  // rbuf := A^T (A rbuf - b); returns this CTA's share of ||A x - b||^2
+  template <class T> __device__ double resid_t() {
+    if constexpr (std::is_same<T, df>::value) {
+      return dct_chain<G, dfc, MODE_RESID>(reinterpret_cast<dfc*>(buf64), geo, twdf);
+    } else {
+      return dct_chain<G, double2, MODE_RESID>(buf64, geo, tw64);
     }
-    __syncthreads();
-    const double acc = dct_chain<G, dfc, MODE_RESID>(bd, geo, twdf);
-    for (int64_t i = threadIdx.x; i < M; i += kThreads) {
-      const dfc v = bd[i];
-      buf64[i] = make_double2(to_double(v.x), to_double(v.y));
-    }
-    __syncthreads();
-    return acc;
   }
-  // r32() := A^T A r32(); returns share of ||A w||^2
   template <class PS> __device__ double normal(PS*) { return dct_chain<G, float2, MODE_NORMAL>(buf32, geo, tw32); }
   __device__ int64_t natural(int64_t q) const { return dct_natural_index(gbase + q, geo.logM, G); }
   template <int GG> __device__ void setup(RedSmem&, int&) {}
@@ -354,7 +343,10 @@ template <int G> struct DenseOp {
     b = pd.b;
   }
   __device__ __forceinline__ bool valid(int64_t q) const { return gbase + q < n; }
-  __device__ __forceinline__ double* r64() const { return buf64; }
+  template <class T> __device__ __forceinline__ T* rbuf() const {
+    static_assert(std::is_same<T, double>::value, "dense operators keep a float64 iterate");
+    return reinterpret_cast<T*>(buf64);
+  }
   template <class PS> __device__ __forceinline__ PS* wbuf() const { return reinterpret_cast<PS*>(bufP); }
   __device__ __forceinline__ int64_t natural(int64_t q) const { return gbase + q; }
 
@@ -398,7 +390,7 @@ template <int G> struct DenseOp {
     __syncthreads();
     return acc;
   }
-  __device__ double resid() { return chain<double, MODE_RESID>(buf64); }
+  template <class T> __device__ double resid_t() { return chain<double, MODE_RESID>(buf64); }
   template <class PS> __device__ double normal(PS* v) { return chain<PS, MODE_NORMAL>(v); }
 
   // rho = ||A||_F^2 / n: the Frobenius-closest multiple of I to A^T A (equals m/n when
@@ -458,17 +450,68 @@ __device__ __forceinline__ Dir<H> direction(H z, H s, H dz1, H dz2, const ScH<H>
   return r;
 }
 
+// ------------------------------------------------------------------ iterate storage
+// The iterate z = [u; v], s = [s_u; s_v] is kept per index as {u, v, s_u, s_v} (32 bytes)
+// either in float64 (StateF64) or in double-float (StateDF: two float32 words per value,
+// about 48 significant bits, all arithmetic on the float32 pipes).  Both policies expose
+// the same operations on their component type T.
+struct StateF64 {
+  using T = double;
+  struct Q { double u, v, su, sv; };
+  __device__ static __forceinline__ Q load(const void* zs, int64_t gi) {
+    const double2* p = static_cast<const double2*>(zs) + 2 * gi;
+    const double2 z = p[0], s = p[1];
+    return Q{z.x, z.y, s.x, s.y};
+  }
+  __device__ static __forceinline__ void store(void* zs, int64_t gi, const Q& q) {
+    double2* p = static_cast<double2*>(zs) + 2 * gi;
+    p[0] = make_double2(q.u, q.v);
+    p[1] = make_double2(q.su, q.sv);
+  }
+  __device__ static __forceinline__ float hf(double a) { return (float)a; }
+  __device__ static __forceinline__ double axpy(double z, double a, float d) { return fma(a, (double)d, z); }
+  __device__ static __forceinline__ double sub(double a, double b) { return a - b; }
+  __device__ static __forceinline__ double add(double a, double b) { return a + b; }
+  __device__ static __forceinline__ bool positive(double a) { return a > 0.0; }
+  __device__ static __forceinline__ double scale(double a, double k) { return a * k; }
+  __device__ static __forceinline__ double from_d(double a) { return a; }
+  __device__ static __forceinline__ double to_d(double a) { return a; }
+};
+struct StateDF {
+  using T = df;
+  struct Q { df u, v, su, sv; };
+  __device__ static __forceinline__ Q load(const void* zs, int64_t gi) {
+    const float4* p = static_cast<const float4*>(zs) + 2 * gi;
+    const float4 z = p[0], s = p[1];
+    return Q{df(z.x, z.y), df(z.z, z.w), df(s.x, s.y), df(s.z, s.w)};
+  }
+  __device__ static __forceinline__ void store(void* zs, int64_t gi, const Q& q) {
+    float4* p = static_cast<float4*>(zs) + 2 * gi;
+    p[0] = make_float4(q.u.hi, q.u.lo, q.v.hi, q.v.lo);
+    p[1] = make_float4(q.su.hi, q.su.lo, q.sv.hi, q.sv.lo);
+  }
+  __device__ static __forceinline__ float hf(df a) { return a.hi; }
+  __device__ static __forceinline__ df axpy(df z, df a, float d) { return z + a * df(d); }
+  __device__ static __forceinline__ df sub(df a, df b) { return a - b; }
+  __device__ static __forceinline__ df add(df a, df b) { return a + b; }
+  __device__ static __forceinline__ bool positive(df a) { return a.hi > 0.f; }
+  __device__ static __forceinline__ df scale(df a, df k) { return a * k; }
+  __device__ static __forceinline__ df from_d(double a) { return to_df(a); }
+  __device__ static __forceinline__ double to_d(df a) { return to_double(a); }
+};
+
 // Scalars of one solve, written by thread 0 inside cluster_reduce and read by every
 // thread after its closing barrier (identical in all CTAs of the cluster).
-template <class H> struct IpmShared {
+template <class H, class T> struct IpmShared {
   double mu, sigma, alpha_p, alpha_d, mu_t, alpha_p1, alpha_d1, prev_ap, prev_ad;
   double rel_gap, P_obj, cn, rz0, rz;
+  T apT, adT, ap1T, ad1T, tauT, keepT;  // step lengths etc. in the iterate's arithmetic
   H smu, ap1, ad1, s3mut, apH, adH, alpha, beta;
   int corr, corr_next, stop, pcg_stop, correctors;
 };
 
-template <class H>
-__device__ __forceinline__ ScH<H> steering(const IpmShared<H>& sh, bool corr) {
+template <class H, class T>
+__device__ __forceinline__ ScH<H> steering(const IpmShared<H, T>& sh, bool corr) {
   ScH<H> c;
   c.smu = sh.smu;
   c.ap1 = sh.ap1;
@@ -478,24 +521,27 @@ __device__ __forceinline__ ScH<H> steering(const IpmShared<H>& sh, bool corr) {
   return c;
 }
 
-template <int G, class Op, class PS>
-__device__ void solve_one(const ProbDesc& pd, const KernelArgs& a, Op& op, RedSmem& rs, IpmShared<PS>& sh,
-                          int& par) {
+template <int G, class Op, class PS, class S>
+__device__ void solve_one(const ProbDesc& pd, const KernelArgs& a, Op& op, RedSmem& rs,
+                          IpmShared<PS, typename S::T>& sh, int& par) {
   using P2 = typename V2<PS>::T;
   using H = PS;
+  using T = typename S::T;
+  using Q = typename S::Q;
   const SolveParams& prm = a.prm;
   const int tid = threadIdx.x;
   const int64_t n = pd.n;
   const double tau = pd.tau;
   const int64_t chunk = op.chunk, gb = op.gbase;
-  double2* __restrict__ zs = reinterpret_cast<double2*>(pd.zs);
+  void* __restrict__ zs = pd.zs;
   P2* __restrict__ X1 = reinterpret_cast<P2*>(pd.pcg);
   P2* __restrict__ X2 = X1 + n;
   P2* __restrict__ Rv = X2 + n;
   P2* __restrict__ Pv = Rv + n;
   P2* __restrict__ Dv = Pv + n;
-  double* __restrict__ g64 = op.r64();
+  T* __restrict__ gbuf = op.template rbuf<T>();
   PS* __restrict__ w = op.template wbuf<PS>();
+  const T zeroT = S::from_d(0.0);
   int64_t nmat = 0;
   int pcg_total = 0, it = 0;
 
@@ -503,20 +549,26 @@ __device__ void solve_one(const ProbDesc& pd, const KernelArgs& a, Op& op, RedSm
   const PS rho = (PS)op.rho;
 
   // ||c||^2 = sum 2 tau^2 + 2 (A^T b)_i^2 with A^T b = -A^T (A 0 - b)  (c: Sec. 3)
-  for (int64_t q = tid; q < chunk; q += kThreads) g64[q] = 0.0;
+  for (int64_t q = tid; q < chunk; q += kThreads) gbuf[q] = zeroT;
   __syncthreads();
   {
-    const double bb = op.resid();
+    const double bb = op.template resid_t<T>();
     ++nmat;
     double atb2 = 0.0;
     for (int64_t q = tid; q < chunk; q += kThreads)
-      if (op.valid(q)) atb2 += g64[q] * g64[q];
+      if (op.valid(q)) {
+        const double g = S::to_d(gbuf[q]);
+        atb2 += g * g;
+      }
     double v[2] = {atb2, bb};
     cluster_reduce<G, 2>(rs, par, v, [&](const double (&t)[2]) {
       sh.cn = sqrt(2.0 * (double)n * tau * tau + 2.0 * t[0]);
       sh.alpha_p = sh.alpha_d = 1.0;
       sh.prev_ap = sh.prev_ad = 1.0;
       sh.apH = sh.adH = (H)1;
+      sh.apT = sh.adT = S::from_d(1.0);
+      sh.tauT = S::from_d(tau);
+      sh.keepT = S::from_d(1.0 - prm.eta);
       sh.corr = sh.corr_next = 0;
       sh.correctors = 0;
       sh.stop = 0;
@@ -524,6 +576,7 @@ __device__ void solve_one(const ProbDesc& pd, const KernelArgs& a, Op& op, RedSm
       sh.P_obj = 0.0;
     });
   }
+  const T tauT = sh.tauT, keepT = sh.keepT;
 
   // PCG on (Theta^-1 + F F^T) dz = rhs (Sec. 4).  On entry r = rhs and p = P^-1 r are
   // stored, the operator input w = p_u - p_v is in the shared buffer, and rz_part, pdp_part
@@ -607,7 +660,7 @@ __device__ void solve_one(const ProbDesc& pd, const KernelArgs& a, Op& op, RedSm
     pcg_total += k;
   };
 
-  // PCG initialisation: r = rhs (from rhs_fn(q, gi, z, s) in precision H), p = P^-1 r,
+  // PCG initialisation: r = rhs (from rhs_fn(q, gi, state) in precision H), p = P^-1 r,
   // w = p_u - p_v.  Writes Theta^-1 = s/z when write_d.
   auto pcg_init = [&](auto rhs_fn, bool write_d, PS& rz_part, PS& pdp_part) {
     rz_part = 0;
@@ -616,16 +669,16 @@ __device__ void solve_one(const ProbDesc& pd, const KernelArgs& a, Op& op, RedSm
     for (int64_t q = tid; q < chunk; q += kThreads) {
       if (!op.valid(q)) { w[q] = (PS)0; continue; }
       const int64_t gi = gb + q;
-      const double2 z = zs[2 * gi], s = zs[2 * gi + 1];
+      const Q st = S::load(zs, gi);
       P2 d;
       if (write_d) {
-        d.x = (H)s.x * rcpH((H)z.x);
-        d.y = (H)s.y * rcpH((H)z.y);
+        d.x = (H)S::hf(st.su) * rcpH((H)S::hf(st.u));
+        d.y = (H)S::hf(st.sv) * rcpH((H)S::hf(st.v));
         Dv[gi] = d;
       } else {
         d = Dv[gi];
       }
-      const P2 r = rhs_fn(q, gi, z, s);
+      const P2 r = rhs_fn(q, gi, st);
       const P2 p = precond<PS>(d, r, rho);
       Rv[gi] = r;
       Pv[gi] = p;
@@ -636,14 +689,14 @@ __device__ void solve_one(const ProbDesc& pd, const KernelArgs& a, Op& op, RedSm
     __syncthreads();
   };
 
-  auto load_dir = [&](int64_t gi, const double2& z, const double2& s, const ScH<H>& c, Dir<H>& du, Dir<H>& dv) {
+  auto load_dir = [&](int64_t gi, const Q& st, const ScH<H>& c, Dir<H>& du, Dir<H>& dv) {
     const P2 x1 = X1[gi];
     P2 x2;
     x2.x = (PS)0;
     x2.y = (PS)0;
     if (c.corr) x2 = X2[gi];
-    du = direction<H>((H)z.x, (H)s.x, x1.x, x2.x, c);
-    dv = direction<H>((H)z.y, (H)s.y, x1.y, x2.y, c);
+    du = direction<H>((H)S::hf(st.u), (H)S::hf(st.su), x1.x, x2.x, c);
+    dv = direction<H>((H)S::hf(st.v), (H)S::hf(st.sv), x1.y, x2.y, c);
   };
 
   // step lengths alpha = min(1, eta * min_{dv<0} -v/dv) for z and s (reading R4); then the
@@ -655,13 +708,13 @@ __device__ void solve_one(const ProbDesc& pd, const KernelArgs& a, Op& op, RedSm
     for (int64_t q = tid; q < chunk; q += kThreads) {
       if (!op.valid(q)) continue;
       const int64_t gi = gb + q;
-      const double2 z = zs[2 * gi], s = zs[2 * gi + 1];
+      const Q st = S::load(zs, gi);
       Dir<H> du, dv;
-      load_dir(gi, z, s, c, du, dv);
-      if (du.dz < (H)0) mp = fmin(mp, (H)z.x * rcpH(-du.dz));
-      if (dv.dz < (H)0) mp = fmin(mp, (H)z.y * rcpH(-dv.dz));
-      if (du.ds < (H)0) md = fmin(md, (H)s.x * rcpH(-du.ds));
-      if (dv.ds < (H)0) md = fmin(md, (H)s.y * rcpH(-dv.ds));
+      load_dir(gi, st, c, du, dv);
+      if (du.dz < (H)0) mp = fmin(mp, (H)S::hf(st.u) * rcpH(-du.dz));
+      if (dv.dz < (H)0) mp = fmin(mp, (H)S::hf(st.v) * rcpH(-dv.dz));
+      if (du.ds < (H)0) md = fmin(md, (H)S::hf(st.su) * rcpH(-du.ds));
+      if (dv.ds < (H)0) md = fmin(md, (H)S::hf(st.sv) * rcpH(-dv.ds));
     }
     H v[2] = {mp, md};
     cluster_reduce<G, 2, true>(rs, par, v, [&](const double (&t)[2]) {
@@ -672,12 +725,16 @@ __device__ void solve_one(const ProbDesc& pd, const KernelArgs& a, Op& op, RedSm
       sh.alpha_d = ad;
       sh.apH = (H)ap;
       sh.adH = (H)ad;
+      sh.apT = S::from_d(ap);
+      sh.adT = S::from_d(ad);
       sh.corr_next = corr ? 0 : (ap <= prm.alpha_tilde || ad <= prm.alpha_tilde);
       if (sh.corr_next) {
         sh.alpha_p1 = ap;
         sh.alpha_d1 = ad;
         sh.ap1 = (H)ap;
         sh.ad1 = (H)ad;
+        sh.ap1T = sh.apT;
+        sh.ad1T = sh.adT;
         ++sh.correctors;
       }
       sh.corr = corr;
@@ -691,41 +748,38 @@ __device__ void solve_one(const ProbDesc& pd, const KernelArgs& a, Op& op, RedSm
     H part[3] = {0, 0, 0};  // z.s, 1^T z, ||x||^2
     {
       const ScH<H> c = steering(sh, sh.corr != 0);
-      const double ap = sh.alpha_p, ad = sh.alpha_d;
+      const T apT = sh.apT, adT = sh.adT;
       const H apH = sh.apH, adH = sh.adH;
-      const double keep = 1.0 - prm.eta;
 #pragma unroll 2
       for (int64_t q = tid; q < chunk; q += kThreads) {
-        if (!op.valid(q)) { g64[q] = 0.0; continue; }
+        if (!op.valid(q)) { gbuf[q] = zeroT; continue; }
         const int64_t gi = gb + q;
-        double2 z, s;
+        Q st;
         H zu, zv, su, sv;
         if (it == 1) {
-          z = make_double2(1.0, 1.0);  // reading R3: z0 = s0 = 1
-          s = z;
+          const T one = S::from_d(1.0);  // reading R3: z0 = s0 = 1
+          st = Q{one, one, one, one};
           zu = zv = su = sv = (H)1;
         } else {
-          z = zs[2 * gi];
-          s = zs[2 * gi + 1];
+          const Q o = S::load(zs, gi);
           Dir<H> du, dv;
-          load_dir(gi, z, s, c, du, dv);
-          double nu = fma(ap, (double)du.dz, z.x), nv = fma(ap, (double)dv.dz, z.y);
-          double nsu = fma(ad, (double)du.ds, s.x), nsv = fma(ad, (double)dv.ds, s.y);
+          load_dir(gi, o, c, du, dv);
+          st.u = S::axpy(o.u, apT, du.dz);
+          st.v = S::axpy(o.v, apT, dv.dz);
+          st.su = S::axpy(o.su, adT, du.ds);
+          st.sv = S::axpy(o.sv, adT, dv.ds);
           // the step keeps z, s > 0 by construction; guard against a rounding-level crossing
-          if (!(nu > 0.0)) nu = z.x * keep;
-          if (!(nv > 0.0)) nv = z.y * keep;
-          if (!(nsu > 0.0)) nsu = s.x * keep;
-          if (!(nsv > 0.0)) nsv = s.y * keep;
-          zu = (H)z.x + apH * du.dz;
-          zv = (H)z.y + apH * dv.dz;
-          su = (H)s.x + adH * du.ds;
-          sv = (H)s.y + adH * dv.ds;
-          z = make_double2(nu, nv);
-          s = make_double2(nsu, nsv);
+          if (!S::positive(st.u)) st.u = S::scale(o.u, keepT);
+          if (!S::positive(st.v)) st.v = S::scale(o.v, keepT);
+          if (!S::positive(st.su)) st.su = S::scale(o.su, keepT);
+          if (!S::positive(st.sv)) st.sv = S::scale(o.sv, keepT);
+          zu = (H)S::hf(o.u) + apH * du.dz;
+          zv = (H)S::hf(o.v) + apH * dv.dz;
+          su = (H)S::hf(o.su) + adH * du.ds;
+          sv = (H)S::hf(o.sv) + adH * dv.ds;
         }
-        zs[2 * gi] = z;
-        zs[2 * gi + 1] = s;
-        g64[q] = z.x - z.y;
+        S::store(zs, gi, st);
+        gbuf[q] = S::sub(st.u, st.v);
         const H xh = zu - zv;
         part[0] += zu * su + zv * sv;
         part[1] += zu + zv;
@@ -733,8 +787,8 @@ __device__ void solve_one(const ProbDesc& pd, const KernelArgs& a, Op& op, RedSm
       }
     }
     __syncthreads();
-    // ---- float64 residual g = A^T (A x - b)  (f_z of Eq. fzfs needs F F^T z + c)
-    const double res2 = op.resid();
+    // ---- residual g = A^T (A x - b)  (f_z of Eq. fzfs needs F F^T z + c)
+    const double res2 = op.template resid_t<T>();
     nmat += 2;
     {
       double v[4] = {(double)part[0], (double)part[1], (double)part[2], res2};
@@ -758,11 +812,11 @@ __device__ void solve_one(const ProbDesc& pd, const KernelArgs& a, Op& op, RedSm
     {
       const H smuH = sh.smu;
       // rhs = f_z + Z^-1 f_s = sigma mu / z - (c + F F^T z) = sigma mu / z - [tau + g; tau - g]
-      pcg_init([&](int64_t q, int64_t, const double2& z, const double2&) {
-                 const double g = g64[q];
+      pcg_init([&](int64_t q, int64_t, const Q& st) {
+                 const T g = gbuf[q];
                  P2 r;
-                 r.x = smuH * rcpH((H)z.x) - (H)(tau + g);
-                 r.y = smuH * rcpH((H)z.y) - (H)(tau - g);
+                 r.x = smuH * rcpH((H)S::hf(st.u)) - (H)S::hf(S::add(tauT, g));
+                 r.y = smuH * rcpH((H)S::hf(st.v)) - (H)S::hf(S::sub(tauT, g));
                  return r;
                }, true, rzp, pdpp);
     }
@@ -773,22 +827,22 @@ __device__ void solve_one(const ProbDesc& pd, const KernelArgs& a, Op& op, RedSm
       H zts_t = 0;
       {
         const ScH<H> c = steering(sh, false);  // predictor direction only
-        const double ap1 = sh.alpha_p1;
+        const T ap1T = sh.ap1T;
 #pragma unroll 2
         for (int64_t q = tid; q < chunk; q += kThreads) {
-          if (!op.valid(q)) { g64[q] = 0.0; continue; }
+          if (!op.valid(q)) { gbuf[q] = zeroT; continue; }
           const int64_t gi = gb + q;
-          const double2 z = zs[2 * gi], s = zs[2 * gi + 1];
+          const Q st = S::load(zs, gi);
           Dir<H> du, dv;
-          load_dir(gi, z, s, c, du, dv);
-          g64[q] = fma(ap1, (double)du.dz, z.x) - fma(ap1, (double)dv.dz, z.y);
-          const H zu = (H)z.x + c.ap1 * du.dz, zv = (H)z.y + c.ap1 * dv.dz;
-          const H su = (H)s.x + c.ad1 * du.ds, sv = (H)s.y + c.ad1 * dv.ds;
+          load_dir(gi, st, c, du, dv);
+          gbuf[q] = S::sub(S::axpy(st.u, ap1T, du.dz), S::axpy(st.v, ap1T, dv.dz));
+          const H zu = (H)S::hf(st.u) + c.ap1 * du.dz, zv = (H)S::hf(st.v) + c.ap1 * dv.dz;
+          const H su = (H)S::hf(st.su) + c.ad1 * du.ds, sv = (H)S::hf(st.sv) + c.ad1 * dv.ds;
           zts_t += zu * su + zv * sv;
         }
       }
       __syncthreads();
-      op.resid();
+      op.template resid_t<T>();
       nmat += 2;
       {
         PS v[1] = {zts_t};
@@ -799,20 +853,20 @@ __device__ void solve_one(const ProbDesc& pd, const KernelArgs& a, Op& op, RedSm
       }
       {
         const ScH<H> c = steering(sh, false);
-        const double ad1 = sh.alpha_d1;
-        // rhs~ = f_z~ + Z^-1 f_s~ with f_z~ = s~ - [tau + g~; tau - g~] (float64),
+        const T ad1T = sh.ad1T;
+        // rhs~ = f_z~ + Z^-1 f_s~ with f_z~ = s~ - [tau + g~; tau - g~] (iterate arithmetic),
         // f_s~ = sigma3 mu~ - z~ s~
-        pcg_init([&](int64_t q, int64_t gi, const double2& z, const double2& s) {
-                   const double g = g64[q];
+        pcg_init([&](int64_t q, int64_t gi, const Q& st) {
+                   const T g = gbuf[q];
                    Dir<H> du, dv;
-                   load_dir(gi, z, s, c, du, dv);
-                   const H zu = (H)z.x + c.ap1 * du.dz, zv = (H)z.y + c.ap1 * dv.dz;
-                   const H su = (H)s.x + c.ad1 * du.ds, sv = (H)s.y + c.ad1 * dv.ds;
-                   const double fzu = fma(ad1, (double)du.ds, s.x) - (tau + g);
-                   const double fzv = fma(ad1, (double)dv.ds, s.y) - (tau - g);
+                   load_dir(gi, st, c, du, dv);
+                   const H zu = (H)S::hf(st.u) + c.ap1 * du.dz, zv = (H)S::hf(st.v) + c.ap1 * dv.dz;
+                   const H su = (H)S::hf(st.su) + c.ad1 * du.ds, sv = (H)S::hf(st.sv) + c.ad1 * dv.ds;
+                   const T fzu = S::sub(S::axpy(st.su, ad1T, du.ds), S::add(tauT, g));
+                   const T fzv = S::sub(S::axpy(st.sv, ad1T, dv.ds), S::sub(tauT, g));
                    P2 r;
-                   r.x = (H)fzu + (c.s3mut - zu * su) * rcpH((H)z.x);
-                   r.y = (H)fzv + (c.s3mut - zv * sv) * rcpH((H)z.y);
+                   r.x = (H)S::hf(fzu) + (c.s3mut - zu * su) * rcpH((H)S::hf(st.u));
+                   r.y = (H)S::hf(fzv) + (c.s3mut - zv * sv) * rcpH((H)S::hf(st.v));
                    return r;
                  }, false, rzp, pdpp);
       }
@@ -821,27 +875,28 @@ __device__ void solve_one(const ProbDesc& pd, const KernelArgs& a, Op& op, RedSm
     }
   }
 
-  // ---- exit: certificates and outputs (g64 holds A^T(Ax - b) of the final iterate)
+  // ---- exit: certificates and outputs in float64 (gbuf holds A^T(Ax - b) of the final iterate)
   double fin[3] = {0.0, 0.0, 0.0};  // ||f_z||^2, kkt^2, ||x||^2
   for (int64_t q = tid; q < chunk; q += kThreads) {
     if (!op.valid(q)) continue;
     const int64_t gi = gb + q;
-    const double2 z = zs[2 * gi], s = zs[2 * gi + 1];
-    const double g = g64[q];
-    const double fzu = s.x - (tau + g), fzv = s.y - (tau - g);
-    const double x = z.x - z.y;
+    const Q st = S::load(zs, gi);
+    const double g = S::to_d(gbuf[q]);
+    const double u = S::to_d(st.u), v = S::to_d(st.v), su = S::to_d(st.su), sv = S::to_d(st.sv);
+    const double fzu = su - (tau + g), fzv = sv - (tau - g);
+    const double x = S::to_d(S::sub(st.u, st.v));
     const double y = x - g;
-    const double st = copysign(fmax(fabs(y) - tau, 0.0), y);
+    const double sth = copysign(fmax(fabs(y) - tau, 0.0), y);
     fin[0] += fzu * fzu + fzv * fzv;
-    fin[1] += (x - st) * (x - st);
+    fin[1] += (x - sth) * (x - sth);
     fin[2] += x * x;
     const int64_t ni = op.natural(q);
     pd.x_out[ni] = x;
     if (pd.zs_out) {
-      pd.zs_out[ni] = z.x;
-      pd.zs_out[n + ni] = z.y;
-      pd.zs_out[2 * n + ni] = s.x;
-      pd.zs_out[3 * n + ni] = s.y;
+      pd.zs_out[ni] = u;
+      pd.zs_out[n + ni] = v;
+      pd.zs_out[2 * n + ni] = su;
+      pd.zs_out[3 * n + ni] = sv;
     }
   }
   const int its = it;
@@ -869,11 +924,11 @@ __device__ void solve_one(const ProbDesc& pd, const KernelArgs& a, Op& op, RedSm
 // (one problem per CTA uses the SMs more efficiently than a cluster per problem).  There is
 // no grid-wide barrier between the phases: a cluster that runs out of large problems
 // starts on small ones while others finish theirs.
-template <int G, class Op, class Op1, class PS>
+template <int G, class Op, class Op1, class PS, class S>
 __global__ void __launch_bounds__(kThreads, 1) ipm_kernel(KernelArgs a) {
   extern __shared__ __align__(256) unsigned char smem[];
   __shared__ RedSmem rs;
-  __shared__ IpmShared<PS> sh;
+  __shared__ IpmShared<PS, typename S::T> sh;
   int par = 0;
   int rank = 0;
   if constexpr (G > 1) rank = (int)cg::this_cluster().block_rank();
@@ -890,7 +945,7 @@ __global__ void __launch_bounds__(kThreads, 1) ipm_kernel(KernelArgs a) {
     const ProbDesc pd = a.probs[pid];
     Op op;
     op.init(pd, a, smem, rank);
-    solve_one<G, Op, PS>(pd, a, op, rs, sh, par);
+    solve_one<G, Op, PS, S>(pd, a, op, rs, sh, par);
     cluster_barrier<G>();
   }
   cluster_barrier<G>();  // every CTA has read rank 0's last fetch before it is reused
@@ -902,15 +957,15 @@ __global__ void __launch_bounds__(kThreads, 1) ipm_kernel(KernelArgs a) {
     const ProbDesc pd = a.probs[pid];
     Op1 op;
     op.init(pd, a, smem, 0);
-    solve_one<1, Op1, PS>(pd, a, op, rs, sh, par);
+    solve_one<1, Op1, PS, S>(pd, a, op, rs, sh, par);
     __syncthreads();
   }
   cluster_barrier<G>();  // no CTA leaves while another may still read its shared memory
 }
 
-template <int G, class Op, class Op1, class PS>
+template <int G, class Op, class Op1, class PS, class S>
 inline cudaError_t launch_t(const KernelArgs& a, size_t smem, int grid_clusters, cudaStream_t st) {
-  auto kern = ipm_kernel<G, Op, Op1, PS>;
+  auto kern = ipm_kernel<G, Op, Op1, PS, S>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   if (G > 8) {
@@ -932,9 +987,9 @@ inline cudaError_t launch_t(const KernelArgs& a, size_t smem, int grid_clusters,
   return cudaLaunchKernelEx(&cfg, kern, a);
 }
 
-template <int G, class Op, class Op1, class PS>
+template <int G, class Op, class Op1, class PS, class S>
 inline int occupancy_t(size_t smem) {
-  auto kern = ipm_kernel<G, Op, Op1, PS>;
+  auto kern = ipm_kernel<G, Op, Op1, PS, S>;
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
   if (G > 8 && cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) return 0;
   cudaLaunchConfig_t cfg = {};

@@ -157,12 +157,12 @@ def test_full_size_dct_65536_certificates():
 
 
 @pytest.mark.parametrize("n,G", [(1024, 4), (4096, 8), (4096, 1)])
-def test_dct_float64_residual_mode_matches_oracle_and_df_mode(n, G):
-    """The native float64 residual chain and the double-float one reach the same minimiser."""
+def test_dct_float64_outer_mode_matches_oracle_and_df_mode(n, G):
+    """The native float64 outer loop and the double-float one reach the same minimiser."""
     p = W.dct_problem(n, n // 4, max(1, n // 100), seed=77, j=n)
     xo = oracle_solution(p)
-    x64, info64 = gpu_solve(p, cluster_size=G, residual=1)
-    xdf, infodf = gpu_solve(p, cluster_size=G, residual=0)
+    x64, info64 = gpu_solve(p, cluster_size=G, outer=1)
+    xdf, infodf = gpu_solve(p, cluster_size=G, outer=0)
     assert info64["status"] == 0 and infodf["status"] == 0
     assert relx(x64, xo) <= RELX_TOL and relx(xdf, xo) <= RELX_TOL
     assert relx(xdf, x64) <= 1e-7
