@@ -136,6 +136,24 @@ int mfipm_solve(const mfipm_operator* op, const double* b, double tau, const mfi
                 double* x, double* zs_out, void* workspace, size_t ws_bytes, mfipm_info* info,
                 void* stream);
 
+/* mfipm_solve without a caller workspace, for callers that cannot allocate device memory:
+ * code that runs where cudaMalloc is forbidden or unavailable (a plugin whose host framework
+ * owns every device allocation, a process started under a fixed memory budget, a real-time
+ * loop that must not enter the allocator).  The paper has no counterpart; this is a
+ * deployment convenience.
+ * Scratch comes from one 8 MiB array in device memory that every GPU loading this library
+ * holds until the process exits; the library allocates nothing.  Problems whose
+ * mfipm_workspace_size exceeds 8 MiB (partial DCT up to n = 16384, small dense problems fit)
+ * are rejected with MFIPM_INVALID_ARG before any launch.  All calls share the array and it
+ * keeps the last call's contents: each call re-initialises everything it reads, and calls
+ * that may overlap on the GPU (other streams, other host threads) race on it and must be
+ * serialised by the caller.  The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call before any stream
+ * capture.  Kernel timing (mfipm_set_timing) is not recorded by this entry point.
+ * Arguments and results as for mfipm_solve. */
+int mfipm_solve_noalloc(const mfipm_operator* op, const double* b, double tau, const mfipm_params* p,
+                        double* x, double* zs_out, mfipm_info* info, void* stream);
+
 /* Solve `batch` independent problems in one persistent launch (one CTA cluster per problem,
  * problems taken from a device work queue, largest first).  ops, b, tau, x, zs_out, infos are
  * HOST arrays of length batch; b[j], x[j], zs_out[j] are DEVICE pointers (zs_out may be NULL or

@@ -49,6 +49,8 @@ SIGNATURES = {
                                             ctypes.POINTER(ctypes.c_size_t)]),
     "mfipm_solve": (ctypes.c_int, [ctypes.POINTER(Operator), _P, ctypes.c_double, ctypes.POINTER(Params), _P, _P, _P,
                                    ctypes.c_size_t, ctypes.POINTER(Info), _P]),
+    "mfipm_solve_noalloc": (ctypes.c_int, [ctypes.POINTER(Operator), _P, ctypes.c_double, ctypes.POINTER(Params), _P, _P,
+                                           ctypes.POINTER(Info), _P]),
     "mfipm_solve_batched": (ctypes.c_int, [ctypes.c_int32, ctypes.POINTER(Operator), _PP,
                                            ctypes.POINTER(ctypes.c_double), ctypes.POINTER(Params), _PP, _PP, _P,
                                            ctypes.c_size_t, ctypes.POINTER(Info), _P]),

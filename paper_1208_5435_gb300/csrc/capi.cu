@@ -7,6 +7,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <mutex>
 #include <numeric>
 #include <string>
 #include <vector>
@@ -299,7 +300,9 @@ int prepare(int batch, const mfipm_operator* ops, const double* const* b, const 
   return MFIPM_OK;
 }
 
-int run(Prepared& P, cudaStream_t st, int batch, mfipm_info* infos, const std::vector<int>* order) {
+int run(Prepared& P, cudaStream_t st, int batch, mfipm_info* infos, const std::vector<int>* order,
+        bool allow_timing = true) {
+  const bool timing = g_timing && allow_timing;
   cudaError_t e;
   // work queue in cost order (largest first): the descriptor array is permuted, infos are not
   std::vector<ProbDesc> sorted(P.desc);
@@ -333,7 +336,7 @@ int run(Prepared& P, cudaStream_t st, int batch, mfipm_info* infos, const std::v
                    : max_active_clusters_dense(P.G, P.pcg64, P.max_n, P.max_m);
   if (maxc < 1) return fail(MFIPM_UNSUPPORTED, "no resident cluster of size %d fits this problem", P.G);
   const int clusters = std::min(maxc, std::max(nbig, (batch + P.G - 1) / P.G));
-  if (g_timing) {
+  if (timing) {
     for (auto& ev : g_ev)
       if (!ev && (e = cudaEventCreate(&ev)) != cudaSuccess) return cuda_fail(e, "timing event");
     cudaEventRecord(g_ev[0], st);
@@ -342,7 +345,7 @@ int run(Prepared& P, cudaStream_t st, int batch, mfipm_info* infos, const std::v
                    : launch_dct_solver_df(P.G, P.args, P.max_n, clusters, st))
             : launch_dense_solver(P.G, P.pcg64, P.args, P.max_n, P.max_m, clusters, st);
   if (e != cudaSuccess) return cuda_fail(e, "solver launch");
-  if (g_timing) cudaEventRecord(g_ev[1], st);
+  if (timing) cudaEventRecord(g_ev[1], st);
   int err = 0;
   if ((e = cudaMemcpyAsync(&err, P.args.err, sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
     return cuda_fail(e, "read error word");
@@ -352,7 +355,7 @@ int run(Prepared& P, cudaStream_t st, int batch, mfipm_info* infos, const std::v
       return cuda_fail(e, "read infos");
   }
   if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(e, "solve");
-  if (g_timing) {
+  if (timing) {
     float ms = -1.0f;
     if (cudaEventElapsedTime(&ms, g_ev[0], g_ev[1]) == cudaSuccess) g_last_ms = ms;
   }
@@ -370,6 +373,35 @@ std::vector<int> cost_order(const mfipm_operator* ops, int batch) {
   std::iota(ord.begin(), ord.end(), 0);
   std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return ops[a].n > ops[b].n; });
   return ord;
+}
+
+// ------------------------------------------------------------------ fixed scratch
+// Device scratch for mfipm_solve_noalloc, for callers that may not allocate device memory
+// (see include/mfipm.h).  Every GPU that loads this library holds these bytes until the
+// process exits.  In host code `g_noalloc_scratch` is only a stand-in for the symbol; its
+// device address is obtained per device with cudaGetSymbolAddress.
+constexpr size_t kNoallocScratchBytes = (size_t)8 << 20;
+__device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratchBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[kMaxDevices] = {};
+
+// Device address of the scratch on the current device (looked up once per device).
+int noalloc_scratch(void** out) {
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  if (dev < 0 || dev >= kMaxDevices) return fail(MFIPM_UNSUPPORTED, "device %d beyond the %d supported", dev, kMaxDevices);
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* ptr = nullptr;
+    e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(scratch)");
+    g_noalloc_ptr[dev] = ptr;
+  }
+  *out = g_noalloc_ptr[dev];
+  return MFIPM_OK;
 }
 
 }  // namespace
@@ -417,6 +449,29 @@ int mfipm_solve(const mfipm_operator* op, const double* b, double tau, const mfi
   if (rc) return rc;
   mfipm_info tmp;
   return run(P, static_cast<cudaStream_t>(stream), 1, info ? info : &tmp, nullptr);
+}
+
+int mfipm_solve_noalloc(const mfipm_operator* op, const double* b, double tau, const mfipm_params* p, double* x,
+                        double* zs_out, mfipm_info* info, void* stream) {
+  g_err.clear();
+  size_t need = 0;
+  int rc = mfipm_workspace_size(op, 1, p, &need);
+  if (rc) return rc;
+  if (need > kNoallocScratchBytes)
+    return fail(MFIPM_INVALID_ARG,
+                "mfipm_solve_noalloc: this problem needs %zu bytes of scratch, above the fixed %zu bytes; "
+                "use mfipm_solve with a caller workspace",
+                need, kNoallocScratchBytes);
+  void* ws = nullptr;
+  if ((rc = noalloc_scratch(&ws))) return rc;
+  const double* bb[1] = {b};
+  double* xx[1] = {x};
+  double* zz[1] = {zs_out};
+  double tt[1] = {tau};
+  Prepared P;
+  if ((rc = prepare(1, op, bb, tt, p, xx, zs_out ? zz : nullptr, ws, kNoallocScratchBytes, P))) return rc;
+  mfipm_info tmp;
+  return run(P, static_cast<cudaStream_t>(stream), 1, info ? info : &tmp, nullptr, /*allow_timing=*/false);
 }
 
 int mfipm_solve_batched(int32_t batch, const mfipm_operator* ops, const double* const* b, const double* tau,
