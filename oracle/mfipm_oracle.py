@@ -412,3 +412,42 @@ def dual_gap_certificate(op: Operator, b, tau, x):
     P = tau * float(np.abs(x).sum()) + 0.5 * float(r @ r)
     D = -0.5 * float(nu @ nu) - float(b @ nu)
     return P, D
+
+
+# --------------------------------------------------------------------------------------
+# Derivatives of the solution map (b, tau, A) -> x*  (the paper has none; they follow from
+# differentiating the perturbed KKT conditions of Eq. fzfs at fixed mu)
+# --------------------------------------------------------------------------------------
+def adjoint_kkt(op: Operator, b, tau, z, s, grad_x):
+    """Reverse-mode derivative at an interior iterate (z, s): with
+    H = Theta^-1 + F F^T (Eq. eq:ne2_matrix) and J = [I; -I], dz = -H^-1 dc - H^-1 dQ z,
+    so for L with dL/dx = grad_x:  y = H^-1 J grad_x,  w = J^T y,
+      dL/db = A w,   dL/dtau = -1^T y,   dL/dA = r w^T - (A w) x^T,  r = b - A x.
+    H is solved exactly (Cholesky / Woodbury).  Returns (grad_b, grad_tau, grad_A or None)."""
+    n = op.n
+    d = s / z
+    y = solve_newton_direct(op, d, np.concatenate([grad_x, -grad_x]))
+    w = y[:n] - y[n:]
+    aw = op.mv(w)
+    grad_tau = -float(y.sum())
+    grad_A = None
+    if op.dense is not None:
+        x = z[:n] - z[n:]
+        r = b - op.mv(x)
+        grad_A = np.outer(r, w) - np.outer(aw, x)
+    return aw, grad_tau, grad_A
+
+
+def adjoint_support(A: np.ndarray, b, tau, x, grad_x, support_tol: float = 1e-7):
+    """The same derivatives from the closed form on the support S of x* (valid under strict
+    complementarity): x_S = (A_S^T A_S)^-1 (A_S^T b - tau sign(x_S)), x = 0 off S, so with
+    w_S = (A_S^T A_S)^-1 grad_x_S (w = 0 off S):  dL/db = A w,
+    dL/dtau = -sign(x_S)^T w_S,  dL/dA = r w^T - (A w) x^T."""
+    S = np.abs(x) > support_tol
+    AS = A[:, S]
+    wS = np.linalg.solve(AS.T @ AS, grad_x[S])
+    w = np.zeros_like(x)
+    w[S] = wS
+    aw = A @ w
+    r = b - A @ x
+    return aw, -float(np.sign(x[S]) @ wS), np.outer(r, w) - np.outer(aw, x)
