@@ -423,13 +423,24 @@ def adjoint_kkt(op: Operator, b, tau, z, s, grad_x):
     H = Theta^-1 + F F^T (Eq. eq:ne2_matrix) and J = [I; -I], dz = -H^-1 dc - H^-1 dQ z,
     so for L with dL/dx = grad_x:  y = H^-1 J grad_x,  w = J^T y,
       dL/db = A w,   dL/dtau = -1^T y,   dL/dA = r w^T - (A w) x^T,  r = b - A x.
-    H is solved exactly (Cholesky / Woodbury).  Returns (grad_b, grad_tau, grad_A or None)."""
+    H y = J grad_x is solved exactly by eliminating y_u + y_v (the reduction behind Theorem
+    thm:ne2_prec): ((Theta_u + Theta_v)^-1 + A^T A) w = grad_x, then
+    y_u = d_v w / (d_u + d_v), y_v = -d_u w / (d_u + d_v) with d = Theta^-1 = s/z.  Near the
+    solution Theta spans ~1e+-12 and this n x n system stays well conditioned where the
+    m x m Woodbury matrix I + A (Theta_u + Theta_v) A^T does not.
+    Returns (grad_b, grad_tau, grad_A or None)."""
     n = op.n
     d = s / z
-    y = solve_newton_direct(op, d, np.concatenate([grad_x, -grad_x]))
-    w = y[:n] - y[n:]
+    du, dv = d[:n], d[n:]
+    A = op.dense
+    K = A.T @ A
+    K[np.diag_indices_from(K)] += du * dv / (du + dv)
+    cf = scipy.linalg.cho_factor(K, lower=True, check_finite=False)
+    w = scipy.linalg.cho_solve(cf, grad_x, check_finite=False)
+    y_u = dv * w / (du + dv)
+    y_v = -du * w / (du + dv)
     aw = op.mv(w)
-    grad_tau = -float(y.sum())
+    grad_tau = -float(np.sum(y_u + y_v))
     grad_A = None
     if op.dense is not None:
         x = z[:n] - z[n:]
