@@ -164,17 +164,20 @@ int mfipm_solve_batched(int32_t batch, const mfipm_operator* ops, const double* 
                         double* const* zs_out, void* workspace, size_t ws_bytes,
                         mfipm_info* infos, void* stream);
 
-/* Reverse-mode derivative of the solution map (b, tau) -> x* of (1) at a solution returned by
- * mfipm_solve[_batched] (not in the paper, which has no derivative; derived from the
- * perturbed KKT conditions of Sec. 3, Eq. fzfs, at the final iterate).  Given grad_x = dL/dx*,
- * solves ((Theta_u + Theta_v)^-1 + A^T A) w = grad_x by PCG with the preconditioner
- * (Theta_u + Theta_v)^-1 + rho I (Lemma lem:ne2_prec) and returns
- *   grad_b = A w,   grad_tau = -sum_i (Theta_u - Theta_v)_i/(Theta_u + Theta_v)_i * (.)...
- * (exact formulas in the implementation's documentation).
- *   zs        DEVICE 4n: the zs_out of the forward solve.
+/* Reverse-mode derivative of the solution map (b, tau, A) -> x* of (1) at a solution returned by
+ * mfipm_solve[_batched] (the paper has no derivative).  Differentiating the perturbed KKT
+ * conditions Q z + c - s = 0, Z S e = mu e of Sec. 3, Eq. fzfs at the final iterate, with mu
+ * fixed, gives (Theta^-1 + F F^T) dz = -dc - dQ z.  Hence, for dL/dx* = grad_x and
+ * J = [I; -I]: y = H^-1 J grad_x is solved by the same PCG and preconditioner as a Newton
+ * system (tolerance min(tol_pcg, 1e-6)), w = y_u - y_v, and
+ *   grad_b = A w,   grad_tau = -sum(y),   grad_A = r w^T - (A w) x^T with r = b - A x.
+ * These are the derivatives of x* wherever its support is locally constant (strict
+ * complementarity).
+ *   x         DEVICE n: the forward solution.     zs  DEVICE 4n: the zs_out of the forward solve.
  *   grad_x    DEVICE n.   grad_b DEVICE m or NULL.   grad_tau HOST (batch) or NULL.
- *   grad_A    DEVICE m x n row-major or NULL (dense operators only).
- * Arrays are HOST arrays of DEVICE pointers, as in mfipm_solve_batched. */
+ *   grad_A    DEVICE m x n row-major or NULL (dense operators only; MFIPM_UNSUPPORTED otherwise).
+ * Arrays are HOST arrays of DEVICE pointers, as in mfipm_solve_batched; infos[i].pcg_iters and
+ * n_mat count the work of each derivative. */
 int mfipm_backward(int32_t batch, const mfipm_operator* ops, const double* const* b,
                    const double* tau, const double* const* x, const double* const* zs,
                    const double* const* grad_x, double* const* grad_b, double* grad_tau,

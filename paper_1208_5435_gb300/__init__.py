@@ -151,3 +151,40 @@ def solve_batched(ops: Sequence, bs: Sequence, taus: Sequence[float], params: Op
         C.check(rc, allow=(C.MFIPM_OK, C.MFIPM_NOT_CONVERGED))
     out = [i.as_dict() for i in infos]
     return (xs, out, zss) if return_zs else (xs, out)
+
+
+def backward(ops, bs, taus, xs, zss, grad_xs, params: Optional[SolverParams] = None, want_A: bool = False,
+             ws=None, stream=None):
+    """mfipm_backward for a list of problems (forward outputs xs and zss from solve(...,
+    return_zs=True)).  Returns (grad_bs, grad_taus, grad_As or None, infos)."""
+    torch = _torch()
+    params = params or SolverParams()
+    B = len(ops)
+    bs = [bb.to(device="cuda", dtype=torch.float64).contiguous() for bb in bs]
+    gxs = [g.to(device="cuda", dtype=torch.float64).contiguous() for g in grad_xs]
+    gbs = [torch.empty(o.m, dtype=torch.float64, device="cuda") for o in ops]
+    gAs = [torch.empty(o.m, o.n, dtype=torch.float64, device="cuda") for o in ops] if want_A else None
+    arr = (C.Operator * B)(*[o.c_op() for o in ops])
+    ptrs = lambda ts: (ctypes.c_void_p * B)(*[t.data_ptr() for t in ts])
+    tp = (ctypes.c_double * B)(*[float(t) for t in taus])
+    gtau = (ctypes.c_double * B)()
+    p = params.to_c(ops[0].default_precision)
+    if ws is None:
+        ws = _alloc_ws(workspace_bytes(ops, params))
+    infos = (C.Info * B)()
+    rc = lib().mfipm_backward(B, arr, ptrs(bs), tp, ptrs(xs), ptrs(zss), ptrs(gxs), ptrs(gbs), gtau,
+                              ptrs(gAs) if want_A else None, ctypes.byref(p), ws.data_ptr(), ws.numel(), infos,
+                              _stream_handle(stream))
+    C.check(rc)
+    return gbs, [gtau[i] for i in range(B)], gAs, [i.as_dict() for i in infos]
+
+
+def solve_differentiable(op, b, tau, params: Optional[SolverParams] = None):
+    """x* as a differentiable function of b, tau (and of A for a Dense operator whose A requires
+    grad): torch.autograd calls mfipm_backward, which solves the adjoint KKT system at the
+    solution with the same PCG (no unrolling of iterations)."""
+    from .autograd import MfipmFunction
+    torch = _torch()
+    tau_t = tau if torch.is_tensor(tau) else torch.tensor(float(tau), dtype=torch.float64)
+    A = op.A if isinstance(op, Dense) else None
+    return MfipmFunction.apply(b, tau_t, A, op, params or SolverParams())

@@ -134,7 +134,7 @@ size_t problem_bytes(const mfipm_operator& op, bool pcg64) {
 }
 
 struct Layout {
-  size_t off_hdr, off_tw64, off_tw32, off_twdf, off_desc, off_info, off_probs, total;
+  size_t off_hdr, off_tw64, off_tw32, off_twdf, off_desc, off_info, off_gtau, off_probs, total;
   int log2_tw;
 };
 
@@ -157,6 +157,8 @@ Layout make_layout(const mfipm_operator* ops, int batch, bool pcg64) {
   o += align256(sizeof(ProbDesc) * (size_t)batch);
   L.off_info = o;
   o += align256(sizeof(mfipm_info) * (size_t)batch);
+  L.off_gtau = o;
+  o += align256(sizeof(double) * (size_t)batch);
   L.off_probs = o;
   for (int i = 0; i < batch; ++i) o += problem_bytes(ops[i], pcg64);
   L.total = o;
@@ -282,7 +284,9 @@ int prepare(int batch, const mfipm_operator* ops, const double* const* b, const 
     q += align256(32 * n);
     d.pcg = ws + q;
     q += align256(5 * n * (P.pcg64 ? 16 : 8));
+    d.scratch = reinterpret_cast<double*>(ws + q);
     q += align256(8 * n);
+    d.grad_tau = reinterpret_cast<double*>(ws + P.lay.off_gtau) + i;
     d.info = info_dev + i;
     o += problem_bytes(op, P.pcg64);
   }
@@ -490,10 +494,65 @@ int mfipm_solve_batched(int32_t batch, const mfipm_operator* ops, const double* 
   return run(P, static_cast<cudaStream_t>(stream), batch, infos, &ord);
 }
 
-int mfipm_backward(int32_t, const mfipm_operator*, const double* const*, const double*, const double* const*,
-                   const double* const*, const double* const*, double* const*, double*, double* const*,
-                   const mfipm_params*, void*, size_t, mfipm_info*, void*) {
-  return fail(MFIPM_UNSUPPORTED, "mfipm_backward is not built yet");
+int mfipm_backward(int32_t batch, const mfipm_operator* ops, const double* const* b, const double* tau,
+                   const double* const* x, const double* const* zs, const double* const* grad_x,
+                   double* const* grad_b, double* grad_tau, double* const* grad_A, const mfipm_params* p,
+                   void* workspace, size_t ws_bytes, mfipm_info* infos, void* stream) {
+  g_err.clear();
+  if (!zs || !grad_x) return fail(MFIPM_INVALID_ARG, "zs and grad_x are required");
+  Prepared P;
+  int rc = prepare(batch, ops, b, tau, p, const_cast<double* const*>(x), nullptr, workspace, ws_bytes, P);
+  if (rc) return rc;
+  for (int i = 0; i < batch; ++i) {
+    if (!zs[i] || !grad_x[i]) return fail(MFIPM_INVALID_ARG, "zs[%d] or grad_x[%d] is NULL", i, i);
+    if (grad_A && grad_A[i] && ops[i].kind != MFIPM_OP_DENSE)
+      return fail(MFIPM_UNSUPPORTED, "grad_A is defined for dense operators only (operator %d)", i);
+    ProbDesc& d = P.desc[i];
+    d.zs_in = zs[i];
+    d.gx = grad_x[i];
+    d.x_in = x[i];
+    d.grad_b = grad_b ? grad_b[i] : nullptr;
+    d.grad_A = grad_A ? grad_A[i] : nullptr;
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaError_t e;
+  if ((e = cudaMemcpyAsync(P.ws + P.lay.off_desc, P.desc.data(), sizeof(ProbDesc) * batch, cudaMemcpyHostToDevice,
+                           st)) != cudaSuccess)
+    return cuda_fail(e, "upload descriptors");
+  if ((e = cudaMemsetAsync(P.ws + P.lay.off_hdr, 0, 256, st)) != cudaSuccess) return cuda_fail(e, "clear header");
+  if (P.dct) {
+    if ((e = launch_twiddles(const_cast<double2*>(P.args.tw64), const_cast<float2*>(P.args.tw32),
+                             const_cast<float4*>(P.args.twdf), P.args.log2_tw, st)) != cudaSuccess)
+      return cuda_fail(e, "twiddle kernel");
+    if ((e = launch_dct_setup(P.args.probs, batch, P.max_n, P.args.err, st)) != cudaSuccess)
+      return cuda_fail(e, "setup kernel");
+  }
+  const int maxc = P.dct ? max_active_clusters_bwd_dct(P.G, P.max_n)
+                         : max_active_clusters_bwd_dense(P.G, P.pcg64, P.max_n, P.max_m);
+  if (maxc < 1) return fail(MFIPM_UNSUPPORTED, "no resident cluster of size %d fits this problem", P.G);
+  const int clusters = std::min(maxc, batch);
+  e = P.dct ? launch_bwd_dct(P.G, P.args, P.max_n, clusters, st)
+            : launch_bwd_dense(P.G, P.pcg64, P.args, P.max_n, P.max_m, clusters, st);
+  if (e != cudaSuccess) return cuda_fail(e, "backward launch");
+  std::vector<double> gt(batch);
+  std::vector<mfipm_info> tmp;
+  if (!infos) {
+    tmp.resize(batch);
+    infos = tmp.data();
+  }
+  int err = 0;
+  if ((e = cudaMemcpyAsync(&err, P.args.err, sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(gt.data(), P.ws + P.lay.off_gtau, sizeof(double) * batch, cudaMemcpyDeviceToHost, st)) !=
+          cudaSuccess ||
+      (e = cudaMemcpyAsync(infos, P.ws + P.lay.off_info, sizeof(mfipm_info) * batch, cudaMemcpyDeviceToHost, st)) !=
+          cudaSuccess)
+    return cuda_fail(e, "read results");
+  if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(e, "backward");
+  if (err == -1) return fail(MFIPM_INVALID_ARG, "rows must be distinct, ascending and inside [0, n)");
+  if (err == -2) return fail(MFIPM_NUMERIC, "b contains a non-finite value");
+  if (grad_tau)
+    for (int i = 0; i < batch; ++i) grad_tau[i] = gt[i];
+  return MFIPM_OK;
 }
 
 int mfipm_apply_A(const mfipm_operator*, const double*, double*, void*, size_t, void*) {

@@ -38,6 +38,14 @@ struct ProbDesc {
   int64_t lda;
   // state
   double* zs;             // DEVICE 4n: per index {u, v, s_u, s_v}
+  double* scratch;        // DEVICE n doubles: operator output scratch
+  // mfipm_backward only
+  const double* zs_in;    // DEVICE 4n: final [u; v; s_u; s_v] of the forward solve (natural order)
+  const double* gx;       // DEVICE n: dL/dx
+  const double* x_in;     // DEVICE n: the forward solution (dense dL/dA)
+  double* grad_b;         // DEVICE m or null
+  double* grad_A;         // DEVICE m x n or null (dense)
+  double* grad_tau;       // DEVICE 1
   void* pcg;              // DEVICE 5 vectors of n pairs (x1, x2, r, p, d), float or double pairs
   mfipm_info* info;       // DEVICE
 };
@@ -68,6 +76,12 @@ int max_active_clusters_dct_f64(int G, int64_t max_n);
 int max_active_clusters_dense(int G, bool fp64_pcg, int64_t max_n, int64_t max_m);
 size_t dct_smem_bytes(int G, int64_t max_n);
 size_t dense_smem_bytes(int G, bool fp64_pcg, int64_t max_n, int64_t max_m);
+
+cudaError_t launch_bwd_dct(int G, const KernelArgs& a, int64_t max_n, int grid_clusters, cudaStream_t st);
+cudaError_t launch_bwd_dense(int G, bool fp64_pcg, const KernelArgs& a, int64_t max_n, int64_t max_m,
+                             int grid_clusters, cudaStream_t st);
+int max_active_clusters_bwd_dct(int G, int64_t max_n);
+int max_active_clusters_bwd_dense(int G, bool fp64_pcg, int64_t max_n, int64_t max_m);
 
 // Operator-only kernels for mfipm_apply_A / mfipm_apply_At / mfipm_kkt_residual:
 // mode 0 = A x (out m), 1 = A^T y (out n), 2 = kkt_rel (out 1 double, device).

@@ -60,7 +60,7 @@ size_t dct_smem_bytes(int G, int64_t max_n) {
 size_t dense_smem_bytes(int G, bool, int64_t max_n, int64_t max_m) {
   const int64_t chunk = (max_n + G - 1) / G;
   const size_t c8 = ((size_t)chunk * 8 + 255) & ~(size_t)255;
-  return 2 * c8 + 2 * (size_t)((max_m + 31) & ~31) * 8;
+  return 2 * c8 + 3 * (size_t)((max_m + 31) & ~31) * 8;
 }
 
 cudaError_t launch_twiddles(double2* tw64, float2* tw32, float4* twdf, int log2_tw, cudaStream_t st) {

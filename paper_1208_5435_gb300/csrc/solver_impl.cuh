@@ -307,6 +307,17 @@ template <int G> struct DctOp {
     }
   }
   template <class PS> __device__ double normal(PS*) { return dct_chain<G, float2, MODE_NORMAL>(buf32, geo, tw32); }
+  // grad_b = A w for w in rbuf<double>() (float64 chain): all n DCT coefficients go to
+  // pd.scratch, then the sampled rows are gathered.  Overwrites rbuf.
+  __device__ void apply_A_out(const ProbDesc& pd) {
+    dct_chain<G, double2, MODE_FORWARD>(buf64, geo, tw64, pd.scratch);
+    __threadfence();
+    cluster_barrier<G>();
+    if (pd.grad_b)
+      for (int64_t i = (int64_t)rank * kThreads + threadIdx.x; i < pd.m; i += (int64_t)G * kThreads)
+        pd.grad_b[i] = pd.scratch[pd.rows[i]];
+  }
+  __device__ void grad_A_out(const ProbDesc&, const void*) {}
   __device__ int64_t natural(int64_t q) const { return dct_natural_index(gbase + q, geo.logM, G); }
   template <int GG> __device__ void setup(RedSmem&, int&) {}
 };
@@ -322,6 +333,7 @@ template <int G> struct DenseOp {
   void* bufP;
   double* tpart;  // m: this CTA's partial A w
   double* tfull;  // m: reduced A w (identical in every CTA)
+  double* aw;     // m: A w kept by the backward
   const double* b;
   double rho;
   int rank;
@@ -340,6 +352,7 @@ template <int G> struct DenseOp {
     bufP = smem + c8;
     tpart = reinterpret_cast<double*>(smem + 2 * c8);
     tfull = tpart + ((m + 31) & ~31);
+    aw = tfull + ((m + 31) & ~31);
     b = pd.b;
   }
   __device__ __forceinline__ bool valid(int64_t q) const { return gbase + q < n; }
@@ -375,6 +388,7 @@ template <int G> struct DenseOp {
       if (rank == 0) acc += t * t;
     }
     __syncthreads();
+    if constexpr (MODE == MODE_FORWARD) return acc;
     // v = A[:, own]^T t
     for (int64_t j = threadIdx.x; j < cols; j += kThreads) {
       const double* Aj = A + gbase + j;
@@ -391,6 +405,28 @@ template <int G> struct DenseOp {
     return acc;
   }
   template <class T> __device__ double resid_t() { return chain<double, MODE_RESID>(buf64); }
+  // grad_b = A w for w in rbuf<double>(); keeps A w in aw for grad_A_out
+  __device__ void apply_A_out(const ProbDesc& pd) {
+    chain<double, MODE_FORWARD>(buf64);
+    for (int64_t i = threadIdx.x; i < m; i += kThreads) {
+      aw[i] = tfull[i];
+      if (pd.grad_b && rank == 0) pd.grad_b[i] = tfull[i];
+    }
+    __syncthreads();
+  }
+  // dL/dA = r w^T - (A w) x^T with r = b - A x, for this CTA's columns; w from the PCG pairs
+  template <class P2> __device__ void grad_A_out(const ProbDesc& pd, const P2* Y) {
+    const int64_t cols = min(chunk, n - gbase);
+    for (int64_t q = threadIdx.x; q < chunk; q += kThreads) buf64[q] = (q < cols) ? pd.x_in[gbase + q] : 0.0;
+    __syncthreads();
+    chain<double, MODE_RESID>(buf64);  // tfull = A x - b
+    for (int64_t idx = threadIdx.x; idx < m * cols; idx += kThreads) {
+      const int64_t i = idx / cols, j = idx % cols;
+      const P2 y = Y[gbase + j];
+      const double wj = (double)y.x - (double)y.y;
+      pd.grad_A[i * n + gbase + j] = -tfull[i] * wj - aw[i] * pd.x_in[gbase + j];
+    }
+  }
   template <class PS> __device__ double normal(PS* v) { return chain<PS, MODE_NORMAL>(v); }
 
   // rho = ||A||_F^2 / n: the Frobenius-closest multiple of I to A^T A (equals m/n when
@@ -521,6 +557,96 @@ __device__ __forceinline__ ScH<H> steering(const IpmShared<H, T>& sh, bool corr)
   return c;
 }
 
+// PCG on (Theta^-1 + F F^T) y = rhs (Sec. 4, preconditioner of Eq. eq:ne2_P).  On entry
+// r = rhs and p = P^-1 r are stored, the operator input w = p_u - p_v is in the shared buffer,
+// and rz_part, pdp_part are this thread's shares of r.P^-1 r and p.(Theta^-1 p).  Stops when
+// sqrt(r.P^-1 r) <= tol * its initial value (reading R9) or after max_iter iterations; y = 0
+// for a zero right-hand side.  Returns the iteration count; adds 2 per iteration to nmat.
+template <int G, class Op, class PS, class SH>
+__device__ int pcg_solve(Op& op, RedSmem& rs, SH& sh, int& par, typename V2<PS>::T* __restrict__ Xo,
+                         typename V2<PS>::T* __restrict__ Rv, typename V2<PS>::T* __restrict__ Pv,
+                         const typename V2<PS>::T* __restrict__ Dv, PS* __restrict__ w, PS rho, double tol,
+                         int max_iter, PS rz_part, PS pdp_part, int64_t& nmat) {
+  using P2 = typename V2<PS>::T;
+  const int tid = threadIdx.x;
+  const int64_t chunk = op.chunk, gb = op.gbase;
+  int k = 0;
+  PS pdp_acc = pdp_part;
+  for (;;) {
+    const double aw2 = op.normal(w);
+    nmat += 2;
+    {
+      PS v[2] = {pdp_acc + (PS)aw2, k == 0 ? rz_part : (PS)0};
+      cluster_reduce<G, 2>(rs, par, v, [&](const double (&t)[2]) {
+        if (k == 0) {
+          sh.rz0 = sh.rz = t[1];
+          sh.pcg_stop = !(t[1] > 0.0) || !isfinite(t[1]);
+        }
+        sh.alpha = (PS)(sh.rz / t[0]);
+      });
+    }
+    if (sh.pcg_stop) {  // zero right-hand side: y = 0
+      P2 zero;
+      zero.x = (PS)0;
+      zero.y = (PS)0;
+      for (int64_t q = tid; q < chunk; q += kThreads)
+        if (op.valid(q)) Xo[gb + q] = zero;
+      break;
+    }
+    const PS alpha = sh.alpha;
+    PS rzn_part = 0;
+    const bool first = (k == 0);
+#pragma unroll 4
+    for (int64_t q = tid; q < chunk; q += kThreads) {
+      if (!op.valid(q)) continue;
+      const int64_t gi = gb + q;
+      const P2 p = Pv[gi], d = Dv[gi];
+      P2 r = Rv[gi];
+      P2 x;
+      if (first) { x.x = (PS)0; x.y = (PS)0; } else { x = Xo[gi]; }
+      const PS y = w[q];
+      const PS qu = d.x * p.x + y, qv = d.y * p.y - y;
+      x.x += alpha * p.x;
+      x.y += alpha * p.y;
+      r.x -= alpha * qu;
+      r.y -= alpha * qv;
+      const P2 zz = precond<PS>(d, r, rho);
+      rzn_part += r.x * zz.x + r.y * zz.y;
+      Xo[gi] = x;
+      Rv[gi] = r;
+    }
+    ++k;
+    {
+      PS v[1] = {rzn_part};
+      cluster_reduce<G, 1>(rs, par, v, [&](const double (&t)[1]) {
+        const double rzn = t[0];
+        sh.pcg_stop = !(rzn > tol * tol * sh.rz0) || k >= max_iter || !isfinite(rzn);
+        sh.beta = (PS)(rzn / sh.rz);
+        sh.rz = rzn;
+      });
+    }
+    if (sh.pcg_stop) break;
+    const PS beta = sh.beta;
+    PS pdp = 0;
+#pragma unroll 4
+    for (int64_t q = tid; q < chunk; q += kThreads) {
+      if (!op.valid(q)) { w[q] = (PS)0; continue; }
+      const int64_t gi = gb + q;
+      const P2 d = Dv[gi], r = Rv[gi];
+      P2 p = Pv[gi];
+      const P2 zz = precond<PS>(d, r, rho);
+      p.x = zz.x + beta * p.x;
+      p.y = zz.y + beta * p.y;
+      Pv[gi] = p;
+      w[q] = p.x - p.y;
+      pdp += d.x * p.x * p.x + d.y * p.y * p.y;
+    }
+    __syncthreads();
+    pdp_acc = pdp;
+  }
+  return k;
+}
+
 template <int G, class Op, class PS, class S>
 __device__ void solve_one(const ProbDesc& pd, const KernelArgs& a, Op& op, RedSmem& rs,
                           IpmShared<PS, typename S::T>& sh, int& par) {
@@ -578,86 +704,9 @@ __device__ void solve_one(const ProbDesc& pd, const KernelArgs& a, Op& op, RedSm
   }
   const T tauT = sh.tauT, keepT = sh.keepT;
 
-  // PCG on (Theta^-1 + F F^T) dz = rhs (Sec. 4).  On entry r = rhs and p = P^-1 r are
-  // stored, the operator input w = p_u - p_v is in the shared buffer, and rz_part, pdp_part
-  // are this thread's shares of r.P^-1 r and p.(Theta^-1 p).  Stops when
-  // sqrt(r.P^-1 r) <= tol_pcg * its initial value or after max_iter_pcg iterations.
   auto pcg = [&](P2* __restrict__ Xo, PS rz_part, PS pdp_part) {
-    int k = 0;
-    PS pdp_acc = pdp_part;
-    for (;;) {
-      const double aw2 = op.normal(w);
-      nmat += 2;
-      {
-        PS v[2] = {pdp_acc + (PS)aw2, k == 0 ? rz_part : (PS)0};
-        cluster_reduce<G, 2>(rs, par, v, [&](const double (&t)[2]) {
-          if (k == 0) {
-            sh.rz0 = sh.rz = t[1];
-            sh.pcg_stop = !(t[1] > 0.0) || !isfinite(t[1]);
-          }
-          sh.alpha = (PS)(sh.rz / t[0]);
-        });
-      }
-      if (sh.pcg_stop) {  // zero right-hand side: dz = 0
-        P2 zero;
-        zero.x = (PS)0;
-        zero.y = (PS)0;
-        for (int64_t q = tid; q < chunk; q += kThreads)
-          if (op.valid(q)) Xo[gb + q] = zero;
-        break;
-      }
-      const PS alpha = sh.alpha;
-      PS rzn_part = 0;
-      const bool first = (k == 0);
-#pragma unroll 4
-      for (int64_t q = tid; q < chunk; q += kThreads) {
-        if (!op.valid(q)) continue;
-        const int64_t gi = gb + q;
-        const P2 p = Pv[gi], d = Dv[gi];
-        P2 r = Rv[gi];
-        P2 x;
-        if (first) { x.x = (PS)0; x.y = (PS)0; } else { x = Xo[gi]; }
-        const PS y = w[q];
-        const PS qu = d.x * p.x + y, qv = d.y * p.y - y;
-        x.x += alpha * p.x;
-        x.y += alpha * p.y;
-        r.x -= alpha * qu;
-        r.y -= alpha * qv;
-        const P2 zz = precond<PS>(d, r, rho);
-        rzn_part += r.x * zz.x + r.y * zz.y;
-        Xo[gi] = x;
-        Rv[gi] = r;
-      }
-      ++k;
-      {
-        PS v[1] = {rzn_part};
-        cluster_reduce<G, 1>(rs, par, v, [&](const double (&t)[1]) {
-          const double rzn = t[0];
-          sh.pcg_stop = !(rzn > prm.tol_pcg * prm.tol_pcg * sh.rz0) || k >= prm.max_iter_pcg || !isfinite(rzn);
-          sh.beta = (PS)(rzn / sh.rz);
-          sh.rz = rzn;
-        });
-      }
-      if (sh.pcg_stop) break;
-      const PS beta = sh.beta;
-      PS pdp = 0;
-#pragma unroll 4
-      for (int64_t q = tid; q < chunk; q += kThreads) {
-        if (!op.valid(q)) { w[q] = (PS)0; continue; }
-        const int64_t gi = gb + q;
-        const P2 d = Dv[gi], r = Rv[gi];
-        P2 p = Pv[gi];
-        const P2 zz = precond<PS>(d, r, rho);
-        p.x = zz.x + beta * p.x;
-        p.y = zz.y + beta * p.y;
-        Pv[gi] = p;
-        w[q] = p.x - p.y;
-        pdp += d.x * p.x * p.x + d.y * p.y * p.y;
-      }
-      __syncthreads();
-      pdp_acc = pdp;
-    }
-    pcg_total += k;
+    pcg_total += pcg_solve<G>(op, rs, sh, par, Xo, Rv, Pv, Dv, w, rho, prm.tol_pcg, prm.max_iter_pcg, rz_part,
+                              pdp_part, nmat);
   };
 
   // PCG initialisation: r = rhs (from rhs_fn(q, gi, state) in precision H), p = P^-1 r,
@@ -916,6 +965,148 @@ __device__ void solve_one(const ProbDesc& pd, const KernelArgs& a, Op& op, RedSm
       if (info.status != MFIPM_OK) atomicCAS(a.err, 0, info.status);
     }
   });
+}
+
+// Reverse mode (mfipm_backward; the paper has no derivative): differentiating the KKT
+// conditions Q z + c - s = 0, Z S e = mu e of Eq. fzfs at fixed mu gives
+// (Theta^-1 + F F^T) dz = -dc - dQ z, so for dL/dx = g and J = [I; -I]:
+//   y = H^-1 J g (the PCG of the forward, same matrix and preconditioner),
+//   w = J^T y,  dL/db = A w,  dL/dtau = -1^T y,  dL/dA = r w^T - (A w) x^T (r = b - A x).
+template <int G, class Op, class PS>
+__device__ void backward_one(const ProbDesc& pd, const KernelArgs& a, Op& op, RedSmem& rs,
+                             IpmShared<PS, double>& sh, int& par) {
+  using P2 = typename V2<PS>::T;
+  const SolveParams& prm = a.prm;
+  const int tid = threadIdx.x;
+  const int64_t n = pd.n, chunk = op.chunk, gb = op.gbase;
+  P2* __restrict__ Y = reinterpret_cast<P2*>(pd.pcg);
+  P2* __restrict__ Rv = Y + 2 * n;
+  P2* __restrict__ Pv = Rv + n;
+  P2* __restrict__ Dv = Pv + n;
+  PS* __restrict__ w = op.template wbuf<PS>();
+  double* __restrict__ buf = op.template rbuf<double>();
+  int64_t nmat = 0;
+  op.template setup<G>(rs, par);
+  const PS rho = (PS)op.rho;
+  PS rz_part = 0, pdp_part = 0;
+  for (int64_t q = tid; q < chunk; q += kThreads) {
+    if (!op.valid(q)) { w[q] = (PS)0; continue; }
+    const int64_t gi = gb + q, ni = op.natural(q);
+    const double u = pd.zs_in[ni], v = pd.zs_in[n + ni], su = pd.zs_in[2 * n + ni], sv = pd.zs_in[3 * n + ni];
+    P2 d, r;
+    d.x = (PS)(su / u);
+    d.y = (PS)(sv / v);
+    r.x = (PS)pd.gx[ni];
+    r.y = -r.x;
+    const P2 p = precond<PS>(d, r, rho);
+    Dv[gi] = d;
+    Rv[gi] = r;
+    Pv[gi] = p;
+    w[q] = p.x - p.y;
+    rz_part += r.x * p.x + r.y * p.y;
+    pdp_part += d.x * p.x * p.x + d.y * p.y * p.y;
+  }
+  __syncthreads();
+  // the derivative needs a tighter solve than a Newton direction
+  const double tol = fmin(prm.tol_pcg, 1e-6);
+  const int k = pcg_solve<G>(op, rs, sh, par, Y, Rv, Pv, Dv, w, rho, tol, prm.max_iter_pcg, rz_part, pdp_part, nmat);
+  double tsum = 0.0;
+  for (int64_t q = tid; q < chunk; q += kThreads) {
+    if (!op.valid(q)) { buf[q] = 0.0; continue; }
+    const P2 y = Y[gb + q];
+    buf[q] = (double)y.x - (double)y.y;
+    tsum += (double)y.x + (double)y.y;
+  }
+  __syncthreads();
+  op.apply_A_out(pd);
+  ++nmat;
+  if (pd.grad_A) op.grad_A_out(pd, Y);
+  double v[1] = {tsum};
+  cluster_reduce<G, 1>(rs, par, v, [&](const double (&t)[1]) {
+    if (op.rank == 0) {
+      *pd.grad_tau = -t[0];
+      mfipm_info info{};
+      info.status = MFIPM_OK;
+      info.pcg_iters = k;
+      info.n_mat = nmat;
+      *pd.info = info;
+    }
+  });
+}
+
+template <int G, class Op, class PS>
+__global__ void __launch_bounds__(kThreads, 1) bwd_kernel(KernelArgs a) {
+  extern __shared__ __align__(256) unsigned char smem[];
+  __shared__ RedSmem rs;
+  __shared__ IpmShared<PS, double> sh;
+  int par = 0;
+  int rank = 0;
+  if constexpr (G > 1) rank = (int)cg::this_cluster().block_rank();
+  for (;;) {
+    if (rank == 0 && threadIdx.x == 0) rs.fetched = atomicAdd(a.queue, 1);
+    cluster_barrier<G>();
+    int pid;
+    if constexpr (G == 1) {
+      pid = rs.fetched;
+    } else {
+      pid = cg::this_cluster().map_shared_rank(&rs, 0)->fetched;
+    }
+    if (pid >= a.batch) break;
+    const ProbDesc pd = a.probs[pid];
+    Op op;
+    op.init(pd, a, smem, rank);
+    backward_one<G, Op, PS>(pd, a, op, rs, sh, par);
+    cluster_barrier<G>();
+  }
+  cluster_barrier<G>();
+}
+
+template <int G, class Op, class PS>
+inline cudaError_t launch_bwd_t(const KernelArgs& a, size_t smem, int grid_clusters, cudaStream_t st) {
+  auto kern = bwd_kernel<G, Op, PS>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  if (G > 8) {
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e != cudaSuccess) return e;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid_clusters * G);
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = G;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, a);
+}
+
+template <int G, class Op, class PS>
+inline int occupancy_bwd_t(size_t smem) {
+  auto kern = bwd_kernel<G, Op, PS>;
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
+  if (G > 8 && cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) return 0;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(G);
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = smem;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = G;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int n = 0;
+  if (cudaOccupancyMaxActiveClusters(&n, kern, &cfg) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return n;
 }
 
 // Persistent solver kernel.  Phase 1: whole clusters take problems [0, nbig) from queue[0]
