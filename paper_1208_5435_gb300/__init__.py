@@ -11,7 +11,7 @@ from typing import List, Optional, Sequence
 from . import _capi as C
 from ._capi import MfipmError, lib
 
-__all__ = ["Dense", "PartialDCT", "SolverParams", "solve", "solve_batched", "workspace_bytes", "MfipmError", "lib"]
+__all__ = ["Dense", "DenseBF16", "PartialDCT", "SolverParams", "solve", "solve_batched", "workspace_bytes", "MfipmError", "lib"]
 
 
 def _torch():
@@ -79,6 +79,31 @@ class Dense:
     def c_op(self) -> C.Operator:
         op = C.Operator()
         op.kind, op.a_dtype, op.m, op.n = C.OP_DENSE, C.A_F64, self.m, self.n
+        op.A, op.a_scale, op.lda = self.A.data_ptr(), self.a_scale, self.n
+        op.rows = None
+        return op
+
+
+class DenseBF16:
+    """A = a_scale * A_bf16 with A_bf16 an m x n bfloat16 CUDA tensor (or its uint16 bit
+    patterns), shared by the right-hand sides of one mfipm_solve_batched call
+    (MFIPM_PREC_BF16_A: tensor-core products, float64 outer loop)."""
+
+    def __init__(self, A_bf16, a_scale: float = 1.0):
+        torch = _torch()
+        if A_bf16.dtype == torch.uint16 if hasattr(torch, "uint16") else False:
+            A_bf16 = A_bf16.view(torch.bfloat16)
+        if A_bf16.dtype == torch.int16:
+            A_bf16 = A_bf16.view(torch.bfloat16)
+        self.A = A_bf16.to(device="cuda").contiguous()
+        assert self.A.dtype == torch.bfloat16
+        self.m, self.n = (int(s) for s in self.A.shape)
+        self.a_scale = float(a_scale)
+        self.default_precision = C.PREC_BF16_A
+
+    def c_op(self) -> C.Operator:
+        op = C.Operator()
+        op.kind, op.a_dtype, op.m, op.n = C.OP_DENSE, C.A_BF16, self.m, self.n
         op.A, op.a_scale, op.lda = self.A.data_ptr(), self.a_scale, self.n
         op.rows = None
         return op

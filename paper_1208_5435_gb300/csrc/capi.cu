@@ -14,6 +14,7 @@
 
 #include "device_common.cuh"
 #include "internal.h"
+#include "mrhs.h"
 
 using namespace mfipm;
 
@@ -69,9 +70,9 @@ int validate_op(const mfipm_operator* op, int idx) {
     if (op->lda < op->n) return fail(MFIPM_INVALID_ARG, "operator %d: lda < n", idx);
     if (!(op->a_scale > 0.0) || !isfinite(op->a_scale))
       return fail(MFIPM_INVALID_ARG, "operator %d: a_scale must be positive and finite", idx);
+    if (op->a_dtype == MFIPM_A_BF16) return MFIPM_OK;  // shared-A multi-RHS solver
     if (op->a_dtype != MFIPM_A_F64)
-      return fail(MFIPM_UNSUPPORTED, "operator %d: this entry point takes float64 dense A (a_dtype=%d)", idx,
-                  op->a_dtype);
+      return fail(MFIPM_UNSUPPORTED, "operator %d: dense A must be float64 or bf16 (a_dtype=%d)", idx, op->a_dtype);
     if (op->m > kDenseMaxM)
       return fail(MFIPM_UNSUPPORTED, "operator %d: dense m=%lld above %lld for the per-problem solver", idx,
                   (long long)op->m, (long long)kDenseMaxM);
@@ -195,6 +196,28 @@ int pick_G(const std::vector<mfipm_operator>& ops, const mfipm_params* p, int ba
   return g;
 }
 
+// The bf16 shared-A multi-RHS path: every operator dense bf16 with the same A, m, n, lda = n
+// and a_scale, and precision MFIPM_PREC_BF16_A.
+int check_shared_bf16(const mfipm_operator* ops, int batch, const mfipm_params* p, bool* is_shared) {
+  *is_shared = false;
+  bool any_bf16 = false;
+  for (int i = 0; i < batch; ++i) any_bf16 |= ops[i].kind == MFIPM_OP_DENSE && ops[i].a_dtype == MFIPM_A_BF16;
+  if (!any_bf16 && p->precision != MFIPM_PREC_BF16_A) return MFIPM_OK;
+  if (p->precision != MFIPM_PREC_BF16_A)
+    return fail(MFIPM_UNSUPPORTED, "bf16 A needs precision MFIPM_PREC_BF16_A (the shared-A multi-RHS solver)");
+  for (int i = 0; i < batch; ++i) {
+    const mfipm_operator& o = ops[i];
+    if (o.kind != MFIPM_OP_DENSE || o.a_dtype != MFIPM_A_BF16)
+      return fail(MFIPM_UNSUPPORTED, "MFIPM_PREC_BF16_A needs dense bf16 operators (operator %d)", i);
+    if (o.A != ops[0].A || o.m != ops[0].m || o.n != ops[0].n || o.a_scale != ops[0].a_scale || o.lda != ops[0].lda)
+      return fail(MFIPM_UNSUPPORTED, "the bf16 solver shares one A between right-hand sides (operator %d differs)", i);
+    if (o.lda != o.n) return fail(MFIPM_UNSUPPORTED, "bf16 A must be packed (lda == n)");
+    if (o.m < 1) return fail(MFIPM_INVALID_ARG, "bf16 A needs m >= 1");
+  }
+  *is_shared = true;
+  return MFIPM_OK;
+}
+
 struct Prepared {
   Layout lay;
   std::vector<ProbDesc> desc;
@@ -221,6 +244,9 @@ int prepare(int batch, const mfipm_operator* ops, const double* const* b, const 
     if (ops[i].m > 0 && !b[i]) return fail(MFIPM_INVALID_ARG, "b[%d] is NULL", i);
     if (!x[i]) return fail(MFIPM_INVALID_ARG, "x[%d] is NULL", i);
   }
+  for (int i = 0; i < batch; ++i)
+    if (ops[i].kind == MFIPM_OP_DENSE && ops[i].a_dtype == MFIPM_A_BF16)
+      return fail(MFIPM_UNSUPPORTED, "bf16 A is solved by the shared-A multi-RHS solver (precision MFIPM_PREC_BF16_A)");
   P.dct = kind == MFIPM_OP_PARTIAL_DCT;
   if (P.dct && p->precision != MFIPM_PREC_FP32_PCG)
     return fail(MFIPM_UNSUPPORTED, "the partial-DCT solver runs its PCG in float32 (precision=%d)", p->precision);
@@ -379,6 +405,65 @@ std::vector<int> cost_order(const mfipm_operator* ops, int batch) {
   return ord;
 }
 
+// ------------------------------------------------------------------ bf16 shared-A solver
+int solve_shared_bf16(int batch, const mfipm_operator* ops, const double* const* b, const double* tau,
+                      const mfipm_params* p, double* const* x, double* const* zs_out, void* workspace,
+                      size_t ws_bytes, mfipm_info* infos, void* stream) {
+  for (int i = 0; i < batch; ++i) {
+    if (!(tau[i] > 0.0) || !isfinite(tau[i])) return fail(MFIPM_INVALID_ARG, "tau[%d] must be positive and finite", i);
+    if (!b[i] || !x[i]) return fail(MFIPM_INVALID_ARG, "b[%d] or x[%d] is NULL", i, i);
+  }
+  size_t need = 0;
+  int rc = mfipm_workspace_size(ops, batch, p, &need);
+  if (rc) return rc;
+  if (!workspace || ((uintptr_t)workspace & 255)) return fail(MFIPM_INVALID_ARG, "workspace NULL or not 256-byte aligned");
+  if (ws_bytes < need) return fail(MFIPM_INVALID_ARG, "workspace too small: %zu < %zu bytes", ws_bytes, need);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  char* ws = static_cast<char*>(workspace);
+  double* fro = reinterpret_cast<double*>(ws);
+  mfipm_info* info_dev = reinterpret_cast<mfipm_info*>(ws + 256);
+  const size_t off = 256 + ((sizeof(mfipm_info) * batch + 255) & ~(size_t)255) + 256;
+  cudaError_t e = bf16_fro2(ops[0].A, ops[0].m, ops[0].n, ops[0].lda, fro, st);
+  if (e) return cuda_fail(e, "norm of A");
+  double fro2 = 0.0;
+  if ((e = cudaMemcpyAsync(&fro2, fro, 8, cudaMemcpyDeviceToHost, st)) || (e = cudaStreamSynchronize(st)))
+    return cuda_fail(e, "norm of A");
+  MrhsCall call{};
+  call.m = ops[0].m;
+  call.n = ops[0].n;
+  call.lda = ops[0].lda;
+  call.R = batch;
+  call.A = ops[0].A;
+  call.a_scale = ops[0].a_scale;
+  // rho = ||A||_F^2 / n (reading R2) for the true matrix a_scale * A
+  call.rho = fro2 * ops[0].a_scale * ops[0].a_scale / (double)ops[0].n;
+  call.b = b;
+  call.tau = tau;
+  call.x = x;
+  call.zs_out = zs_out;
+  call.infos_dev = info_dev;
+  call.workspace = ws + off;
+  call.ws_bytes = ws_bytes - off;
+  call.prm = to_solve(p);
+  call.stream = st;
+  call.gemm = gemm_simple;
+  call.gemm_ctx = nullptr;
+  std::string msg;
+  rc = mrhs_solve(call, &msg);
+  if (rc) return fail(rc, "%s", msg.c_str());
+  std::vector<mfipm_info> tmp;
+  if (!infos) {
+    tmp.resize(batch);
+    infos = tmp.data();
+  }
+  if ((e = cudaMemcpyAsync(infos, info_dev, sizeof(mfipm_info) * batch, cudaMemcpyDeviceToHost, st)) ||
+      (e = cudaStreamSynchronize(st)))
+    return cuda_fail(e, "read infos");
+  for (int i = 0; i < batch; ++i)
+    if (infos[i].status != MFIPM_OK) return infos[i].status;
+  return MFIPM_OK;
+}
+
 // ------------------------------------------------------------------ fixed scratch
 // Device scratch for mfipm_solve_noalloc, for callers that may not allocate device memory
 // (see include/mfipm.h).  Every GPU that loads this library holds these bytes until the
@@ -437,6 +522,12 @@ int mfipm_workspace_size(const mfipm_operator* ops, int32_t batch, const mfipm_p
   if (rc) return rc;
   for (int i = 0; i < batch; ++i)
     if ((rc = validate_op(&ops[i], i))) return rc;
+  bool shared = false;
+  if ((rc = check_shared_bf16(ops, batch, p, &shared))) return rc;
+  if (shared) {
+    *bytes = 256 + ((sizeof(mfipm_info) * batch + 255) & ~(size_t)255) + 256 + mrhs_workspace_bytes(ops[0].m, ops[0].n, batch);
+    return MFIPM_OK;
+  }
   *bytes = make_layout(ops, batch, pcg_in_fp64(ops[0], p)).total;
   return MFIPM_OK;
 }
@@ -448,6 +539,11 @@ int mfipm_solve(const mfipm_operator* op, const double* b, double tau, const mfi
   double* xx[1] = {x};
   double* zz[1] = {zs_out};
   double tt[1] = {tau};
+  if (op && p && op->kind == MFIPM_OP_DENSE && op->a_dtype == MFIPM_A_BF16 && p->precision == MFIPM_PREC_BF16_A) {
+    int rc = validate_params(p);
+    if (rc || (rc = validate_op(op, 0))) return rc;
+    return solve_shared_bf16(1, op, bb, tt, p, xx, zs_out ? zz : nullptr, workspace, ws_bytes, info, stream);
+  }
   Prepared P;
   int rc = prepare(1, op, bb, tt, p, xx, zs_out ? zz : nullptr, workspace, ws_bytes, P);
   if (rc) return rc;
@@ -482,6 +578,16 @@ int mfipm_solve_batched(int32_t batch, const mfipm_operator* ops, const double* 
                         const mfipm_params* p, double* const* x, double* const* zs_out, void* workspace,
                         size_t ws_bytes, mfipm_info* infos, void* stream) {
   g_err.clear();
+  {
+    int rc = validate_params(p);
+    if (rc) return rc;
+    if (batch < 1 || !ops || !b || !tau || !x) return fail(MFIPM_INVALID_ARG, "NULL argument array or batch < 1");
+    for (int i = 0; i < batch; ++i)
+      if ((rc = validate_op(&ops[i], i))) return rc;
+    bool shared = false;
+    if ((rc = check_shared_bf16(ops, batch, p, &shared))) return rc;
+    if (shared) return solve_shared_bf16(batch, ops, b, tau, p, x, zs_out, workspace, ws_bytes, infos, stream);
+  }
   Prepared P;
   int rc = prepare(batch, ops, b, tau, p, x, zs_out, workspace, ws_bytes, P);
   if (rc) return rc;

@@ -1,0 +1,799 @@
+// Shared-A multi-right-hand-side solver: R problems  min tau_j ||x_j||_1 + 1/2 ||A x_j - b_j||^2
+// with one dense A stored as bf16 times a per-tensor scale (MFIPM_PREC_BF16_A).  All right-hand
+// sides run the single-corrector IPM of Sec. 5.1 in lockstep, each with its own scalars (mu,
+// sigma, step lengths, corrector decision, stop flag); a column that has converged keeps its
+// iterate.  Every PCG operator product (Sec. 4) needs A^T A w for all columns at once, so A is
+// read once per product for all R columns:
+//     T = A W,  Y = A^T T      (two GEMMs, bf16 operands, float32 accumulation)
+// where W (and T) are split into bf16 high and low halves, W = W_hi + W_lo, which keeps the
+// product accurate to ~2^-16 at the cost of doubling the GEMM's N (the GEMMs are bounded by
+// reading A, not by the tensor rate).  A transposed copy of A in the workspace makes both
+// GEMMs K-major.  The outer loop is float64: the residual A^T (A x - b) accumulates the exact
+// products of bf16 A and double-float x in double-float on the float32 pipes.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "device_common.cuh"
+#include "internal.h"
+#include "mrhs.h"
+
+namespace mfipm {
+namespace mr {
+
+constexpr int kT = 256;       // threads per block of the per-column passes
+constexpr int kIdx = 512;     // indices per block (2 per thread)
+constexpr int kPart = 8;      // partial sums per (column, block)
+
+__device__ __forceinline__ float bf(const __nv_bfloat16 v) { return __bfloat162float(v); }
+
+// P^-1 r for one index (Eq. eq:ne2_P), float32
+__device__ __forceinline__ float2 precond2(float2 d, float2 r, float rho) {
+  const float a = d.x + rho, c = d.y + rho;
+  const float inv = 1.f / (d.x * d.y + rho * (d.x + d.y));
+  return make_float2((c * r.x + rho * r.y) * inv, (rho * r.x + a * r.y) * inv);
+}
+
+// block sum of up to kPart values; thread 0 writes part[(col * nb + blk) * kPart + k]
+template <int K>
+__device__ __forceinline__ void block_partials(const double (&v)[K], double* part, int col, int nb, int blk) {
+  __shared__ double red[kT / 32][K];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    double w = warp_sum(v[k]);
+    if (lane == 0) red[warp][k] = w;
+  }
+  __syncthreads();
+  if (threadIdx.x < K) {
+    double s = 0.0;
+    for (int w = 0; w < kT / 32; ++w) s += red[w][threadIdx.x];
+    part[((int64_t)col * nb + blk) * kPart + threadIdx.x] = s;
+  }
+}
+template <int K>
+__device__ __forceinline__ void block_minima(const double (&v)[K], double* part, int col, int nb, int blk) {
+  __shared__ double red[kT / 32][K];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    double w = v[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) w = fmin(w, __shfl_xor_sync(0xffffffffu, w, o));
+    if (lane == 0) red[warp][k] = w;
+  }
+  __syncthreads();
+  if (threadIdx.x < K) {
+    double s = INFINITY;
+    for (int w = 0; w < kT / 32; ++w) s = fmin(s, red[w][threadIdx.x]);
+    part[((int64_t)col * nb + blk) * kPart + threadIdx.x] = s;
+  }
+}
+// column total of partial k (fixed order: deterministic)
+__device__ __forceinline__ double col_total(const double* part, int col, int nb, int k, bool is_min = false) {
+  double s = is_min ? INFINITY : 0.0;
+  for (int b = 0; b < nb; ++b) {
+    const double v = part[((int64_t)col * nb + b) * kPart + k];
+    s = is_min ? fmin(s, v) : s + v;
+  }
+  return s;
+}
+
+// ------------------------------------------------------------------ setup
+__global__ void transpose_bf16(const __nv_bfloat16* __restrict__ A, int64_t lda, __nv_bfloat16* __restrict__ At,
+                               int m, int n) {
+  __shared__ __nv_bfloat16 tile[32][33];
+  const int bx = blockIdx.x * 32, by = blockIdx.y * 32;
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int i = by + r, k = bx + threadIdx.x;
+    if (i < m && k < n) tile[r][threadIdx.x] = A[(int64_t)i * lda + k];
+  }
+  __syncthreads();
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int k = bx + r, i = by + threadIdx.x;
+    if (k < n && i < m) At[(int64_t)k * m + i] = tile[threadIdx.x][r];
+  }
+}
+
+__global__ void gather_b(const double* const* __restrict__ bptr, double* __restrict__ Bm, int m) {
+  const int j = blockIdx.y;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x)
+    Bm[(int64_t)j * m + i] = bptr[j][i];
+}
+
+// ------------------------------------------------------------------ GEMMs
+// C[c][r] = sum_k Aop[r][k] * Bop[c][k]   (Aop: rows x K bf16, Bop: N x K bf16, C: N x rows f32)
+// Plain CUDA-core tile (64 x 64 outputs per block, float32 accumulation).
+__global__ void gemm_bf16_simple(const __nv_bfloat16* __restrict__ Aop, const __nv_bfloat16* __restrict__ Bop,
+                                 float* __restrict__ C, int rows, int N, int K) {
+  __shared__ float As[32][65];
+  __shared__ float Bs[32][65];
+  const int r0 = blockIdx.x * 64, c0 = blockIdx.y * 64;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  float acc[4][4] = {};
+  for (int k0 = 0; k0 < K; k0 += 32) {
+    for (int e = threadIdx.x; e < 64 * 32; e += kT) {
+      const int rr = e / 32, kk = e % 32;
+      As[kk][rr] = (r0 + rr < rows && k0 + kk < K) ? bf(Aop[(int64_t)(r0 + rr) * K + k0 + kk]) : 0.f;
+      Bs[kk][rr] = (c0 + rr < N && k0 + kk < K) ? bf(Bop[(int64_t)(c0 + rr) * K + k0 + kk]) : 0.f;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int kk = 0; kk < 32; ++kk) {
+      float a[4], b[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        a[q] = As[kk][ty * 4 + q];
+        b[q] = Bs[kk][tx * 4 + q];
+      }
+#pragma unroll
+      for (int p = 0; p < 4; ++p)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[p][q] = fmaf(a[p], b[q], acc[p][q]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int p = 0; p < 4; ++p)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int r = r0 + ty * 4 + p, c = c0 + tx * 4 + q;
+      if (r < rows && c < N) C[(int64_t)c * rows + r] = acc[p][q];
+    }
+}
+
+// Out[j][r] = scale * sum_k Aop[r][k] X[j][k] - (Bsub ? Bsub[j][r] : 0), float64 result.
+// bf16 A is exact in float32; each product with x = xh + xl (double-float) is formed
+// exactly (FMA error term) and accumulated in double-float.
+__global__ void resid_gemm_df(const __nv_bfloat16* __restrict__ Aop, const double* __restrict__ X,
+                              const double* __restrict__ Bsub, double* __restrict__ Out, double scale, int rows,
+                              int R, int K) {
+  __shared__ float As[32][65];
+  __shared__ float Xh[32][65];
+  __shared__ float Xl[32][65];
+  const int r0 = blockIdx.x * 64, j0 = blockIdx.y * 64;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  df acc[4][4];
+  for (int k0 = 0; k0 < K; k0 += 32) {
+    for (int e = threadIdx.x; e < 64 * 32; e += kT) {
+      const int rr = e / 32, kk = e % 32;
+      As[kk][rr] = (r0 + rr < rows && k0 + kk < K) ? bf(Aop[(int64_t)(r0 + rr) * K + k0 + kk]) : 0.f;
+      const double xv = (j0 + rr < R && k0 + kk < K) ? X[(int64_t)(j0 + rr) * K + k0 + kk] : 0.0;
+      const df xd = to_df(xv);
+      Xh[kk][rr] = xd.hi;
+      Xl[kk][rr] = xd.lo;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int kk = 0; kk < 32; ++kk) {
+      float a[4], xh[4], xl[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        a[q] = As[kk][ty * 4 + q];
+        xh[q] = Xh[kk][tx * 4 + q];
+        xl[q] = Xl[kk][tx * 4 + q];
+      }
+#pragma unroll
+      for (int p = 0; p < 4; ++p)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const float pr = __fmul_rn(a[p], xh[q]);
+          float e = __fmaf_rn(a[p], xh[q], -pr);
+          e = __fmaf_rn(a[p], xl[q], e);
+          acc[p][q] += df(pr, e);
+        }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int p = 0; p < 4; ++p)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int r = r0 + ty * 4 + p, j = j0 + tx * 4 + q;
+      if (r < rows && j < R) {
+        double v = scale * to_double(acc[p][q]);
+        if (Bsub) v -= Bsub[(int64_t)j * rows + r];
+        Out[(int64_t)j * rows + r] = v;
+      }
+    }
+}
+
+// ------------------------------------------------------------------ per-column state
+struct Col {
+  double tau, cn, mu, sigma, alpha_p, alpha_d, alpha_p1, alpha_d1, mu_t, prev_ap, prev_ad;
+  double rel_gap, P_obj, rz0, rz, res2;
+  float alpha, beta;
+  int stop, active, corr, corr_next, correctors, pcg_iters, ipm_iters, done;
+  int64_t nmat;
+};
+
+struct Dev {
+  int m, n, R, nb;                 // nb: blocks per column of the index passes
+  double a_scale, rho;
+  const __nv_bfloat16* A;          // m x n (lda)
+  int64_t lda;
+  const __nv_bfloat16* At;         // n x m
+  double* X;                       // R x n   residual input (x or trial x)
+  double* Rr;                      // R x m   A x - b
+  double* Gr;                      // R x n   A^T (A x - b)
+  double* Bm;                      // R x m
+  double* zs;                      // R x n x 4 {u, v, s_u, s_v}
+  float2 *X1, *X2, *Rv, *Pv, *Dv;  // R x n each
+  __nv_bfloat16* W;                // 2R x n
+  __nv_bfloat16* Tb;               // 2R x m
+  float* C1;                       // 2R x m
+  float* C2;                       // 2R x n
+  double* part;                    // R x nb x kPart
+  Col* col;
+  int* counters;                   // [0] active PCG columns, [1] unfinished columns, [2] corrector columns
+  SolveParams prm;
+};
+
+// dz, ds of one index from the PCG pairs (Eq. redNewtonB; corrector reading R6), in float64
+struct D2 {
+  double dz, ds;
+};
+__device__ __forceinline__ D2 dirn(double z, double s, float dz1f, float dz2f, const Col& c, double sigma3, bool corr) {
+  const double dz1 = dz1f, dz2 = dz2f;
+  const double rz = 1.0 / z, d = s * rz;
+  const double ds1 = c.sigma * c.mu * rz - s - d * dz1;
+  D2 r{dz1, ds1};
+  if (corr) {
+    const double zt = z + c.alpha_p1 * dz1, st = s + c.alpha_d1 * ds1;
+    r.dz = dz1 + dz2;
+    r.ds = ds1 + (sigma3 * c.mu_t - zt * st) * rz - d * dz2;
+  }
+  return r;
+}
+
+// iterate update (previous direction) and x = u - v; partials z.s, 1^T z, ||x||^2
+__global__ void k_update(Dev d, int first) {
+  const int j = blockIdx.y, blk = blockIdx.x;
+  const Col c = d.col[j];
+  double v[3] = {0, 0, 0};
+  for (int i = blk * kIdx + threadIdx.x; i < min(d.n, (blk + 1) * kIdx); i += kT) {
+    const int64_t gi = (int64_t)j * d.n + i;
+    double4 st;
+    double* zp = d.zs + 4 * gi;
+    if (first) {
+      st = make_double4(1.0, 1.0, 1.0, 1.0);  // reading R3
+    } else {
+      st = make_double4(zp[0], zp[1], zp[2], zp[3]);
+      if (!c.done) {
+        const float2 x1 = d.X1[gi];
+        const float2 x2 = c.corr ? d.X2[gi] : make_float2(0.f, 0.f);
+        const D2 du = dirn(st.x, st.z, x1.x, x2.x, c, d.prm.sigma3, c.corr);
+        const D2 dv = dirn(st.y, st.w, x1.y, x2.y, c, d.prm.sigma3, c.corr);
+        double nu = st.x + c.alpha_p * du.dz, nv = st.y + c.alpha_p * dv.dz;
+        double nsu = st.z + c.alpha_d * du.ds, nsv = st.w + c.alpha_d * dv.ds;
+        const double keep = 1.0 - d.prm.eta;
+        if (!(nu > 0.0)) nu = st.x * keep;
+        if (!(nv > 0.0)) nv = st.y * keep;
+        if (!(nsu > 0.0)) nsu = st.z * keep;
+        if (!(nsv > 0.0)) nsv = st.w * keep;
+        st = make_double4(nu, nv, nsu, nsv);
+      }
+    }
+    zp[0] = st.x;
+    zp[1] = st.y;
+    zp[2] = st.z;
+    zp[3] = st.w;
+    const double x = st.x - st.y;
+    d.X[gi] = x;
+    v[0] += st.x * st.z + st.y * st.w;
+    v[1] += st.x + st.y;
+    v[2] += x * x;
+  }
+  block_partials<3>(v, d.part, j, d.nb, blk);
+}
+
+__global__ void k_colnorm2(const double* __restrict__ V, int len, double* part, int nb) {
+  const int j = blockIdx.y, blk = blockIdx.x;
+  double v[1] = {0.0};
+  const int per = (len + nb - 1) / nb;
+  for (int i = blk * per + threadIdx.x; i < min(len, (blk + 1) * per); i += kT) {
+    const double t = V[(int64_t)j * len + i];
+    v[0] += t * t;
+  }
+  block_partials<1>(v, part, j, nb, blk);
+}
+
+// gap test, mu, sigma (one thread per column)
+__global__ void k_stats(Dev d, int it, const double* part2) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= d.R) return;
+  Col& c = d.col[j];
+  if (c.done) return;
+  const double zts = col_total(d.part, j, d.nb, 0), l1 = col_total(d.part, j, d.nb, 1);
+  const double res2 = col_total(part2, j, d.nb, 0);
+  c.res2 = res2;
+  c.mu = zts / (2.0 * d.n);
+  c.P_obj = c.tau * l1 + 0.5 * res2;
+  c.rel_gap = zts / (1.0 + fabs(c.P_obj));
+  c.corr = 0;
+  c.ipm_iters = it - 1;
+  if (!isfinite(c.rel_gap)) { c.stop = MFIPM_NUMERIC; c.done = 1; }
+  else if (c.rel_gap <= d.prm.tol) { c.stop = MFIPM_OK; c.done = 1; }
+  else if (it > d.prm.max_iter) { c.stop = MFIPM_NOT_CONVERGED; c.done = 1; }
+  c.sigma = (it != 1 && (c.prev_ap <= d.prm.alpha_bar || c.prev_ad <= d.prm.alpha_bar)) ? d.prm.sigma2 : d.prm.sigma1;
+  c.nmat += 2;
+  if (!c.done) atomicAdd(&d.counters[1], 1);
+}
+
+// PCG initialisation.  corr = 0: rhs = sigma mu / z - [tau + g; tau - g], writes Theta^-1.
+// corr = 1: rhs~ = f_z~ + Z^-1 f_s~ at the trial point (reading R6), only for columns that
+// take a corrector.  Columns that are done (or take no corrector) get rhs = 0.
+__global__ void k_pcg_init(Dev d, int corr) {
+  const int j = blockIdx.y, blk = blockIdx.x;
+  const Col c = d.col[j];
+  const bool live = !c.done && (!corr || c.corr_next);
+  double v[2] = {0, 0};
+  for (int i = blk * kIdx + threadIdx.x; i < min(d.n, (blk + 1) * kIdx); i += kT) {
+    const int64_t gi = (int64_t)j * d.n + i;
+    const double* zp = d.zs + 4 * gi;
+    const double u = zp[0], vv = zp[1], su = zp[2], sv = zp[3];
+    float2 dd;
+    if (!corr) {
+      dd = make_float2((float)(su / u), (float)(sv / vv));
+      d.Dv[gi] = dd;
+    } else {
+      dd = d.Dv[gi];
+    }
+    float2 r = make_float2(0.f, 0.f);
+    if (live) {
+      const double g = d.Gr[gi];
+      if (!corr) {
+        const double smu = c.sigma * c.mu;
+        r.x = (float)(smu / u - (c.tau + g));
+        r.y = (float)(smu / vv - (c.tau - g));
+      } else {
+        const float2 x1 = d.X1[gi];
+        const D2 du = dirn(u, su, x1.x, 0.f, c, d.prm.sigma3, false);
+        const D2 dv = dirn(vv, sv, x1.y, 0.f, c, d.prm.sigma3, false);
+        const double zu = u + c.alpha_p1 * du.dz, zv = vv + c.alpha_p1 * dv.dz;
+        const double tsu = su + c.alpha_d1 * du.ds, tsv = sv + c.alpha_d1 * dv.ds;
+        const double s3mu = d.prm.sigma3 * c.mu_t;
+        r.x = (float)((tsu - (c.tau + g)) + (s3mu - zu * tsu) / u);
+        r.y = (float)((tsv - (c.tau - g)) + (s3mu - zv * tsv) / vv);
+      }
+    }
+    const float2 p = precond2(dd, r, (float)d.rho);
+    d.Rv[gi] = r;
+    d.Pv[gi] = p;
+    const float w = p.x - p.y;
+    const __nv_bfloat16 wh = __float2bfloat16_rn(w);
+    d.W[(int64_t)j * d.n + i] = wh;
+    d.W[(int64_t)(d.R + j) * d.n + i] = __float2bfloat16_rn(w - __bfloat162float(wh));
+    v[0] += (double)(r.x * p.x + r.y * p.y);
+    v[1] += (double)(dd.x * p.x * p.x + dd.y * p.y * p.y);
+  }
+  block_partials<2>(v, d.part, j, d.nb, blk);
+}
+
+// T = a_scale (C1_hi + C1_lo) -> bf16 hi/lo halves; partial ||T_j||^2 = ||A w_j||^2
+__global__ void k_split_t(Dev d, double* part2) {
+  const int j = blockIdx.y, blk = blockIdx.x;
+  double v[1] = {0.0};
+  const int per = (d.m + d.nb - 1) / d.nb;
+  for (int i = blk * per + threadIdx.x; i < min(d.m, (blk + 1) * per); i += kT) {
+    const float t = (float)d.a_scale * (d.C1[(int64_t)j * d.m + i] + d.C1[(int64_t)(d.R + j) * d.m + i]);
+    const __nv_bfloat16 th = __float2bfloat16_rn(t);
+    d.Tb[(int64_t)j * d.m + i] = th;
+    d.Tb[(int64_t)(d.R + j) * d.m + i] = __float2bfloat16_rn(t - __bfloat162float(th));
+    v[0] += (double)t * t;
+  }
+  block_partials<1>(v, part2, j, d.nb, blk);
+}
+
+// alpha = r.P^-1 r / (p.Theta^-1 p + ||A w||^2); first iteration records rz0
+__global__ void k_alpha(Dev d, int first, const double* part2) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= d.R) return;
+  Col& c = d.col[j];
+  const double pdp = col_total(d.part, j, d.nb, 1), aw2 = col_total(part2, j, d.nb, 0);
+  if (first) {
+    const double rz = col_total(d.part, j, d.nb, 0);
+    c.rz0 = c.rz = rz;
+    c.active = rz > 0.0 && isfinite(rz);
+  }
+  c.alpha = c.active ? (float)(c.rz / (pdp + aw2)) : 0.f;
+  if (c.active) c.nmat += 2;
+}
+
+__global__ void k_pcg_D(Dev d, float2* __restrict__ Xo, int first) {
+  const int j = blockIdx.y, blk = blockIdx.x;
+  const Col c = d.col[j];
+  const float alpha = c.alpha, rho = (float)d.rho, sc = (float)d.a_scale;
+  double v[1] = {0.0};
+  for (int i = blk * kIdx + threadIdx.x; i < min(d.n, (blk + 1) * kIdx); i += kT) {
+    const int64_t gi = (int64_t)j * d.n + i;
+    float2 x = first ? make_float2(0.f, 0.f) : Xo[gi];
+    float2 r = d.Rv[gi];
+    const float2 p = d.Pv[gi], dd = d.Dv[gi];
+    const float y = sc * (d.C2[(int64_t)j * d.n + i] + d.C2[(int64_t)(d.R + j) * d.n + i]);
+    x.x += alpha * p.x;
+    x.y += alpha * p.y;
+    r.x -= alpha * (dd.x * p.x + y);
+    r.y -= alpha * (dd.y * p.y - y);
+    const float2 zz = precond2(dd, r, rho);
+    v[0] += (double)(r.x * zz.x + r.y * zz.y);
+    Xo[gi] = x;
+    d.Rv[gi] = r;
+  }
+  block_partials<1>(v, d.part, j, d.nb, blk);
+}
+
+__global__ void k_beta(Dev d, int k) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= d.R) return;
+  Col& c = d.col[j];
+  if (!c.active) { c.beta = 0.f; return; }
+  const double rzn = col_total(d.part, j, d.nb, 0);
+  c.pcg_iters += 1;
+  const bool stop = !(rzn > d.prm.tol_pcg * d.prm.tol_pcg * c.rz0) || k >= d.prm.max_iter_pcg || !isfinite(rzn);
+  c.beta = (float)(rzn / c.rz);
+  c.rz = rzn;
+  if (stop) c.active = 0;
+  else atomicAdd(&d.counters[0], 1);
+}
+
+__global__ void k_pcg_E(Dev d) {
+  const int j = blockIdx.y, blk = blockIdx.x;
+  const Col c = d.col[j];
+  const float beta = c.beta, rho = (float)d.rho;
+  double v[2] = {0, 0};
+  for (int i = blk * kIdx + threadIdx.x; i < min(d.n, (blk + 1) * kIdx); i += kT) {
+    const int64_t gi = (int64_t)j * d.n + i;
+    const float2 dd = d.Dv[gi], r = d.Rv[gi];
+    float2 p = d.Pv[gi];
+    if (c.active) {
+      const float2 zz = precond2(dd, r, rho);
+      p.x = zz.x + beta * p.x;
+      p.y = zz.y + beta * p.y;
+      d.Pv[gi] = p;
+    } else {
+      p = make_float2(0.f, 0.f);  // finished column: no further change
+    }
+    const float w = p.x - p.y;
+    const __nv_bfloat16 wh = __float2bfloat16_rn(w);
+    d.W[(int64_t)j * d.n + i] = wh;
+    d.W[(int64_t)(d.R + j) * d.n + i] = __float2bfloat16_rn(w - __bfloat162float(wh));
+    v[1] += (double)(dd.x * p.x * p.x + dd.y * p.y * p.y);
+  }
+  block_partials<2>(v, d.part, j, d.nb, blk);
+}
+
+// fraction-to-boundary ratios (reading R4)
+__global__ void k_steps(Dev d, int corr) {
+  const int j = blockIdx.y, blk = blockIdx.x;
+  const Col c = d.col[j];
+  double v[2] = {INFINITY, INFINITY};
+  for (int i = blk * kIdx + threadIdx.x; i < min(d.n, (blk + 1) * kIdx); i += kT) {
+    const int64_t gi = (int64_t)j * d.n + i;
+    const double* zp = d.zs + 4 * gi;
+    const float2 x1 = d.X1[gi];
+    const float2 x2 = corr ? d.X2[gi] : make_float2(0.f, 0.f);
+    const D2 du = dirn(zp[0], zp[2], x1.x, x2.x, c, d.prm.sigma3, corr);
+    const D2 dv = dirn(zp[1], zp[3], x1.y, x2.y, c, d.prm.sigma3, corr);
+    if (du.dz < 0.0) v[0] = fmin(v[0], -zp[0] / du.dz);
+    if (dv.dz < 0.0) v[0] = fmin(v[0], -zp[1] / dv.dz);
+    if (du.ds < 0.0) v[1] = fmin(v[1], -zp[2] / du.ds);
+    if (dv.ds < 0.0) v[1] = fmin(v[1], -zp[3] / dv.ds);
+  }
+  block_minima<2>(v, d.part, j, d.nb, blk);
+}
+
+__global__ void k_steps_fin(Dev d, int corr) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= d.R) return;
+  Col& c = d.col[j];
+  if (c.done) {
+    c.alpha_p = c.alpha_d = 0.0;
+    c.corr_next = 0;
+    return;
+  }
+  if (corr && !c.corr_next) return;  // keeps its predictor steps
+  double ap = fmin(1.0, d.prm.eta * col_total(d.part, j, d.nb, 0, true));
+  double ad = fmin(1.0, d.prm.eta * col_total(d.part, j, d.nb, 1, true));
+  if (d.prm.equal_steps) ap = ad = fmin(ap, ad);
+  c.alpha_p = ap;
+  c.alpha_d = ad;
+  if (!corr) {
+    c.corr_next = (ap <= d.prm.alpha_tilde || ad <= d.prm.alpha_tilde);
+    if (c.corr_next) {
+      c.alpha_p1 = ap;
+      c.alpha_d1 = ad;
+      ++c.correctors;
+      atomicAdd(&d.counters[2], 1);
+    }
+  } else {
+    c.corr = 1;
+  }
+  c.prev_ap = ap;
+  c.prev_ad = ad;
+}
+
+// trial point x~ = z~_u - z~_v of the corrector columns; partial z~.s~
+__global__ void k_trial(Dev d) {
+  const int j = blockIdx.y, blk = blockIdx.x;
+  const Col c = d.col[j];
+  double v[1] = {0.0};
+  for (int i = blk * kIdx + threadIdx.x; i < min(d.n, (blk + 1) * kIdx); i += kT) {
+    const int64_t gi = (int64_t)j * d.n + i;
+    const double* zp = d.zs + 4 * gi;
+    const float2 x1 = d.X1[gi];
+    const D2 du = dirn(zp[0], zp[2], x1.x, 0.f, c, d.prm.sigma3, false);
+    const D2 dv = dirn(zp[1], zp[3], x1.y, 0.f, c, d.prm.sigma3, false);
+    const double zu = zp[0] + c.alpha_p1 * du.dz, zv = zp[1] + c.alpha_p1 * dv.dz;
+    const double su = zp[2] + c.alpha_d1 * du.ds, sv = zp[3] + c.alpha_d1 * dv.ds;
+    d.X[gi] = zu - zv;
+    v[0] += zu * su + zv * sv;
+  }
+  block_partials<1>(v, d.part, j, d.nb, blk);
+}
+
+__global__ void k_mu_t(Dev d) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= d.R) return;
+  Col& c = d.col[j];
+  if (c.corr_next) {
+    c.mu_t = col_total(d.part, j, d.nb, 0) / (2.0 * d.n);
+    c.nmat += 2;
+  }
+}
+
+// ||c||: with x = 0 the residual kernel gives Gr = -A^T b
+__global__ void k_setup_cols(Dev d, const double* __restrict__ taus) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= d.R) return;
+  Col c{};
+  c.tau = taus[j];
+  c.alpha_p = c.alpha_d = c.prev_ap = c.prev_ad = 1.0;
+  c.cn = sqrt(2.0 * d.n * c.tau * c.tau + 2.0 * col_total(d.part, j, d.nb, 0));
+  c.nmat = 1;
+  d.col[j] = c;
+}
+
+// outputs in natural order and the float64 certificates (Gr holds the final residual)
+__global__ void k_exit(Dev d, double* const* __restrict__ xout, double* const* __restrict__ zsout) {
+  const int j = blockIdx.y, blk = blockIdx.x;
+  const double tau = d.col[j].tau;
+  double v[3] = {0, 0, 0};
+  for (int i = blk * kIdx + threadIdx.x; i < min(d.n, (blk + 1) * kIdx); i += kT) {
+    const int64_t gi = (int64_t)j * d.n + i;
+    const double* zp = d.zs + 4 * gi;
+    const double g = d.Gr[gi];
+    const double fzu = zp[2] - (tau + g), fzv = zp[3] - (tau - g);
+    const double x = zp[0] - zp[1];
+    const double y = x - g;
+    const double st = copysign(fmax(fabs(y) - tau, 0.0), y);
+    v[0] += fzu * fzu + fzv * fzv;
+    v[1] += (x - st) * (x - st);
+    v[2] += x * x;
+    xout[j][i] = x;
+    if (zsout && zsout[j]) {
+      zsout[j][i] = zp[0];
+      zsout[j][d.n + i] = zp[1];
+      zsout[j][2 * d.n + i] = zp[2];
+      zsout[j][3 * d.n + i] = zp[3];
+    }
+  }
+  block_partials<3>(v, d.part, j, d.nb, blk);
+}
+
+__global__ void k_info(Dev d, mfipm_info* infos) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= d.R) return;
+  const Col& c = d.col[j];
+  mfipm_info info{};
+  info.status = c.done ? c.stop : MFIPM_NOT_CONVERGED;
+  info.ipm_iters = c.ipm_iters;
+  info.correctors = c.correctors;
+  info.pcg_iters = c.pcg_iters;
+  info.n_mat = c.nmat;
+  info.rel_gap = c.rel_gap;
+  info.dual_res = sqrt(col_total(d.part, j, d.nb, 0)) / (1.0 + c.cn);
+  info.kkt_rel = sqrt(col_total(d.part, j, d.nb, 1)) / (1.0 + sqrt(col_total(d.part, j, d.nb, 2)));
+  info.primal_obj = c.P_obj;
+  infos[j] = info;
+}
+
+}  // namespace mr
+
+// ------------------------------------------------------------------ host orchestration
+size_t mrhs_workspace_bytes(int64_t m, int64_t n, int R) {
+  auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  const int nb = (int)((n + mr::kIdx - 1) / mr::kIdx);
+  size_t b = 0;
+  b += al((size_t)n * m * 2);             // At
+  b += al((size_t)R * n * 8) * 2;         // X, Gr
+  b += al((size_t)R * m * 8) * 2;         // Rr, Bm
+  b += al((size_t)R * n * 32);            // zs
+  b += al((size_t)R * n * 8) * 5;         // PCG pairs
+  b += al((size_t)2 * R * n * 2);         // W
+  b += al((size_t)2 * R * m * 2);         // Tb
+  b += al((size_t)2 * R * m * 4);         // C1
+  b += al((size_t)2 * R * n * 4);         // C2
+  b += al((size_t)R * nb * mr::kPart * 8) * 2;  // part, part2
+  b += al(sizeof(mr::Col) * R);
+  b += al(256);                           // counters
+  b += al((size_t)R * 8) * 3;             // taus, b / x / zs pointer arrays
+  b += al(sizeof(void*) * R);
+  return b;
+}
+
+namespace {
+int mr_fail(cudaError_t e, std::string* msg, const char* where) {
+  *msg = std::string(where) + ": " + cudaGetErrorString(e);
+  return MFIPM_CUDA;
+}
+}  // namespace
+
+int mrhs_solve(const MrhsCall& call, std::string* msg) {
+  using namespace mr;
+  const int64_t m = call.m, n = call.n;
+  const int R = call.R;
+  cudaStream_t st = call.stream;
+  char* ws = static_cast<char*>(call.workspace);
+  auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  const int nb = (int)((n + kIdx - 1) / kIdx);
+  Dev d{};
+  d.m = (int)m;
+  d.n = (int)n;
+  d.R = R;
+  d.nb = nb;
+  d.a_scale = call.a_scale;
+  d.A = static_cast<const __nv_bfloat16*>(call.A);
+  d.lda = call.lda;
+  d.prm = call.prm;
+  size_t o = 0;
+  auto take = [&](size_t bytes) { char* p = ws + o; o += al(bytes); return p; };
+  __nv_bfloat16* At = reinterpret_cast<__nv_bfloat16*>(take((size_t)n * m * 2));
+  d.At = At;
+  d.X = reinterpret_cast<double*>(take((size_t)R * n * 8));
+  d.Gr = reinterpret_cast<double*>(take((size_t)R * n * 8));
+  d.Rr = reinterpret_cast<double*>(take((size_t)R * m * 8));
+  d.Bm = reinterpret_cast<double*>(take((size_t)R * m * 8));
+  d.zs = reinterpret_cast<double*>(take((size_t)R * n * 32));
+  d.X1 = reinterpret_cast<float2*>(take((size_t)R * n * 8));
+  d.X2 = reinterpret_cast<float2*>(take((size_t)R * n * 8));
+  d.Rv = reinterpret_cast<float2*>(take((size_t)R * n * 8));
+  d.Pv = reinterpret_cast<float2*>(take((size_t)R * n * 8));
+  d.Dv = reinterpret_cast<float2*>(take((size_t)R * n * 8));
+  d.W = reinterpret_cast<__nv_bfloat16*>(take((size_t)2 * R * n * 2));
+  d.Tb = reinterpret_cast<__nv_bfloat16*>(take((size_t)2 * R * m * 2));
+  d.C1 = reinterpret_cast<float*>(take((size_t)2 * R * m * 4));
+  d.C2 = reinterpret_cast<float*>(take((size_t)2 * R * n * 4));
+  d.part = reinterpret_cast<double*>(take((size_t)R * nb * kPart * 8));
+  double* part2 = reinterpret_cast<double*>(take((size_t)R * nb * kPart * 8));
+  d.col = reinterpret_cast<Col*>(take(sizeof(Col) * R));
+  d.counters = reinterpret_cast<int*>(take(256));
+  double* taus = reinterpret_cast<double*>(take((size_t)R * 8));
+  const double** bptr = reinterpret_cast<const double**>(take((size_t)R * 8));
+  double** xptr = reinterpret_cast<double**>(take((size_t)R * 8));
+  double** zptr = reinterpret_cast<double**>(take(sizeof(void*) * R));
+  if (o > call.ws_bytes) {
+    *msg = "workspace too small for the shared-A solver";
+    return MFIPM_INVALID_ARG;
+  }
+  cudaError_t e;
+  std::vector<void*> hz(R, nullptr);
+  for (int j = 0; j < R; ++j) hz[j] = call.zs_out ? call.zs_out[j] : nullptr;
+  if ((e = cudaMemcpyAsync(taus, call.tau, R * 8, cudaMemcpyHostToDevice, st)) ||
+      (e = cudaMemcpyAsync(bptr, call.b, R * sizeof(void*), cudaMemcpyHostToDevice, st)) ||
+      (e = cudaMemcpyAsync(xptr, call.x, R * sizeof(void*), cudaMemcpyHostToDevice, st)) ||
+      (e = cudaMemcpyAsync(zptr, hz.data(), R * sizeof(void*), cudaMemcpyHostToDevice, st)))
+    return mr_fail(e, msg, "upload arguments");
+  // d.prm.rho: the Frobenius-closest multiple of I to A^T A (reading R2) is supplied by the caller
+  d.rho = call.rho;
+
+  const dim3 gIdx(nb, R);
+  const int colBlocks = (R + 127) / 128;
+  transpose_bf16<<<dim3((unsigned)((n + 31) / 32), (unsigned)((m + 31) / 32)), dim3(32, 8), 0, st>>>(d.A, d.lda, At,
+                                                                                                   (int)m, (int)n);
+  gather_b<<<dim3(8, R), 256, 0, st>>>(bptr, d.Bm, (int)m);
+  if ((e = cudaGetLastError())) return mr_fail(e, msg, "setup kernels");
+
+  auto residual = [&]() -> cudaError_t {
+    // Rr = a_scale A X - B ; Gr = a_scale A^T Rr
+    resid_gemm_df<<<dim3((unsigned)((m + 63) / 64), (unsigned)((R + 63) / 64)), kT, 0, st>>>(d.A, d.X, d.Bm, d.Rr,
+                                                                                                d.a_scale, (int)m, R,
+                                                                                                (int)n);
+    resid_gemm_df<<<dim3((unsigned)((n + 63) / 64), (unsigned)((R + 63) / 64)), kT, 0, st>>>(At, d.Rr, nullptr, d.Gr,
+                                                                                                d.a_scale, (int)n, R,
+                                                                                                (int)m);
+    k_colnorm2<<<dim3(nb, R), kT, 0, st>>>(d.Rr, (int)m, part2, nb);
+    return cudaGetLastError();
+  };
+  auto gemms = [&]() -> cudaError_t {
+    e = call.gemm(call.gemm_ctx, d.A, d.W, d.C1, (int)m, 2 * R, (int)n, st);
+    if (e) return e;
+    k_split_t<<<dim3(nb, R), kT, 0, st>>>(d, part2);
+    e = call.gemm(call.gemm_ctx, At, d.Tb, d.C2, (int)n, 2 * R, (int)m, st);
+    if (e) return e;
+    return cudaGetLastError();
+  };
+  auto pcg = [&](float2* Xo) -> cudaError_t {
+    for (int k = 0;; ++k) {
+      if ((e = gemms())) return e;
+      k_alpha<<<colBlocks, 128, 0, st>>>(d, k == 0, part2);
+      k_pcg_D<<<gIdx, kT, 0, st>>>(d, Xo, k == 0);
+      if ((e = cudaMemsetAsync(d.counters, 0, 4, st))) return e;
+      k_beta<<<colBlocks, 128, 0, st>>>(d, k + 1);
+      int active = 0;
+      if ((e = cudaMemcpyAsync(&active, d.counters, 4, cudaMemcpyDeviceToHost, st))) return e;
+      if ((e = cudaStreamSynchronize(st))) return e;
+      if (active == 0) return cudaSuccess;
+      k_pcg_E<<<gIdx, kT, 0, st>>>(d);
+    }
+  };
+
+  // setup: ||A^T b|| for ||c||
+  if ((e = cudaMemsetAsync(d.X, 0, (size_t)R * n * 8, st))) return mr_fail(e, msg, "clear x");
+  if ((e = residual())) return mr_fail(e, msg, "residual");
+  k_colnorm2<<<dim3(nb, R), kT, 0, st>>>(d.Gr, (int)n, d.part, nb);
+  k_setup_cols<<<colBlocks, 128, 0, st>>>(d, taus);
+  for (int it = 1;; ++it) {
+    k_update<<<gIdx, kT, 0, st>>>(d, it == 1);
+    if ((e = residual())) return mr_fail(e, msg, "residual");
+    if ((e = cudaMemsetAsync(d.counters, 0, 16, st))) return mr_fail(e, msg, "counters");
+    k_stats<<<colBlocks, 128, 0, st>>>(d, it, part2);
+    int unfinished = 0;
+    if ((e = cudaMemcpyAsync(&unfinished, d.counters + 1, 4, cudaMemcpyDeviceToHost, st)) ||
+        (e = cudaStreamSynchronize(st)))
+      return mr_fail(e, msg, "gap test");
+    if (unfinished == 0) break;
+    k_pcg_init<<<gIdx, kT, 0, st>>>(d, 0);
+    if ((e = pcg(d.X1))) return mr_fail(e, msg, "predictor PCG");
+    k_steps<<<gIdx, kT, 0, st>>>(d, 0);
+    k_steps_fin<<<colBlocks, 128, 0, st>>>(d, 0);
+    int ncorr = 0;
+    if ((e = cudaMemcpyAsync(&ncorr, d.counters + 2, 4, cudaMemcpyDeviceToHost, st)) ||
+        (e = cudaStreamSynchronize(st)))
+      return mr_fail(e, msg, "step lengths");
+    if (ncorr > 0) {
+      k_trial<<<gIdx, kT, 0, st>>>(d);
+      k_mu_t<<<colBlocks, 128, 0, st>>>(d);
+      if ((e = residual())) return mr_fail(e, msg, "trial residual");
+      k_pcg_init<<<gIdx, kT, 0, st>>>(d, 1);
+      if ((e = pcg(d.X2))) return mr_fail(e, msg, "corrector PCG");
+      k_steps<<<gIdx, kT, 0, st>>>(d, 1);
+      k_steps_fin<<<colBlocks, 128, 0, st>>>(d, 1);
+    }
+  }
+  k_exit<<<gIdx, kT, 0, st>>>(d, xptr, zptr);
+  k_info<<<colBlocks, 128, 0, st>>>(d, call.infos_dev);
+  if ((e = cudaGetLastError())) return mr_fail(e, msg, "exit");
+  return MFIPM_OK;
+}
+
+namespace mr {
+__global__ void k_fro2(const __nv_bfloat16* __restrict__ A, int64_t m, int64_t n, int64_t lda, double* out) {
+  double s = 0.0;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m * n; e += (int64_t)gridDim.x * blockDim.x) {
+    const double a = bf(A[(e / n) * lda + e % n]);
+    s += a * a;
+  }
+  s = warp_sum(s);
+  if ((threadIdx.x & 31) == 0) atomicAdd(out, s);
+}
+}  // namespace mr
+
+cudaError_t bf16_fro2(const void* A, int64_t m, int64_t n, int64_t lda, double* out, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(out, 0, 8, st);
+  if (e) return e;
+  mr::k_fro2<<<1024, 256, 0, st>>>(static_cast<const __nv_bfloat16*>(A), m, n, lda, out);
+  return cudaGetLastError();
+}
+
+cudaError_t gemm_simple(void*, const void* Aop, const void* Bop, float* C, int rows, int N, int K, cudaStream_t st) {
+  mr::gemm_bf16_simple<<<dim3((unsigned)((rows + 63) / 64), (unsigned)((N + 63) / 64)), mr::kT, 0, st>>>(
+      static_cast<const __nv_bfloat16*>(Aop), static_cast<const __nv_bfloat16*>(Bop), C, rows, N, K);
+  return cudaGetLastError();
+}
+
+}  // namespace mfipm

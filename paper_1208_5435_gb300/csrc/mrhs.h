@@ -1,0 +1,42 @@
+// Host interface of the shared-A multi-right-hand-side solver (mrhs.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "internal.h"
+
+namespace mfipm {
+
+// C[c][r] = sum_k Aop[r][k] * Bop[c][k]: Aop rows x K and Bop N x K, both bf16 row-major
+// (K-major); C is N x rows float32.
+using GemmFn = cudaError_t (*)(void* ctx, const void* Aop, const void* Bop, float* C, int rows, int N, int K,
+                               cudaStream_t st);
+
+struct MrhsCall {
+  int64_t m, n, lda;
+  int R;
+  const void* A;          // DEVICE bf16 m x n
+  double a_scale, rho;
+  const double* const* b; // HOST array of DEVICE pointers
+  const double* tau;      // HOST
+  double* const* x;       // HOST array of DEVICE pointers
+  double* const* zs_out;  // HOST array or null
+  mfipm_info* infos_dev;  // DEVICE
+  void* workspace;
+  size_t ws_bytes;
+  SolveParams prm;
+  cudaStream_t stream;
+  GemmFn gemm;
+  void* gemm_ctx;
+};
+
+size_t mrhs_workspace_bytes(int64_t m, int64_t n, int R);
+int mrhs_solve(const MrhsCall& call, std::string* msg);
+cudaError_t gemm_simple(void*, const void* Aop, const void* Bop, float* C, int rows, int N, int K, cudaStream_t st);
+// ||A||_F^2 of a bf16 matrix (device result in *out)
+cudaError_t bf16_fro2(const void* A, int64_t m, int64_t n, int64_t lda, double* out, cudaStream_t st);
+
+}  // namespace mfipm
