@@ -204,6 +204,18 @@ int mfipm_kkt_residual(const mfipm_operator* op, const double* b, double tau, co
 int mfipm_set_timing(int32_t enable);
 double mfipm_last_kernel_ms(void);
 
+/* The bf16 GEMM of the shared-A solver (MFIPM_PREC_BF16_A), exposed for testing and reuse (not
+ * in the paper):  C_s[c][r] = sum_{k in slice s} Aop[r][k] * Bop[c][k]  for s < splits, with
+ * Aop (rows x K) and Bop (N x K) bf16 row-major DEVICE arrays and C a DEVICE array of
+ * splits x N x rows float32 (the sum of the slices is the product; split-K).  tensor_cores = 1
+ * runs the tcgen05/TMA kernel (N <= 256, K % 8 == 0, 16-byte aligned operands), 0 a plain
+ * CUDA-core kernel (splits = 1).  Synchronises `stream`; MFIPM_TIMEOUT if a bounded device
+ * wait expired. */
+int mfipm_gemm_bf16(const void* Aop, const void* Bop, float* C, int32_t rows, int32_t N, int32_t K, int32_t splits,
+                    int32_t tensor_cores, void* stream);
+/* Use (1, default) or bypass (0) the tensor-core GEMM inside the bf16 solver on this process. */
+int mfipm_set_gemm_mode(int32_t tensor_cores);
+
 /* Message of the last failing call on this thread ("" if none). */
 const char* mfipm_last_error(void);
 

@@ -62,6 +62,9 @@ SIGNATURES = {
     "mfipm_kkt_residual": (ctypes.c_int, [ctypes.POINTER(Operator), _P, ctypes.c_double, _P, _P, ctypes.c_size_t,
                                           ctypes.POINTER(ctypes.c_double), _P]),
     "mfipm_last_error": (ctypes.c_char_p, []),
+    "mfipm_gemm_bf16": (ctypes.c_int, [_P, _P, _P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                       ctypes.c_int32, _P]),
+    "mfipm_set_gemm_mode": (ctypes.c_int, [ctypes.c_int32]),
     "mfipm_set_timing": (ctypes.c_int, [ctypes.c_int32]),
     "mfipm_last_kernel_ms": (ctypes.c_double, []),
 }

@@ -22,6 +22,9 @@ namespace {
 
 thread_local std::string g_err;
 
+// Plain CUDA-core GEMM instead of tcgen05 in the bf16 solver (mfipm_set_gemm_mode; for tests).
+bool g_force_simple_gemm = false;
+
 // Optional timing of the solver kernel (mfipm_set_timing / mfipm_last_kernel_ms).
 thread_local bool g_timing = false;
 thread_local cudaEvent_t g_ev[2] = {nullptr, nullptr};
@@ -405,6 +408,13 @@ std::vector<int> cost_order(const mfipm_operator* ops, int batch) {
   return ord;
 }
 
+__device__ int g_gemm_err_word;
+int* g_gemm_err_ptr() {
+  void* p = nullptr;
+  if (cudaGetSymbolAddress(&p, g_gemm_err_word) != cudaSuccess) return nullptr;
+  return static_cast<int*>(p);
+}
+
 // ------------------------------------------------------------------ bf16 shared-A solver
 int solve_shared_bf16(int batch, const mfipm_operator* ops, const double* const* b, const double* tau,
                       const mfipm_params* p, double* const* x, double* const* zs_out, void* workspace,
@@ -446,11 +456,31 @@ int solve_shared_bf16(int batch, const mfipm_operator* ops, const double* const*
   call.ws_bytes = ws_bytes - off;
   call.prm = to_solve(p);
   call.stream = st;
-  call.gemm = gemm_simple;
-  call.gemm_ctx = nullptr;
+  int* err_dev = reinterpret_cast<int*>(ws + 64);
+  if ((e = cudaMemsetAsync(err_dev, 0, 4, st))) return cuda_fail(e, "clear error word");
+  call.err_dev = err_dev;
+  const int m32 = (int)ops[0].m, n32 = (int)ops[0].n;
+  if (tc_gemm_supported(m32, 2 * batch, n32) && tc_gemm_supported(n32, 2 * batch, m32) && !g_force_simple_gemm) {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    call.gemm = [](void* ctx, const void* Aop, const void* Bop, float* C, int rows, int N, int K, int splits,
+                   cudaStream_t s2) { return tc_gemm(Aop, Bop, C, rows, N, K, splits, static_cast<int*>(ctx), s2); };
+    call.gemm_ctx = err_dev;
+    call.splits1 = std::min(kMaxSplits, tc_gemm_splits(m32, n32, sms));
+    call.splits2 = std::min(kMaxSplits, tc_gemm_splits(n32, m32, sms));
+  } else {
+    call.gemm = gemm_simple;
+    call.gemm_ctx = nullptr;
+    call.splits1 = call.splits2 = 1;
+  }
   std::string msg;
   rc = mrhs_solve(call, &msg);
   if (rc) return fail(rc, "%s", msg.c_str());
+  int gemm_err = 0;
+  if ((e = cudaMemcpyAsync(&gemm_err, err_dev, 4, cudaMemcpyDeviceToHost, st)) || (e = cudaStreamSynchronize(st)))
+    return cuda_fail(e, "read GEMM status");
+  if (gemm_err) return fail(gemm_err, "tensor-core GEMM: a bounded mbarrier wait expired");
   std::vector<mfipm_info> tmp;
   if (!infos) {
     tmp.resize(batch);
@@ -680,5 +710,37 @@ int mfipm_set_timing(int32_t enable) {
 }
 
 double mfipm_last_kernel_ms(void) { return (double)g_last_ms; }
+
+int mfipm_set_gemm_mode(int32_t tensor_cores) {
+  g_force_simple_gemm = tensor_cores == 0;
+  return MFIPM_OK;
+}
+
+int mfipm_gemm_bf16(const void* Aop, const void* Bop, float* C, int32_t rows, int32_t N, int32_t K, int32_t splits,
+                    int32_t tensor_cores, void* stream) {
+  g_err.clear();
+  if (!Aop || !Bop || !C || rows < 1 || N < 1 || K < 1 || splits < 1 || splits > kMaxSplits)
+    return fail(MFIPM_INVALID_ARG, "mfipm_gemm_bf16: bad arguments");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaError_t e;
+  if (tensor_cores) {
+    if (!tc_gemm_supported(rows, N, K)) return fail(MFIPM_UNSUPPORTED, "tensor-core GEMM needs N <= 256, K % 8 == 0");
+    int* err_dev = nullptr;
+    // the error word lives in the caller's C buffer tail? no: use a tiny static device flag
+    err_dev = g_gemm_err_ptr();
+    if (!err_dev) return fail(MFIPM_CUDA, "no device error word");
+    if ((e = cudaMemsetAsync(err_dev, 0, 4, st))) return cuda_fail(e, "clear error word");
+    if ((e = tc_gemm(Aop, Bop, C, rows, N, K, splits, err_dev, st))) return cuda_fail(e, "tc_gemm");
+    int herr = 0;
+    if ((e = cudaMemcpyAsync(&herr, err_dev, 4, cudaMemcpyDeviceToHost, st)) || (e = cudaStreamSynchronize(st)))
+      return cuda_fail(e, "tc_gemm status");
+    if (herr) return fail(herr, "tensor-core GEMM: a bounded mbarrier wait expired");
+    return MFIPM_OK;
+  }
+  if (splits != 1) return fail(MFIPM_INVALID_ARG, "the CUDA-core GEMM has no split-K");
+  if ((e = gemm_simple(nullptr, Aop, Bop, C, rows, N, K, 1, st))) return cuda_fail(e, "gemm_simple");
+  if ((e = cudaStreamSynchronize(st))) return cuda_fail(e, "gemm_simple");
+  return MFIPM_OK;
+}
 
 }  // extern "C"

@@ -225,8 +225,9 @@ struct Dev {
   float2 *X1, *X2, *Rv, *Pv, *Dv;  // R x n each
   __nv_bfloat16* W;                // 2R x n
   __nv_bfloat16* Tb;               // 2R x m
-  float* C1;                       // 2R x m
-  float* C2;                       // 2R x n
+  float* C1;                       // s1 x 2R x m  (split-K slices)
+  float* C2;                       // s2 x 2R x n
+  int s1, s2;
   double* part;                    // R x nb x kPart
   Col* col;
   int* counters;                   // [0] active PCG columns, [1] unfinished columns, [2] corrector columns
@@ -380,7 +381,12 @@ __global__ void k_split_t(Dev d, double* part2) {
   double v[1] = {0.0};
   const int per = (d.m + d.nb - 1) / d.nb;
   for (int i = blk * per + threadIdx.x; i < min(d.m, (blk + 1) * per); i += kT) {
-    const float t = (float)d.a_scale * (d.C1[(int64_t)j * d.m + i] + d.C1[(int64_t)(d.R + j) * d.m + i]);
+    float acc = 0.f;
+    for (int sp = 0; sp < d.s1; ++sp) {
+      const float* C = d.C1 + (int64_t)sp * 2 * d.R * d.m;
+      acc += C[(int64_t)j * d.m + i] + C[(int64_t)(d.R + j) * d.m + i];
+    }
+    const float t = (float)d.a_scale * acc;
     const __nv_bfloat16 th = __float2bfloat16_rn(t);
     d.Tb[(int64_t)j * d.m + i] = th;
     d.Tb[(int64_t)(d.R + j) * d.m + i] = __float2bfloat16_rn(t - __bfloat162float(th));
@@ -414,7 +420,12 @@ __global__ void k_pcg_D(Dev d, float2* __restrict__ Xo, int first) {
     float2 x = first ? make_float2(0.f, 0.f) : Xo[gi];
     float2 r = d.Rv[gi];
     const float2 p = d.Pv[gi], dd = d.Dv[gi];
-    const float y = sc * (d.C2[(int64_t)j * d.n + i] + d.C2[(int64_t)(d.R + j) * d.n + i]);
+    float yacc = 0.f;
+    for (int sp = 0; sp < d.s2; ++sp) {
+      const float* C = d.C2 + (int64_t)sp * 2 * d.R * d.n;
+      yacc += C[(int64_t)j * d.n + i] + C[(int64_t)(d.R + j) * d.n + i];
+    }
+    const float y = sc * yacc;
     x.x += alpha * p.x;
     x.y += alpha * p.y;
     r.x -= alpha * (dd.x * p.x + y);
@@ -616,8 +627,8 @@ size_t mrhs_workspace_bytes(int64_t m, int64_t n, int R) {
   b += al((size_t)R * n * 8) * 5;         // PCG pairs
   b += al((size_t)2 * R * n * 2);         // W
   b += al((size_t)2 * R * m * 2);         // Tb
-  b += al((size_t)2 * R * m * 4);         // C1
-  b += al((size_t)2 * R * n * 4);         // C2
+  b += al((size_t)kMaxSplits * 2 * R * m * 4);  // C1
+  b += al((size_t)kMaxSplits * 2 * R * n * 4);  // C2
   b += al((size_t)R * nb * mr::kPart * 8) * 2;  // part, part2
   b += al(sizeof(mr::Col) * R);
   b += al(256);                           // counters
@@ -666,8 +677,10 @@ int mrhs_solve(const MrhsCall& call, std::string* msg) {
   d.Dv = reinterpret_cast<float2*>(take((size_t)R * n * 8));
   d.W = reinterpret_cast<__nv_bfloat16*>(take((size_t)2 * R * n * 2));
   d.Tb = reinterpret_cast<__nv_bfloat16*>(take((size_t)2 * R * m * 2));
-  d.C1 = reinterpret_cast<float*>(take((size_t)2 * R * m * 4));
-  d.C2 = reinterpret_cast<float*>(take((size_t)2 * R * n * 4));
+  d.C1 = reinterpret_cast<float*>(take((size_t)kMaxSplits * 2 * R * m * 4));
+  d.C2 = reinterpret_cast<float*>(take((size_t)kMaxSplits * 2 * R * n * 4));
+  d.s1 = std::min(call.splits1, kMaxSplits);
+  d.s2 = std::min(call.splits2, kMaxSplits);
   d.part = reinterpret_cast<double*>(take((size_t)R * nb * kPart * 8));
   double* part2 = reinterpret_cast<double*>(take((size_t)R * nb * kPart * 8));
   d.col = reinterpret_cast<Col*>(take(sizeof(Col) * R));
@@ -710,10 +723,10 @@ int mrhs_solve(const MrhsCall& call, std::string* msg) {
     return cudaGetLastError();
   };
   auto gemms = [&]() -> cudaError_t {
-    e = call.gemm(call.gemm_ctx, d.A, d.W, d.C1, (int)m, 2 * R, (int)n, st);
+    e = call.gemm(call.gemm_ctx, d.A, d.W, d.C1, (int)m, 2 * R, (int)n, d.s1, st);
     if (e) return e;
     k_split_t<<<dim3(nb, R), kT, 0, st>>>(d, part2);
-    e = call.gemm(call.gemm_ctx, At, d.Tb, d.C2, (int)n, 2 * R, (int)m, st);
+    e = call.gemm(call.gemm_ctx, At, d.Tb, d.C2, (int)n, 2 * R, (int)m, d.s2, st);
     if (e) return e;
     return cudaGetLastError();
   };
@@ -790,7 +803,9 @@ cudaError_t bf16_fro2(const void* A, int64_t m, int64_t n, int64_t lda, double* 
   return cudaGetLastError();
 }
 
-cudaError_t gemm_simple(void*, const void* Aop, const void* Bop, float* C, int rows, int N, int K, cudaStream_t st) {
+cudaError_t gemm_simple(void*, const void* Aop, const void* Bop, float* C, int rows, int N, int K, int splits,
+                        cudaStream_t st) {
+  if (splits != 1) return cudaErrorInvalidValue;
   mr::gemm_bf16_simple<<<dim3((unsigned)((rows + 63) / 64), (unsigned)((N + 63) / 64)), mr::kT, 0, st>>>(
       static_cast<const __nv_bfloat16*>(Aop), static_cast<const __nv_bfloat16*>(Bop), C, rows, N, K);
   return cudaGetLastError();

@@ -12,8 +12,9 @@ namespace mfipm {
 
 // C[c][r] = sum_k Aop[r][k] * Bop[c][k]: Aop rows x K and Bop N x K, both bf16 row-major
 // (K-major); C is N x rows float32.
+// With split-K the result is `splits` slices of N x rows (their sum is the product).
 using GemmFn = cudaError_t (*)(void* ctx, const void* Aop, const void* Bop, float* C, int rows, int N, int K,
-                               cudaStream_t st);
+                               int splits, cudaStream_t st);
 
 struct MrhsCall {
   int64_t m, n, lda;
@@ -31,11 +32,21 @@ struct MrhsCall {
   cudaStream_t stream;
   GemmFn gemm;
   void* gemm_ctx;
+  int splits1, splits2;   // split-K slices of T = A W and Y = A^T T
+  int* err_dev;           // DEVICE error word of the GEMMs (MFIPM_TIMEOUT)
 };
+
+constexpr int kMaxSplits = 8;
 
 size_t mrhs_workspace_bytes(int64_t m, int64_t n, int R);
 int mrhs_solve(const MrhsCall& call, std::string* msg);
-cudaError_t gemm_simple(void*, const void* Aop, const void* Bop, float* C, int rows, int N, int K, cudaStream_t st);
+cudaError_t gemm_simple(void*, const void* Aop, const void* Bop, float* C, int rows, int N, int K, int splits,
+                        cudaStream_t st);
+// tensor-core GEMM (tc_gemm.cu)
+bool tc_gemm_supported(int rows, int N, int K);
+int tc_gemm_splits(int rows, int K, int num_sms);
+cudaError_t tc_gemm(const void* Aop, const void* Bop, float* C, int rows, int N, int K, int splits, int* err,
+                    cudaStream_t st);
 // ||A||_F^2 of a bf16 matrix (device result in *out)
 cudaError_t bf16_fro2(const void* A, int64_t m, int64_t n, int64_t lda, double* out, cudaStream_t st);
 

@@ -47,6 +47,20 @@ def test_shared_bf16_uneven_columns_and_odd_sizes():
         assert np.linalg.norm(x - xo) <= 1e-6 * np.linalg.norm(xo)
 
 
+def test_shared_bf16_cuda_core_gemm_agrees():
+    """The solver with the CUDA-core GEMM reaches the same minimisers as with tcgen05."""
+    import paper_1208_5435_gb300 as M
+    probs = W.bf16_dense_problems(256, 1024, 10, 4, seed=2003)
+    xt, _ = _solve(probs, tol=1e-12)
+    M.lib().mfipm_set_gemm_mode(0)
+    try:
+        xs, infos = _solve(probs, tol=1e-12)
+    finally:
+        M.lib().mfipm_set_gemm_mode(1)
+    for a, b in zip(xt, xs):
+        assert np.linalg.norm(a - b) <= 1e-6 * np.linalg.norm(b)
+
+
 def test_shared_bf16_full_size_certificates():
     """4096 x 16384, 64 right-hand sides: every column reaches kkt_rel <= 1e-6 (float64,
     computed on the GPU) and four columns are re-certified on the CPU."""
