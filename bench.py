@@ -197,8 +197,10 @@ def run_ours(args, rank, world, local_rank):
     L = M.lib()
     dev = torch.device("cuda", local_rank)
     probs = W.make_workload(args.workload, count=args.count)
+    if probs[0].a_bf16 is not None:
+        return run_bf16(args, rank, world, local_rank, probs)
     if probs[0].kind != "dct":
-        raise SystemExit("bench.py times the partial-DCT workloads")
+        raise SystemExit("bench.py times the partial-DCT and the shared-A bf16 workloads")
     ops = [M.PartialDCT(p.n, torch.from_numpy(p.rows).to(dev)) for p in probs]
     bs = [torch.from_numpy(p.b).to(dev) for p in probs]
     taus = [p.tau for p in probs]
@@ -327,6 +329,99 @@ def run_ours(args, rank, world, local_rank):
         "cpu_baseline": cpu,
         "gpu_launches": 4 * args.steps,
         "clocks": clk.summary(),
+        "iterations": {"ipm_mean": statistics.mean(i["ipm_iters"] for i in infos),
+                       "pcg_mean": statistics.mean(i["pcg_iters"] for i in infos),
+                       "kkt_max": max(i["kkt_rel"] for i in infos)},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_bf16(args, rank, world, local_rank, probs):
+    """Shared-A bf16 workload: one step = one mfipm_solve_batched over all right-hand sides."""
+    import ctypes
+    import torch
+    import paper_1208_5435_gb300 as M
+
+    dev = torch.device("cuda", local_rank)
+    L = M.lib()
+    bits = torch.from_numpy(probs[0].a_bf16.view(np.int16)).view(torch.bfloat16).to(dev)
+    op = M.DenseBF16(bits, probs[0].a_scale)
+    ops = [op] * len(probs)
+    bs = [torch.from_numpy(p.b).to(dev) for p in probs]
+    taus = [p.tau for p in probs]
+    params = M.SolverParams()
+    ws = torch.empty(M.workspace_bytes(ops, params), dtype=torch.uint8, device=dev)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        M.solve_batched(ops, bs, taus, params, ws=ws)
+    torch.cuda.synchronize()
+    step_ms = []
+    with ClockSampler(local_rank) as clk:
+        for _ in range(args.steps):
+            flush.fill_(1)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            xs, infos = M.solve_batched(ops, bs, taus, params, ws=ws)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            step_ms.append(e0.elapsed_time(e1))
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ok = sum(1 for i in infos if i["status"] == 0 and i["kkt_rel"] <= KKT_GATE)
+    ms_per_step = total_ms / args.steps
+    # the tensor-core GEMMs of one PCG operator product, timed alone on their real shapes
+    m, n, R = probs[0].m, probs[0].n, len(probs)
+    W_ = torch.randn(2 * R, n, device=dev).to(torch.bfloat16)
+    T_ = torch.randn(2 * R, m, device=dev).to(torch.bfloat16)
+    At = bits.T.contiguous()
+    C1 = torch.empty(4, 2 * R, m, device=dev)
+    C2 = torch.empty(1, 2 * R, n, device=dev)
+    sh = ctypes.c_void_p(stream.cuda_stream)
+    def gemm_pair():
+        assert L.mfipm_gemm_bf16(bits.data_ptr(), W_.data_ptr(), C1.data_ptr(), m, 2 * R, n, 4, 1, sh) == 0
+        assert L.mfipm_gemm_bf16(At.data_ptr(), T_.data_ptr(), C2.data_ptr(), n, 2 * R, m, 1, 1, sh) == 0
+    for _ in range(3):
+        gemm_pair()
+    reps = 20
+    g_ms = []
+    for _ in range(reps):
+        flush.fill_(1)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        gemm_pair()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        g_ms.append(e0.elapsed_time(e1))
+    gms = statistics.median(g_ms)
+    gbytes = 2 * (m * n * 2) + 2 * R * (n + m) * 2 + (4 * 2 * R * m + 2 * R * n) * 4
+    gflop = 2 * 2 * m * n * 2 * R
+    peak, peak_kind = measured_peaks()
+    if rank != 0:
+        return
+    cpu = None
+    if not args.no_cpu and world == 1:
+        from oracle import mfipm_oracle as O
+        A = probs[0].A
+        t0 = time.perf_counter()
+        O.ipm(O.Operator.from_dense(A), probs[0].b, probs[0].tau, O.OracleParams(tol=1e-10, solver="woodbury"))
+        secs = time.perf_counter() - t0
+        cpu = {"value": 1.0 / secs, "unit": UNIT, "cores": cpu_threads(), "kind": "oracle",
+               "sample": f"1 of {len(probs)} right-hand sides, {secs:.1f} s: direct-solve float64 IPM (Woodbury m x m)"}
+    line = {
+        "metric": METRIC, "value": world * ok / (ms_per_step / 1e3), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "bf16 A / f32 PCG / f64 IPM", "data": "synthetic",
+        "config": {"workload": args.workload, "m": m, "n": n, "rhs": R, "l2": "flushed (512 MiB write) before each step",
+                   "solved_at_kkt_1e-6": ok},
+        "roofline": {"bound": "hbm", "achieved": gbytes / (gms / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
+                     "frac": gbytes / (gms / 1e3) / 1e9 / peak, "traffic": None, "peak_kind": peak_kind,
+                     "kernel": "tc_gemm_kernel pair (T = A W, Y = A^T T), timed alone", "kernel_ms": gms,
+                     "algorithmic_bytes": gbytes, "tensor_tflops": gflop / (gms / 1e3) / 1e12},
+        "cpu_baseline": cpu, "clocks": clk.summary(),
         "iterations": {"ipm_mean": statistics.mean(i["ipm_iters"] for i in infos),
                        "pcg_mean": statistics.mean(i["pcg_iters"] for i in infos),
                        "kkt_max": max(i["kkt_rel"] for i in infos)},
