@@ -8,8 +8,8 @@
 // where W (and T) are split into bf16 high and low halves, W = W_hi + W_lo, which keeps the
 // product accurate to ~2^-16 at the cost of doubling the GEMM's N (the GEMMs are bounded by
 // reading A, not by the tensor rate).  A transposed copy of A in the workspace makes both
-// GEMMs K-major.  The outer loop is float64: the residual A^T (A x - b) accumulates the exact
-// products of bf16 A and double-float x in double-float on the float32 pipes.
+// GEMMs K-major.  The outer loop is float64: the residual A^T (A x - b) is formed on the float32
+// pipes with a biased accumulator that captures every rounding error exactly (resid_gemm).
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <math.h>
@@ -146,48 +146,195 @@ __global__ void gemm_bf16_simple(const __nv_bfloat16* __restrict__ Aop, const __
     }
 }
 
-// Out[j][r] = scale * sum_k Aop[r][k] X[j][k] - (Bsub ? Bsub[j][r] : 0), float64 result.
-// bf16 A is exact in float32; each product with x = xh + xl (double-float) is formed
-// exactly (FMA error term) and accumulated in double-float.
-__global__ void resid_gemm_df(const __nv_bfloat16* __restrict__ Aop, const double* __restrict__ X,
-                              const double* __restrict__ Bsub, double* __restrict__ Out, double scale, int rows,
-                              int R, int K) {
-  __shared__ float As[32][65];
-  __shared__ float Xh[32][65];
-  __shared__ float Xl[32][65];
-  const int r0 = blockIdx.x * 64, j0 = blockIdx.y * 64;
+// ------------------------------------------------------------------ float64-grade residual GEMMs
+// Out[j][r] = scale * sum_k Aop[r][k] X[j][k] (- Bsub[j][r]) for the outer residual
+// A^T (A x - b) of Eq. fzfs.  bf16 A is exact in float32 and x = xh + xl is carried as two
+// float32 halves.  Each output keeps a biased float32 accumulator H that starts at
+// H0 = 1.5 * 2^E, with 2^E >= 4 ||a_r|| ||x_j|| over the block's K range (Cauchy-Schwarz),
+// so H never leaves the binade [2^E, 2^(E+1)).  For a term t = a * xh:
+//     H' = fma(a, xh, H)            (one rounding)
+//     q  = H' - H                   (exact: H, H' in one binade)
+//     e  = fma(a, xh, -q)           (the rounding error of H', exact when a * xh fits
+//                                    24 bits below ulp(H); else rounded at 2^-24 |e|)
+// and the small remainders e + a * xl accumulate in float32 c, folded every K-tile into a
+// double-float sum.  Five float32 operations per term; the result H - H0 + sum(c) carries
+// ~2^-40 of ||a|| ||x||, which is what the float64 outer loop of Sec. 5.1 needs.
+constexpr int kRB = 64;   // rows per block
+constexpr int kJB = 64;   // columns (right-hand sides) per block
+constexpr int kKB = 32;   // K per tile
+constexpr int kMaxRsplit = 32;
+
+// K range [k0, k1) of split s out of S (whole tiles of kKB, identical in every kernel)
+__host__ __device__ __forceinline__ void split_range(int K, int S, int s, int* k0, int* k1) {
+  const int64_t T = (K + kKB - 1) / kKB;
+  const int t0 = (int)((int64_t)s * T / S), t1 = (int)((int64_t)(s + 1) * T / S);
+  *k0 = t0 * kKB;
+  *k1 = min(K, t1 * kKB);
+}
+// smallest power of two >= v, clamped to [2^-50, 2^50]
+__device__ __forceinline__ float pow2_ceil(float v) {
+  if (!(v > 0x1p-50f)) return 0x1p-50f;
+  if (v >= 0x1p50f) return 0x1p50f;
+  int e;
+  const float f = frexpf(v, &e);  // v = f 2^e, f in [0.5, 1)
+  return f == 0.5f ? ldexpf(1.f, e - 1) : ldexpf(1.f, e);
+}
+
+// pw[s * rows + r] >= ||Aop[r][range s]||_2, one warp per (row, split)
+__global__ void k_rowpow(const __nv_bfloat16* __restrict__ Aop, int64_t lda, int rows, int K, int S,
+                         float* __restrict__ pw) {
+  const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (w >= (int64_t)rows * S) return;
+  const int r = (int)(w / S), s = (int)(w % S);
+  int k0, k1;
+  split_range(K, S, s, &k0, &k1);
+  float acc = 0.f;
+  for (int k = k0 + lane; k < k1; k += 32) {
+    const float v = bf(Aop[(int64_t)r * lda + k]);
+    acc = fmaf(v, v, acc);
+  }
+  acc = warp_sum(acc);
+  if (lane == 0) pw[(int64_t)s * rows + r] = pow2_ceil(sqrtf(acc) * 1.0001f);
+}
+
+// X (float64, R x K) -> Xf = (hi, lo) float32 pairs, and cp[s * R + j] >= ||x_j[range s]||_2.
+// Block (s, j).
+__global__ void k_split_x(const double* __restrict__ X, float2* __restrict__ Xf, float* __restrict__ cp, int K,
+                          int R, int S) {
+  const int s = blockIdx.x, j = blockIdx.y;
+  int k0, k1;
+  split_range(K, S, s, &k0, &k1);
+  float acc = 0.f;
+  for (int k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
+    const double v = X[(int64_t)j * K + k];
+    const float h = __double2float_rn(v);
+    Xf[(int64_t)j * K + k] = make_float2(h, __double2float_rn(v - (double)h));
+    acc = fmaf(h, h, acc);
+  }
+  __shared__ float red[32];
+  acc = warp_sum(acc);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float t = 0.f;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    cp[(int64_t)s * R + j] = pow2_ceil(sqrtf(t) * 1.0001f);
+  }
+}
+
+// Part[s][j][r] (double-float) = sum over K range s of Aop[r][k] * (xh + xl)[j][k].
+// Block (row tile, column tile, split); 256 threads, 4 x 4 outputs each.  K tiles are double
+// buffered: A through registers (converted to float32 in shared memory), X by cp.async.
+// vecA: Aop rows and base 16-byte aligned with lda % 8 == 0.
+__device__ __forceinline__ void cp_async8(void* sdst, const void* gsrc, bool valid) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(sdst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(gsrc), "r"(valid ? 8 : 0) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+__global__ void __launch_bounds__(256, 2)
+resid_gemm(const __nv_bfloat16* __restrict__ Aop, int64_t lda, const float* __restrict__ rp,
+           const float2* __restrict__ Xf, const float* __restrict__ cp, float2* __restrict__ Part, int rows, int R,
+           int K, int S, int vecA) {
+  __shared__ __align__(16) float As[2][kKB][kRB];
+  __shared__ __align__(16) float2 Xs[2][kKB][kJB];
+  const int r0 = blockIdx.x * kRB, j0 = blockIdx.y * kJB, s = blockIdx.z;
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  df acc[4][4];
-  for (int k0 = 0; k0 < K; k0 += 32) {
-    for (int e = threadIdx.x; e < 64 * 32; e += kT) {
-      const int rr = e / 32, kk = e % 32;
-      As[kk][rr] = (r0 + rr < rows && k0 + kk < K) ? bf(Aop[(int64_t)(r0 + rr) * K + k0 + kk]) : 0.f;
-      const double xv = (j0 + rr < R && k0 + kk < K) ? X[(int64_t)(j0 + rr) * K + k0 + kk] : 0.0;
-      const df xd = to_df(xv);
-      Xh[kk][rr] = xd.hi;
-      Xl[kk][rr] = xd.lo;
-    }
-    __syncthreads();
-#pragma unroll 4
-    for (int kk = 0; kk < 32; ++kk) {
-      float a[4], xh[4], xl[4];
+  int k0, k1;
+  split_range(K, S, s, &k0, &k1);
+  // loader coordinates: 8 consecutive k of one row (A) / one column (X)
+  const int lrow = threadIdx.x >> 2, lk = (threadIdx.x & 3) * 8;
+  uint4 ra;
+  auto fetchA = [&](int kb) {
+    const int k = kb + lk, r = r0 + lrow;
+    if (r < rows && vecA && k + 8 <= k1) {
+      ra = *reinterpret_cast<const uint4*>(Aop + (int64_t)r * lda + k);
+    } else {
+      __nv_bfloat16 t[8];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        a[q] = As[kk][ty * 4 + q];
-        xh[q] = Xh[kk][tx * 4 + q];
-        xl[q] = Xl[kk][tx * 4 + q];
-      }
+      for (int i = 0; i < 8; ++i)
+        t[i] = (r < rows && k + i < k1) ? Aop[(int64_t)r * lda + k + i] : __float2bfloat16_rn(0.f);
+      ra = *reinterpret_cast<const uint4*>(t);
+    }
+  };
+  auto stashA = [&](int buf) {
+    const __nv_bfloat16* t = reinterpret_cast<const __nv_bfloat16*>(&ra);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) As[buf][lk + i][lrow] = bf(t[i]);
+  };
+  auto copyX = [&](int kb, int buf) {
+    const int k = kb + lk, j = j0 + lrow;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const bool ok = j < R && k + i < k1;
+      cp_async8(&Xs[buf][lk + i][lrow], ok ? (const void*)(Xf + (int64_t)j * K + k + i) : (const void*)Xf, ok);
+    }
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+  };
+
+  // H0 = 1.5 * 2^E with 2^E = 4 rp cp (exact: rp, cp are powers of two)
+  auto bias = [&](int p, int q) {
+    const int r = min(r0 + ty * 4 + p, rows - 1), j = min(j0 + tx * 4 + q, R - 1);
+    return 6.f * rp[(int64_t)s * rows + r] * cp[(int64_t)s * R + j];
+  };
+  float H[4][4], c[4][4], Sh[4][4], Sl[4][4];
+#pragma unroll
+  for (int p = 0; p < 4; ++p)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      H[p][q] = bias(p, q);
+      c[p][q] = Sh[p][q] = Sl[p][q] = 0.f;
+    }
+  if (k0 < k1) {
+    copyX(k0, 0);
+    fetchA(k0);
+    stashA(0);
+    cp_async_wait_all();
+  }
+  __syncthreads();
+  int buf = 0;
+  for (int kb = k0; kb < k1; kb += kKB) {
+    const bool more = kb + kKB < k1;
+    if (more) {
+      copyX(kb + kKB, buf ^ 1);
+      fetchA(kb + kKB);
+    }
+#pragma unroll 4
+    for (int kk = 0; kk < kKB; ++kk) {
+      const float4 a4 = *reinterpret_cast<const float4*>(&As[buf][kk][ty * 4]);
+      const float4 x01 = *reinterpret_cast<const float4*>(&Xs[buf][kk][tx * 4]);
+      const float4 x23 = *reinterpret_cast<const float4*>(&Xs[buf][kk][tx * 4 + 2]);
+      const float a[4] = {a4.x, a4.y, a4.z, a4.w};
+      const float xh[4] = {x01.x, x01.z, x23.x, x23.z};
+      const float xl[4] = {x01.y, x01.w, x23.y, x23.w};
 #pragma unroll
       for (int p = 0; p < 4; ++p)
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-          const float pr = __fmul_rn(a[p], xh[q]);
-          float e = __fmaf_rn(a[p], xh[q], -pr);
-          e = __fmaf_rn(a[p], xl[q], e);
-          acc[p][q] += df(pr, e);
+          const float hn = __fmaf_rn(a[p], xh[q], H[p][q]);
+          const float qv = __fsub_rn(hn, H[p][q]);
+          const float e = __fmaf_rn(a[p], xh[q], -qv);
+          c[p][q] = __fmaf_rn(a[p], xl[q], __fadd_rn(c[p][q], e));
+          H[p][q] = hn;
         }
     }
+    // fold the tile's remainders into the double-float sum
+#pragma unroll
+    for (int p = 0; p < 4; ++p)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const df t = df_two_sum(Sh[p][q], c[p][q]);
+        Sh[p][q] = t.hi;
+        Sl[p][q] = __fadd_rn(Sl[p][q], t.lo);
+        c[p][q] = 0.f;
+      }
+    if (more) {
+      stashA(buf ^ 1);
+      cp_async_wait_all();
+    }
     __syncthreads();
+    buf ^= 1;
   }
 #pragma unroll
   for (int p = 0; p < 4; ++p)
@@ -195,11 +342,56 @@ __global__ void resid_gemm_df(const __nv_bfloat16* __restrict__ Aop, const doubl
     for (int q = 0; q < 4; ++q) {
       const int r = r0 + ty * 4 + p, j = j0 + tx * 4 + q;
       if (r < rows && j < R) {
-        double v = scale * to_double(acc[p][q]);
-        if (Bsub) v -= Bsub[(int64_t)j * rows + r];
-        Out[(int64_t)j * rows + r] = v;
+        const df v = df(__fsub_rn(H[p][q], bias(p, q))) + df(Sh[p][q], Sl[p][q]);
+        Part[((int64_t)s * R + j) * rows + r] = make_float2(v.hi, v.lo);
       }
     }
+}
+
+// Rr = scale * sum_s Part1 - Bm (float64), its (hi, lo) split for the second GEMM, and
+// cp2[s2 * R + j] >= ||Rr_j[range s2]||.  Block (s2, j) over the K ranges of the second GEMM.
+__global__ void k_fin1(const float2* __restrict__ Part, int S1, const double* __restrict__ Bm, double scale,
+                       double* __restrict__ Rr, float2* __restrict__ Rf, float* __restrict__ cp2, int m, int R,
+                       int S2) {
+  const int s2 = blockIdx.x, j = blockIdx.y;
+  int k0, k1;
+  split_range(m, S2, s2, &k0, &k1);
+  float acc = 0.f;
+  for (int r = k0 + threadIdx.x; r < k1; r += blockDim.x) {
+    df v(0.f);
+    for (int s = 0; s < S1; ++s) {
+      const float2 t = Part[((int64_t)s * R + j) * m + r];
+      v = v + df(t.x, t.y);
+    }
+    const int64_t gi = (int64_t)j * m + r;
+    const double rv = scale * to_double(v) - Bm[gi];
+    Rr[gi] = rv;
+    const float h = __double2float_rn(rv);
+    Rf[gi] = make_float2(h, __double2float_rn(rv - (double)h));
+    acc = fmaf(h, h, acc);
+  }
+  __shared__ float red[32];
+  acc = warp_sum(acc);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float t = 0.f;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    cp2[(int64_t)s2 * R + j] = pow2_ceil(sqrtf(t) * 1.0001f);
+  }
+}
+// Gr = scale * sum_s Part2 (float64)
+__global__ void k_fin2(const float2* __restrict__ Part, int S2, double scale, double* __restrict__ Gr, int n, int R) {
+  const int64_t total = (int64_t)R * n;
+  for (int64_t gi = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; gi < total;
+       gi += (int64_t)gridDim.x * blockDim.x) {
+    df v(0.f);
+    for (int s = 0; s < S2; ++s) {
+      const float2 t = Part[(int64_t)s * total + gi];
+      v = v + df(t.x, t.y);
+    }
+    Gr[gi] = scale * to_double(v);
+  }
 }
 
 // ------------------------------------------------------------------ per-column state
@@ -634,10 +826,28 @@ size_t mrhs_workspace_bytes(int64_t m, int64_t n, int R) {
   b += al(256);                           // counters
   b += al((size_t)R * 8) * 3;             // taus, b / x / zs pointer arrays
   b += al(sizeof(void*) * R);
+  b += al((size_t)R * n * 8) + al((size_t)R * m * 8);                      // Xf, Rf
+  b += al((size_t)mr::kMaxRsplit * m * 4) + al((size_t)mr::kMaxRsplit * n * 4);  // row bounds
+  b += al((size_t)mr::kMaxRsplit * R * 4) * 2;                             // column bounds
   return b;
 }
 
 namespace {
+// split count S <= cap (and <= K tiles) whose tiles * S blocks fill whole waves best
+int pick_rsplit(int64_t tiles, int ktiles, int64_t slots, int cap) {
+  cap = std::max(1, std::min(cap, ktiles));
+  int best = 1;
+  double best_eff = 0.0;
+  for (int S = 1; S <= cap; ++S) {
+    const int64_t blocks = tiles * S, waves = (blocks + slots - 1) / slots;
+    const double eff = (double)blocks / (double)(waves * slots);
+    if (eff > best_eff + 1e-9) {
+      best = S;
+      best_eff = eff;
+    }
+  }
+  return best;
+}
 int mr_fail(cudaError_t e, std::string* msg, const char* where) {
   *msg = std::string(where) + ": " + cudaGetErrorString(e);
   return MFIPM_CUDA;
@@ -689,6 +899,12 @@ int mrhs_solve(const MrhsCall& call, std::string* msg) {
   const double** bptr = reinterpret_cast<const double**>(take((size_t)R * 8));
   double** xptr = reinterpret_cast<double**>(take((size_t)R * 8));
   double** zptr = reinterpret_cast<double**>(take(sizeof(void*) * R));
+  float2* Xf = reinterpret_cast<float2*>(take((size_t)R * n * 8));
+  float2* Rf = reinterpret_cast<float2*>(take((size_t)R * m * 8));
+  float* rp1 = reinterpret_cast<float*>(take((size_t)kMaxRsplit * m * 4));
+  float* rp2 = reinterpret_cast<float*>(take((size_t)kMaxRsplit * n * 4));
+  float* cp1 = reinterpret_cast<float*>(take((size_t)kMaxRsplit * R * 4));
+  float* cp2 = reinterpret_cast<float*>(take((size_t)kMaxRsplit * R * 4));
   if (o > call.ws_bytes) {
     *msg = "workspace too small for the shared-A solver";
     return MFIPM_INVALID_ARG;
@@ -711,14 +927,35 @@ int mrhs_solve(const MrhsCall& call, std::string* msg) {
   gather_b<<<dim3(8, R), 256, 0, st>>>(bptr, d.Bm, (int)m);
   if ((e = cudaGetLastError())) return mr_fail(e, msg, "setup kernels");
 
+  // residual GEMM splits: fill whole waves of resident blocks
+  int sms = 0, occ = 0, dev = 0;
+  if ((e = cudaGetDevice(&dev)) || (e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) ||
+      (e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, resid_gemm, 256, 0)))
+    return mr_fail(e, msg, "residual occupancy");
+  const int64_t slots = (int64_t)sms * std::max(occ, 1);
+  const int64_t part_cap = (int64_t)kMaxSplits * 2 * R * n * 4;  // bytes of C2, reused for the partials
+  const int jt = (R + kJB - 1) / kJB;
+  const int S1 = pick_rsplit((int64_t)((m + kRB - 1) / kRB) * jt, (int)((n + kKB - 1) / kKB), slots,
+                             (int)std::min<int64_t>(kMaxRsplit, part_cap / ((int64_t)R * m * 8)));
+  const int S2 = pick_rsplit((int64_t)((n + kRB - 1) / kRB) * jt, (int)((m + kKB - 1) / kKB), slots,
+                             (int)std::min<int64_t>(kMaxRsplit, part_cap / ((int64_t)R * n * 8)));
+  float2* Part = reinterpret_cast<float2*>(d.C2);
+  const bool vecA1 = (reinterpret_cast<uintptr_t>(d.A) & 15) == 0 && d.lda % 8 == 0;
+  const bool vecA2 = m % 8 == 0;
+  k_rowpow<<<(unsigned)(((int64_t)m * S1 * 32 + 255) / 256), 256, 0, st>>>(d.A, d.lda, (int)m, (int)n, S1, rp1);
+  k_rowpow<<<(unsigned)(((int64_t)n * S2 * 32 + 255) / 256), 256, 0, st>>>(At, m, (int)n, (int)m, S2, rp2);
+  if ((e = cudaGetLastError())) return mr_fail(e, msg, "row bounds");
+
   auto residual = [&]() -> cudaError_t {
     // Rr = a_scale A X - B ; Gr = a_scale A^T Rr
-    resid_gemm_df<<<dim3((unsigned)((m + 63) / 64), (unsigned)((R + 63) / 64)), kT, 0, st>>>(d.A, d.X, d.Bm, d.Rr,
-                                                                                                d.a_scale, (int)m, R,
-                                                                                                (int)n);
-    resid_gemm_df<<<dim3((unsigned)((n + 63) / 64), (unsigned)((R + 63) / 64)), kT, 0, st>>>(At, d.Rr, nullptr, d.Gr,
-                                                                                                d.a_scale, (int)n, R,
-                                                                                                (int)m);
+    k_split_x<<<dim3(S1, R), 256, 0, st>>>(d.X, Xf, cp1, (int)n, R, S1);
+    resid_gemm<<<dim3((unsigned)((m + kRB - 1) / kRB), jt, S1), 256, 0, st>>>(d.A, d.lda, rp1, Xf, cp1, Part, (int)m,
+                                                                            R, (int)n, S1, vecA1);
+    k_fin1<<<dim3(S2, R), 256, 0, st>>>(Part, S1, d.Bm, d.a_scale, d.Rr, Rf, cp2, (int)m, R, S2);
+    resid_gemm<<<dim3((unsigned)((n + kRB - 1) / kRB), jt, S2), 256, 0, st>>>(At, m, rp2, Rf, cp2, Part, (int)n, R,
+                                                                            (int)m, S2, vecA2);
+    k_fin2<<<(unsigned)std::min<int64_t>(((int64_t)R * n + 255) / 256, 4096), 256, 0, st>>>(Part, S2, d.a_scale,
+                                                                                           d.Gr, (int)n, R);
     k_colnorm2<<<dim3(nb, R), kT, 0, st>>>(d.Rr, (int)m, part2, nb);
     return cudaGetLastError();
   };
