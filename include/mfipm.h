@@ -54,7 +54,10 @@ typedef enum {
  *   MFIPM_OP_PARTIAL_DCT  A = m distinct rows of the orthonormal n x n DCT-II matrix
  *                         C[j,k] = a_j cos(pi*j*(2k+1)/(2n)), a_0 = sqrt(1/n), a_j = sqrt(2/n),
  *                         so that A A^T = I_m (Eq. eq:orthonormality).  n must be a power of
- *                         two with 64 <= n <= 65536. */
+ *                         two with 64 <= n <= 1048576: up to 65536 one thread-block
+ *                         cluster holds a problem's FFT in shared memory; from 131072 the
+ *                         problems of one length run in lockstep with a three-pass FFT
+ *                         through device memory (see mfipm_set_large_dct_threshold). */
 typedef enum { MFIPM_OP_DENSE = 0, MFIPM_OP_PARTIAL_DCT = 1 } mfipm_op_kind;
 
 /* Storage type of a dense A. */
@@ -155,7 +158,9 @@ int mfipm_solve_noalloc(const mfipm_operator* op, const double* b, double tau, c
                         double* x, double* zs_out, mfipm_info* info, void* stream);
 
 /* Solve `batch` independent problems in one persistent launch (one CTA cluster per problem,
- * problems taken from a device work queue, largest first).  ops, b, tau, x, zs_out, infos are
+ * problems taken from a device work queue, largest first).  Partial-DCT problems at or above
+ * the multi-pass threshold are solved after it, each group of equal n as one lockstep batch
+ * (every problem keeps its own IPM scalars; the operator passes cover the whole group).  ops, b, tau, x, zs_out, infos are
  * HOST arrays of length batch; b[j], x[j], zs_out[j] are DEVICE pointers (zs_out may be NULL or
  * hold NULLs).  Returns MFIPM_OK if every problem converged, else the first non-OK problem
  * status. */
@@ -203,6 +208,14 @@ int mfipm_kkt_residual(const mfipm_operator* op, const double* b, double tau, co
  * device time of the last solve in milliseconds (-1 if none).  Not in the paper. */
 int mfipm_set_timing(int32_t enable);
 double mfipm_last_kernel_ms(void);
+/* With timing enabled, the multi-pass partial-DCT solver (n at or above the threshold of
+ * mfipm_set_large_dct_threshold) records CUDA events around each operator product
+ * y = A^T A w of its PCG (the three FFT passes, Sec. 4's only use of A).  For the last such
+ * solve or backward on this thread: *ms = their summed device time (-1 if none),
+ * *bytes = their algorithmic bytes (w read and y written: 8 bytes per index of every problem
+ * the product covers), *products = how many products, *launches = how many kernels the
+ * whole call launched.  Not in the paper. */
+int mfipm_last_operator_stats(double* ms, double* bytes, int64_t* products, int64_t* launches);
 
 /* The bf16 GEMM of the shared-A solver (MFIPM_PREC_BF16_A), exposed for testing and reuse (not
  * in the paper):  C_s[c][r] = sum_{k in slice s} Aop[r][k] * Bop[c][k]  for s < splits, with
@@ -215,6 +228,13 @@ int mfipm_gemm_bf16(const void* Aop, const void* Bop, float* C, int32_t rows, in
                     int32_t tensor_cores, void* stream);
 /* Use (1, default) or bypass (0) the tensor-core GEMM inside the bf16 solver on this process. */
 int mfipm_set_gemm_mode(int32_t tensor_cores);
+/* Partial-DCT problems with n >= threshold (a power of two, default 131072 = twice the
+ * cluster solver's largest n; accepted range [1024, 131072]) are solved by the lockstep
+ * multi-pass solver, whose operator is the same chain of Sec. 2 (Eq. eq:orthonormality) as
+ * a three-pass four-step FFT over global memory; smaller ones by the cluster-resident
+ * persistent kernel.  Not in the paper: a process-wide switch, mainly so that tests can run
+ * the multi-pass path at sizes the oracle reaches.  MFIPM_INVALID_ARG below 1024. */
+int mfipm_set_large_dct_threshold(int64_t n);
 
 /* Message of the last failing call on this thread ("" if none). */
 const char* mfipm_last_error(void);

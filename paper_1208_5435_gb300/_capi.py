@@ -65,6 +65,9 @@ SIGNATURES = {
     "mfipm_gemm_bf16": (ctypes.c_int, [_P, _P, _P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                        ctypes.c_int32, _P]),
     "mfipm_set_gemm_mode": (ctypes.c_int, [ctypes.c_int32]),
+    "mfipm_set_large_dct_threshold": (ctypes.c_int, [ctypes.c_int64]),
+    "mfipm_last_operator_stats": (ctypes.c_int, [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                                                 ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
     "mfipm_set_timing": (ctypes.c_int, [ctypes.c_int32]),
     "mfipm_last_kernel_ms": (ctypes.c_double, []),
 }

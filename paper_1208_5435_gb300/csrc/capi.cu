@@ -14,6 +14,7 @@
 
 #include "device_common.cuh"
 #include "internal.h"
+#include "large_dct.h"
 #include "mrhs.h"
 
 using namespace mfipm;
@@ -56,15 +57,22 @@ bool is_pow2(int64_t v) { return v > 0 && (v & (v - 1)) == 0; }
 constexpr int64_t kDctMinN = 64, kDctMaxN = 65536;
 constexpr int64_t kDenseMaxM = 6144;
 
+// Partial-DCT problems with n >= this go to the lockstep multi-pass solver (large_dct.cu);
+// the rest to the cluster-resident persistent kernel (mfipm_set_large_dct_threshold).
+int64_t g_large_dct_min_n = 2 * kDctMaxN;
+bool is_large_dct(const mfipm_operator& o) {
+  return o.kind == MFIPM_OP_PARTIAL_DCT && o.n >= g_large_dct_min_n && o.n >= kLdMinN;
+}
+
 int validate_op(const mfipm_operator* op, int idx) {
   if (!op) return fail(MFIPM_INVALID_ARG, "operator %d is NULL", idx);
   if (op->m < 0 || op->n <= 0 || op->m > op->n)
     return fail(MFIPM_INVALID_ARG, "operator %d: need 0 <= m <= n, n > 0 (m=%lld n=%lld)", idx,
                 (long long)op->m, (long long)op->n);
   if (op->kind == MFIPM_OP_PARTIAL_DCT) {
-    if (!is_pow2(op->n) || op->n < kDctMinN || op->n > kDctMaxN)
+    if (!is_pow2(op->n) || op->n < kDctMinN || op->n > kLdMaxN)
       return fail(MFIPM_INVALID_ARG, "operator %d: partial DCT needs n a power of two in [%lld, %lld] (n=%lld)",
-                  idx, (long long)kDctMinN, (long long)kDctMaxN, (long long)op->n);
+                  idx, (long long)kDctMinN, (long long)kLdMaxN, (long long)op->n);
     if (op->m > 0 && !op->rows) return fail(MFIPM_INVALID_ARG, "operator %d: rows is NULL", idx);
     return MFIPM_OK;
   }
@@ -251,6 +259,10 @@ int prepare(int batch, const mfipm_operator* ops, const double* const* b, const 
     if (ops[i].kind == MFIPM_OP_DENSE && ops[i].a_dtype == MFIPM_A_BF16)
       return fail(MFIPM_UNSUPPORTED, "bf16 A is solved by the shared-A multi-RHS solver (precision MFIPM_PREC_BF16_A)");
   P.dct = kind == MFIPM_OP_PARTIAL_DCT;
+  for (int i = 0; i < batch; ++i)
+    if (P.dct && ops[i].n > kDctMaxN)
+      return fail(MFIPM_UNSUPPORTED, "operator %d: n=%lld above the cluster solver's %lld", i, (long long)ops[i].n,
+                  (long long)kDctMaxN);
   if (P.dct && p->precision != MFIPM_PREC_FP32_PCG)
     return fail(MFIPM_UNSUPPORTED, "the partial-DCT solver runs its PCG in float32 (precision=%d)", p->precision);
   if (!P.dct && p->precision == MFIPM_PREC_BF16_A)
@@ -408,6 +420,96 @@ std::vector<int> cost_order(const mfipm_operator* ops, int batch) {
   return ord;
 }
 
+// ------------------------------------------------------------------ large partial-DCT problems
+// A batch splits into the problems of the persistent kernel and groups of equal n for the
+// lockstep multi-pass solver, run one after the other on the caller's stream.
+struct Split {
+  std::vector<int> small;
+  std::vector<std::pair<int64_t, std::vector<int>>> groups;
+  bool any_large() const { return !groups.empty(); }
+};
+Split split_batch(const mfipm_operator* ops, int batch) {
+  Split sp;
+  for (int i = 0; i < batch; ++i) {
+    if (!is_large_dct(ops[i])) {
+      sp.small.push_back(i);
+      continue;
+    }
+    auto it = std::find_if(sp.groups.begin(), sp.groups.end(), [&](auto& g) { return g.first == ops[i].n; });
+    if (it == sp.groups.end()) sp.groups.push_back({ops[i].n, {i}});
+    else it->second.push_back(i);
+  }
+  return sp;
+}
+size_t split_small_bytes(const mfipm_operator* ops, const Split& sp, const mfipm_params* p) {
+  if (sp.small.empty()) return 0;
+  std::vector<mfipm_operator> sub;
+  for (int i : sp.small) sub.push_back(ops[i]);
+  return align256(make_layout(sub.data(), (int)sub.size(), pcg_in_fp64(sub[0], p)).total);
+}
+size_t split_large_bytes(const Split& sp) {
+  size_t b = 0;
+  for (auto& g : sp.groups) b = std::max(b, large_dct_workspace_bytes(g.first, (int)g.second.size()));
+  return b;
+}
+template <class T> std::vector<T> pick(const T* a, const std::vector<int>& idx) {
+  std::vector<T> r;
+  for (int i : idx) r.push_back(a ? a[i] : T{});
+  return r;
+}
+
+// forward (gx == null) or backward solve of the large groups
+int run_large_groups(const mfipm_operator* ops, const Split& sp, const double* const* b, const double* tau,
+                     double* const* x, double* const* zs_out, const double* const* zs_in,
+                     const double* const* gx, double* const* grad_b, double* grad_tau, const mfipm_params* p,
+                     char* ws, size_t ws_bytes, mfipm_info* infos, cudaStream_t st) {
+  for (auto& g : sp.groups) {
+    const std::vector<int>& idx = g.second;
+    const int R = (int)idx.size();
+    std::vector<int64_t> ms;
+    std::vector<const int64_t*> rows;
+    for (int i : idx) {
+      ms.push_back(ops[i].m);
+      rows.push_back(ops[i].rows);
+    }
+    auto vb = pick(b, idx);
+    auto vt = pick(tau, idx);
+    auto vx = pick(x, idx);
+    auto vz = pick(zs_out, idx);
+    auto vzi = pick(zs_in, idx);
+    auto vgx = pick(gx, idx);
+    auto vgb = pick(grad_b, idx);
+    std::vector<double> gt(R, 0.0);
+    std::vector<mfipm_info> inf(R);
+    LdCall c{};
+    c.n = g.first;
+    c.R = R;
+    c.m = ms.data();
+    c.rows = rows.data();
+    c.b = vb.data();
+    c.tau = tau ? vt.data() : nullptr;
+    c.x = x ? vx.data() : nullptr;
+    c.zs_out = zs_out ? vz.data() : nullptr;
+    c.zs_in = zs_in ? vzi.data() : nullptr;
+    c.gx = gx ? vgx.data() : nullptr;
+    c.grad_b = grad_b ? vgb.data() : nullptr;
+    c.grad_tau = gt.data();
+    c.infos = inf.data();
+    c.workspace = ws;
+    c.ws_bytes = ws_bytes;
+    c.prm = to_solve(p);
+    c.stream = st;
+    std::string msg;
+    const int rc = gx ? large_dct_backward(c, &msg) : large_dct_solve(c, &msg);
+    if (rc) return fail(rc, "%s", msg.c_str());
+    for (int k = 0; k < R; ++k) {
+      if (infos) infos[idx[k]] = inf[k];
+      if (grad_tau && gx) grad_tau[idx[k]] = gt[k];
+    }
+  }
+  return MFIPM_OK;
+}
+
 __device__ int g_gemm_err_word;
 int* g_gemm_err_ptr() {
   void* p = nullptr;
@@ -523,119 +625,60 @@ int noalloc_scratch(void** out) {
   return MFIPM_OK;
 }
 
-}  // namespace
-
-extern "C" {
-
-int mfipm_params_default(mfipm_params* p) {
-  if (!p) return fail(MFIPM_INVALID_ARG, "params is NULL");
-  memset(p, 0, sizeof(*p));
-  p->tol = 1e-10;
-  p->max_iter = 100;
-  p->tol_pcg = 1e-2;
-  p->max_iter_pcg = 200;
-  p->sigma1 = 0.1;
-  p->sigma2 = 0.5;
-  p->sigma3 = 0.8;
-  p->alpha_bar = 0.5;
-  p->alpha_tilde = 0.1;
-  p->eta = 0.995;
-  p->precision = MFIPM_PREC_FP32_PCG;
-  p->equal_steps = 0;
-  p->cluster_size = 0;
-  return MFIPM_OK;
-}
-
-int mfipm_workspace_size(const mfipm_operator* ops, int32_t batch, const mfipm_params* p, size_t* bytes) {
-  if (!ops || !bytes || batch < 1) return fail(MFIPM_INVALID_ARG, "NULL argument or batch < 1");
-  int rc = validate_params(p);
-  if (rc) return rc;
+int first_bad_status(const mfipm_info* infos, int batch) {
   for (int i = 0; i < batch; ++i)
-    if ((rc = validate_op(&ops[i], i))) return rc;
-  bool shared = false;
-  if ((rc = check_shared_bf16(ops, batch, p, &shared))) return rc;
-  if (shared) {
-    *bytes = 256 + ((sizeof(mfipm_info) * batch + 255) & ~(size_t)255) + 256 + mrhs_workspace_bytes(ops[0].m, ops[0].n, batch);
-    return MFIPM_OK;
-  }
-  *bytes = make_layout(ops, batch, pcg_in_fp64(ops[0], p)).total;
+    if (infos[i].status != MFIPM_OK) return infos[i].status;
   return MFIPM_OK;
 }
 
-int mfipm_solve(const mfipm_operator* op, const double* b, double tau, const mfipm_params* p, double* x,
-                double* zs_out, void* workspace, size_t ws_bytes, mfipm_info* info, void* stream) {
-  g_err.clear();
-  const double* bb[1] = {b};
-  double* xx[1] = {x};
-  double* zz[1] = {zs_out};
-  double tt[1] = {tau};
-  if (op && p && op->kind == MFIPM_OP_DENSE && op->a_dtype == MFIPM_A_BF16 && p->precision == MFIPM_PREC_BF16_A) {
-    int rc = validate_params(p);
-    if (rc || (rc = validate_op(op, 0))) return rc;
-    return solve_shared_bf16(1, op, bb, tt, p, xx, zs_out ? zz : nullptr, workspace, ws_bytes, info, stream);
+// a batch with large partial-DCT problems: the rest by the persistent kernel, then the
+// large groups, on one stream and one workspace
+int solve_split(int batch, const mfipm_operator* ops, const double* const* b, const double* tau,
+                const mfipm_params* p, double* const* x, double* const* zs_out, void* workspace, size_t ws_bytes,
+                mfipm_info* infos, void* stream, const Split& sp) {
+  for (int i = 0; i < batch; ++i) {
+    if (!(tau[i] > 0.0) || !isfinite(tau[i])) return fail(MFIPM_INVALID_ARG, "tau[%d] must be positive and finite", i);
+    if ((ops[i].m > 0 && !b[i]) || !x[i]) return fail(MFIPM_INVALID_ARG, "b[%d] or x[%d] is NULL", i, i);
+    if (ops[i].kind != MFIPM_OP_PARTIAL_DCT) return fail(MFIPM_UNSUPPORTED, "a batch must use one operator kind");
   }
-  Prepared P;
-  int rc = prepare(1, op, bb, tt, p, xx, zs_out ? zz : nullptr, workspace, ws_bytes, P);
-  if (rc) return rc;
-  mfipm_info tmp;
-  return run(P, static_cast<cudaStream_t>(stream), 1, info ? info : &tmp, nullptr);
-}
-
-int mfipm_solve_noalloc(const mfipm_operator* op, const double* b, double tau, const mfipm_params* p, double* x,
-                        double* zs_out, mfipm_info* info, void* stream) {
-  g_err.clear();
-  size_t need = 0;
-  int rc = mfipm_workspace_size(op, 1, p, &need);
-  if (rc) return rc;
-  if (need > kNoallocScratchBytes)
-    return fail(MFIPM_INVALID_ARG,
-                "mfipm_solve_noalloc: this problem needs %zu bytes of scratch, above the fixed %zu bytes; "
-                "use mfipm_solve with a caller workspace",
-                need, kNoallocScratchBytes);
-  void* ws = nullptr;
-  if ((rc = noalloc_scratch(&ws))) return rc;
-  const double* bb[1] = {b};
-  double* xx[1] = {x};
-  double* zz[1] = {zs_out};
-  double tt[1] = {tau};
-  Prepared P;
-  if ((rc = prepare(1, op, bb, tt, p, xx, zs_out ? zz : nullptr, ws, kNoallocScratchBytes, P))) return rc;
-  mfipm_info tmp;
-  return run(P, static_cast<cudaStream_t>(stream), 1, info ? info : &tmp, nullptr, /*allow_timing=*/false);
-}
-
-int mfipm_solve_batched(int32_t batch, const mfipm_operator* ops, const double* const* b, const double* tau,
-                        const mfipm_params* p, double* const* x, double* const* zs_out, void* workspace,
-                        size_t ws_bytes, mfipm_info* infos, void* stream) {
-  g_err.clear();
-  {
-    int rc = validate_params(p);
-    if (rc) return rc;
-    if (batch < 1 || !ops || !b || !tau || !x) return fail(MFIPM_INVALID_ARG, "NULL argument array or batch < 1");
-    for (int i = 0; i < batch; ++i)
-      if ((rc = validate_op(&ops[i], i))) return rc;
-    bool shared = false;
-    if ((rc = check_shared_bf16(ops, batch, p, &shared))) return rc;
-    if (shared) return solve_shared_bf16(batch, ops, b, tau, p, x, zs_out, workspace, ws_bytes, infos, stream);
-  }
-  Prepared P;
-  int rc = prepare(batch, ops, b, tau, p, x, zs_out, workspace, ws_bytes, P);
-  if (rc) return rc;
+  if (p->precision != MFIPM_PREC_FP32_PCG)
+    return fail(MFIPM_UNSUPPORTED, "the partial-DCT solver runs its PCG in float32 (precision=%d)", p->precision);
+  const size_t small = split_small_bytes(ops, sp, p), need = small + split_large_bytes(sp);
+  if (!workspace || ((uintptr_t)workspace & 255)) return fail(MFIPM_INVALID_ARG, "workspace NULL or not 256-byte aligned");
+  if (ws_bytes < need) return fail(MFIPM_INVALID_ARG, "workspace too small: %zu < %zu bytes", ws_bytes, need);
   std::vector<mfipm_info> tmp;
   if (!infos) {
     tmp.resize(batch);
     infos = tmp.data();
   }
-  std::vector<int> ord = cost_order(ops, batch);
-  return run(P, static_cast<cudaStream_t>(stream), batch, infos, &ord);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (!sp.small.empty()) {
+    const int ns = (int)sp.small.size();
+    auto vo = pick(ops, sp.small);
+    auto vb = pick(b, sp.small);
+    auto vt = pick(tau, sp.small);
+    auto vx = pick(x, sp.small);
+    auto vz = pick(zs_out, sp.small);
+    Prepared P;
+    int rc = prepare(ns, vo.data(), vb.data(), vt.data(), p, vx.data(), zs_out ? vz.data() : nullptr, workspace,
+                     small, P);
+    if (rc) return rc;
+    std::vector<mfipm_info> si(ns);
+    std::vector<int> ord = cost_order(vo.data(), ns);
+    rc = run(P, st, ns, si.data(), &ord);
+    for (int k = 0; k < ns; ++k) infos[sp.small[k]] = si[k];
+    if (rc && rc != MFIPM_NOT_CONVERGED && rc != MFIPM_NUMERIC) return rc;
+  }
+  int rc = run_large_groups(ops, sp, b, tau, x, zs_out, nullptr, nullptr, nullptr, nullptr, p,
+                            static_cast<char*>(workspace) + small, ws_bytes - small, infos, st);
+  if (rc) return rc;
+  return first_bad_status(infos, batch);
 }
 
-int mfipm_backward(int32_t batch, const mfipm_operator* ops, const double* const* b, const double* tau,
+int backward_persistent(int32_t batch, const mfipm_operator* ops, const double* const* b, const double* tau,
                    const double* const* x, const double* const* zs, const double* const* grad_x,
                    double* const* grad_b, double* grad_tau, double* const* grad_A, const mfipm_params* p,
                    void* workspace, size_t ws_bytes, mfipm_info* infos, void* stream) {
-  g_err.clear();
-  if (!zs || !grad_x) return fail(MFIPM_INVALID_ARG, "zs and grad_x are required");
   Prepared P;
   int rc = prepare(batch, ops, b, tau, p, const_cast<double* const*>(x), nullptr, workspace, ws_bytes, P);
   if (rc) return rc;
@@ -691,6 +734,180 @@ int mfipm_backward(int32_t batch, const mfipm_operator* ops, const double* const
   return MFIPM_OK;
 }
 
+}  // namespace
+
+extern "C" {
+
+int mfipm_params_default(mfipm_params* p) {
+  if (!p) return fail(MFIPM_INVALID_ARG, "params is NULL");
+  memset(p, 0, sizeof(*p));
+  p->tol = 1e-10;
+  p->max_iter = 100;
+  p->tol_pcg = 1e-2;
+  p->max_iter_pcg = 200;
+  p->sigma1 = 0.1;
+  p->sigma2 = 0.5;
+  p->sigma3 = 0.8;
+  p->alpha_bar = 0.5;
+  p->alpha_tilde = 0.1;
+  p->eta = 0.995;
+  p->precision = MFIPM_PREC_FP32_PCG;
+  p->equal_steps = 0;
+  p->cluster_size = 0;
+  return MFIPM_OK;
+}
+
+int mfipm_workspace_size(const mfipm_operator* ops, int32_t batch, const mfipm_params* p, size_t* bytes) {
+  if (!ops || !bytes || batch < 1) return fail(MFIPM_INVALID_ARG, "NULL argument or batch < 1");
+  int rc = validate_params(p);
+  if (rc) return rc;
+  for (int i = 0; i < batch; ++i)
+    if ((rc = validate_op(&ops[i], i))) return rc;
+  bool shared = false;
+  if ((rc = check_shared_bf16(ops, batch, p, &shared))) return rc;
+  if (shared) {
+    *bytes = 256 + ((sizeof(mfipm_info) * batch + 255) & ~(size_t)255) + 256 + mrhs_workspace_bytes(ops[0].m, ops[0].n, batch);
+    return MFIPM_OK;
+  }
+  const Split sp = split_batch(ops, batch);
+  if (sp.any_large()) {
+    *bytes = split_small_bytes(ops, sp, p) + split_large_bytes(sp);
+    return MFIPM_OK;
+  }
+  *bytes = make_layout(ops, batch, pcg_in_fp64(ops[0], p)).total;
+  return MFIPM_OK;
+}
+
+int mfipm_solve(const mfipm_operator* op, const double* b, double tau, const mfipm_params* p, double* x,
+                double* zs_out, void* workspace, size_t ws_bytes, mfipm_info* info, void* stream) {
+  g_err.clear();
+  const double* bb[1] = {b};
+  double* xx[1] = {x};
+  double* zz[1] = {zs_out};
+  double tt[1] = {tau};
+  if (op && p && op->kind == MFIPM_OP_DENSE && op->a_dtype == MFIPM_A_BF16 && p->precision == MFIPM_PREC_BF16_A) {
+    int rc = validate_params(p);
+    if (rc || (rc = validate_op(op, 0))) return rc;
+    return solve_shared_bf16(1, op, bb, tt, p, xx, zs_out ? zz : nullptr, workspace, ws_bytes, info, stream);
+  }
+  if (op && p && is_large_dct(*op)) {
+    int rc = validate_params(p);
+    if (rc || (rc = validate_op(op, 0))) return rc;
+    return solve_split(1, op, bb, tt, p, xx, zs_out ? zz : nullptr, workspace, ws_bytes, info, stream,
+                       split_batch(op, 1));
+  }
+  Prepared P;
+  int rc = prepare(1, op, bb, tt, p, xx, zs_out ? zz : nullptr, workspace, ws_bytes, P);
+  if (rc) return rc;
+  mfipm_info tmp;
+  return run(P, static_cast<cudaStream_t>(stream), 1, info ? info : &tmp, nullptr);
+}
+
+int mfipm_solve_noalloc(const mfipm_operator* op, const double* b, double tau, const mfipm_params* p, double* x,
+                        double* zs_out, mfipm_info* info, void* stream) {
+  g_err.clear();
+  size_t need = 0;
+  int rc = mfipm_workspace_size(op, 1, p, &need);
+  if (rc) return rc;
+  if (need > kNoallocScratchBytes)
+    return fail(MFIPM_INVALID_ARG,
+                "mfipm_solve_noalloc: this problem needs %zu bytes of scratch, above the fixed %zu bytes; "
+                "use mfipm_solve with a caller workspace",
+                need, kNoallocScratchBytes);
+  void* ws = nullptr;
+  if ((rc = noalloc_scratch(&ws))) return rc;
+  const double* bb[1] = {b};
+  double* xx[1] = {x};
+  double* zz[1] = {zs_out};
+  double tt[1] = {tau};
+  Prepared P;
+  if ((rc = prepare(1, op, bb, tt, p, xx, zs_out ? zz : nullptr, ws, kNoallocScratchBytes, P))) return rc;
+  mfipm_info tmp;
+  return run(P, static_cast<cudaStream_t>(stream), 1, info ? info : &tmp, nullptr, /*allow_timing=*/false);
+}
+
+int mfipm_solve_batched(int32_t batch, const mfipm_operator* ops, const double* const* b, const double* tau,
+                        const mfipm_params* p, double* const* x, double* const* zs_out, void* workspace,
+                        size_t ws_bytes, mfipm_info* infos, void* stream) {
+  g_err.clear();
+  {
+    int rc = validate_params(p);
+    if (rc) return rc;
+    if (batch < 1 || !ops || !b || !tau || !x) return fail(MFIPM_INVALID_ARG, "NULL argument array or batch < 1");
+    for (int i = 0; i < batch; ++i)
+      if ((rc = validate_op(&ops[i], i))) return rc;
+    bool shared = false;
+    if ((rc = check_shared_bf16(ops, batch, p, &shared))) return rc;
+    if (shared) return solve_shared_bf16(batch, ops, b, tau, p, x, zs_out, workspace, ws_bytes, infos, stream);
+    const Split sp = split_batch(ops, batch);
+    if (sp.any_large()) return solve_split(batch, ops, b, tau, p, x, zs_out, workspace, ws_bytes, infos, stream, sp);
+  }
+  Prepared P;
+  int rc = prepare(batch, ops, b, tau, p, x, zs_out, workspace, ws_bytes, P);
+  if (rc) return rc;
+  std::vector<mfipm_info> tmp;
+  if (!infos) {
+    tmp.resize(batch);
+    infos = tmp.data();
+  }
+  std::vector<int> ord = cost_order(ops, batch);
+  return run(P, static_cast<cudaStream_t>(stream), batch, infos, &ord);
+}
+
+int mfipm_backward(int32_t batch, const mfipm_operator* ops, const double* const* b, const double* tau,
+                   const double* const* x, const double* const* zs, const double* const* grad_x,
+                   double* const* grad_b, double* grad_tau, double* const* grad_A, const mfipm_params* p,
+                   void* workspace, size_t ws_bytes, mfipm_info* infos, void* stream) {
+  g_err.clear();
+  if (!zs || !grad_x) return fail(MFIPM_INVALID_ARG, "zs and grad_x are required");
+  if (batch < 1 || !ops || !b || !tau || !x) return fail(MFIPM_INVALID_ARG, "NULL argument array or batch < 1");
+  int rc = validate_params(p);
+  if (rc) return rc;
+  for (int i = 0; i < batch; ++i)
+    if ((rc = validate_op(&ops[i], i))) return rc;
+  const Split sp = split_batch(ops, batch);
+  if (!sp.any_large())
+    return backward_persistent(batch, ops, b, tau, x, zs, grad_x, grad_b, grad_tau, grad_A, p, workspace, ws_bytes,
+                               infos, stream);
+  for (int i = 0; i < batch; ++i) {
+    if (!zs[i] || !grad_x[i] || !b[i] || !x[i]) return fail(MFIPM_INVALID_ARG, "argument %d is NULL", i);
+    if (ops[i].kind != MFIPM_OP_PARTIAL_DCT) return fail(MFIPM_UNSUPPORTED, "a batch must use one operator kind");
+    if (grad_A && grad_A[i]) return fail(MFIPM_UNSUPPORTED, "grad_A is defined for dense operators only (operator %d)", i);
+  }
+  if (p->precision != MFIPM_PREC_FP32_PCG)
+    return fail(MFIPM_UNSUPPORTED, "the partial-DCT solver runs its PCG in float32 (precision=%d)", p->precision);
+  const size_t small = split_small_bytes(ops, sp, p), need = small + split_large_bytes(sp);
+  if (!workspace || ((uintptr_t)workspace & 255)) return fail(MFIPM_INVALID_ARG, "workspace NULL or not 256-byte aligned");
+  if (ws_bytes < need) return fail(MFIPM_INVALID_ARG, "workspace too small: %zu < %zu bytes", ws_bytes, need);
+  std::vector<mfipm_info> tmp;
+  if (!infos) {
+    tmp.resize(batch);
+    infos = tmp.data();
+  }
+  if (!sp.small.empty()) {
+    const int ns = (int)sp.small.size();
+    auto vo = pick(ops, sp.small);
+    auto vb = pick(b, sp.small);
+    auto vt = pick(tau, sp.small);
+    auto vx = pick(x, sp.small);
+    auto vz = pick(zs, sp.small);
+    auto vg = pick(grad_x, sp.small);
+    auto vgb = pick(grad_b, sp.small);
+    std::vector<double> gt(ns, 0.0);
+    std::vector<mfipm_info> si(ns);
+    rc = backward_persistent(ns, vo.data(), vb.data(), vt.data(), vx.data(), vz.data(), vg.data(),
+                             grad_b ? vgb.data() : nullptr, gt.data(), nullptr, p, workspace, small, si.data(), stream);
+    if (rc) return rc;
+    for (int k = 0; k < ns; ++k) {
+      infos[sp.small[k]] = si[k];
+      if (grad_tau) grad_tau[sp.small[k]] = gt[k];
+    }
+  }
+  return run_large_groups(ops, sp, b, tau, nullptr, nullptr, zs, grad_x, grad_b, grad_tau, p,
+                          static_cast<char*>(workspace) + small, ws_bytes - small, infos,
+                          static_cast<cudaStream_t>(stream));
+}
+
 int mfipm_apply_A(const mfipm_operator*, const double*, double*, void*, size_t, void*) {
   return fail(MFIPM_UNSUPPORTED, "mfipm_apply_A is not built yet");
 }
@@ -706,13 +923,26 @@ const char* mfipm_last_error(void) { return g_err.c_str(); }
 int mfipm_set_timing(int32_t enable) {
   g_timing = enable != 0;
   g_last_ms = -1.0f;
+  large_dct_set_timing(enable != 0);
   return MFIPM_OK;
 }
 
 double mfipm_last_kernel_ms(void) { return (double)g_last_ms; }
 
+int mfipm_last_operator_stats(double* ms, double* bytes, int64_t* products, int64_t* launches) {
+  if (!ms || !bytes || !products || !launches) return fail(MFIPM_INVALID_ARG, "NULL output");
+  large_dct_timing(ms, bytes, products, launches);
+  return MFIPM_OK;
+}
+
 int mfipm_set_gemm_mode(int32_t tensor_cores) {
   g_force_simple_gemm = tensor_cores == 0;
+  return MFIPM_OK;
+}
+
+int mfipm_set_large_dct_threshold(int64_t n) {
+  if (n < kLdMinN) return fail(MFIPM_INVALID_ARG, "threshold below the multi-pass minimum %lld", (long long)kLdMinN);
+  g_large_dct_min_n = std::min<int64_t>(n, 2 * kDctMaxN);
   return MFIPM_OK;
 }
 

@@ -14,7 +14,7 @@ __global__ void twiddle_kernel(double2* tw64, float2* tw32, float4* twdf, int lo
     double s, c;
     // exp(-2 pi i j / 2^l) = cos(pi * 2j/2^l) - i sin(pi * 2j/2^l)
     sincospi(2.0 * (double)j / (double)((int64_t)1 << l), &s, &c);
-    tw64[e] = make_double2(c, -s);
+    if (tw64) tw64[e] = make_double2(c, -s);
     tw32[e] = make_float2((float)c, (float)-s);
     const df re = to_df(c), im = to_df(-s);
     twdf[e] = make_float4(re.hi, re.lo, im.hi, im.lo);

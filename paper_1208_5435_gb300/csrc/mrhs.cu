@@ -14,12 +14,15 @@
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
+#include <string.h>
 
 #include <algorithm>
 #include <vector>
 
 #include "device_common.cuh"
 #include "internal.h"
+#include "large_dct.h"
+#include "lockstep.h"
 #include "mrhs.h"
 
 namespace mfipm {
@@ -395,17 +398,12 @@ __global__ void k_fin2(const float2* __restrict__ Part, int S2, double scale, do
 }
 
 // ------------------------------------------------------------------ per-column state
-struct Col {
-  double tau, cn, mu, sigma, alpha_p, alpha_d, alpha_p1, alpha_d1, mu_t, prev_ap, prev_ad;
-  double rel_gap, P_obj, rz0, rz, res2;
-  float alpha, beta;
-  int stop, active, corr, corr_next, correctors, pcg_iters, ipm_iters, done;
-  int64_t nmat;
-};
-
 struct Dev {
   int m, n, R, nb;                 // nb: blocks per column of the index passes
+  int op;                          // OP_SHARED_BF16 or OP_LARGE_DCT
+  int nb2;                         // blocks per column of the operator's partial sums (part2)
   double a_scale, rho;
+  float* Yv;                       // R x n   A^T A w (OP_LARGE_DCT)
   const __nv_bfloat16* A;          // m x n (lda)
   int64_t lda;
   const __nv_bfloat16* At;         // n x m
@@ -502,7 +500,7 @@ __global__ void k_stats(Dev d, int it, const double* part2) {
   Col& c = d.col[j];
   if (c.done) return;
   const double zts = col_total(d.part, j, d.nb, 0), l1 = col_total(d.part, j, d.nb, 1);
-  const double res2 = col_total(part2, j, d.nb, 0);
+  const double res2 = col_total(part2, j, d.nb2, 0);
   c.res2 = res2;
   c.mu = zts / (2.0 * d.n);
   c.P_obj = c.tau * l1 + 0.5 * res2;
@@ -554,13 +552,15 @@ __global__ void k_pcg_init(Dev d, int corr) {
         r.y = (float)((tsv - (c.tau - g)) + (s3mu - zv * tsv) / vv);
       }
     }
-    const float2 p = precond2(dd, r, (float)d.rho);
+    const float2 p = precond2(dd, r, (float)c.rho);
     d.Rv[gi] = r;
     d.Pv[gi] = p;
-    const float w = p.x - p.y;
-    const __nv_bfloat16 wh = __float2bfloat16_rn(w);
-    d.W[(int64_t)j * d.n + i] = wh;
-    d.W[(int64_t)(d.R + j) * d.n + i] = __float2bfloat16_rn(w - __bfloat162float(wh));
+    if (d.op == OP_SHARED_BF16) {
+      const float w = p.x - p.y;
+      const __nv_bfloat16 wh = __float2bfloat16_rn(w);
+      d.W[(int64_t)j * d.n + i] = wh;
+      d.W[(int64_t)(d.R + j) * d.n + i] = __float2bfloat16_rn(w - __bfloat162float(wh));
+    }
     v[0] += (double)(r.x * p.x + r.y * p.y);
     v[1] += (double)(dd.x * p.x * p.x + dd.y * p.y * p.y);
   }
@@ -592,7 +592,7 @@ __global__ void k_alpha(Dev d, int first, const double* part2) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= d.R) return;
   Col& c = d.col[j];
-  const double pdp = col_total(d.part, j, d.nb, 1), aw2 = col_total(part2, j, d.nb, 0);
+  const double pdp = col_total(d.part, j, d.nb, 1), aw2 = col_total(part2, j, d.nb2, 0);
   if (first) {
     const double rz = col_total(d.part, j, d.nb, 0);
     c.rz0 = c.rz = rz;
@@ -605,19 +605,24 @@ __global__ void k_alpha(Dev d, int first, const double* part2) {
 __global__ void k_pcg_D(Dev d, float2* __restrict__ Xo, int first) {
   const int j = blockIdx.y, blk = blockIdx.x;
   const Col c = d.col[j];
-  const float alpha = c.alpha, rho = (float)d.rho, sc = (float)d.a_scale;
+  const float alpha = c.alpha, rho = (float)c.rho, sc = (float)d.a_scale;
   double v[1] = {0.0};
   for (int i = blk * kIdx + threadIdx.x; i < min(d.n, (blk + 1) * kIdx); i += kT) {
     const int64_t gi = (int64_t)j * d.n + i;
     float2 x = first ? make_float2(0.f, 0.f) : Xo[gi];
     float2 r = d.Rv[gi];
     const float2 p = d.Pv[gi], dd = d.Dv[gi];
-    float yacc = 0.f;
-    for (int sp = 0; sp < d.s2; ++sp) {
-      const float* C = d.C2 + (int64_t)sp * 2 * d.R * d.n;
-      yacc += C[(int64_t)j * d.n + i] + C[(int64_t)(d.R + j) * d.n + i];
+    float y;
+    if (d.op == OP_SHARED_BF16) {
+      float yacc = 0.f;
+      for (int sp = 0; sp < d.s2; ++sp) {
+        const float* C = d.C2 + (int64_t)sp * 2 * d.R * d.n;
+        yacc += C[(int64_t)j * d.n + i] + C[(int64_t)(d.R + j) * d.n + i];
+      }
+      y = sc * yacc;
+    } else {
+      y = d.Yv[gi];
     }
-    const float y = sc * yacc;
     x.x += alpha * p.x;
     x.y += alpha * p.y;
     r.x -= alpha * (dd.x * p.x + y);
@@ -647,7 +652,7 @@ __global__ void k_beta(Dev d, int k) {
 __global__ void k_pcg_E(Dev d) {
   const int j = blockIdx.y, blk = blockIdx.x;
   const Col c = d.col[j];
-  const float beta = c.beta, rho = (float)d.rho;
+  const float beta = c.beta, rho = (float)c.rho;
   double v[2] = {0, 0};
   for (int i = blk * kIdx + threadIdx.x; i < min(d.n, (blk + 1) * kIdx); i += kT) {
     const int64_t gi = (int64_t)j * d.n + i;
@@ -661,10 +666,12 @@ __global__ void k_pcg_E(Dev d) {
     } else {
       p = make_float2(0.f, 0.f);  // finished column: no further change
     }
-    const float w = p.x - p.y;
-    const __nv_bfloat16 wh = __float2bfloat16_rn(w);
-    d.W[(int64_t)j * d.n + i] = wh;
-    d.W[(int64_t)(d.R + j) * d.n + i] = __float2bfloat16_rn(w - __bfloat162float(wh));
+    if (d.op == OP_SHARED_BF16) {
+      const float w = p.x - p.y;
+      const __nv_bfloat16 wh = __float2bfloat16_rn(w);
+      d.W[(int64_t)j * d.n + i] = wh;
+      d.W[(int64_t)(d.R + j) * d.n + i] = __float2bfloat16_rn(w - __bfloat162float(wh));
+    }
     v[1] += (double)(dd.x * p.x * p.x + dd.y * p.y * p.y);
   }
   block_partials<2>(v, d.part, j, d.nb, blk);
@@ -750,11 +757,12 @@ __global__ void k_mu_t(Dev d) {
 }
 
 // ||c||: with x = 0 the residual kernel gives Gr = -A^T b
-__global__ void k_setup_cols(Dev d, const double* __restrict__ taus) {
+__global__ void k_setup_cols(Dev d, const double* __restrict__ taus, const double* __restrict__ rhos) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= d.R) return;
   Col c{};
   c.tau = taus[j];
+  c.rho = rhos ? rhos[j] : d.rho;
   c.alpha_p = c.alpha_d = c.prev_ap = c.prev_ad = 1.0;
   c.cn = sqrt(2.0 * d.n * c.tau * c.tau + 2.0 * col_total(d.part, j, d.nb, 0));
   c.nmat = 1;
@@ -822,7 +830,7 @@ size_t mrhs_workspace_bytes(int64_t m, int64_t n, int R) {
   b += al((size_t)kMaxSplits * 2 * R * m * 4);  // C1
   b += al((size_t)kMaxSplits * 2 * R * n * 4);  // C2
   b += al((size_t)R * nb * mr::kPart * 8) * 2;  // part, part2
-  b += al(sizeof(mr::Col) * R);
+  b += al(sizeof(Col) * R);
   b += al(256);                           // counters
   b += al((size_t)R * 8) * 3;             // taus, b / x / zs pointer arrays
   b += al(sizeof(void*) * R);
@@ -833,6 +841,9 @@ size_t mrhs_workspace_bytes(int64_t m, int64_t n, int R) {
 }
 
 namespace {
+// kernels launched by the last lockstep solve on this thread (reported with the operator timing)
+thread_local int64_t g_nlaunch = 0;
+
 // split count S <= cap (and <= K tiles) whose tiles * S blocks fill whole waves best
 int pick_rsplit(int64_t tiles, int ktiles, int64_t slots, int cap) {
   cap = std::max(1, std::min(cap, ktiles));
@@ -852,6 +863,92 @@ int mr_fail(cudaError_t e, std::string* msg, const char* where) {
   *msg = std::string(where) + ": " + cudaGetErrorString(e);
   return MFIPM_CUDA;
 }
+
+// The single-corrector IPM of Sec. 5.1 for all R problems in lockstep, each with its own
+// scalars.  residual(gate) computes Gr = A^T (A X - b) and part2 slot 0 = ||A X - b||^2;
+// normal(k, nprob) computes A^T A (p_u - p_v) for PCG iteration k (nprob: problems it covers) and
+// part2 slot 0 = ||A w||^2.
+template <class Resid, class Normal>
+int lockstep_run(mr::Dev& d, double* part2, const double* taus, const double* rhos, Resid& residual, Normal& normal,
+                 double* const* xptr, double* const* zptr, mfipm_info* infos, cudaStream_t st, std::string* msg) {
+  using namespace mr;
+  const int R = d.R, nb = d.nb;
+  const dim3 gIdx(nb, R);
+  const int colBlocks = (R + 127) / 128;
+  cudaError_t e;
+  int live = R, active = R;  // problems covered by the next operator product (host view)
+  auto pcg = [&](float2* Xo) -> cudaError_t {
+    for (int k = 0;; ++k) {
+      if ((e = normal(k, k == 0 ? live : active))) return e;
+      k_alpha<<<colBlocks, 128, 0, st>>>(d, k == 0, part2);
+      ++g_nlaunch;
+      k_pcg_D<<<gIdx, kT, 0, st>>>(d, Xo, k == 0);
+      ++g_nlaunch;
+      if ((e = cudaMemsetAsync(d.counters, 0, 4, st))) return e;
+      k_beta<<<colBlocks, 128, 0, st>>>(d, k + 1);
+      ++g_nlaunch;
+      active = 0;
+      if ((e = cudaMemcpyAsync(&active, d.counters, 4, cudaMemcpyDeviceToHost, st))) return e;
+      if ((e = cudaStreamSynchronize(st))) return e;
+      if (active == 0) return cudaSuccess;
+      k_pcg_E<<<gIdx, kT, 0, st>>>(d);
+      ++g_nlaunch;
+    }
+  };
+
+  // setup: ||A^T b|| for ||c||
+  if ((e = cudaMemsetAsync(d.X, 0, (size_t)R * d.n * 8, st))) return mr_fail(e, msg, "clear x");
+  if ((e = residual(GATE_ALL))) return mr_fail(e, msg, "residual");
+  k_colnorm2<<<gIdx, kT, 0, st>>>(d.Gr, d.n, d.part, nb);
+  ++g_nlaunch;
+  k_setup_cols<<<colBlocks, 128, 0, st>>>(d, taus, rhos);
+  ++g_nlaunch;
+  for (int it = 1;; ++it) {
+    k_update<<<gIdx, kT, 0, st>>>(d, it == 1);
+    ++g_nlaunch;
+    if ((e = residual(GATE_LIVE))) return mr_fail(e, msg, "residual");
+    if ((e = cudaMemsetAsync(d.counters, 0, 16, st))) return mr_fail(e, msg, "counters");
+    k_stats<<<colBlocks, 128, 0, st>>>(d, it, part2);
+    ++g_nlaunch;
+    int unfinished = 0;
+    if ((e = cudaMemcpyAsync(&unfinished, d.counters + 1, 4, cudaMemcpyDeviceToHost, st)) ||
+        (e = cudaStreamSynchronize(st)))
+      return mr_fail(e, msg, "gap test");
+    if (unfinished == 0) break;
+    live = unfinished;
+    k_pcg_init<<<gIdx, kT, 0, st>>>(d, 0);
+    ++g_nlaunch;
+    if ((e = pcg(d.X1))) return mr_fail(e, msg, "predictor PCG");
+    k_steps<<<gIdx, kT, 0, st>>>(d, 0);
+    ++g_nlaunch;
+    k_steps_fin<<<colBlocks, 128, 0, st>>>(d, 0);
+    ++g_nlaunch;
+    int ncorr = 0;
+    if ((e = cudaMemcpyAsync(&ncorr, d.counters + 2, 4, cudaMemcpyDeviceToHost, st)) ||
+        (e = cudaStreamSynchronize(st)))
+      return mr_fail(e, msg, "step lengths");
+    if (ncorr > 0) {
+      k_trial<<<gIdx, kT, 0, st>>>(d);
+      ++g_nlaunch;
+      k_mu_t<<<colBlocks, 128, 0, st>>>(d);
+      ++g_nlaunch;
+      if ((e = residual(GATE_LIVE))) return mr_fail(e, msg, "trial residual");
+      k_pcg_init<<<gIdx, kT, 0, st>>>(d, 1);
+      ++g_nlaunch;
+      if ((e = pcg(d.X2))) return mr_fail(e, msg, "corrector PCG");
+      k_steps<<<gIdx, kT, 0, st>>>(d, 1);
+      ++g_nlaunch;
+      k_steps_fin<<<colBlocks, 128, 0, st>>>(d, 1);
+      ++g_nlaunch;
+    }
+  }
+  k_exit<<<gIdx, kT, 0, st>>>(d, xptr, zptr);
+  ++g_nlaunch;
+  k_info<<<colBlocks, 128, 0, st>>>(d, infos);
+  ++g_nlaunch;
+  if ((e = cudaGetLastError())) return mr_fail(e, msg, "exit");
+  return MFIPM_OK;
+}
 }  // namespace
 
 int mrhs_solve(const MrhsCall& call, std::string* msg) {
@@ -867,6 +964,8 @@ int mrhs_solve(const MrhsCall& call, std::string* msg) {
   d.n = (int)n;
   d.R = R;
   d.nb = nb;
+  d.op = OP_SHARED_BF16;
+  d.nb2 = nb;
   d.a_scale = call.a_scale;
   d.A = static_cast<const __nv_bfloat16*>(call.A);
   d.lda = call.lda;
@@ -920,8 +1019,6 @@ int mrhs_solve(const MrhsCall& call, std::string* msg) {
   // d.prm.rho: the Frobenius-closest multiple of I to A^T A (reading R2) is supplied by the caller
   d.rho = call.rho;
 
-  const dim3 gIdx(nb, R);
-  const int colBlocks = (R + 127) / 128;
   transpose_bf16<<<dim3((unsigned)((n + 31) / 32), (unsigned)((m + 31) / 32)), dim3(32, 8), 0, st>>>(d.A, d.lda, At,
                                                                                                    (int)m, (int)n);
   gather_b<<<dim3(8, R), 256, 0, st>>>(bptr, d.Bm, (int)m);
@@ -959,7 +1056,7 @@ int mrhs_solve(const MrhsCall& call, std::string* msg) {
     k_colnorm2<<<dim3(nb, R), kT, 0, st>>>(d.Rr, (int)m, part2, nb);
     return cudaGetLastError();
   };
-  auto gemms = [&]() -> cudaError_t {
+  auto normal = [&](int, int) -> cudaError_t {
     e = call.gemm(call.gemm_ctx, d.A, d.W, d.C1, (int)m, 2 * R, (int)n, d.s1, st);
     if (e) return e;
     k_split_t<<<dim3(nb, R), kT, 0, st>>>(d, part2);
@@ -967,58 +1064,423 @@ int mrhs_solve(const MrhsCall& call, std::string* msg) {
     if (e) return e;
     return cudaGetLastError();
   };
-  auto pcg = [&](float2* Xo) -> cudaError_t {
-    for (int k = 0;; ++k) {
-      if ((e = gemms())) return e;
-      k_alpha<<<colBlocks, 128, 0, st>>>(d, k == 0, part2);
-      k_pcg_D<<<gIdx, kT, 0, st>>>(d, Xo, k == 0);
-      if ((e = cudaMemsetAsync(d.counters, 0, 4, st))) return e;
-      k_beta<<<colBlocks, 128, 0, st>>>(d, k + 1);
-      int active = 0;
-      if ((e = cudaMemcpyAsync(&active, d.counters, 4, cudaMemcpyDeviceToHost, st))) return e;
-      if ((e = cudaStreamSynchronize(st))) return e;
-      if (active == 0) return cudaSuccess;
-      k_pcg_E<<<gIdx, kT, 0, st>>>(d);
-    }
-  };
+  auto resid = [&](int) -> cudaError_t { return residual(); };
+  return lockstep_run(d, part2, taus, nullptr, resid, normal, xptr, zptr, call.infos_dev, st, msg);
+}
 
-  // setup: ||A^T b|| for ||c||
-  if ((e = cudaMemsetAsync(d.X, 0, (size_t)R * n * 8, st))) return mr_fail(e, msg, "clear x");
-  if ((e = residual())) return mr_fail(e, msg, "residual");
-  k_colnorm2<<<dim3(nb, R), kT, 0, st>>>(d.Gr, (int)n, d.part, nb);
-  k_setup_cols<<<colBlocks, 128, 0, st>>>(d, taus);
-  for (int it = 1;; ++it) {
-    k_update<<<gIdx, kT, 0, st>>>(d, it == 1);
-    if ((e = residual())) return mr_fail(e, msg, "residual");
-    if ((e = cudaMemsetAsync(d.counters, 0, 16, st))) return mr_fail(e, msg, "counters");
-    k_stats<<<colBlocks, 128, 0, st>>>(d, it, part2);
-    int unfinished = 0;
-    if ((e = cudaMemcpyAsync(&unfinished, d.counters + 1, 4, cudaMemcpyDeviceToHost, st)) ||
-        (e = cudaStreamSynchronize(st)))
-      return mr_fail(e, msg, "gap test");
-    if (unfinished == 0) break;
-    k_pcg_init<<<gIdx, kT, 0, st>>>(d, 0);
-    if ((e = pcg(d.X1))) return mr_fail(e, msg, "predictor PCG");
-    k_steps<<<gIdx, kT, 0, st>>>(d, 0);
-    k_steps_fin<<<colBlocks, 128, 0, st>>>(d, 0);
-    int ncorr = 0;
-    if ((e = cudaMemcpyAsync(&ncorr, d.counters + 2, 4, cudaMemcpyDeviceToHost, st)) ||
-        (e = cudaStreamSynchronize(st)))
-      return mr_fail(e, msg, "step lengths");
-    if (ncorr > 0) {
-      k_trial<<<gIdx, kT, 0, st>>>(d);
-      k_mu_t<<<colBlocks, 128, 0, st>>>(d);
-      if ((e = residual())) return mr_fail(e, msg, "trial residual");
-      k_pcg_init<<<gIdx, kT, 0, st>>>(d, 1);
-      if ((e = pcg(d.X2))) return mr_fail(e, msg, "corrector PCG");
-      k_steps<<<gIdx, kT, 0, st>>>(d, 1);
-      k_steps_fin<<<colBlocks, 128, 0, st>>>(d, 1);
-    }
+// ------------------------------------------------------------------ large partial DCT
+namespace mr {
+// adjoint solve H y = [g_x; -g_x] at the forward solution's final iterate (the derivative of
+// the perturbed KKT system of Eq. fzfs at fixed mu): Theta^-1 = s / z, y0 = 0
+__global__ void k_bwd_init(Dev d, const double* const* __restrict__ zs_in, const double* const* __restrict__ gx) {
+  const int j = blockIdx.y, blk = blockIdx.x;
+  const Col c = d.col[j];
+  const double* z = zs_in[j];
+  double v[2] = {0, 0};
+  for (int i = blk * kIdx + threadIdx.x; i < min(d.n, (blk + 1) * kIdx); i += kT) {
+    const int64_t gi = (int64_t)j * d.n + i;
+    const double u = z[i], vv = z[d.n + i], su = z[2 * (int64_t)d.n + i], sv = z[3 * (int64_t)d.n + i];
+    const float2 dd = make_float2((float)(su / u), (float)(sv / vv));
+    const float g = (float)gx[j][i];
+    const float2 r = make_float2(g, -g);
+    const float2 p = precond2(dd, r, (float)c.rho);
+    d.Dv[gi] = dd;
+    d.Rv[gi] = r;
+    d.Pv[gi] = p;
+    v[0] += (double)(r.x * p.x + r.y * p.y);
+    v[1] += (double)(dd.x * p.x * p.x + dd.y * p.y * p.y);
   }
-  k_exit<<<gIdx, kT, 0, st>>>(d, xptr, zptr);
-  k_info<<<colBlocks, 128, 0, st>>>(d, call.infos_dev);
-  if ((e = cudaGetLastError())) return mr_fail(e, msg, "exit");
+  block_partials<2>(v, d.part, j, d.nb, blk);
+}
+__global__ void k_bwd_cols(Dev d, const double* __restrict__ rhos) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= d.R) return;
+  Col c{};
+  c.rho = rhos[j];
+  d.col[j] = c;
+}
+// w = y_u - y_v (float64) for the forward transform, and sum(y_u + y_v)
+__global__ void k_bwd_w(Dev d) {
+  const int j = blockIdx.y, blk = blockIdx.x;
+  double v[1] = {0.0};
+  for (int i = blk * kIdx + threadIdx.x; i < min(d.n, (blk + 1) * kIdx); i += kT) {
+    const int64_t gi = (int64_t)j * d.n + i;
+    const float2 y = d.X1[gi];
+    d.X[gi] = (double)y.x - (double)y.y;
+    v[0] += (double)y.x + (double)y.y;
+  }
+  block_partials<1>(v, d.part, j, d.nb, blk);
+}
+// grad_b = A w = (C w)[rows], grad_tau = -sum(y_u + y_v), info
+__global__ void k_bwd_out(Dev d, const int64_t* const* __restrict__ rows, const int64_t* __restrict__ ms,
+                          double* const* __restrict__ grad_b, double* __restrict__ gtau, mfipm_info* infos) {
+  const int j = blockIdx.y;
+  const int64_t m = ms[j];
+  double* gb = grad_b[j];
+  if (gb)
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x)
+      gb[i] = d.Gr[(int64_t)j * d.n + rows[j][i]];
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    const Col& c = d.col[j];
+    gtau[j] = -col_total(d.part, j, d.nb, 0);
+    mfipm_info info{};
+    info.status = MFIPM_OK;
+    info.pcg_iters = c.pcg_iters;
+    info.n_mat = c.nmat + 1;
+    infos[j] = info;
+  }
+}
+}  // namespace mr
+
+namespace {
+// Device time of the multi-pass operator products (mfipm_set_timing): CUDA events on the
+// solve's stream around every A^T A w, read after the solve's final synchronisation.
+struct OpTimer {
+  bool on = false;
+  std::vector<cudaEvent_t> ev;
+  std::vector<double> units;  // problems x n per recorded product
+  size_t used = 0;
+  double ms = -1.0, bytes = 0.0;
+  int64_t products = 0;
+  cudaError_t begin(cudaStream_t st) {
+    if (used + 2 > ev.size()) {
+      for (int i = 0; i < 64; ++i) {
+        cudaEvent_t e;
+        cudaError_t r = cudaEventCreate(&e);
+        if (r) return r;
+        ev.push_back(e);
+      }
+    }
+    return cudaEventRecord(ev[used], st);
+  }
+  cudaError_t end(cudaStream_t st, double u) {
+    cudaError_t r = cudaEventRecord(ev[used + 1], st);
+    used += 2;
+    units.push_back(u);
+    return r;
+  }
+  void reset() {
+    used = 0;
+    units.clear();
+    ms = -1.0;
+    bytes = 0.0;
+    products = 0;
+  }
+  // after the stream has been synchronised; algorithmic bytes: w read and y written, 8 per index
+  void collect() {
+    if (!on) return;
+    double t = 0.0;
+    for (size_t i = 0; i + 1 < used; i += 2) {
+      float x = 0.f;
+      if (cudaEventElapsedTime(&x, ev[i], ev[i + 1]) == cudaSuccess) t += x;
+    }
+    ms = t;
+    bytes = 0.0;
+    for (double u : units) bytes += 8.0 * u;
+    products = (int64_t)units.size();
+  }
+};
+thread_local OpTimer g_optimer;
+
+struct LdLayout {
+  int nb, nb2;
+  LdShape sh;
+  int log2_tw;
+  size_t total;
+};
+LdLayout ld_layout(int64_t n, int R) {
+  auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  LdLayout L{};
+  L.sh = ld_shape(n);
+  L.nb = (int)((n + mr::kIdx - 1) / mr::kIdx);
+  L.nb2 = 1 << (L.sh.logN1 - 1);
+  L.log2_tw = L.sh.logN + 2;
+  const size_t Rn = (size_t)R * n;
+  size_t b = 0;
+  b += al(Rn * 8) * 2;                  // X, Gr
+  b += al(Rn * 32);                     // zs
+  b += al(Rn * 8) * 5;                  // X1 X2 Rv Pv Dv
+  b += al(Rn * 4);                      // Yv
+  b += al(Rn * 8);                      // intermediate (L double-float complex)
+  b += al(Rn) + al(Rn * 8) * 2;         // mask, bsu, bsu_df
+  b += al((size_t)R * std::max(L.nb, L.nb2) * mr::kPart * 8) * 2;  // part, part2
+  b += al(sizeof(Col) * R) + al(256);   // col, counters
+  b += al((size_t)R * 8) * 10;          // taus, rhos, ms, grad_tau, pointer arrays
+  b += al(sizeof(ProbDesc) * R) + al(256);  // descriptors, error word
+  b += al(((size_t)2 << L.log2_tw) * 8) + al(((size_t)2 << L.log2_tw) * 16);  // twiddles
+  b += al((size_t)R * sizeof(mfipm_info));
+  L.total = b;
+  return L;
+}
+
+struct LdState {
+  mr::Dev d;
+  double* part2;
+  double *taus, *rhos, *gtau;
+  int64_t* ms;
+  double **xptr, **zptr, **gbptr;
+  const double **zinptr, **gxptr;
+  const int64_t** rowsptr;
+  mfipm_info* infos_dev;
+  LdArgs base;
+};
+
+// carve the workspace, upload per-problem arguments, build mask / b_u and the twiddles
+int ld_setup(const LdCall& call, LdState& S, std::string* msg) {
+  using namespace mr;
+  g_nlaunch = 0;
+  const int64_t n = call.n;
+  const int R = call.R;
+  cudaStream_t st = call.stream;
+  const LdLayout L = ld_layout(n, R);
+  if (call.ws_bytes < L.total) {
+    *msg = "workspace too small for the multi-pass partial-DCT solver";
+    return MFIPM_INVALID_ARG;
+  }
+  auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  char* ws = static_cast<char*>(call.workspace);
+  size_t o = 0;
+  auto take = [&](size_t bytes) { char* p = ws + o; o += al(bytes); return p; };
+  const size_t Rn = (size_t)R * n;
+  Dev& d = S.d;
+  d = Dev{};
+  d.n = (int)n;
+  d.R = R;
+  d.nb = L.nb;
+  d.nb2 = L.nb2;
+  d.op = OP_LARGE_DCT;
+  d.a_scale = 1.0;
+  d.prm = call.prm;
+  d.X = reinterpret_cast<double*>(take(Rn * 8));
+  d.Gr = reinterpret_cast<double*>(take(Rn * 8));
+  d.zs = reinterpret_cast<double*>(take(Rn * 32));
+  d.X1 = reinterpret_cast<float2*>(take(Rn * 8));
+  d.X2 = reinterpret_cast<float2*>(take(Rn * 8));
+  d.Rv = reinterpret_cast<float2*>(take(Rn * 8));
+  d.Pv = reinterpret_cast<float2*>(take(Rn * 8));
+  d.Dv = reinterpret_cast<float2*>(take(Rn * 8));
+  d.Yv = reinterpret_cast<float*>(take(Rn * 4));
+  void* inter = take(Rn * 8);
+  uint8_t* mask = reinterpret_cast<uint8_t*>(take(Rn));
+  double* bsu = reinterpret_cast<double*>(take(Rn * 8));
+  float2* bsu_df = reinterpret_cast<float2*>(take(Rn * 8));
+  const size_t partb = (size_t)R * std::max(L.nb, L.nb2) * kPart * 8;
+  d.part = reinterpret_cast<double*>(take(partb));
+  S.part2 = reinterpret_cast<double*>(take(partb));
+  d.col = reinterpret_cast<Col*>(take(sizeof(Col) * R));
+  d.counters = reinterpret_cast<int*>(take(256));
+  S.taus = reinterpret_cast<double*>(take((size_t)R * 8));
+  S.rhos = reinterpret_cast<double*>(take((size_t)R * 8));
+  S.gtau = reinterpret_cast<double*>(take((size_t)R * 8));
+  S.ms = reinterpret_cast<int64_t*>(take((size_t)R * 8));
+  S.xptr = reinterpret_cast<double**>(take((size_t)R * 8));
+  S.zptr = reinterpret_cast<double**>(take((size_t)R * 8));
+  S.gbptr = reinterpret_cast<double**>(take((size_t)R * 8));
+  S.zinptr = reinterpret_cast<const double**>(take((size_t)R * 8));
+  S.gxptr = reinterpret_cast<const double**>(take((size_t)R * 8));
+  S.rowsptr = reinterpret_cast<const int64_t**>(take((size_t)R * 8));
+  ProbDesc* probs = reinterpret_cast<ProbDesc*>(take(sizeof(ProbDesc) * R));
+  int* err = reinterpret_cast<int*>(take(256));
+  float2* tw32 = reinterpret_cast<float2*>(take(((size_t)2 << L.log2_tw) * 8));
+  float4* twdf = reinterpret_cast<float4*>(take(((size_t)2 << L.log2_tw) * 16));
+  S.infos_dev = reinterpret_cast<mfipm_info*>(take((size_t)R * sizeof(mfipm_info)));
+
+  std::vector<ProbDesc> desc(R);
+  std::vector<double> rh(R), taus(R, 1.0);
+  std::vector<const void*> xs(R, nullptr), zo(R, nullptr), gb(R, nullptr), zi(R, nullptr), gx(R, nullptr),
+      rw(R, nullptr);
+  for (int j = 0; j < R; ++j) {
+    ProbDesc& pd = desc[j];
+    memset(&pd, 0, sizeof(pd));
+    pd.n = n;
+    pd.m = call.m[j];
+    pd.kind = MFIPM_OP_PARTIAL_DCT;
+    pd.log2n = L.sh.logN;
+    pd.b = call.b[j];
+    pd.rows = call.rows[j];
+    pd.mask = mask + (size_t)j * n;
+    pd.bsu = bsu + (size_t)j * n;
+    pd.bsu_df = bsu_df + (size_t)j * n;
+    rh[j] = (double)call.m[j] / (double)n;  // reading R2: A A^T = I, ||A||_F^2 = m
+    if (call.tau) taus[j] = call.tau[j];
+    xs[j] = call.x ? call.x[j] : nullptr;
+    zo[j] = call.zs_out ? call.zs_out[j] : nullptr;
+    gb[j] = call.grad_b ? call.grad_b[j] : nullptr;
+    zi[j] = call.zs_in ? call.zs_in[j] : nullptr;
+    gx[j] = call.gx ? call.gx[j] : nullptr;
+    rw[j] = call.rows[j];
+  }
+  cudaError_t e;
+  auto up = [&](void* dst, const void* src, size_t bytes) {
+    if (!e) e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st);
+  };
+  e = cudaSuccess;
+  up(probs, desc.data(), sizeof(ProbDesc) * R);
+  up(S.taus, taus.data(), (size_t)R * 8);
+  up(S.rhos, rh.data(), (size_t)R * 8);
+  up(S.ms, call.m, (size_t)R * 8);
+  up(S.xptr, xs.data(), (size_t)R * 8);
+  up(S.zptr, zo.data(), (size_t)R * 8);
+  up(S.gbptr, gb.data(), (size_t)R * 8);
+  up(S.zinptr, zi.data(), (size_t)R * 8);
+  up(S.gxptr, gx.data(), (size_t)R * 8);
+  up(S.rowsptr, rw.data(), (size_t)R * 8);
+  if (e) return mr_fail(e, msg, "upload arguments");
+  if ((e = cudaMemsetAsync(err, 0, 4, st)) || (e = cudaMemsetAsync(d.Yv, 0, Rn * 4, st)) ||
+      (e = cudaMemsetAsync(S.part2, 0, partb, st)) ||
+      (e = launch_twiddles(nullptr, tw32, twdf, L.log2_tw, st)) || (e = launch_dct_setup(probs, R, n, err, st)))
+    return mr_fail(e, msg, "setup kernels");
+  g_nlaunch += 3;
+  int herr = 0;
+  if ((e = cudaMemcpyAsync(&herr, err, 4, cudaMemcpyDeviceToHost, st)) || (e = cudaStreamSynchronize(st)))
+    return mr_fail(e, msg, "setup kernels");
+  if (herr == -1) {
+    *msg = "rows must be distinct, ascending and inside [0, n)";
+    return MFIPM_INVALID_ARG;
+  }
+  if (herr == -2) {
+    *msg = "b contains a non-finite value";
+    return MFIPM_NUMERIC;
+  }
+  LdArgs& a = S.base;
+  a = LdArgs{};
+  a.logN = L.sh.logN;
+  a.logL = L.sh.logL;
+  a.logN1 = L.sh.logN1;
+  a.logN2 = L.sh.logN2;
+  a.log2_tw = L.log2_tw;
+  a.col = d.col;
+  a.inter = inter;
+  a.mask = mask;
+  a.bsu = bsu;
+  a.bsu_df = bsu_df;
+  a.part2 = S.part2;
+  a.nb2 = L.nb2;
+  a.kpart = kPart;
+  a.tw32 = tw32;
+  a.twdf = twdf;
   return MFIPM_OK;
+}
+
+int ld_read_infos(const LdCall& call, const LdState& S, std::string* msg) {
+  cudaError_t e;
+  if ((e = cudaMemcpyAsync(call.infos, S.infos_dev, sizeof(mfipm_info) * call.R, cudaMemcpyDeviceToHost,
+                           call.stream)) ||
+      (e = cudaStreamSynchronize(call.stream)))
+    return mr_fail(e, msg, "read infos");
+  return MFIPM_OK;
+}
+}  // namespace
+
+size_t large_dct_workspace_bytes(int64_t n, int R) { return ld_layout(n, R).total; }
+
+int large_dct_solve(const LdCall& call, std::string* msg) {
+  LdState S;
+  int rc = ld_setup(call, S, msg);
+  if (rc) return rc;
+  mr::Dev& d = S.d;
+  cudaStream_t st = call.stream;
+  auto residual = [&](int gate) -> cudaError_t {
+    LdArgs a = S.base;
+    a.gate = gate;
+    a.din = d.X;
+    a.dout = d.Gr;
+    g_nlaunch += 3;
+    return ld_resid(a, d.R, st);
+  };
+  OpTimer& T = g_optimer;
+  T.reset();
+  auto normal = [&](int k, int nprob) -> cudaError_t {
+    LdArgs a = S.base;
+    // the first product of a PCG solve precedes its activity test
+    a.gate = k == 0 ? GATE_LIVE : GATE_ACTIVE;
+    a.pin = d.Pv;
+    a.yout = d.Yv;
+    cudaError_t r;
+    if (T.on && (r = T.begin(st))) return r;
+    if ((r = ld_normal(a, d.R, st))) return r;
+    g_nlaunch += 3;
+    return T.on ? T.end(st, (double)nprob * (double)call.n) : cudaSuccess;
+  };
+  rc = lockstep_run(d, S.part2, S.taus, S.rhos, residual, normal, S.xptr, S.zptr, S.infos_dev, st, msg);
+  if (rc) return rc;
+  rc = ld_read_infos(call, S, msg);
+  T.collect();
+  return rc;
+}
+
+int large_dct_backward(const LdCall& call, std::string* msg) {
+  using namespace mr;
+  LdState S;
+  int rc = ld_setup(call, S, msg);
+  if (rc) return rc;
+  Dev& d = S.d;
+  // the derivative needs a tighter solve than a Newton direction
+  d.prm.tol_pcg = std::min(d.prm.tol_pcg, 1e-6);
+  cudaStream_t st = call.stream;
+  const dim3 gIdx(d.nb, d.R);
+  const int colBlocks = (d.R + 127) / 128;
+  cudaError_t e;
+  k_bwd_cols<<<colBlocks, 128, 0, st>>>(d, S.rhos);
+  ++g_nlaunch;
+  k_bwd_init<<<gIdx, kT, 0, st>>>(d, S.zinptr, S.gxptr);
+  ++g_nlaunch;
+  if ((e = cudaGetLastError())) return mr_fail(e, msg, "adjoint setup");
+  // PCG as in the solve, with every problem live
+  OpTimer& T = g_optimer;
+  T.reset();
+  int active = d.R;
+  for (int k = 0;; ++k) {
+    LdArgs a = S.base;
+    a.gate = k == 0 ? GATE_ALL : GATE_ACTIVE;
+    a.pin = d.Pv;
+    a.yout = d.Yv;
+    if (T.on && (e = T.begin(st))) return mr_fail(e, msg, "timing event");
+    if ((e = ld_normal(a, d.R, st))) return mr_fail(e, msg, "adjoint PCG");
+    g_nlaunch += 3;
+    if (T.on && (e = T.end(st, (double)active * (double)call.n))) return mr_fail(e, msg, "timing event");
+    k_alpha<<<colBlocks, 128, 0, st>>>(d, k == 0, S.part2);
+    ++g_nlaunch;
+    k_pcg_D<<<gIdx, kT, 0, st>>>(d, d.X1, k == 0);
+    ++g_nlaunch;
+    if ((e = cudaMemsetAsync(d.counters, 0, 4, st))) return mr_fail(e, msg, "adjoint PCG");
+    k_beta<<<colBlocks, 128, 0, st>>>(d, k + 1);
+    ++g_nlaunch;
+    active = 0;
+    if ((e = cudaMemcpyAsync(&active, d.counters, 4, cudaMemcpyDeviceToHost, st)) ||
+        (e = cudaStreamSynchronize(st)))
+      return mr_fail(e, msg, "adjoint PCG");
+    if (active == 0) break;
+    k_pcg_E<<<gIdx, kT, 0, st>>>(d);
+    ++g_nlaunch;
+  }
+  k_bwd_w<<<gIdx, kT, 0, st>>>(d);
+  ++g_nlaunch;
+  LdArgs a = S.base;
+  a.gate = GATE_ALL;
+  a.din = d.X;
+  a.fwd = d.Gr;
+  if ((e = ld_forward(a, d.R, st))) return mr_fail(e, msg, "A w");
+  g_nlaunch += 2;
+  k_bwd_out<<<dim3(64, d.R), 256, 0, st>>>(d, S.rowsptr, S.ms, S.gbptr, S.gtau, S.infos_dev);
+  ++g_nlaunch;
+  if ((e = cudaGetLastError())) return mr_fail(e, msg, "adjoint outputs");
+  if (call.grad_tau && (e = cudaMemcpyAsync(call.grad_tau, S.gtau, (size_t)d.R * 8, cudaMemcpyDeviceToHost, st)))
+    return mr_fail(e, msg, "read grad_tau");
+  rc = ld_read_infos(call, S, msg);
+  T.collect();
+  return rc;
+}
+
+void large_dct_set_timing(bool on) {
+  g_optimer.on = on;
+  g_optimer.reset();
+}
+void large_dct_timing(double* ms, double* bytes, int64_t* products, int64_t* launches) {
+  *ms = g_optimer.ms;
+  *bytes = g_optimer.bytes;
+  *products = g_optimer.products;
+  *launches = g_nlaunch;
 }
 
 namespace mr {

@@ -39,6 +39,36 @@ struct MrhsCall {
 constexpr int kMaxSplits = 8;
 
 size_t mrhs_workspace_bytes(int64_t m, int64_t n, int R);
+
+// Partial-DCT problems of one length n above the cluster solver's reach: the same lockstep
+// IPM with the multi-pass operator of large_dct.cu.
+struct LdCall {
+  int64_t n;
+  int R;
+  const int64_t* m;              // HOST, rows per problem
+  const int64_t* const* rows;    // HOST array of DEVICE pointers
+  const double* const* b;        // HOST array of DEVICE pointers
+  const double* tau;             // HOST (solve)
+  double* const* x;              // HOST array of DEVICE pointers (solve output)
+  double* const* zs_out;         // HOST array or null (solve)
+  const double* const* zs_in;    // backward: final iterates of the forward solve
+  const double* const* gx;       // backward: dL/dx
+  double* const* grad_b;         // backward: HOST array or null
+  double* grad_tau;              // backward: HOST or null
+  mfipm_info* infos;             // HOST, R entries
+  void* workspace;
+  size_t ws_bytes;
+  SolveParams prm;
+  cudaStream_t stream;
+};
+size_t large_dct_workspace_bytes(int64_t n, int R);
+int large_dct_solve(const LdCall& call, std::string* msg);
+int large_dct_backward(const LdCall& call, std::string* msg);
+// CUDA-event time of the operator products A^T A w of the last large_dct_solve / _backward
+// on this thread (ms = -1 if none), their algorithmic bytes (8 per index per product) and
+// the number of kernels that solve launched
+void large_dct_set_timing(bool on);
+void large_dct_timing(double* ms, double* bytes, int64_t* products, int64_t* launches);
 int mrhs_solve(const MrhsCall& call, std::string* msg);
 cudaError_t gemm_simple(void*, const void* Aop, const void* Bop, float* C, int rows, int N, int K, int splits,
                         cudaStream_t st);

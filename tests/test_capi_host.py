@@ -72,7 +72,7 @@ def test_invalid_arguments_rejected_before_launch(L, case):
     elif case == "m_gt_n":
         op.m = 5000
     elif case == "n_too_big":
-        op.n, op.m = 1 << 20, 1 << 18
+        op.n, op.m = 1 << 21, 1 << 19
     elif case == "tau_nonpositive":
         tau = 0.0
     elif case == "null_ws":
@@ -90,5 +90,60 @@ def test_invalid_arguments_rejected_before_launch(L, case):
     info = C.Info()
     rc = L.mfipm_solve(ctypes.byref(op), ctypes.c_void_p(0x3000), tau, ctypes.byref(p), ctypes.c_void_p(0x4000),
                        None, ws, wsb, ctypes.byref(info), None)
+    assert rc in (C.MFIPM_INVALID_ARG, C.MFIPM_UNSUPPORTED), (case, rc)
+    assert L.mfipm_last_error() and len(L.mfipm_last_error()) > 5
+
+
+def test_large_dct_workspace_and_threshold(L):
+    """n above the cluster solver's 65536 goes to the lockstep multi-pass solver; its
+    workspace holds about 130 bytes per index and grows with the group."""
+    from paper_1208_5435_gb300 import _capi as C
+    p = C.Params()
+    L.mfipm_params_default(ctypes.byref(p))
+    sizes = []
+    for batch in (1, 4):
+        ops = (C.Operator * batch)(*[_dct_op(C, 1 << 20, 1 << 18) for _ in range(batch)])
+        nb = ctypes.c_size_t()
+        assert L.mfipm_workspace_size(ops, batch, ctypes.byref(p), ctypes.byref(nb)) == 0
+        sizes.append(nb.value)
+    assert sizes[0] >= (1 << 20) * 120 and sizes[1] > 3 * sizes[0] // 2
+    # the threshold hook moves n = 4096 onto the multi-pass path and back
+    one = (C.Operator * 1)(_dct_op(C, 4096, 1024))
+    nb0, nb1 = ctypes.c_size_t(), ctypes.c_size_t()
+    assert L.mfipm_workspace_size(one, 1, ctypes.byref(p), ctypes.byref(nb0)) == 0
+    assert L.mfipm_set_large_dct_threshold(512) == C.MFIPM_INVALID_ARG
+    assert L.mfipm_set_large_dct_threshold(1024) == 0
+    try:
+        assert L.mfipm_workspace_size(one, 1, ctypes.byref(p), ctypes.byref(nb1)) == 0
+    finally:
+        assert L.mfipm_set_large_dct_threshold(1 << 17) == 0
+    assert nb1.value != nb0.value
+
+
+@pytest.mark.parametrize("case", ["small_ws", "null_ws", "fp64_pcg", "n_not_pow2", "backward_no_zs"])
+def test_large_dct_rejected_before_launch(L, case):
+    from paper_1208_5435_gb300 import _capi as C
+    p = C.Params()
+    L.mfipm_params_default(ctypes.byref(p))
+    op = _dct_op(C, 1 << 20, 1 << 18)
+    ws, wsb = ctypes.c_void_p(0x10000), 1 << 40
+    if case == "small_ws":
+        wsb = 1 << 20
+    elif case == "null_ws":
+        ws = None
+    elif case == "fp64_pcg":
+        p.precision = C.PREC_FP64
+    elif case == "n_not_pow2":
+        op.n = (1 << 20) - 64
+    info = C.Info()
+    if case == "backward_no_zs":
+        ops = (C.Operator * 1)(op)
+        P = ctypes.c_void_p
+        arr = (P * 1)(P(0x3000))
+        rc = L.mfipm_backward(1, ops, arr, (ctypes.c_double * 1)(0.1), arr, None, arr, None, None, None,
+                              ctypes.byref(p), ws, wsb, ctypes.byref(info), None)
+    else:
+        rc = L.mfipm_solve(ctypes.byref(op), ctypes.c_void_p(0x3000), 0.1, ctypes.byref(p), ctypes.c_void_p(0x4000),
+                           None, ws, wsb, ctypes.byref(info), None)
     assert rc in (C.MFIPM_INVALID_ARG, C.MFIPM_UNSUPPORTED), (case, rc)
     assert L.mfipm_last_error() and len(L.mfipm_last_error()) > 5
