@@ -170,6 +170,73 @@ __global__ void __launch_bounds__(kThr) pass_a(LdArgs a) {
   }
 }
 
+// Work item e of row-pair block rb in pass B: frequencies kA = rowA + N1 k2A and its partner
+// kB = L - kA = rowB + N1 k2B, their buffer positions (bit-reversed order, row B at +stride)
+// and whether kB is a second frequency (false when kA pairs with itself: k = 0 and L/2).
+// Row pair (rb, N1 - rb): N2 items.  rb = 0 holds rows 0 and N1/2: N2/2 + 1 items pair
+// k2 <-> N2 - k2 in row 0, then N2/2 items pair k2 <-> N2 - 1 - k2 in row N1/2.
+struct PairItem {
+  int rowA, k2A, rowB, k2B, pA, pB;
+  bool two;
+};
+__device__ __forceinline__ PairItem pair_item(int rb, int e, int logN1, int logN2) {
+  const int N1 = 1 << logN1, N2 = 1 << logN2, stride = N2 + 1;
+  PairItem it;
+  if (rb != 0) {
+    it.rowA = rb;
+    it.k2A = e;
+    it.rowB = N1 - rb;
+    it.k2B = N2 - 1 - e;
+    it.pA = bitrev(it.k2A, logN2);
+    it.pB = stride + bitrev(it.k2B, logN2);
+    it.two = true;
+  } else if (e <= (N2 >> 1)) {
+    it.rowA = it.rowB = 0;
+    it.k2A = e;
+    it.k2B = (N2 - e) & (N2 - 1);
+    it.pA = bitrev(it.k2A, logN2);
+    it.pB = bitrev(it.k2B, logN2);
+    it.two = (e != 0 && e != (N2 >> 1));
+  } else {
+    it.rowA = it.rowB = N1 >> 1;
+    it.k2A = e - (N2 >> 1) - 1;
+    it.k2B = N2 - 1 - it.k2A;
+    it.pA = stride + bitrev(it.k2A, logN2);
+    it.pB = stride + bitrev(it.k2B, logN2);
+    it.two = true;
+  }
+  return it;
+}
+__device__ __forceinline__ int items_of(int rb, int logN2) { return (1 << logN2) + (rb == 0 ? 1 : 0); }
+
+// bits 0..3 of the pointwise step's row mask for frequency k (rows k, n-k, L-k, L+k)
+__device__ __forceinline__ unsigned mask_bits(const uint8_t* mask, int64_t k, int64_t n) {
+  const int64_t L = n >> 1;
+  return (mask[k] ? 1u : 0u) | ((k > 0 && mask[n - k]) ? 2u : 0u) | (mask[L - k] ? 4u : 0u) | (mask[L + k] ? 8u : 0u);
+}
+
+// The mask bits of every pass-B work item, once per solve: code[j][rb][e] = bits(kA) | bits(kB) << 4.
+__global__ void mask_codes(LdArgs a) {
+  const int j = blockIdx.y, rb = blockIdx.x;
+  const int N1 = 1 << a.logN1, N2 = 1 << a.logN2;
+  const int64_t n = (int64_t)1 << a.logN;
+  const uint8_t* mask = a.mask + (int64_t)j * n;
+  uint8_t* code = a.mcode + ((int64_t)j * (N1 >> 1) + rb) * (N2 + 1);
+  for (int e = threadIdx.x; e < items_of(rb, a.logN2); e += blockDim.x) {
+    const PairItem it = pair_item(rb, e, a.logN1, a.logN2);
+    const int64_t kA = it.rowA + (int64_t)N1 * it.k2A, kB = it.rowB + (int64_t)N1 * it.k2B;
+    code[e] = (uint8_t)(mask_bits(mask, kA, n) | (it.two ? mask_bits(mask, kB, n) << 4 : 0u));
+  }
+}
+
+// exp(-2 pi i (row + N1 k2) / 2^l) = exp(-2 pi i row / 2^l) exp(-2 pi i k2 / 2^(l - logN1)):
+// consecutive k2 read consecutive table entries
+template <class C>
+__device__ __forceinline__ C tw_rowcol(const Twiddle<C>& tw, int row, int k2, int l, int logN1) {
+  const C f = tw.root(k2, l - logN1);
+  return row ? cmul(tw.root(row, l), f) : f;
+}
+
 // MODE_NORMAL / MODE_RESID: rows through the pointwise chain and back; MODE_FORWARD:
 // alpha_j X_j of the forward transform into fwd (float64, natural order).
 template <class C, int MODE>
@@ -204,41 +271,23 @@ __global__ void __launch_bounds__(kThr) pass_b(LdArgs a) {
   double* fwd = MODE == MODE_FORWARD ? a.fwd + (int64_t)j * n : nullptr;
   const PwConst<R> pc(geo);
   R acc = pc.zero;
-  // one work item per pair (k, L - k); the pair's two new values overwrite the old ones.
-  // Row pair (rb, N1 - rb): N2 items.  Rows 0 and N1/2 (rb = 0): N2/2 + 1 items for row 0
-  // and N2/2 for row N1/2.
-  const int items = N2 + (rb == 0 ? 1 : 0);
-  for (int e = threadIdx.x; e < items; e += blockDim.x) {
-    int pA, pB;  // buffer positions (bit-reversed order)
-    int64_t kA, kB;
-    bool two;
-    if (rb != 0) {
-      kA = rA + (int64_t)N1 * e;
-      kB = rB + (int64_t)N1 * (N2 - 1 - e);
-      pA = bitrev(e, a.logN2);
-      pB = stride + bitrev(N2 - 1 - e, a.logN2);
-      two = true;
-    } else if (e <= (N2 >> 1)) {  // row 0: k2 <-> N2 - k2 (0 and N2/2 self-paired)
-      kA = (int64_t)N1 * e;
-      kB = (int64_t)N1 * ((N2 - e) & (N2 - 1));
-      pA = bitrev(e, a.logN2);
-      pB = bitrev((N2 - e) & (N2 - 1), a.logN2);
-      two = (e != 0 && e != (N2 >> 1));
-    } else {  // row N1/2: k2 <-> N2 - 1 - k2 for k2 = e - N2/2 - 1 < N2/2
-      const int k2 = e - (N2 >> 1) - 1;
-      kA = (N1 >> 1) + (int64_t)N1 * k2;
-      kB = (N1 >> 1) + (int64_t)N1 * (N2 - 1 - k2);
-      pA = stride + bitrev(k2, a.logN2);
-      pB = stride + bitrev(N2 - 1 - k2, a.logN2);
-      two = true;
+  // one work item per pair (k, L - k); the pair's two new values overwrite the old ones
+  const uint8_t* code = a.mcode + ((int64_t)j * (N1 >> 1) + rb) * (N2 + 1);
+  for (int e = threadIdx.x; e < items_of(rb, a.logN2); e += blockDim.x) {
+    const PairItem it = pair_item(rb, e, a.logN1, a.logN2);
+    const int64_t kA = it.rowA + (int64_t)N1 * it.k2A, kB = it.rowB + (int64_t)N1 * it.k2B;
+    const unsigned mb = MODE == MODE_FORWARD ? 0u : code[e];
+    const C zA = buf[it.pA], zB = buf[it.pB];
+    const C nA = dct_pointwise_w<C, MODE>(kA, zA, zB, tw_rowcol(tw, it.rowA, it.k2A, a.logN, a.logN1),
+                                          tw_rowcol(tw, it.rowA, it.k2A, a.logN + 2, a.logN1), mb & 15u, geo, pc,
+                                          true, acc, fwd);
+    if (it.two) {
+      const C nB = dct_pointwise_w<C, MODE>(kB, zB, zA, tw_rowcol(tw, it.rowB, it.k2B, a.logN, a.logN1),
+                                            tw_rowcol(tw, it.rowB, it.k2B, a.logN + 2, a.logN1), mb >> 4, geo, pc,
+                                            true, acc, fwd);
+      if (MODE != MODE_FORWARD) buf[it.pB] = nB;
     }
-    const C zA = buf[pA], zB = buf[pB];
-    const C nA = dct_pointwise<C, MODE>(kA, zA, zB, geo, tw, pc, true, acc, fwd);
-    if (two) {
-      const C nB = dct_pointwise<C, MODE>(kB, zB, zA, geo, tw, pc, true, acc, fwd);
-      if (MODE != MODE_FORWARD) buf[pB] = nB;
-    }
-    if (MODE != MODE_FORWARD) buf[pA] = nA;
+    if (MODE != MODE_FORWARD) buf[it.pA] = nA;
   }
   if (MODE == MODE_FORWARD) return;
   // block total of the masked energy (||A w||^2 or ||A x - b||^2)
@@ -317,6 +366,15 @@ static cudaError_t launch_rows(void (*k)(LdArgs), const LdArgs& a, int R, cudaSt
   if (e != cudaSuccess) return e;
   k<<<dim3((1u << a.logN1) / 2, R), ld::kThr, sm, st>>>(a);
   return cudaGetLastError();
+}
+
+cudaError_t ld_mask_codes(const LdArgs& a, int R, cudaStream_t st) {
+  ld::mask_codes<<<dim3((1u << a.logN1) / 2, R), 256, 0, st>>>(a);
+  return cudaGetLastError();
+}
+size_t ld_mask_code_bytes(int64_t n, int R) {
+  const LdShape s = ld_shape(n);
+  return (size_t)R * ((size_t)1 << (s.logN1 - 1)) * (((size_t)1 << s.logN2) + 1);
 }
 
 // y = A^T A w for w = p_u - p_v (float32)

@@ -28,6 +28,7 @@ struct LdArgs {
   double* dout;              // resid: A^T (A x - b)
   void* inter;               // R x L complex intermediate (double-float size)
   const uint8_t* mask;       // R x n sampled-row mask
+  uint8_t* mcode;            // R x (N1/2) x (N2+1) mask bits per pass-B work item (ld_mask_codes)
   const double* bsu;         // R x n  b scattered / DCT scale
   const float2* bsu_df;      // the same, double-float
   double* fwd;               // forward: R x n orthonormal DCT-II coefficients
@@ -37,6 +38,9 @@ struct LdArgs {
   const float4* twdf;
 };
 
+// once per solve, after the mask is built
+cudaError_t ld_mask_codes(const LdArgs& a, int R, cudaStream_t st);
+size_t ld_mask_code_bytes(int64_t n, int R);
 cudaError_t ld_normal(const LdArgs& a, int R, cudaStream_t st);
 cudaError_t ld_resid(const LdArgs& a, int R, cudaStream_t st);
 cudaError_t ld_forward(const LdArgs& a, int R, cudaStream_t st);

@@ -76,6 +76,31 @@ __device__ __forceinline__ void block_minima(const double (&v)[K], double* part,
     part[((int64_t)col * nb + blk) * kPart + threadIdx.x] = s;
   }
 }
+// column total of partial k over the nb block partials, computed by a whole block of kT
+// threads (every thread gets the result; fixed order, so deterministic)
+__device__ double block_col_total(const double* part, int col, int nb, int k, bool is_min = false) {
+  __shared__ double red[kT / 32];
+  __shared__ double out;
+  double s = is_min ? INFINITY : 0.0;
+  for (int b = threadIdx.x; b < nb; b += kT) {
+    const double v = part[((int64_t)col * nb + b) * kPart + k];
+    s = is_min ? fmin(s, v) : s + v;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const double t = __shfl_xor_sync(0xffffffffu, s, o);
+    s = is_min ? fmin(s, t) : s + t;
+  }
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = is_min ? INFINITY : 0.0;
+    for (int w = 0; w < kT / 32; ++w) t = is_min ? fmin(t, red[w]) : t + red[w];
+    out = t;
+  }
+  __syncthreads();
+  return out;
+}
 // column total of partial k (fixed order: deterministic)
 __device__ __forceinline__ double col_total(const double* part, int col, int nb, int k, bool is_min = false) {
   double s = is_min ? INFINITY : 0.0;
@@ -424,19 +449,31 @@ struct Dev {
   SolveParams prm;
 };
 
-// dz, ds of one index from the PCG pairs (Eq. redNewtonB; corrector reading R6), in float64
-struct D2 {
-  double dz, ds;
+// dz, ds of one index from the PCG pairs (Eq. redNewtonB; corrector reading R6).  Precision
+// split: the direction, Theta^-1 = s/z, sigma mu / z and the step-to-boundary ratios only steer
+// the iteration and are float32 (the PCG precision); the iterate (z, s), its update
+// z + alpha dz, x = u - v, the residual and the gap sums stay float64.  The ratio test and the
+// update evaluate the direction by the same function from the same inputs, so the
+// fraction-to-boundary rule keeps z, s > 0.
+struct Steer {
+  float smu, s3mut, ap1, ad1;
+  bool corr;
 };
-__device__ __forceinline__ D2 dirn(double z, double s, float dz1f, float dz2f, const Col& c, double sigma3, bool corr) {
-  const double dz1 = dz1f, dz2 = dz2f;
-  const double rz = 1.0 / z, d = s * rz;
-  const double ds1 = c.sigma * c.mu * rz - s - d * dz1;
+__device__ __forceinline__ Steer steer(const Col& c, double sigma3, bool corr) {
+  return Steer{(float)(c.sigma * c.mu), (float)(sigma3 * c.mu_t), (float)c.alpha_p1, (float)c.alpha_d1, corr};
+}
+struct D2 {
+  float dz, ds;
+};
+__device__ __forceinline__ D2 dirn(double zd, double sd, float dz1, float dz2, const Steer& c) {
+  const float z = (float)zd, s = (float)sd;
+  const float rz = __frcp_rn(z), d = s * rz;
+  const float ds1 = (c.smu * rz - s) - d * dz1;
   D2 r{dz1, ds1};
-  if (corr) {
-    const double zt = z + c.alpha_p1 * dz1, st = s + c.alpha_d1 * ds1;
+  if (c.corr) {
+    const float zt = z + c.ap1 * dz1, st = s + c.ad1 * ds1;
     r.dz = dz1 + dz2;
-    r.ds = ds1 + (sigma3 * c.mu_t - zt * st) * rz - d * dz2;
+    r.ds = ds1 + ((c.s3mut - zt * st) * rz - d * dz2);
   }
   return r;
 }
@@ -445,7 +482,7 @@ __device__ __forceinline__ D2 dirn(double z, double s, float dz1f, float dz2f, c
 __global__ void k_update(Dev d, int first) {
   const int j = blockIdx.y, blk = blockIdx.x;
   const Col c = d.col[j];
-  double v[3] = {0, 0, 0};
+  float a[3] = {0.f, 0.f, 0.f};
   for (int i = blk * kIdx + threadIdx.x; i < min(d.n, (blk + 1) * kIdx); i += kT) {
     const int64_t gi = (int64_t)j * d.n + i;
     double4 st;
@@ -457,10 +494,11 @@ __global__ void k_update(Dev d, int first) {
       if (!c.done) {
         const float2 x1 = d.X1[gi];
         const float2 x2 = c.corr ? d.X2[gi] : make_float2(0.f, 0.f);
-        const D2 du = dirn(st.x, st.z, x1.x, x2.x, c, d.prm.sigma3, c.corr);
-        const D2 dv = dirn(st.y, st.w, x1.y, x2.y, c, d.prm.sigma3, c.corr);
-        double nu = st.x + c.alpha_p * du.dz, nv = st.y + c.alpha_p * dv.dz;
-        double nsu = st.z + c.alpha_d * du.ds, nsv = st.w + c.alpha_d * dv.ds;
+        const Steer sc = steer(c, d.prm.sigma3, c.corr);
+        const D2 du = dirn(st.x, st.z, x1.x, x2.x, sc);
+        const D2 dv = dirn(st.y, st.w, x1.y, x2.y, sc);
+        double nu = fma(c.alpha_p, (double)du.dz, st.x), nv = fma(c.alpha_p, (double)dv.dz, st.y);
+        double nsu = fma(c.alpha_d, (double)du.ds, st.z), nsv = fma(c.alpha_d, (double)dv.ds, st.w);
         const double keep = 1.0 - d.prm.eta;
         if (!(nu > 0.0)) nu = st.x * keep;
         if (!(nv > 0.0)) nv = st.y * keep;
@@ -475,10 +513,12 @@ __global__ void k_update(Dev d, int first) {
     zp[3] = st.w;
     const double x = st.x - st.y;
     d.X[gi] = x;
-    v[0] += st.x * st.z + st.y * st.w;
-    v[1] += st.x + st.y;
-    v[2] += x * x;
+    // float32 terms of positive sums (no cancellation), float64 across threads
+    a[0] += (float)st.x * (float)st.z + (float)st.y * (float)st.w;
+    a[1] += (float)(st.x + st.y);
+    a[2] += (float)x * (float)x;
   }
+  const double v[3] = {a[0], a[1], a[2]};
   block_partials<3>(v, d.part, j, d.nb, blk);
 }
 
@@ -494,13 +534,14 @@ __global__ void k_colnorm2(const double* __restrict__ V, int len, double* part, 
 }
 
 // gap test, mu, sigma (one thread per column)
+// one block of kT threads per column
 __global__ void k_stats(Dev d, int it, const double* part2) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= d.R) return;
+  const int j = blockIdx.x;
   Col& c = d.col[j];
   if (c.done) return;
-  const double zts = col_total(d.part, j, d.nb, 0), l1 = col_total(d.part, j, d.nb, 1);
-  const double res2 = col_total(part2, j, d.nb2, 0);
+  const double zts = block_col_total(d.part, j, d.nb, 0), l1 = block_col_total(d.part, j, d.nb, 1);
+  const double res2 = block_col_total(part2, j, d.nb2, 0);
+  if (threadIdx.x) return;
   c.res2 = res2;
   c.mu = zts / (2.0 * d.n);
   c.P_obj = c.tau * l1 + 0.5 * res2;
@@ -522,6 +563,7 @@ __global__ void k_pcg_init(Dev d, int corr) {
   const int j = blockIdx.y, blk = blockIdx.x;
   const Col c = d.col[j];
   const bool live = !c.done && (!corr || c.corr_next);
+  const Steer sc = steer(c, d.prm.sigma3, false);
   double v[2] = {0, 0};
   for (int i = blk * kIdx + threadIdx.x; i < min(d.n, (blk + 1) * kIdx); i += kT) {
     const int64_t gi = (int64_t)j * d.n + i;
@@ -529,7 +571,7 @@ __global__ void k_pcg_init(Dev d, int corr) {
     const double u = zp[0], vv = zp[1], su = zp[2], sv = zp[3];
     float2 dd;
     if (!corr) {
-      dd = make_float2((float)(su / u), (float)(sv / vv));
+      dd = make_float2(__fdiv_rn((float)su, (float)u), __fdiv_rn((float)sv, (float)vv));
       d.Dv[gi] = dd;
     } else {
       dd = d.Dv[gi];
@@ -538,18 +580,18 @@ __global__ void k_pcg_init(Dev d, int corr) {
     if (live) {
       const double g = d.Gr[gi];
       if (!corr) {
-        const double smu = c.sigma * c.mu;
-        r.x = (float)(smu / u - (c.tau + g));
-        r.y = (float)(smu / vv - (c.tau - g));
+        r.x = sc.smu * __frcp_rn((float)u) - (float)(c.tau + g);
+        r.y = sc.smu * __frcp_rn((float)vv) - (float)(c.tau - g);
       } else {
+        // f_z~ at the trial point in float64, Z^-1 f_s~ in float32
         const float2 x1 = d.X1[gi];
-        const D2 du = dirn(u, su, x1.x, 0.f, c, d.prm.sigma3, false);
-        const D2 dv = dirn(vv, sv, x1.y, 0.f, c, d.prm.sigma3, false);
-        const double zu = u + c.alpha_p1 * du.dz, zv = vv + c.alpha_p1 * dv.dz;
-        const double tsu = su + c.alpha_d1 * du.ds, tsv = sv + c.alpha_d1 * dv.ds;
-        const double s3mu = d.prm.sigma3 * c.mu_t;
-        r.x = (float)((tsu - (c.tau + g)) + (s3mu - zu * tsu) / u);
-        r.y = (float)((tsv - (c.tau - g)) + (s3mu - zv * tsv) / vv);
+        const D2 du = dirn(u, su, x1.x, 0.f, sc);
+        const D2 dv = dirn(vv, sv, x1.y, 0.f, sc);
+        const double zu = fma(c.alpha_p1, (double)du.dz, u), zv = fma(c.alpha_p1, (double)dv.dz, vv);
+        const double tsu = fma(c.alpha_d1, (double)du.ds, su), tsv = fma(c.alpha_d1, (double)dv.ds, sv);
+        const float s3mu = (float)(d.prm.sigma3 * c.mu_t);
+        r.x = (float)(tsu - (c.tau + g)) + (s3mu - (float)zu * (float)tsu) * __frcp_rn((float)u);
+        r.y = (float)(tsv - (c.tau - g)) + (s3mu - (float)zv * (float)tsv) * __frcp_rn((float)vv);
       }
     }
     const float2 p = precond2(dd, r, (float)c.rho);
@@ -588,13 +630,14 @@ __global__ void k_split_t(Dev d, double* part2) {
 }
 
 // alpha = r.P^-1 r / (p.Theta^-1 p + ||A w||^2); first iteration records rz0
+// one block of kT threads per column
 __global__ void k_alpha(Dev d, int first, const double* part2) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= d.R) return;
+  const int j = blockIdx.x;
   Col& c = d.col[j];
-  const double pdp = col_total(d.part, j, d.nb, 1), aw2 = col_total(part2, j, d.nb2, 0);
+  const double pdp = block_col_total(d.part, j, d.nb, 1), aw2 = block_col_total(part2, j, d.nb2, 0);
+  const double rz = first ? block_col_total(d.part, j, d.nb, 0) : 0.0;
+  if (threadIdx.x) return;
   if (first) {
-    const double rz = col_total(d.part, j, d.nb, 0);
     c.rz0 = c.rz = rz;
     c.active = rz > 0.0 && isfinite(rz);
   }
@@ -635,12 +678,16 @@ __global__ void k_pcg_D(Dev d, float2* __restrict__ Xo, int first) {
   block_partials<1>(v, d.part, j, d.nb, blk);
 }
 
+// one block of kT threads per column
 __global__ void k_beta(Dev d, int k) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= d.R) return;
+  const int j = blockIdx.x;
   Col& c = d.col[j];
-  if (!c.active) { c.beta = 0.f; return; }
-  const double rzn = col_total(d.part, j, d.nb, 0);
+  if (!c.active) {
+    if (threadIdx.x == 0) c.beta = 0.f;
+    return;
+  }
+  const double rzn = block_col_total(d.part, j, d.nb, 0);
+  if (threadIdx.x) return;
   c.pcg_iters += 1;
   const bool stop = !(rzn > d.prm.tol_pcg * d.prm.tol_pcg * c.rz0) || k >= d.prm.max_iter_pcg || !isfinite(rzn);
   c.beta = (float)(rzn / c.rz);
@@ -681,34 +728,41 @@ __global__ void k_pcg_E(Dev d) {
 __global__ void k_steps(Dev d, int corr) {
   const int j = blockIdx.y, blk = blockIdx.x;
   const Col c = d.col[j];
-  double v[2] = {INFINITY, INFINITY};
+  const Steer sc = steer(c, d.prm.sigma3, corr);
+  float v[2] = {INFINITY, INFINITY};
   for (int i = blk * kIdx + threadIdx.x; i < min(d.n, (blk + 1) * kIdx); i += kT) {
     const int64_t gi = (int64_t)j * d.n + i;
     const double* zp = d.zs + 4 * gi;
     const float2 x1 = d.X1[gi];
     const float2 x2 = corr ? d.X2[gi] : make_float2(0.f, 0.f);
-    const D2 du = dirn(zp[0], zp[2], x1.x, x2.x, c, d.prm.sigma3, corr);
-    const D2 dv = dirn(zp[1], zp[3], x1.y, x2.y, c, d.prm.sigma3, corr);
-    if (du.dz < 0.0) v[0] = fmin(v[0], -zp[0] / du.dz);
-    if (dv.dz < 0.0) v[0] = fmin(v[0], -zp[1] / dv.dz);
-    if (du.ds < 0.0) v[1] = fmin(v[1], -zp[2] / du.ds);
-    if (dv.ds < 0.0) v[1] = fmin(v[1], -zp[3] / dv.ds);
+    const D2 du = dirn(zp[0], zp[2], x1.x, x2.x, sc);
+    const D2 dv = dirn(zp[1], zp[3], x1.y, x2.y, sc);
+    // ratios in float32: eta < 1 leaves a margin far above their rounding
+    if (du.dz < 0.f) v[0] = fminf(v[0], -(float)zp[0] * __frcp_rn(du.dz));
+    if (dv.dz < 0.f) v[0] = fminf(v[0], -(float)zp[1] * __frcp_rn(dv.dz));
+    if (du.ds < 0.f) v[1] = fminf(v[1], -(float)zp[2] * __frcp_rn(du.ds));
+    if (dv.ds < 0.f) v[1] = fminf(v[1], -(float)zp[3] * __frcp_rn(dv.ds));
   }
-  block_minima<2>(v, d.part, j, d.nb, blk);
+  const double vd[2] = {v[0], v[1]};
+  block_minima<2>(vd, d.part, j, d.nb, blk);
 }
 
+// one block of kT threads per column
 __global__ void k_steps_fin(Dev d, int corr) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= d.R) return;
+  const int j = blockIdx.x;
   Col& c = d.col[j];
   if (c.done) {
-    c.alpha_p = c.alpha_d = 0.0;
-    c.corr_next = 0;
+    if (threadIdx.x == 0) {
+      c.alpha_p = c.alpha_d = 0.0;
+      c.corr_next = 0;
+    }
     return;
   }
   if (corr && !c.corr_next) return;  // keeps its predictor steps
-  double ap = fmin(1.0, d.prm.eta * col_total(d.part, j, d.nb, 0, true));
-  double ad = fmin(1.0, d.prm.eta * col_total(d.part, j, d.nb, 1, true));
+  const double rp = block_col_total(d.part, j, d.nb, 0, true), rd = block_col_total(d.part, j, d.nb, 1, true);
+  if (threadIdx.x) return;
+  double ap = fmin(1.0, d.prm.eta * rp);
+  double ad = fmin(1.0, d.prm.eta * rd);
   if (d.prm.equal_steps) ap = ad = fmin(ap, ad);
   c.alpha_p = ap;
   c.alpha_d = ad;
@@ -731,40 +785,45 @@ __global__ void k_steps_fin(Dev d, int corr) {
 __global__ void k_trial(Dev d) {
   const int j = blockIdx.y, blk = blockIdx.x;
   const Col c = d.col[j];
+  const Steer sc = steer(c, d.prm.sigma3, false);
   double v[1] = {0.0};
   for (int i = blk * kIdx + threadIdx.x; i < min(d.n, (blk + 1) * kIdx); i += kT) {
     const int64_t gi = (int64_t)j * d.n + i;
     const double* zp = d.zs + 4 * gi;
     const float2 x1 = d.X1[gi];
-    const D2 du = dirn(zp[0], zp[2], x1.x, 0.f, c, d.prm.sigma3, false);
-    const D2 dv = dirn(zp[1], zp[3], x1.y, 0.f, c, d.prm.sigma3, false);
-    const double zu = zp[0] + c.alpha_p1 * du.dz, zv = zp[1] + c.alpha_p1 * dv.dz;
-    const double su = zp[2] + c.alpha_d1 * du.ds, sv = zp[3] + c.alpha_d1 * dv.ds;
+    const D2 du = dirn(zp[0], zp[2], x1.x, 0.f, sc);
+    const D2 dv = dirn(zp[1], zp[3], x1.y, 0.f, sc);
+    const double zu = fma(c.alpha_p1, (double)du.dz, zp[0]), zv = fma(c.alpha_p1, (double)dv.dz, zp[1]);
+    const double su = fma(c.alpha_d1, (double)du.ds, zp[2]), sv = fma(c.alpha_d1, (double)dv.ds, zp[3]);
     d.X[gi] = zu - zv;
     v[0] += zu * su + zv * sv;
   }
   block_partials<1>(v, d.part, j, d.nb, blk);
 }
 
+// one block of kT threads per column
 __global__ void k_mu_t(Dev d) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= d.R) return;
+  const int j = blockIdx.x;
   Col& c = d.col[j];
   if (c.corr_next) {
-    c.mu_t = col_total(d.part, j, d.nb, 0) / (2.0 * d.n);
+    const double zts = block_col_total(d.part, j, d.nb, 0);
+    if (threadIdx.x) return;
+    c.mu_t = zts / (2.0 * d.n);
     c.nmat += 2;
   }
 }
 
 // ||c||: with x = 0 the residual kernel gives Gr = -A^T b
+// one block of kT threads per column
 __global__ void k_setup_cols(Dev d, const double* __restrict__ taus, const double* __restrict__ rhos) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= d.R) return;
+  const int j = blockIdx.x;
+  const double atb2 = block_col_total(d.part, j, d.nb, 0);
+  if (threadIdx.x) return;
   Col c{};
   c.tau = taus[j];
   c.rho = rhos ? rhos[j] : d.rho;
   c.alpha_p = c.alpha_d = c.prev_ap = c.prev_ad = 1.0;
-  c.cn = sqrt(2.0 * d.n * c.tau * c.tau + 2.0 * col_total(d.part, j, d.nb, 0));
+  c.cn = sqrt(2.0 * d.n * c.tau * c.tau + 2.0 * atb2);
   c.nmat = 1;
   d.col[j] = c;
 }
@@ -796,10 +855,13 @@ __global__ void k_exit(Dev d, double* const* __restrict__ xout, double* const* _
   block_partials<3>(v, d.part, j, d.nb, blk);
 }
 
+// one block of kT threads per column
 __global__ void k_info(Dev d, mfipm_info* infos) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= d.R) return;
+  const int j = blockIdx.x;
   const Col& c = d.col[j];
+  const double fz2 = block_col_total(d.part, j, d.nb, 0), kk2 = block_col_total(d.part, j, d.nb, 1),
+               x2 = block_col_total(d.part, j, d.nb, 2);
+  if (threadIdx.x) return;
   mfipm_info info{};
   info.status = c.done ? c.stop : MFIPM_NOT_CONVERGED;
   info.ipm_iters = c.ipm_iters;
@@ -807,8 +869,8 @@ __global__ void k_info(Dev d, mfipm_info* infos) {
   info.pcg_iters = c.pcg_iters;
   info.n_mat = c.nmat;
   info.rel_gap = c.rel_gap;
-  info.dual_res = sqrt(col_total(d.part, j, d.nb, 0)) / (1.0 + c.cn);
-  info.kkt_rel = sqrt(col_total(d.part, j, d.nb, 1)) / (1.0 + sqrt(col_total(d.part, j, d.nb, 2)));
+  info.dual_res = sqrt(fz2) / (1.0 + c.cn);
+  info.kkt_rel = sqrt(kk2) / (1.0 + sqrt(x2));
   info.primal_obj = c.P_obj;
   infos[j] = info;
 }
@@ -874,18 +936,17 @@ int lockstep_run(mr::Dev& d, double* part2, const double* taus, const double* rh
   using namespace mr;
   const int R = d.R, nb = d.nb;
   const dim3 gIdx(nb, R);
-  const int colBlocks = (R + 127) / 128;
   cudaError_t e;
   int live = R, active = R;  // problems covered by the next operator product (host view)
   auto pcg = [&](float2* Xo) -> cudaError_t {
     for (int k = 0;; ++k) {
       if ((e = normal(k, k == 0 ? live : active))) return e;
-      k_alpha<<<colBlocks, 128, 0, st>>>(d, k == 0, part2);
+      k_alpha<<<R, kT, 0, st>>>(d, k == 0, part2);
       ++g_nlaunch;
       k_pcg_D<<<gIdx, kT, 0, st>>>(d, Xo, k == 0);
       ++g_nlaunch;
       if ((e = cudaMemsetAsync(d.counters, 0, 4, st))) return e;
-      k_beta<<<colBlocks, 128, 0, st>>>(d, k + 1);
+      k_beta<<<R, kT, 0, st>>>(d, k + 1);
       ++g_nlaunch;
       active = 0;
       if ((e = cudaMemcpyAsync(&active, d.counters, 4, cudaMemcpyDeviceToHost, st))) return e;
@@ -901,14 +962,14 @@ int lockstep_run(mr::Dev& d, double* part2, const double* taus, const double* rh
   if ((e = residual(GATE_ALL))) return mr_fail(e, msg, "residual");
   k_colnorm2<<<gIdx, kT, 0, st>>>(d.Gr, d.n, d.part, nb);
   ++g_nlaunch;
-  k_setup_cols<<<colBlocks, 128, 0, st>>>(d, taus, rhos);
+  k_setup_cols<<<R, kT, 0, st>>>(d, taus, rhos);
   ++g_nlaunch;
   for (int it = 1;; ++it) {
     k_update<<<gIdx, kT, 0, st>>>(d, it == 1);
     ++g_nlaunch;
     if ((e = residual(GATE_LIVE))) return mr_fail(e, msg, "residual");
     if ((e = cudaMemsetAsync(d.counters, 0, 16, st))) return mr_fail(e, msg, "counters");
-    k_stats<<<colBlocks, 128, 0, st>>>(d, it, part2);
+    k_stats<<<R, kT, 0, st>>>(d, it, part2);
     ++g_nlaunch;
     int unfinished = 0;
     if ((e = cudaMemcpyAsync(&unfinished, d.counters + 1, 4, cudaMemcpyDeviceToHost, st)) ||
@@ -921,7 +982,7 @@ int lockstep_run(mr::Dev& d, double* part2, const double* taus, const double* rh
     if ((e = pcg(d.X1))) return mr_fail(e, msg, "predictor PCG");
     k_steps<<<gIdx, kT, 0, st>>>(d, 0);
     ++g_nlaunch;
-    k_steps_fin<<<colBlocks, 128, 0, st>>>(d, 0);
+    k_steps_fin<<<R, kT, 0, st>>>(d, 0);
     ++g_nlaunch;
     int ncorr = 0;
     if ((e = cudaMemcpyAsync(&ncorr, d.counters + 2, 4, cudaMemcpyDeviceToHost, st)) ||
@@ -930,7 +991,7 @@ int lockstep_run(mr::Dev& d, double* part2, const double* taus, const double* rh
     if (ncorr > 0) {
       k_trial<<<gIdx, kT, 0, st>>>(d);
       ++g_nlaunch;
-      k_mu_t<<<colBlocks, 128, 0, st>>>(d);
+      k_mu_t<<<R, kT, 0, st>>>(d);
       ++g_nlaunch;
       if ((e = residual(GATE_LIVE))) return mr_fail(e, msg, "trial residual");
       k_pcg_init<<<gIdx, kT, 0, st>>>(d, 1);
@@ -938,13 +999,13 @@ int lockstep_run(mr::Dev& d, double* part2, const double* taus, const double* rh
       if ((e = pcg(d.X2))) return mr_fail(e, msg, "corrector PCG");
       k_steps<<<gIdx, kT, 0, st>>>(d, 1);
       ++g_nlaunch;
-      k_steps_fin<<<colBlocks, 128, 0, st>>>(d, 1);
+      k_steps_fin<<<R, kT, 0, st>>>(d, 1);
       ++g_nlaunch;
     }
   }
   k_exit<<<gIdx, kT, 0, st>>>(d, xptr, zptr);
   ++g_nlaunch;
-  k_info<<<colBlocks, 128, 0, st>>>(d, infos);
+  k_info<<<R, kT, 0, st>>>(d, infos);
   ++g_nlaunch;
   if ((e = cudaGetLastError())) return mr_fail(e, msg, "exit");
   return MFIPM_OK;
@@ -1209,6 +1270,7 @@ LdLayout ld_layout(int64_t n, int R) {
   b += al(sizeof(ProbDesc) * R) + al(256);  // descriptors, error word
   b += al(((size_t)2 << L.log2_tw) * 8) + al(((size_t)2 << L.log2_tw) * 16);  // twiddles
   b += al((size_t)R * sizeof(mfipm_info));
+  b += al(ld_mask_code_bytes(n, R));
   L.total = b;
   return L;
 }
@@ -1284,6 +1346,7 @@ int ld_setup(const LdCall& call, LdState& S, std::string* msg) {
   float2* tw32 = reinterpret_cast<float2*>(take(((size_t)2 << L.log2_tw) * 8));
   float4* twdf = reinterpret_cast<float4*>(take(((size_t)2 << L.log2_tw) * 16));
   S.infos_dev = reinterpret_cast<mfipm_info*>(take((size_t)R * sizeof(mfipm_info)));
+  uint8_t* mcode = reinterpret_cast<uint8_t*>(take(ld_mask_code_bytes(n, R)));
 
   std::vector<ProbDesc> desc(R);
   std::vector<double> rh(R), taus(R, 1.0);
@@ -1359,6 +1422,9 @@ int ld_setup(const LdCall& call, LdState& S, std::string* msg) {
   a.kpart = kPart;
   a.tw32 = tw32;
   a.twdf = twdf;
+  a.mcode = mcode;
+  if ((e = ld_mask_codes(a, R, st))) return mr_fail(e, msg, "mask codes");
+  ++g_nlaunch;
   return MFIPM_OK;
 }
 
@@ -1439,12 +1505,12 @@ int large_dct_backward(const LdCall& call, std::string* msg) {
     if ((e = ld_normal(a, d.R, st))) return mr_fail(e, msg, "adjoint PCG");
     g_nlaunch += 3;
     if (T.on && (e = T.end(st, (double)active * (double)call.n))) return mr_fail(e, msg, "timing event");
-    k_alpha<<<colBlocks, 128, 0, st>>>(d, k == 0, S.part2);
+    k_alpha<<<d.R, kT, 0, st>>>(d, k == 0, S.part2);
     ++g_nlaunch;
     k_pcg_D<<<gIdx, kT, 0, st>>>(d, d.X1, k == 0);
     ++g_nlaunch;
     if ((e = cudaMemsetAsync(d.counters, 0, 4, st))) return mr_fail(e, msg, "adjoint PCG");
-    k_beta<<<colBlocks, 128, 0, st>>>(d, k + 1);
+    k_beta<<<d.R, kT, 0, st>>>(d, k + 1);
     ++g_nlaunch;
     active = 0;
     if ((e = cudaMemcpyAsync(&active, d.counters, 4, cudaMemcpyDeviceToHost, st)) ||

@@ -105,15 +105,16 @@ __device__ __forceinline__ df load_bsu(const DctGeom& g, int64_t i, df) {
 // inverse chain needs; accumulates this index's share of the masked energy into acc and,
 // in MODE_FORWARD, writes alpha_j X_j instead.  Each DCT coefficient j is counted by
 // exactly one k: j in {k, N-k (k>0)} and, for k = 0, also j = L.
+// With the twiddles wN = exp(-2 pi i k / N), eps = exp(-i pi k / (2N)) and the row-mask bits
+// mb (bit 0..3: rows k, N-k (k > 0), L-k, L+k sampled; unused in MODE_FORWARD) supplied by the
+// caller.
 template <class C, int MODE, class R = decltype(C().x)>
-__device__ __forceinline__ C dct_pointwise(int64_t k, C a, C b, const DctGeom& geo, const Twiddle<C>& tw,
-                                           const PwConst<R>& pc, bool valid, R& acc, double* fwd_out) {
+__device__ __forceinline__ C dct_pointwise_w(int64_t k, C a, C b, C wN, C eps, unsigned mb, const DctGeom& geo,
+                                             const PwConst<R>& pc, bool valid, R& acc, double* fwd_out) {
   const int64_t L = (int64_t)1 << geo.logL, N = geo.N;
   const C c45 = mk(pc.rs2, -pc.rs2);  // exp(-i pi/4)
   const C E = cscale(cadd(a, cconj(b)), pc.half);
   const C O = cscale(cmul_mi(csub(a, cconj(b))), pc.half);
-  const C wN = tw.root(k, geo.logN);       // exp(-2 pi i k / N)
-  const C eps = tw.root(k, geo.logN + 2);  // exp(-i pi k / (2N))
   const C wO = cmul(wN, O);
   const C Wk = cmul(eps, cadd(E, wO));                   // eps^k V[k]
   const C Wlk = cmul(c45, cconj(cmul(eps, csub(E, wO))));  // eps^(L-k) V[L-k]
@@ -128,7 +129,7 @@ __device__ __forceinline__ C dct_pointwise(int64_t k, C a, C b, const DctGeom& g
     }
     return a;
   } else {
-    const bool m1 = geo.mask[i1], m2 = (k > 0) && geo.mask[i2], m3 = geo.mask[i3], m4 = geo.mask[i4];
+    const bool m1 = mb & 1u, m2 = mb & 2u, m3 = mb & 4u, m4 = mb & 8u;
     if constexpr (MODE == MODE_RESID) {
       X1 = m1 ? X1 - load_bsu(geo, i1, R()) : pc.zero;
       X2 = m2 ? X2 - load_bsu(geo, i2, R()) : pc.zero;
@@ -153,6 +154,20 @@ __device__ __forceinline__ C dct_pointwise(int64_t k, C a, C b, const DctGeom& g
     const C Op = cscale(cmulc(csub(Vk, cVlk), wN), pc.half);
     return cscale(cadd(Ep, cmul_i(Op)), pc.invL);
   }
+}
+
+// Twiddles from the level-ordered table and mask bits from geo.mask.
+template <class C, int MODE, class R = decltype(C().x)>
+__device__ __forceinline__ C dct_pointwise(int64_t k, C a, C b, const DctGeom& geo, const Twiddle<C>& tw,
+                                           const PwConst<R>& pc, bool valid, R& acc, double* fwd_out) {
+  unsigned mb = 0;
+  if constexpr (MODE != MODE_FORWARD) {
+    const int64_t L = (int64_t)1 << geo.logL, N = geo.N;
+    mb = (geo.mask[k] ? 1u : 0u) | ((k > 0 && geo.mask[N - k]) ? 2u : 0u) | (geo.mask[L - k] ? 4u : 0u) |
+         (geo.mask[L + k] ? 8u : 0u);
+  }
+  return dct_pointwise_w<C, MODE, R>(k, a, b, tw.root(k, geo.logN), tw.root(k, geo.logN + 2), mb, geo, pc, valid,
+                                     acc, fwd_out);
 }
 
 // The exchange step of the distributed DCT chain (see the file comment).  Returns this
