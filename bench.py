@@ -57,6 +57,43 @@ def parse_args():
     return ap.parse_args()
 
 
+# ----------------------------------------------------------------------------- N GPUs
+# One process per GPU; each solves its own shard of the workload (same sizes, its own random
+# stream), so per-GPU work is fixed as N grows (weak scaling) and nothing is exchanged on
+# the data path.  Only the timing and the solved counts are reduced, once, after the run.
+RANK_STRIDE = 100000
+
+
+def rank_problems(workload, rank, count=None):
+    """This rank's shard: the workload's problems with the random streams of rank r."""
+    return W.make_workload(workload, count=count, offset=rank * RANK_STRIDE)
+
+
+def max_over_ranks(x, world, device="cpu"):
+    if world == 1:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(x, world, device="cpu"):
+    if world == 1:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.SUM)
+    return float(t.item())
+
+
+def job_throughput(ok, total_ms, steps, world, device="cpu"):
+    """Whole-job units per second: solved units summed over ranks / slowest rank's time."""
+    ok_all = sum_over_ranks(ok, world, device)
+    ms = max_over_ranks(total_ms, world, device)
+    return ok_all / (ms / steps / 1e3), ms
+
+
 # ----------------------------------------------------------------------------- clocks
 class ClockSampler:
     """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
@@ -196,7 +233,7 @@ def run_ours(args, rank, world, local_rank):
     B.build()
     L = M.lib()
     dev = torch.device("cuda", local_rank)
-    probs = W.make_workload(args.workload, count=args.count)
+    probs = rank_problems(args.workload, rank, count=args.count)
     if probs[0].a_bf16 is not None:
         return run_bf16(args, rank, world, local_rank, probs)
     if args.workload == "dct_adjoint_32x1M":
@@ -236,14 +273,9 @@ def run_ours(args, rank, world, local_rank):
     if world > 1:
         torch.distributed.barrier()
     L.mfipm_set_timing(0)
-    total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
     ok = sum(1 for i in infos if i["status"] == 0 and i["kkt_rel"] <= KKT_GATE)
+    value, total_ms = job_throughput(ok, sum(step_ms), args.steps, world, dev)
     ms_per_step = total_ms / args.steps
-    value = world * ok / (ms_per_step / 1e3)
 
     # plain: the same problems, one mfipm_solve each (one timed pass)
     plain = None
@@ -285,12 +317,7 @@ def run_ours(args, rank, world, local_rank):
         if it >= args.warmup:
             e2e_ms.append(e0.elapsed_time(e1))
     e2e_ok = sum(1 for i in inf_ if i["status"] == 0 and i["kkt_rel"] <= KKT_GATE)
-    e2e_total = sum(e2e_ms)
-    if world > 1:
-        t = torch.tensor([e2e_total], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_total = float(t.item())
-    e2e_value = world * e2e_ok / (e2e_total / args.steps / 1e3)
+    e2e_value, _ = job_throughput(e2e_ok, sum(e2e_ms), args.steps, world, dev)
 
     # roofline of the dominant kernel (the persistent solver kernel)
     peak, peak_kind = measured_peaks()
@@ -368,12 +395,8 @@ def run_bf16(args, rank, world, local_rank, probs):
             e1.record(stream)
             torch.cuda.synchronize()
             step_ms.append(e0.elapsed_time(e1))
-    total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
     ok = sum(1 for i in infos if i["status"] == 0 and i["kkt_rel"] <= KKT_GATE)
+    value, total_ms = job_throughput(ok, sum(step_ms), args.steps, world, dev)
     ms_per_step = total_ms / args.steps
     # the tensor-core GEMMs of one PCG operator product, timed alone on their real shapes
     m, n, R = probs[0].m, probs[0].n, len(probs)
@@ -414,7 +437,7 @@ def run_bf16(args, rank, world, local_rank, probs):
         cpu = {"value": 1.0 / secs, "unit": UNIT, "cores": cpu_threads(), "kind": "oracle",
                "sample": f"1 of {len(probs)} right-hand sides, {secs:.1f} s: direct-solve float64 IPM (Woodbury m x m)"}
     line = {
-        "metric": METRIC, "value": world * ok / (ms_per_step / 1e3), "unit": UNIT, "n_gpus": world,
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "bf16 A / f32 PCG / f64 IPM", "data": "synthetic",
         "config": {"workload": args.workload, "m": m, "n": n, "rhs": R, "l2": "flushed (512 MiB write) before each step",
@@ -484,14 +507,9 @@ def run_adjoint(args, rank, world, local_rank, probs):
             torch.cuda.synchronize()
             step_ms.append(e0.elapsed_time(e1))
     L.mfipm_set_timing(0)
-    total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
     ok = sum(1 for i, bi in zip(infos, binfos) if i["status"] == 0 and i["kkt_rel"] <= KKT_GATE and bi["status"] == 0)
+    value, total_ms = job_throughput(ok, sum(step_ms), args.steps, world, dev)
     ms_per_step = total_ms / args.steps
-    value = world * ok / (ms_per_step / 1e3)
     op_ms = sum(s[0] for s in stats)
     op_bytes = sum(s[1] for s in stats)
     op_products = sum(s[2] for s in stats)
@@ -527,12 +545,7 @@ def run_adjoint(args, rank, world, local_rank, probs):
         if it >= 1:
             e2e_ms.append(e0.elapsed_time(e1))
     e2e_ok = sum(1 for i, bi in zip(inf_, bi_) if i["status"] == 0 and i["kkt_rel"] <= KKT_GATE and bi["status"] == 0)
-    e2e_total = sum(e2e_ms)
-    if world > 1:
-        t = torch.tensor([e2e_total], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_total = float(t.item())
-    e2e_value = world * e2e_ok / (e2e_total / args.steps / 1e3)
+    e2e_value, _ = job_throughput(e2e_ok, sum(e2e_ms), args.steps, world, dev)
     if rank != 0:
         return
     cpu = None

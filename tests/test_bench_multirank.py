@@ -1,0 +1,91 @@
+"""The multi-GPU logic of bench.py on the CPU: two gloo ranks (world_size 2) take disjoint
+shards of the same workload, and the timing and solved counts reduce to whole-job numbers
+(slowest rank's time, counts summed).  No GPU: the reductions run on CPU tensors."""
+import hashlib
+import os
+import socket
+import sys
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _digest(a):
+    return hashlib.sha1(np.ascontiguousarray(a).tobytes()).hexdigest()
+
+
+def _rank_main(rank, world, port, q):
+    sys.path.insert(0, ROOT)
+    import torch.distributed as dist
+    import bench
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        out = {}
+        # whole-job reductions
+        out["max"] = bench.max_over_ranks(1.5 + rank, world)
+        out["sum"] = bench.sum_over_ranks(10 + rank, world)
+        out["tp"] = bench.job_throughput(ok=4 + rank, total_ms=100.0 * (rank + 1), steps=2, world=world)
+        # shards of the uneven batch and of the shared-A workload
+        dct = bench.rank_problems("dct_batch_256", rank, count=3)
+        out["dct"] = [(p.n, p.m, _digest(p.b), _digest(p.rows)) for p in dct]
+        bf = bench.rank_problems("bf16_4096x16384_64rhs", rank, count=2)
+        out["bf16"] = (_digest(bf[0].a_bf16), [_digest(p.b) for p in bf])
+        gathered = [None] * world
+        dist.all_gather_object(gathered, out)
+        if rank == 0:
+            q.put(gathered)
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.fixture(scope="module")
+def two_ranks():
+    import torch.multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank_main, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = q.get(timeout=600)
+    for p in procs:
+        p.join(timeout=120)
+        assert p.exitcode == 0
+    return res
+
+
+def test_reductions_give_whole_job_numbers(two_ranks):
+    r0, r1 = two_ranks
+    assert r0["max"] == r1["max"] == 2.5
+    assert r0["sum"] == r1["sum"] == 21.0
+    # (4 + 5) problems over the slowest rank's 200 ms for 2 steps = 9 / 0.1 s
+    v, ms = r0["tp"]
+    assert ms == 200.0 and abs(v - 90.0) < 1e-9 and r1["tp"] == r0["tp"]
+
+
+def test_shards_are_disjoint_with_the_same_sizes(two_ranks):
+    r0, r1 = two_ranks
+    assert [x[:2] for x in r0["dct"]] == [x[:2] for x in r1["dct"]]  # weak scaling: same sizes
+    assert not set(x[2] for x in r0["dct"]) & set(x[2] for x in r1["dct"])  # own data
+    assert r0["bf16"][0] == r1["bf16"][0]  # one shared A
+    assert not set(r0["bf16"][1]) & set(r1["bf16"][1])  # own right-hand sides
+
+
+def test_rank_zero_shard_is_the_single_gpu_workload():
+    sys.path.insert(0, ROOT)
+    import bench
+    import workloads as W
+    a = bench.rank_problems("dct_batch_256", 0, count=2)
+    b = W.make_workload("dct_batch_256", count=2)
+    assert all(np.array_equal(x.b, y.b) and np.array_equal(x.rows, y.rows) for x, y in zip(a, b))

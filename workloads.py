@@ -113,7 +113,7 @@ def bf16_to_f64(bits: np.ndarray) -> np.ndarray:
 
 
 def bf16_dense_problems(m: int, n: int, k: int, nrhs: int, seed: int, sigma: float = 1e-3,
-                        tau_frac: float = 0.01):
+                        tau_frac: float = 0.01, first: int = 0):
     """One shared Gaussian A stored as bf16 with a per-tensor scale (a_scale = 1/sqrt(m)),
     and ``nrhs`` right-hand sides from k-sparse +-1 signals.  The problem matrix is exactly
     a_scale * bf16(A/a_scale); b and tau are computed with that exact matrix."""
@@ -122,7 +122,7 @@ def bf16_dense_problems(m: int, n: int, k: int, nrhs: int, seed: int, sigma: flo
     bits = bf16_round(rng.standard_normal((m, n)))
     A = a_scale * bf16_to_f64(bits)
     probs = []
-    for j in range(nrhs):
+    for j in range(first, first + nrhs):
         r = _rng(seed, 1 + j)
         x_hat = _sparse_signal(r, n, k, "pm1")
         b = A @ x_hat + sigma * r.standard_normal(m)
@@ -160,13 +160,15 @@ def batch_sizes(count: int, seed: int):
     return out
 
 
-def make_workload(name: str, count: Optional[int] = None, scale_n: Optional[int] = None):
+def make_workload(name: str, count: Optional[int] = None, scale_n: Optional[int] = None, offset: int = 0):
     """Return the list of Problems of a named workload.  ``count`` truncates the batch;
     ``scale_n`` (DCT only) replaces n by a smaller power of two with the same m/n and k/n
-    ratios, for oracle-sized cases."""
+    ratios, for oracle-sized cases.  ``offset`` shifts the random stream of every problem
+    (sizes, and the shared bf16 matrix, stay those of the workload): another shard of the
+    same workload for another GPU."""
     w = WORKLOADS[name]
     if w["kind"] == "dense":
-        return [dense_problem(w["m"], w["n"], w["k"], w["seed"], j, values=w["values"])
+        return [dense_problem(w["m"], w["n"], w["k"], w["seed"], offset + j, values=w["values"])
                 for j in range(count or w["count"])]
     if w["kind"] == "dct":
         n, m, k = w["n"], w["m"], w["k"]
@@ -174,10 +176,10 @@ def make_workload(name: str, count: Optional[int] = None, scale_n: Optional[int]
             m = m * scale_n // n
             k = max(1, k * scale_n // n)
             n = scale_n
-        return [dct_problem(n, m, k, w["seed"], j, values=w["values"]) for j in range(count or w["count"])]
+        return [dct_problem(n, m, k, w["seed"], offset + j, values=w["values"]) for j in range(count or w["count"])]
     if w["kind"] == "dct_batch":
         sizes = batch_sizes(w["count"], w["seed"])[: (count or w["count"])]
-        return [dct_problem(n, m, k, w["seed"], j) for j, (n, m, k) in enumerate(sizes)]
+        return [dct_problem(n, m, k, w["seed"], offset + j) for j, (n, m, k) in enumerate(sizes)]
     if w["kind"] == "bf16":
-        return bf16_dense_problems(w["m"], w["n"], w["k"], count or w["nrhs"], w["seed"])
+        return bf16_dense_problems(w["m"], w["n"], w["k"], count or w["nrhs"], w["seed"], first=offset)
     raise KeyError(name)
