@@ -20,6 +20,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "device_common.cuh"
 #include "internal.h"
 #include "large_dct.h"
@@ -122,16 +124,17 @@ template <> struct Io<float2> {
   static __device__ __forceinline__ Twiddle<float2> tw(const LdArgs& a) { return Twiddle<float2>{a.tw32, a.log2_tw}; }
   static __device__ __forceinline__ float2* inter(const LdArgs& a) { return reinterpret_cast<float2*>(a.inter); }
 };
-// float64 vectors carried as double-float
+// double-float vectors
 template <> struct Io<dfc> {
   using R = df;
-  static __device__ __forceinline__ df load(const LdArgs& a, int64_t gi) { return to_df(a.din[gi]); }
+  static __device__ __forceinline__ df load(const LdArgs& a, int64_t gi) {
+    const float2 v = a.din[gi];
+    return df(v.x, v.y);
+  }
   static __device__ __forceinline__ void store4(const LdArgs& a, int64_t gi, df w0, df w1, df w2, df w3) {
-    double* o = a.dout + gi;
-    o[0] = to_double(w0);
-    o[1] = to_double(w1);
-    o[2] = to_double(w2);
-    o[3] = to_double(w3);
+    float4* o = reinterpret_cast<float4*>(a.dout + gi);
+    o[0] = make_float4(w0.hi, w0.lo, w1.hi, w1.lo);
+    o[1] = make_float4(w2.hi, w2.lo, w3.hi, w3.lo);
   }
   static __device__ __forceinline__ Twiddle<dfc> tw(const LdArgs& a) { return Twiddle<dfc>{a.twdf, a.log2_tw}; }
   static __device__ __forceinline__ dfc* inter(const LdArgs& a) { return reinterpret_cast<dfc*>(a.inter); }
@@ -229,12 +232,17 @@ __global__ void mask_codes(LdArgs a) {
   }
 }
 
-// exp(-2 pi i (row + N1 k2) / 2^l) = exp(-2 pi i row / 2^l) exp(-2 pi i k2 / 2^(l - logN1)):
-// consecutive k2 read consecutive table entries
+// exp(-2 pi i (row + N1 k2) / 2^l).  float32: as exp(-2 pi i row / 2^l) exp(-2 pi i k2 / 2^(l -
+// logN1)), so consecutive k2 read consecutive table entries; double-float: one table entry
+// (a double-float complex product costs more than the scattered load).
 template <class C>
 __device__ __forceinline__ C tw_rowcol(const Twiddle<C>& tw, int row, int k2, int l, int logN1) {
-  const C f = tw.root(k2, l - logN1);
-  return row ? cmul(tw.root(row, l), f) : f;
+  if constexpr (std::is_same<C, dfc>::value) {
+    return tw.root(row + ((int64_t)k2 << logN1), l);
+  } else {
+    const C f = tw.root(k2, l - logN1);
+    return row ? cmul(tw.root(row, l), f) : f;
+  }
 }
 
 // MODE_NORMAL / MODE_RESID: rows through the pointwise chain and back; MODE_FORWARD:

@@ -24,8 +24,8 @@ struct LdArgs {
   const Col* col;
   const float2* pin;         // normal: (p_u, p_v) pairs, w = p_u - p_v
   float* yout;               // normal: A^T A w
-  const double* din;         // resid / forward: x
-  double* dout;              // resid: A^T (A x - b)
+  const float2* din;         // resid / forward: x, double-float (hi, lo)
+  float2* dout;              // resid: A^T (A x - b), double-float
   void* inter;               // R x L complex intermediate (double-float size)
   const uint8_t* mask;       // R x n sampled-row mask
   uint8_t* mcode;            // R x (N1/2) x (N2+1) mask bits per pass-B work item (ld_mask_codes)

@@ -29,7 +29,7 @@ namespace mfipm {
 namespace mr {
 
 constexpr int kT = 256;       // threads per block of the per-column passes
-constexpr int kIdx = 512;     // indices per block (2 per thread)
+constexpr int kIdx = 2048;    // indices per block (8 per thread)
 constexpr int kPart = 8;      // partial sums per (column, block)
 
 __device__ __forceinline__ float bf(const __nv_bfloat16 v) { return __bfloat162float(v); }
@@ -226,18 +226,14 @@ __global__ void k_rowpow(const __nv_bfloat16* __restrict__ Aop, int64_t lda, int
   if (lane == 0) pw[(int64_t)s * rows + r] = pow2_ceil(sqrtf(acc) * 1.0001f);
 }
 
-// X (float64, R x K) -> Xf = (hi, lo) float32 pairs, and cp[s * R + j] >= ||x_j[range s]||_2.
-// Block (s, j).
-__global__ void k_split_x(const double* __restrict__ X, float2* __restrict__ Xf, float* __restrict__ cp, int K,
-                          int R, int S) {
+// cp[s * R + j] >= ||x_j[range s]||_2 for the double-float X (R x K).  Block (s, j).
+__global__ void k_xbound(const float2* __restrict__ X, float* __restrict__ cp, int K, int R, int S) {
   const int s = blockIdx.x, j = blockIdx.y;
   int k0, k1;
   split_range(K, S, s, &k0, &k1);
   float acc = 0.f;
   for (int k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
-    const double v = X[(int64_t)j * K + k];
-    const float h = __double2float_rn(v);
-    Xf[(int64_t)j * K + k] = make_float2(h, __double2float_rn(v - (double)h));
+    const float h = X[(int64_t)j * K + k].x;
     acc = fmaf(h, h, acc);
   }
   __shared__ float red[32];
@@ -409,8 +405,9 @@ __global__ void k_fin1(const float2* __restrict__ Part, int S1, const double* __
   }
 }
 // Gr = scale * sum_s Part2 (float64)
-__global__ void k_fin2(const float2* __restrict__ Part, int S2, double scale, double* __restrict__ Gr, int n, int R) {
+__global__ void k_fin2(const float2* __restrict__ Part, int S2, double scale, float2* __restrict__ Gr, int n, int R) {
   const int64_t total = (int64_t)R * n;
+  const df sc = to_df(scale);
   for (int64_t gi = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; gi < total;
        gi += (int64_t)gridDim.x * blockDim.x) {
     df v(0.f);
@@ -418,7 +415,8 @@ __global__ void k_fin2(const float2* __restrict__ Part, int S2, double scale, do
       const float2 t = Part[(int64_t)s * total + gi];
       v = v + df(t.x, t.y);
     }
-    Gr[gi] = scale * to_double(v);
+    const df g = sc * v;
+    Gr[gi] = make_float2(g.hi, g.lo);
   }
 }
 
@@ -432,11 +430,11 @@ struct Dev {
   const __nv_bfloat16* A;          // m x n (lda)
   int64_t lda;
   const __nv_bfloat16* At;         // n x m
-  double* X;                       // R x n   residual input (x or trial x)
+  float2* X;                       // R x n   residual input (x or trial x), double-float
   double* Rr;                      // R x m   A x - b
-  double* Gr;                      // R x n   A^T (A x - b)
+  float2* Gr;                      // R x n   A^T (A x - b), double-float
   double* Bm;                      // R x m
-  double* zs;                      // R x n x 4 {u, v, s_u, s_v}
+  float4* zs;                      // R x n x 2 {u, v}, {s_u, s_v} as double-float pairs
   float2 *X1, *X2, *Rv, *Pv, *Dv;  // R x n each
   __nv_bfloat16* W;                // 2R x n
   __nv_bfloat16* Tb;               // 2R x m
@@ -465,8 +463,7 @@ __device__ __forceinline__ Steer steer(const Col& c, double sigma3, bool corr) {
 struct D2 {
   float dz, ds;
 };
-__device__ __forceinline__ D2 dirn(double zd, double sd, float dz1, float dz2, const Steer& c) {
-  const float z = (float)zd, s = (float)sd;
+__device__ __forceinline__ D2 dirn(float z, float s, float dz1, float dz2, const Steer& c) {
   const float rz = __frcp_rn(z), d = s * rz;
   const float ds1 = (c.smu * rz - s) - d * dz1;
   D2 r{dz1, ds1};
@@ -478,48 +475,78 @@ __device__ __forceinline__ D2 dirn(double zd, double sd, float dz1, float dz2, c
   return r;
 }
 
+// The iterate in double-float (about 48 significant bits on the float32 pipes; float64 runs
+// at 1/64 of the float32 rate on this part): per index {u, v} and {s_u, s_v} as (hi, lo)
+// pairs, 32 bytes.  x and the residual g are double-float too.
+struct St {
+  df u, v, su, sv;
+};
+__device__ __forceinline__ St load_st(const float4* zs, int64_t gi) {
+  const float4 a = zs[2 * gi], b = zs[2 * gi + 1];
+  return St{df(a.x, a.y), df(a.z, a.w), df(b.x, b.y), df(b.z, b.w)};
+}
+__device__ __forceinline__ void store_st(float4* zs, int64_t gi, const St& q) {
+  zs[2 * gi] = make_float4(q.u.hi, q.u.lo, q.v.hi, q.v.lo);
+  zs[2 * gi + 1] = make_float4(q.su.hi, q.su.lo, q.sv.hi, q.sv.lo);
+}
+__device__ __forceinline__ df axpy(df z, df a, float d) { return z + a * df(d); }
+__device__ __forceinline__ float2 f2(df a) { return make_float2(a.hi, a.lo); }
+__device__ __forceinline__ df d2(float2 a) { return df(a.x, a.y); }
+
 // iterate update (previous direction) and x = u - v; partials z.s, 1^T z, ||x||^2
 __global__ void k_update(Dev d, int first) {
   const int j = blockIdx.y, blk = blockIdx.x;
-  const Col c = d.col[j];
+  const Col& c = d.col[j];
+  const bool done = c.done, corr = c.corr;
+  const Steer sc = steer(c, d.prm.sigma3, corr);
+  const df ap = to_df(c.alpha_p), ad = to_df(c.alpha_d), keep = to_df(1.0 - d.prm.eta);
   float a[3] = {0.f, 0.f, 0.f};
   for (int i = blk * kIdx + threadIdx.x; i < min(d.n, (blk + 1) * kIdx); i += kT) {
     const int64_t gi = (int64_t)j * d.n + i;
-    double4 st;
-    double* zp = d.zs + 4 * gi;
+    St st;
     if (first) {
-      st = make_double4(1.0, 1.0, 1.0, 1.0);  // reading R3
+      st = St{df(1.f), df(1.f), df(1.f), df(1.f)};  // reading R3
     } else {
-      st = make_double4(zp[0], zp[1], zp[2], zp[3]);
-      if (!c.done) {
+      st = load_st(d.zs, gi);
+      if (!done) {
         const float2 x1 = d.X1[gi];
-        const float2 x2 = c.corr ? d.X2[gi] : make_float2(0.f, 0.f);
-        const Steer sc = steer(c, d.prm.sigma3, c.corr);
-        const D2 du = dirn(st.x, st.z, x1.x, x2.x, sc);
-        const D2 dv = dirn(st.y, st.w, x1.y, x2.y, sc);
-        double nu = fma(c.alpha_p, (double)du.dz, st.x), nv = fma(c.alpha_p, (double)dv.dz, st.y);
-        double nsu = fma(c.alpha_d, (double)du.ds, st.z), nsv = fma(c.alpha_d, (double)dv.ds, st.w);
-        const double keep = 1.0 - d.prm.eta;
-        if (!(nu > 0.0)) nu = st.x * keep;
-        if (!(nv > 0.0)) nv = st.y * keep;
-        if (!(nsu > 0.0)) nsu = st.z * keep;
-        if (!(nsv > 0.0)) nsv = st.w * keep;
-        st = make_double4(nu, nv, nsu, nsv);
+        const float2 x2 = corr ? d.X2[gi] : make_float2(0.f, 0.f);
+        const D2 du = dirn(st.u.hi, st.su.hi, x1.x, x2.x, sc);
+        const D2 dv = dirn(st.v.hi, st.sv.hi, x1.y, x2.y, sc);
+        const St o = st;
+        st.u = axpy(o.u, ap, du.dz);
+        st.v = axpy(o.v, ap, dv.dz);
+        st.su = axpy(o.su, ad, du.ds);
+        st.sv = axpy(o.sv, ad, dv.ds);
+        if (!(st.u.hi > 0.f)) st.u = o.u * keep;
+        if (!(st.v.hi > 0.f)) st.v = o.v * keep;
+        if (!(st.su.hi > 0.f)) st.su = o.su * keep;
+        if (!(st.sv.hi > 0.f)) st.sv = o.sv * keep;
       }
     }
-    zp[0] = st.x;
-    zp[1] = st.y;
-    zp[2] = st.z;
-    zp[3] = st.w;
-    const double x = st.x - st.y;
-    d.X[gi] = x;
+    store_st(d.zs, gi, st);
+    const df x = st.u - st.v;
+    d.X[gi] = f2(x);
     // float32 terms of positive sums (no cancellation), float64 across threads
-    a[0] += (float)st.x * (float)st.z + (float)st.y * (float)st.w;
-    a[1] += (float)(st.x + st.y);
-    a[2] += (float)x * (float)x;
+    a[0] += st.u.hi * st.su.hi + st.v.hi * st.sv.hi;
+    a[1] += st.u.hi + st.v.hi;
+    a[2] += x.hi * x.hi;
   }
   const double v[3] = {a[0], a[1], a[2]};
   block_partials<3>(v, d.part, j, d.nb, blk);
+}
+
+// sum of squares of a double-float vector, per block
+__global__ void k_colnorm2_df(const float2* __restrict__ V, int len, double* part, int nb) {
+  const int j = blockIdx.y, blk = blockIdx.x;
+  float a = 0.f;
+  const int per = (len + nb - 1) / nb;
+  for (int i = blk * per + threadIdx.x; i < min(len, (blk + 1) * per); i += kT) {
+    const float t = V[(int64_t)j * len + i].x;
+    a = fmaf(t, t, a);
+  }
+  const double v[1] = {a};
+  block_partials<1>(v, part, j, nb, blk);
 }
 
 __global__ void k_colnorm2(const double* __restrict__ V, int len, double* part, int nb) {
@@ -561,37 +588,38 @@ __global__ void k_stats(Dev d, int it, const double* part2) {
 // take a corrector.  Columns that are done (or take no corrector) get rhs = 0.
 __global__ void k_pcg_init(Dev d, int corr) {
   const int j = blockIdx.y, blk = blockIdx.x;
-  const Col c = d.col[j];
+  const Col& c = d.col[j];
   const bool live = !c.done && (!corr || c.corr_next);
   const Steer sc = steer(c, d.prm.sigma3, false);
+  const df tau = to_df(c.tau), ap1 = to_df(c.alpha_p1), ad1 = to_df(c.alpha_d1);
+  const float s3mu = (float)(d.prm.sigma3 * c.mu_t);
   double v[2] = {0, 0};
   for (int i = blk * kIdx + threadIdx.x; i < min(d.n, (blk + 1) * kIdx); i += kT) {
     const int64_t gi = (int64_t)j * d.n + i;
-    const double* zp = d.zs + 4 * gi;
-    const double u = zp[0], vv = zp[1], su = zp[2], sv = zp[3];
+    const St st = load_st(d.zs, gi);
     float2 dd;
     if (!corr) {
-      dd = make_float2(__fdiv_rn((float)su, (float)u), __fdiv_rn((float)sv, (float)vv));
+      dd = make_float2(__fdiv_rn(st.su.hi, st.u.hi), __fdiv_rn(st.sv.hi, st.v.hi));
       d.Dv[gi] = dd;
     } else {
       dd = d.Dv[gi];
     }
     float2 r = make_float2(0.f, 0.f);
     if (live) {
-      const double g = d.Gr[gi];
+      const df g = d2(d.Gr[gi]);
+      const df tpg = tau + g, tmg = tau - g;
       if (!corr) {
-        r.x = sc.smu * __frcp_rn((float)u) - (float)(c.tau + g);
-        r.y = sc.smu * __frcp_rn((float)vv) - (float)(c.tau - g);
+        r.x = sc.smu * __frcp_rn(st.u.hi) - tpg.hi;
+        r.y = sc.smu * __frcp_rn(st.v.hi) - tmg.hi;
       } else {
-        // f_z~ at the trial point in float64, Z^-1 f_s~ in float32
+        // f_z~ at the trial point in double-float, Z^-1 f_s~ in float32
         const float2 x1 = d.X1[gi];
-        const D2 du = dirn(u, su, x1.x, 0.f, sc);
-        const D2 dv = dirn(vv, sv, x1.y, 0.f, sc);
-        const double zu = fma(c.alpha_p1, (double)du.dz, u), zv = fma(c.alpha_p1, (double)dv.dz, vv);
-        const double tsu = fma(c.alpha_d1, (double)du.ds, su), tsv = fma(c.alpha_d1, (double)dv.ds, sv);
-        const float s3mu = (float)(d.prm.sigma3 * c.mu_t);
-        r.x = (float)(tsu - (c.tau + g)) + (s3mu - (float)zu * (float)tsu) * __frcp_rn((float)u);
-        r.y = (float)(tsv - (c.tau - g)) + (s3mu - (float)zv * (float)tsv) * __frcp_rn((float)vv);
+        const D2 du = dirn(st.u.hi, st.su.hi, x1.x, 0.f, sc);
+        const D2 dv = dirn(st.v.hi, st.sv.hi, x1.y, 0.f, sc);
+        const df zu = axpy(st.u, ap1, du.dz), zv = axpy(st.v, ap1, dv.dz);
+        const df tsu = axpy(st.su, ad1, du.ds), tsv = axpy(st.sv, ad1, dv.ds);
+        r.x = (tsu - tpg).hi + (s3mu - zu.hi * tsu.hi) * __frcp_rn(st.u.hi);
+        r.y = (tsv - tmg).hi + (s3mu - zv.hi * tsv.hi) * __frcp_rn(st.v.hi);
       }
     }
     const float2 p = precond2(dd, r, (float)c.rho);
@@ -647,7 +675,7 @@ __global__ void k_alpha(Dev d, int first, const double* part2) {
 
 __global__ void k_pcg_D(Dev d, float2* __restrict__ Xo, int first) {
   const int j = blockIdx.y, blk = blockIdx.x;
-  const Col c = d.col[j];
+  const Col& c = d.col[j];
   const float alpha = c.alpha, rho = (float)c.rho, sc = (float)d.a_scale;
   double v[1] = {0.0};
   for (int i = blk * kIdx + threadIdx.x; i < min(d.n, (blk + 1) * kIdx); i += kT) {
@@ -698,7 +726,7 @@ __global__ void k_beta(Dev d, int k) {
 
 __global__ void k_pcg_E(Dev d) {
   const int j = blockIdx.y, blk = blockIdx.x;
-  const Col c = d.col[j];
+  const Col& c = d.col[j];
   const float beta = c.beta, rho = (float)c.rho;
   double v[2] = {0, 0};
   for (int i = blk * kIdx + threadIdx.x; i < min(d.n, (blk + 1) * kIdx); i += kT) {
@@ -727,21 +755,21 @@ __global__ void k_pcg_E(Dev d) {
 // fraction-to-boundary ratios (reading R4)
 __global__ void k_steps(Dev d, int corr) {
   const int j = blockIdx.y, blk = blockIdx.x;
-  const Col c = d.col[j];
+  const Col& c = d.col[j];
   const Steer sc = steer(c, d.prm.sigma3, corr);
   float v[2] = {INFINITY, INFINITY};
   for (int i = blk * kIdx + threadIdx.x; i < min(d.n, (blk + 1) * kIdx); i += kT) {
     const int64_t gi = (int64_t)j * d.n + i;
-    const double* zp = d.zs + 4 * gi;
+    const St st = load_st(d.zs, gi);
     const float2 x1 = d.X1[gi];
     const float2 x2 = corr ? d.X2[gi] : make_float2(0.f, 0.f);
-    const D2 du = dirn(zp[0], zp[2], x1.x, x2.x, sc);
-    const D2 dv = dirn(zp[1], zp[3], x1.y, x2.y, sc);
+    const D2 du = dirn(st.u.hi, st.su.hi, x1.x, x2.x, sc);
+    const D2 dv = dirn(st.v.hi, st.sv.hi, x1.y, x2.y, sc);
     // ratios in float32: eta < 1 leaves a margin far above their rounding
-    if (du.dz < 0.f) v[0] = fminf(v[0], -(float)zp[0] * __frcp_rn(du.dz));
-    if (dv.dz < 0.f) v[0] = fminf(v[0], -(float)zp[1] * __frcp_rn(dv.dz));
-    if (du.ds < 0.f) v[1] = fminf(v[1], -(float)zp[2] * __frcp_rn(du.ds));
-    if (dv.ds < 0.f) v[1] = fminf(v[1], -(float)zp[3] * __frcp_rn(dv.ds));
+    if (du.dz < 0.f) v[0] = fminf(v[0], -st.u.hi * __frcp_rn(du.dz));
+    if (dv.dz < 0.f) v[0] = fminf(v[0], -st.v.hi * __frcp_rn(dv.dz));
+    if (du.ds < 0.f) v[1] = fminf(v[1], -st.su.hi * __frcp_rn(du.ds));
+    if (dv.ds < 0.f) v[1] = fminf(v[1], -st.sv.hi * __frcp_rn(dv.ds));
   }
   const double vd[2] = {v[0], v[1]};
   block_minima<2>(vd, d.part, j, d.nb, blk);
@@ -784,20 +812,22 @@ __global__ void k_steps_fin(Dev d, int corr) {
 // trial point x~ = z~_u - z~_v of the corrector columns; partial z~.s~
 __global__ void k_trial(Dev d) {
   const int j = blockIdx.y, blk = blockIdx.x;
-  const Col c = d.col[j];
+  const Col& c = d.col[j];
   const Steer sc = steer(c, d.prm.sigma3, false);
-  double v[1] = {0.0};
+  const df ap1 = to_df(c.alpha_p1), ad1 = to_df(c.alpha_d1);
+  float a = 0.f;
   for (int i = blk * kIdx + threadIdx.x; i < min(d.n, (blk + 1) * kIdx); i += kT) {
     const int64_t gi = (int64_t)j * d.n + i;
-    const double* zp = d.zs + 4 * gi;
+    const St st = load_st(d.zs, gi);
     const float2 x1 = d.X1[gi];
-    const D2 du = dirn(zp[0], zp[2], x1.x, 0.f, sc);
-    const D2 dv = dirn(zp[1], zp[3], x1.y, 0.f, sc);
-    const double zu = fma(c.alpha_p1, (double)du.dz, zp[0]), zv = fma(c.alpha_p1, (double)dv.dz, zp[1]);
-    const double su = fma(c.alpha_d1, (double)du.ds, zp[2]), sv = fma(c.alpha_d1, (double)dv.ds, zp[3]);
-    d.X[gi] = zu - zv;
-    v[0] += zu * su + zv * sv;
+    const D2 du = dirn(st.u.hi, st.su.hi, x1.x, 0.f, sc);
+    const D2 dv = dirn(st.v.hi, st.sv.hi, x1.y, 0.f, sc);
+    const df zu = axpy(st.u, ap1, du.dz), zv = axpy(st.v, ap1, dv.dz);
+    const df su = axpy(st.su, ad1, du.ds), sv = axpy(st.sv, ad1, dv.ds);
+    d.X[gi] = f2(zu - zv);
+    a += zu.hi * su.hi + zv.hi * sv.hi;
   }
+  const double v[1] = {a};
   block_partials<1>(v, d.part, j, d.nb, blk);
 }
 
@@ -835,10 +865,11 @@ __global__ void k_exit(Dev d, double* const* __restrict__ xout, double* const* _
   double v[3] = {0, 0, 0};
   for (int i = blk * kIdx + threadIdx.x; i < min(d.n, (blk + 1) * kIdx); i += kT) {
     const int64_t gi = (int64_t)j * d.n + i;
-    const double* zp = d.zs + 4 * gi;
-    const double g = d.Gr[gi];
+    const St q = load_st(d.zs, gi);
+    const double zp[4] = {to_double(q.u), to_double(q.v), to_double(q.su), to_double(q.sv)};
+    const double g = to_double(d2(d.Gr[gi]));
     const double fzu = zp[2] - (tau + g), fzv = zp[3] - (tau - g);
-    const double x = zp[0] - zp[1];
+    const double x = to_double(q.u - q.v);
     const double y = x - g;
     const double st = copysign(fmax(fabs(y) - tau, 0.0), y);
     v[0] += fzu * fzu + fzv * fzv;
@@ -896,7 +927,7 @@ size_t mrhs_workspace_bytes(int64_t m, int64_t n, int R) {
   b += al(256);                           // counters
   b += al((size_t)R * 8) * 3;             // taus, b / x / zs pointer arrays
   b += al(sizeof(void*) * R);
-  b += al((size_t)R * n * 8) + al((size_t)R * m * 8);                      // Xf, Rf
+  b += al((size_t)R * m * 8);                                              // Rf
   b += al((size_t)mr::kMaxRsplit * m * 4) + al((size_t)mr::kMaxRsplit * n * 4);  // row bounds
   b += al((size_t)mr::kMaxRsplit * R * 4) * 2;                             // column bounds
   return b;
@@ -960,7 +991,7 @@ int lockstep_run(mr::Dev& d, double* part2, const double* taus, const double* rh
   // setup: ||A^T b|| for ||c||
   if ((e = cudaMemsetAsync(d.X, 0, (size_t)R * d.n * 8, st))) return mr_fail(e, msg, "clear x");
   if ((e = residual(GATE_ALL))) return mr_fail(e, msg, "residual");
-  k_colnorm2<<<gIdx, kT, 0, st>>>(d.Gr, d.n, d.part, nb);
+  k_colnorm2_df<<<gIdx, kT, 0, st>>>(d.Gr, d.n, d.part, nb);
   ++g_nlaunch;
   k_setup_cols<<<R, kT, 0, st>>>(d, taus, rhos);
   ++g_nlaunch;
@@ -1035,11 +1066,11 @@ int mrhs_solve(const MrhsCall& call, std::string* msg) {
   auto take = [&](size_t bytes) { char* p = ws + o; o += al(bytes); return p; };
   __nv_bfloat16* At = reinterpret_cast<__nv_bfloat16*>(take((size_t)n * m * 2));
   d.At = At;
-  d.X = reinterpret_cast<double*>(take((size_t)R * n * 8));
-  d.Gr = reinterpret_cast<double*>(take((size_t)R * n * 8));
+  d.X = reinterpret_cast<float2*>(take((size_t)R * n * 8));
+  d.Gr = reinterpret_cast<float2*>(take((size_t)R * n * 8));
   d.Rr = reinterpret_cast<double*>(take((size_t)R * m * 8));
   d.Bm = reinterpret_cast<double*>(take((size_t)R * m * 8));
-  d.zs = reinterpret_cast<double*>(take((size_t)R * n * 32));
+  d.zs = reinterpret_cast<float4*>(take((size_t)R * n * 32));
   d.X1 = reinterpret_cast<float2*>(take((size_t)R * n * 8));
   d.X2 = reinterpret_cast<float2*>(take((size_t)R * n * 8));
   d.Rv = reinterpret_cast<float2*>(take((size_t)R * n * 8));
@@ -1059,7 +1090,6 @@ int mrhs_solve(const MrhsCall& call, std::string* msg) {
   const double** bptr = reinterpret_cast<const double**>(take((size_t)R * 8));
   double** xptr = reinterpret_cast<double**>(take((size_t)R * 8));
   double** zptr = reinterpret_cast<double**>(take(sizeof(void*) * R));
-  float2* Xf = reinterpret_cast<float2*>(take((size_t)R * n * 8));
   float2* Rf = reinterpret_cast<float2*>(take((size_t)R * m * 8));
   float* rp1 = reinterpret_cast<float*>(take((size_t)kMaxRsplit * m * 4));
   float* rp2 = reinterpret_cast<float*>(take((size_t)kMaxRsplit * n * 4));
@@ -1106,8 +1136,8 @@ int mrhs_solve(const MrhsCall& call, std::string* msg) {
 
   auto residual = [&]() -> cudaError_t {
     // Rr = a_scale A X - B ; Gr = a_scale A^T Rr
-    k_split_x<<<dim3(S1, R), 256, 0, st>>>(d.X, Xf, cp1, (int)n, R, S1);
-    resid_gemm<<<dim3((unsigned)((m + kRB - 1) / kRB), jt, S1), 256, 0, st>>>(d.A, d.lda, rp1, Xf, cp1, Part, (int)m,
+    k_xbound<<<dim3(S1, R), 256, 0, st>>>(d.X, cp1, (int)n, R, S1);
+    resid_gemm<<<dim3((unsigned)((m + kRB - 1) / kRB), jt, S1), 256, 0, st>>>(d.A, d.lda, rp1, d.X, cp1, Part, (int)m,
                                                                             R, (int)n, S1, vecA1);
     k_fin1<<<dim3(S2, R), 256, 0, st>>>(Part, S1, d.Bm, d.a_scale, d.Rr, Rf, cp2, (int)m, R, S2);
     resid_gemm<<<dim3((unsigned)((n + kRB - 1) / kRB), jt, S2), 256, 0, st>>>(At, m, rp2, Rf, cp2, Part, (int)n, R,
@@ -1135,7 +1165,7 @@ namespace mr {
 // the perturbed KKT system of Eq. fzfs at fixed mu): Theta^-1 = s / z, y0 = 0
 __global__ void k_bwd_init(Dev d, const double* const* __restrict__ zs_in, const double* const* __restrict__ gx) {
   const int j = blockIdx.y, blk = blockIdx.x;
-  const Col c = d.col[j];
+  const Col& c = d.col[j];
   const double* z = zs_in[j];
   double v[2] = {0, 0};
   for (int i = blk * kIdx + threadIdx.x; i < min(d.n, (blk + 1) * kIdx); i += kT) {
@@ -1167,7 +1197,8 @@ __global__ void k_bwd_w(Dev d) {
   for (int i = blk * kIdx + threadIdx.x; i < min(d.n, (blk + 1) * kIdx); i += kT) {
     const int64_t gi = (int64_t)j * d.n + i;
     const float2 y = d.X1[gi];
-    d.X[gi] = (double)y.x - (double)y.y;
+    const df w = df_two_sum(y.x, -y.y);  // exact
+    d.X[gi] = make_float2(w.hi, w.lo);
     v[0] += (double)y.x + (double)y.y;
   }
   block_partials<1>(v, d.part, j, d.nb, blk);
@@ -1180,7 +1211,7 @@ __global__ void k_bwd_out(Dev d, const int64_t* const* __restrict__ rows, const 
   double* gb = grad_b[j];
   if (gb)
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x)
-      gb[i] = d.Gr[(int64_t)j * d.n + rows[j][i]];
+      gb[i] = reinterpret_cast<const double*>(d.Gr)[(int64_t)j * d.n + rows[j][i]];
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     const Col& c = d.col[j];
     gtau[j] = -col_total(d.part, j, d.nb, 0);
@@ -1313,9 +1344,9 @@ int ld_setup(const LdCall& call, LdState& S, std::string* msg) {
   d.op = OP_LARGE_DCT;
   d.a_scale = 1.0;
   d.prm = call.prm;
-  d.X = reinterpret_cast<double*>(take(Rn * 8));
-  d.Gr = reinterpret_cast<double*>(take(Rn * 8));
-  d.zs = reinterpret_cast<double*>(take(Rn * 32));
+  d.X = reinterpret_cast<float2*>(take(Rn * 8));
+  d.Gr = reinterpret_cast<float2*>(take(Rn * 8));
+  d.zs = reinterpret_cast<float4*>(take(Rn * 32));
   d.X1 = reinterpret_cast<float2*>(take(Rn * 8));
   d.X2 = reinterpret_cast<float2*>(take(Rn * 8));
   d.Rv = reinterpret_cast<float2*>(take(Rn * 8));
@@ -1525,7 +1556,7 @@ int large_dct_backward(const LdCall& call, std::string* msg) {
   LdArgs a = S.base;
   a.gate = GATE_ALL;
   a.din = d.X;
-  a.fwd = d.Gr;
+  a.fwd = reinterpret_cast<double*>(d.Gr);  // the forward coefficients reuse Gr's memory
   if ((e = ld_forward(a, d.R, st))) return mr_fail(e, msg, "A w");
   g_nlaunch += 2;
   k_bwd_out<<<dim3(64, d.R), 256, 0, st>>>(d, S.rowsptr, S.ms, S.gbptr, S.gtau, S.infos_dev);
