@@ -192,14 +192,21 @@ int mfipm_backward(int32_t batch, const mfipm_operator* ops, const double* const
 /* Matrix-free products with the operator (the only way the solver touches A, Sec. 1):
  *   mfipm_apply_A:   y (DEVICE, m) = A x (x DEVICE, n)
  *   mfipm_apply_At:  x (DEVICE, n) = A^T y (y DEVICE, m)
- * float64 in and out.  `workspace` as for mfipm_solve with batch 1. */
+ * float64 in and out (input and output must not overlap).  Partial DCT with n >= 1024: the
+ * multi-pass FFT chain in double-float (about 2^-44 relative, Sec. 2's A = rows of the
+ * orthonormal DCT-II); n < 1024 and dense A: direct float64 sums.  `workspace`: DEVICE,
+ * 256-byte aligned, at least the bytes mfipm_workspace_size reports for this operator with
+ * batch 1 (a bf16 A: with precision MFIPM_PREC_BF16_A); the caller owns it.  Synchronises
+ * `stream`.  MFIPM_INVALID_ARG for NULL vectors, a small workspace or bad rows. */
 int mfipm_apply_A(const mfipm_operator* op, const double* x, double* y, void* workspace,
                   size_t ws_bytes, void* stream);
 int mfipm_apply_At(const mfipm_operator* op, const double* y, double* x, void* workspace,
                    size_t ws_bytes, void* stream);
 
-/* kkt_rel(x) = ||x - S_tau(x - A^T(Ax - b))||_2 / (1 + ||x||_2) in float64 for a candidate x
- * (DEVICE, n); result in *out (HOST).  Synchronises `stream`. */
+/* kkt_rel(x) = ||x - S_tau(x - A^T(Ax - b))||_2 / (1 + ||x||_2) (the l1 optimality residual:
+ * zero exactly at the minimiser of Eq. formulationsnoisy1's 1/2 form) for a candidate x
+ * (DEVICE, n) and b (DEVICE, m); result in *out (HOST).  Residual by the same arithmetic as
+ * mfipm_apply_A/At; workspace as there.  Synchronises `stream`. */
 int mfipm_kkt_residual(const mfipm_operator* op, const double* b, double tau, const double* x,
                        void* workspace, size_t ws_bytes, double* out, void* stream);
 

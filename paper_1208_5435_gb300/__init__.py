@@ -11,7 +11,8 @@ from typing import List, Optional, Sequence
 from . import _capi as C
 from ._capi import MfipmError, lib
 
-__all__ = ["Dense", "DenseBF16", "PartialDCT", "SolverParams", "solve", "solve_batched", "workspace_bytes", "MfipmError", "lib"]
+__all__ = ["Dense", "DenseBF16", "PartialDCT", "SolverParams", "solve", "solve_batched", "workspace_bytes",
+           "apply_A", "apply_At", "kkt_residual", "MfipmError", "lib"]
 
 
 def _torch():
@@ -213,3 +214,40 @@ def solve_differentiable(op, b, tau, params: Optional[SolverParams] = None):
     tau_t = tau if torch.is_tensor(tau) else torch.tensor(float(tau), dtype=torch.float64)
     A = op.A if isinstance(op, Dense) else None
     return MfipmFunction.apply(b, tau_t, A, op, params or SolverParams())
+
+
+def apply_A(op, x, ws=None, stream=None):
+    """y = A x (float64 CUDA tensors) through mfipm_apply_A."""
+    torch = _torch()
+    x = x.to(device="cuda", dtype=torch.float64).contiguous()
+    y = torch.empty(op.m, dtype=torch.float64, device="cuda")
+    ws = ws if ws is not None else _alloc_ws(workspace_bytes([op]))
+    cop = op.c_op()
+    C.check(lib().mfipm_apply_A(ctypes.byref(cop), x.data_ptr(), y.data_ptr(), ws.data_ptr(), ws.numel(),
+                                _stream_handle(stream)))
+    return y
+
+
+def apply_At(op, y, ws=None, stream=None):
+    """x = A^T y (float64 CUDA tensors) through mfipm_apply_At."""
+    torch = _torch()
+    y = y.to(device="cuda", dtype=torch.float64).contiguous()
+    x = torch.empty(op.n, dtype=torch.float64, device="cuda")
+    ws = ws if ws is not None else _alloc_ws(workspace_bytes([op]))
+    cop = op.c_op()
+    C.check(lib().mfipm_apply_At(ctypes.byref(cop), y.data_ptr(), x.data_ptr(), ws.data_ptr(), ws.numel(),
+                                 _stream_handle(stream)))
+    return x
+
+
+def kkt_residual(op, b, tau: float, x, ws=None, stream=None) -> float:
+    """kkt_rel(x) = ||x - S_tau(x - A^T(Ax - b))|| / (1 + ||x||) through mfipm_kkt_residual."""
+    torch = _torch()
+    b = b.to(device="cuda", dtype=torch.float64).contiguous()
+    x = x.to(device="cuda", dtype=torch.float64).contiguous()
+    ws = ws if ws is not None else _alloc_ws(workspace_bytes([op]))
+    out = ctypes.c_double(0.0)
+    cop = op.c_op()
+    C.check(lib().mfipm_kkt_residual(ctypes.byref(cop), b.data_ptr(), float(tau), x.data_ptr(), ws.data_ptr(),
+                                     ws.numel(), ctypes.byref(out), _stream_handle(stream)))
+    return float(out.value)

@@ -734,6 +734,19 @@ int backward_persistent(int32_t batch, const mfipm_operator* ops, const double* 
   return MFIPM_OK;
 }
 
+int apply_checked(int what, const mfipm_operator* op, const double* in, const double* b, double tau, double* out,
+                  double* kkt, void* workspace, size_t ws_bytes, void* stream) {
+  g_err.clear();
+  int rc = validate_op(op, 0);
+  if (rc) return rc;
+  if (!in || (what < 2 && !out) || (what == 2 && (!kkt || (op->m > 0 && !b))))
+    return fail(MFIPM_INVALID_ARG, "NULL vector argument");
+  if (what == 2 && !(tau > 0.0 && isfinite(tau))) return fail(MFIPM_INVALID_ARG, "tau must be positive and finite");
+  if (!workspace || ((uintptr_t)workspace & 255)) return fail(MFIPM_INVALID_ARG, "workspace NULL or not 256-byte aligned");
+  std::string msg;
+  rc = apply_operator(what, *op, in, b, tau, out, kkt, workspace, ws_bytes, static_cast<cudaStream_t>(stream), &msg);
+  return rc ? fail(rc, "%s", msg.c_str()) : MFIPM_OK;
+}
 }  // namespace
 
 extern "C" {
@@ -908,14 +921,18 @@ int mfipm_backward(int32_t batch, const mfipm_operator* ops, const double* const
                           static_cast<cudaStream_t>(stream));
 }
 
-int mfipm_apply_A(const mfipm_operator*, const double*, double*, void*, size_t, void*) {
-  return fail(MFIPM_UNSUPPORTED, "mfipm_apply_A is not built yet");
+
+int mfipm_apply_A(const mfipm_operator* op, const double* x, double* y, void* workspace, size_t ws_bytes,
+                  void* stream) {
+  return apply_checked(0, op, x, nullptr, 0.0, y, nullptr, workspace, ws_bytes, stream);
 }
-int mfipm_apply_At(const mfipm_operator*, const double*, double*, void*, size_t, void*) {
-  return fail(MFIPM_UNSUPPORTED, "mfipm_apply_At is not built yet");
+int mfipm_apply_At(const mfipm_operator* op, const double* y, double* x, void* workspace, size_t ws_bytes,
+                   void* stream) {
+  return apply_checked(1, op, y, nullptr, 0.0, x, nullptr, workspace, ws_bytes, stream);
 }
-int mfipm_kkt_residual(const mfipm_operator*, const double*, double, const double*, void*, size_t, double*, void*) {
-  return fail(MFIPM_UNSUPPORTED, "mfipm_kkt_residual is not built yet");
+int mfipm_kkt_residual(const mfipm_operator* op, const double* b, double tau, const double* x, void* workspace,
+                       size_t ws_bytes, double* out, void* stream) {
+  return apply_checked(2, op, x, b, tau, nullptr, out, workspace, ws_bytes, stream);
 }
 
 const char* mfipm_last_error(void) { return g_err.c_str(); }

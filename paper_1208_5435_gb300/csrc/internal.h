@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <string>
+
 #include "../../include/mfipm.h"
 
 namespace mfipm {
@@ -67,6 +69,12 @@ struct KernelArgs {
 // Launchers implemented in solver.cu.  Return cudaError_t of the launch.
 cudaError_t launch_twiddles(double2* tw64, float2* tw32, float4* twdf, int log2_tw, cudaStream_t st);
 cudaError_t launch_dct_setup(const ProbDesc* probs_dev, int batch, int64_t max_n, int* err, cudaStream_t st);
+
+// Products with A and the KKT residual of a candidate x (apply.cu): what = 0: out = A in,
+// 1: out = A^T in, 2: *kkt = kkt_rel(in) for (b, tau).  Synchronises st.
+size_t apply_workspace_bytes(const mfipm_operator& op);
+int apply_operator(int what, const mfipm_operator& op, const double* in, const double* b, double tau, double* out,
+                   double* kkt, void* workspace, size_t ws_bytes, cudaStream_t st, std::string* msg);
 cudaError_t launch_dct_solver_df(int G, const KernelArgs& a, int64_t max_n, int grid_clusters, cudaStream_t st);
 cudaError_t launch_dct_solver_f64(int G, const KernelArgs& a, int64_t max_n, int grid_clusters, cudaStream_t st);
 cudaError_t launch_dense_solver(int G, bool fp64_pcg, const KernelArgs& a, int64_t max_n, int64_t max_m,

@@ -42,7 +42,7 @@ __global__ void dct_scatter_kernel(const ProbDesc* probs, int batch, int* err) {
       atomicCAS(err, 0, -1);  // invalid rows: reported by the host as MFIPM_INVALID_ARG
       continue;
     }
-    const double bi = pd.b[i];
+    const double bi = pd.b ? pd.b[i] : 0.0;  // no b: the mask alone
     if (!isfinite(bi)) atomicCAS(err, 0, -2);
     pd.mask[r] = 1;
     const double v = bi * (r == 0 ? sc0 : scj);

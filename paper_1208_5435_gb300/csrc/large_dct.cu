@@ -31,8 +31,12 @@
 namespace mfipm {
 namespace ld {
 
-constexpr int kCols = 16;     // columns per pass A / pass C block (8 + their 8 mirrors)
-constexpr int kThr = 512;     // threads per block
+// columns per pass A / pass C block (half of them and their mirrors): 16 for float32,
+// 8 for double-float (keeps three blocks' shared memory on an SM)
+template <class C> struct ColsOf { static constexpr int v = 16; };
+template <> struct ColsOf<dfc> { static constexpr int v = 8; };
+constexpr int kThr = 512;     // threads per pass A / pass C block
+constexpr int kThrB = 256;    // threads per pass B block
 
 __device__ __forceinline__ bool gated_out(const LdArgs& a, int j) {
   if (a.gate == GATE_ACTIVE) return !a.col[j].active;
@@ -140,11 +144,17 @@ template <> struct Io<dfc> {
   static __device__ __forceinline__ dfc* inter(const LdArgs& a) { return reinterpret_cast<dfc*>(a.inter); }
 };
 
-// column t2 of slot ci (0..7: 8 c + ci; 8..15: the mirrors N2 - 16 - 8 c + ci)
-__device__ __forceinline__ int col_of(int ci, int cb, int N2) { return ci < 8 ? 8 * cb + ci : N2 - 16 - 8 * cb + ci; }
+// column t2 of slot ci of block cb (K columns: h = K/2 slots h cb + ci, then their mirrors
+// N2 - 2h - h cb + ci; slot ci and slot K - 1 - ci hold mirror columns t2 and N2 - 1 - t2)
+template <int K>
+__device__ __forceinline__ int col_of(int ci, int cb, int N2) {
+  constexpr int h = K / 2;
+  return ci < h ? h * cb + ci : N2 - 2 * h - h * cb + ci;
+}
 
 template <class C>
 __global__ void __launch_bounds__(kThr) pass_a(LdArgs a) {
+  constexpr int kCols = ColsOf<C>::v, kLog = kCols == 16 ? 4 : 3;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* buf = reinterpret_cast<C*>(smem_raw);
   const int j = blockIdx.y, cb = blockIdx.x;
@@ -153,10 +163,11 @@ __global__ void __launch_bounds__(kThr) pass_a(LdArgs a) {
   const int64_t n = (int64_t)1 << a.logN, L = n >> 1, base = (int64_t)j * n;
   using IO = Io<C>;
   // pack: t = N2 t1 + t2 (t1 < N1/2) takes w[4t], w[4t+2]; its mirror L-1-t (row N1-1-t1,
-  // slot 15-ci) takes w[4t+3], w[4t+1]
+  // slot kCols-1-ci) takes w[4t+3], w[4t+1]
+#pragma unroll 4
   for (int e = threadIdx.x; e < kCols * (N1 >> 1); e += blockDim.x) {
-    const int ci = e & (kCols - 1), t1 = e >> 4;
-    const int64_t t = (int64_t)t1 * N2 + col_of(ci, cb, N2);
+    const int ci = e & (kCols - 1), t1 = e >> kLog;
+    const int64_t t = (int64_t)t1 * N2 + col_of<kCols>(ci, cb, N2);
     const int64_t gi = base + 4 * t;
     const auto w0 = IO::load(a, gi), w1 = IO::load(a, gi + 1), w2 = IO::load(a, gi + 2), w3 = IO::load(a, gi + 3);
     buf[ci * stride + t1] = mk(w0, w2);
@@ -166,8 +177,9 @@ __global__ void __launch_bounds__(kThr) pass_a(LdArgs a) {
   const Twiddle<C> tw = IO::tw(a);
   cols_fft_dif<C>(buf, a.logN1, kCols, stride, tw);
   C* Y = IO::inter(a) + (int64_t)j * L;
+#pragma unroll 4
   for (int e = threadIdx.x; e < kCols * N1; e += blockDim.x) {
-    const int ci = e & (kCols - 1), k1 = e >> 4, t2 = col_of(ci, cb, N2);
+    const int ci = e & (kCols - 1), k1 = e >> kLog, t2 = col_of<kCols>(ci, cb, N2);
     const C v = buf[ci * stride + bitrev(k1, a.logN1)];
     Y[(int64_t)k1 * N2 + t2] = cmul(v, tw.root((int64_t)t2 * k1, a.logL));
   }
@@ -248,10 +260,10 @@ __device__ __forceinline__ C tw_rowcol(const Twiddle<C>& tw, int row, int k2, in
 // MODE_NORMAL / MODE_RESID: rows through the pointwise chain and back; MODE_FORWARD:
 // alpha_j X_j of the forward transform into fwd (float64, natural order).
 template <class C, int MODE>
-__global__ void __launch_bounds__(kThr) pass_b(LdArgs a) {
+__global__ void __launch_bounds__(kThrB) pass_b(LdArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* buf = reinterpret_cast<C*>(smem_raw);
-  __shared__ double red[kThr / 32];
+  __shared__ double red[kThrB / 32];
   const int j = blockIdx.y, rb = blockIdx.x;
   if (gated_out(a, j)) return;
   using IO = Io<C>;
@@ -260,6 +272,7 @@ __global__ void __launch_bounds__(kThr) pass_b(LdArgs a) {
   const int64_t n = (int64_t)1 << a.logN, L = n >> 1;
   const int rA = rb, rB = rb == 0 ? (N1 >> 1) : N1 - rb;
   C* Y = IO::inter(a) + (int64_t)j * L;
+#pragma unroll 4
   for (int e = threadIdx.x; e < 2 * N2; e += blockDim.x) {
     const int row = e >= N2, t2 = e & (N2 - 1);
     buf[row * stride + t2] = Y[(int64_t)(row ? rB : rA) * N2 + t2];
@@ -317,6 +330,7 @@ __global__ void __launch_bounds__(kThr) pass_b(LdArgs a) {
 
 template <class C>
 __global__ void __launch_bounds__(kThr) pass_c(LdArgs a) {
+  constexpr int kCols = ColsOf<C>::v, kLog = kCols == 16 ? 4 : 3;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* buf = reinterpret_cast<C*>(smem_raw);
   const int j = blockIdx.y, cb = blockIdx.x;
@@ -326,16 +340,17 @@ __global__ void __launch_bounds__(kThr) pass_c(LdArgs a) {
   const int64_t n = (int64_t)1 << a.logN, L = n >> 1, base = (int64_t)j * n;
   const Twiddle<C> tw = IO::tw(a);
   const C* Y = IO::inter(a) + (int64_t)j * L;
+#pragma unroll 4
   for (int e = threadIdx.x; e < kCols * N1; e += blockDim.x) {
-    const int ci = e & (kCols - 1), k1 = e >> 4, t2 = col_of(ci, cb, N2);
+    const int ci = e & (kCols - 1), k1 = e >> kLog, t2 = col_of<kCols>(ci, cb, N2);
     const C v = Y[(int64_t)k1 * N2 + t2];
     buf[ci * stride + bitrev(k1, a.logN1)] = cmulc(v, tw.root((int64_t)t2 * k1, a.logL));
   }
   __syncthreads();
   cols_fft_dit_inv<C>(buf, a.logN1, kCols, stride, tw);
   for (int e = threadIdx.x; e < kCols * (N1 >> 1); e += blockDim.x) {
-    const int ci = e & (kCols - 1), t1 = e >> 4;
-    const int64_t t = (int64_t)t1 * N2 + col_of(ci, cb, N2);
+    const int ci = e & (kCols - 1), t1 = e >> kLog;
+    const int64_t t = (int64_t)t1 * N2 + col_of<kCols>(ci, cb, N2);
     const C h = buf[ci * stride + t1], hm = buf[(kCols - 1 - ci) * stride + (N1 - 1 - t1)];
     IO::store4(a, base + 4 * t, h.x, hm.y, h.y, hm.x);
   }
@@ -356,23 +371,31 @@ LdShape ld_shape(int64_t n) {
 }
 bool ld_supported(int64_t n) { return n >= kLdMinN && n <= kLdMaxN && (n & (n - 1)) == 0; }
 
-static size_t smem_cols(int logN1, size_t elem) { return (size_t)ld::kCols * (((size_t)1 << logN1) + 1) * elem; }
+template <class C> static size_t smem_cols(int logN1) {
+  return (size_t)ld::ColsOf<C>::v * (((size_t)1 << logN1) + 1) * sizeof(C);
+}
 static size_t smem_rows(int logN2, size_t elem) { return (size_t)2 * (((size_t)1 << logN2) + 1) * elem; }
 
-template <class C>
-static cudaError_t launch_cols(void (*k)(LdArgs), const LdArgs& a, int R, cudaStream_t st) {
-  const size_t sm = smem_cols(a.logN1, sizeof(C));
+// shared memory size and the largest carveout, so that several blocks share an SM
+static cudaError_t prep_kernel(void (*k)(LdArgs), size_t sm) {
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
-  k<<<dim3((1u << a.logN2) / ld::kCols, R), ld::kThr, sm, st>>>(a);
+  return cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+}
+template <class C>
+static cudaError_t launch_cols(void (*k)(LdArgs), const LdArgs& a, int R, cudaStream_t st) {
+  const size_t sm = smem_cols<C>(a.logN1);
+  cudaError_t e = prep_kernel(k, sm);
+  if (e != cudaSuccess) return e;
+  k<<<dim3((1u << a.logN2) / ld::ColsOf<C>::v, R), ld::kThr, sm, st>>>(a);
   return cudaGetLastError();
 }
 template <class C>
 static cudaError_t launch_rows(void (*k)(LdArgs), const LdArgs& a, int R, cudaStream_t st) {
   const size_t sm = smem_rows(a.logN2, sizeof(C));
-  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  cudaError_t e = prep_kernel(k, sm);
   if (e != cudaSuccess) return e;
-  k<<<dim3((1u << a.logN1) / 2, R), ld::kThr, sm, st>>>(a);
+  k<<<dim3((1u << a.logN1) / 2, R), ld::kThrB, sm, st>>>(a);
   return cudaGetLastError();
 }
 

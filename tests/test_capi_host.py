@@ -147,3 +147,31 @@ def test_large_dct_rejected_before_launch(L, case):
                            None, ws, wsb, ctypes.byref(info), None)
     assert rc in (C.MFIPM_INVALID_ARG, C.MFIPM_UNSUPPORTED), (case, rc)
     assert L.mfipm_last_error() and len(L.mfipm_last_error()) > 5
+
+
+@pytest.mark.parametrize("fn", ["apply_A", "apply_At", "kkt"])
+@pytest.mark.parametrize("case", ["null_vec", "small_ws", "null_ws", "bad_tau"])
+def test_operator_products_rejected_before_launch(L, fn, case):
+    from paper_1208_5435_gb300 import _capi as C
+    op = _dct_op(C, 4096, 1024)
+    vin, vout = ctypes.c_void_p(0x3000), ctypes.c_void_p(0x4000)
+    ws, wsb, tau = ctypes.c_void_p(0x10000), 1 << 40, 0.1
+    if case == "null_vec":
+        vin = None
+    elif case == "small_ws":
+        wsb = 4096
+    elif case == "null_ws":
+        ws = None
+    elif case == "bad_tau":
+        if fn != "kkt":
+            pytest.skip("tau only enters the KKT residual")
+        tau = -1.0
+    if fn == "apply_A":
+        rc = L.mfipm_apply_A(ctypes.byref(op), vin, vout, ws, wsb, None)
+    elif fn == "apply_At":
+        rc = L.mfipm_apply_At(ctypes.byref(op), vin, vout, ws, wsb, None)
+    else:
+        out = ctypes.c_double()
+        rc = L.mfipm_kkt_residual(ctypes.byref(op), ctypes.c_void_p(0x5000), tau, vin, ws, wsb, ctypes.byref(out), None)
+    assert rc == C.MFIPM_INVALID_ARG, (fn, case, rc)
+    assert len(L.mfipm_last_error()) > 5
