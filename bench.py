@@ -251,6 +251,8 @@ def run_ours(args, rank, world, local_rank):
     def step():
         return M.solve_batched(ops, bs, taus, params, ws=ws)
 
+    # the autotuner picks the cluster size and the single-CTA limit on this batch (untimed)
+    tuning = M.autotune(ops, bs, taus, params, ws=ws)[2]
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
@@ -345,7 +347,10 @@ def run_ours(args, rank, world, local_rank):
         "vs_baseline": None, "dtype": "f32 PCG / f64 IPM", "data": "synthetic",
         "config": {"workload": args.workload, "problems": len(probs), "sum_n": int(sum(p.n for p in probs)),
                    "tol": params.tol, "tol_pcg": params.tol_pcg, "l2": "flushed (512 MiB write) before each step",
-                   "solved_at_kkt_1e-6": ok},
+                   "solved_at_kkt_1e-6": ok,
+                   "tuned": {"cluster_size": tuning["cluster_size"], "cta_max_n": tuning["cta_max_n"],
+                             "candidates": tuning["candidates"], "best_ms": tuning["best_ms"],
+                             "default_ms": tuning["default_ms"]}},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
                      "kernel": "ipm_kernel (persistent, one cluster per problem)", "kernel_ms": kms,
@@ -382,6 +387,7 @@ def run_bf16(args, rank, world, local_rank, probs):
     ws = torch.empty(M.workspace_bytes(ops, params), dtype=torch.uint8, device=dev)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
+    tuning = M.autotune(ops, bs, taus, params, ws=ws)[2]  # split-K of the two GEMMs (untimed)
     for _ in range(args.warmup):
         M.solve_batched(ops, bs, taus, params, ws=ws)
     torch.cuda.synchronize()
@@ -403,12 +409,13 @@ def run_bf16(args, rank, world, local_rank, probs):
     W_ = torch.randn(2 * R, n, device=dev).to(torch.bfloat16)
     T_ = torch.randn(2 * R, m, device=dev).to(torch.bfloat16)
     At = bits.T.contiguous()
-    C1 = torch.empty(4, 2 * R, m, device=dev)
-    C2 = torch.empty(1, 2 * R, n, device=dev)
+    s1, s2 = max(1, tuning["splits1"]), max(1, tuning["splits2"])  # the split-K the solve uses
+    C1 = torch.empty(s1, 2 * R, m, device=dev)
+    C2 = torch.empty(s2, 2 * R, n, device=dev)
     sh = ctypes.c_void_p(stream.cuda_stream)
     def gemm_pair():
-        assert L.mfipm_gemm_bf16(bits.data_ptr(), W_.data_ptr(), C1.data_ptr(), m, 2 * R, n, 4, 1, sh) == 0
-        assert L.mfipm_gemm_bf16(At.data_ptr(), T_.data_ptr(), C2.data_ptr(), n, 2 * R, m, 1, 1, sh) == 0
+        assert L.mfipm_gemm_bf16(bits.data_ptr(), W_.data_ptr(), C1.data_ptr(), m, 2 * R, n, s1, 1, sh) == 0
+        assert L.mfipm_gemm_bf16(At.data_ptr(), T_.data_ptr(), C2.data_ptr(), n, 2 * R, m, s2, 1, sh) == 0
     for _ in range(3):
         gemm_pair()
     reps = 20
@@ -422,7 +429,7 @@ def run_bf16(args, rank, world, local_rank, probs):
         torch.cuda.synchronize()
         g_ms.append(e0.elapsed_time(e1))
     gms = statistics.median(g_ms)
-    gbytes = 2 * (m * n * 2) + 2 * R * (n + m) * 2 + (4 * 2 * R * m + 2 * R * n) * 4
+    gbytes = 2 * (m * n * 2) + 2 * R * (n + m) * 2 + (s1 * 2 * R * m + s2 * 2 * R * n) * 4
     gflop = 2 * 2 * m * n * 2 * R
     peak, peak_kind = measured_peaks()
     if rank != 0:
@@ -441,7 +448,9 @@ def run_bf16(args, rank, world, local_rank, probs):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "bf16 A / f32 PCG / f64 IPM", "data": "synthetic",
         "config": {"workload": args.workload, "m": m, "n": n, "rhs": R, "l2": "flushed (512 MiB write) before each step",
-                   "solved_at_kkt_1e-6": ok},
+                   "solved_at_kkt_1e-6": ok,
+                   "tuned": {"splits1": tuning["splits1"], "splits2": tuning["splits2"],
+                             "best_ms": tuning["best_ms"], "default_ms": tuning["default_ms"]}},
         "roofline": {"bound": "hbm", "achieved": gbytes / (gms / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
                      "frac": gbytes / (gms / 1e3) / 1e9 / peak, "traffic": None, "peak_kind": peak_kind,
                      "kernel": "tc_gemm_kernel pair (T = A W, Y = A^T T), timed alone", "kernel_ms": gms,

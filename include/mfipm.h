@@ -243,6 +243,32 @@ int mfipm_set_gemm_mode(int32_t tensor_cores);
  * the multi-pass path at sizes the oracle reaches.  MFIPM_INVALID_ARG below 1024. */
 int mfipm_set_large_dct_threshold(int64_t n);
 
+/* Autotuner (not in the paper): times candidate decompositions on the caller's actual batch
+ * and keeps the fastest, process-wide, for later calls with cluster_size = 0:
+ *   path 1, partial DCT on the persistent kernel: the cluster size G (the radix of the FFT's
+ *     distributed exchange step; every G that fits the batch's n) and the largest n a single
+ *     CTA solves alone (2048 .. 16384), keyed by the batch's largest n and ceil(log2 batch);
+ *     each candidate is timed by the solver kernel's CUDA events over the real solve;
+ *   path 2, shared bf16 A (MFIPM_PREC_BF16_A): the split-K counts of the two tcgen05 GEMMs
+ *     of the PCG product, each timed alone on its real shapes, keyed by (m, n, batch).
+ * Other batches are solved without tuning (path 0).  Arguments as for mfipm_solve_batched;
+ * x and infos receive a solve with the chosen configuration.  *tuning (HOST, nullable):
+ * the choice, the number of timed candidates, and the device times (ms) of the best and of
+ * the default configuration. */
+typedef struct {
+  int32_t path;
+  int32_t candidates;
+  int32_t cluster_size;     /* path 1 */
+  int32_t splits1, splits2; /* path 2 */
+  int64_t cta_max_n;        /* path 1 */
+  double best_ms, default_ms;
+} mfipm_tuning;
+int mfipm_autotune(int32_t batch, const mfipm_operator* ops, const double* const* b,
+                   const double* tau, const mfipm_params* p, double* const* x, void* workspace,
+                   size_t ws_bytes, mfipm_info* infos, mfipm_tuning* tuning, void* stream);
+/* Forget every tuned configuration of this process. */
+int mfipm_clear_tuning(void);
+
 /* Message of the last failing call on this thread ("" if none). */
 const char* mfipm_last_error(void);
 

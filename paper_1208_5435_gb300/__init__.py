@@ -12,7 +12,7 @@ from . import _capi as C
 from ._capi import MfipmError, lib
 
 __all__ = ["Dense", "DenseBF16", "PartialDCT", "SolverParams", "solve", "solve_batched", "workspace_bytes",
-           "apply_A", "apply_At", "kkt_residual", "MfipmError", "lib"]
+           "apply_A", "apply_At", "kkt_residual", "autotune", "clear_tuning", "MfipmError", "lib"]
 
 
 def _torch():
@@ -251,3 +251,29 @@ def kkt_residual(op, b, tau: float, x, ws=None, stream=None) -> float:
     C.check(lib().mfipm_kkt_residual(ctypes.byref(cop), b.data_ptr(), float(tau), x.data_ptr(), ws.data_ptr(),
                                      ws.numel(), ctypes.byref(out), _stream_handle(stream)))
     return float(out.value)
+
+
+def autotune(ops: Sequence, bs: Sequence, taus: Sequence[float], params: Optional[SolverParams] = None, ws=None,
+             stream=None):
+    """mfipm_autotune: time the candidate decompositions on this batch and keep the fastest for
+    later solves of this process.  Returns (xs, infos, tuning dict)."""
+    torch = _torch()
+    params = params or SolverParams()
+    B = len(ops)
+    bs = [bb.to(device="cuda", dtype=torch.float64).contiguous() for bb in bs]
+    xs = [torch.empty(o.n, dtype=torch.float64, device="cuda") for o in ops]
+    arr = (C.Operator * B)(*[o.c_op() for o in ops])
+    bp = (ctypes.c_void_p * B)(*[bb.data_ptr() for bb in bs])
+    xp = (ctypes.c_void_p * B)(*[xx.data_ptr() for xx in xs])
+    tp = (ctypes.c_double * B)(*[float(t) for t in taus])
+    p = params.to_c(ops[0].default_precision)
+    ws = ws if ws is not None else _alloc_ws(workspace_bytes(ops, params))
+    infos = (C.Info * B)()
+    tun = C.Tuning()
+    C.check(lib().mfipm_autotune(B, arr, bp, tp, ctypes.byref(p), xp, ws.data_ptr(), ws.numel(), infos,
+                                 ctypes.byref(tun), _stream_handle(stream)), allow=(C.MFIPM_OK, C.MFIPM_NOT_CONVERGED))
+    return xs, [i.as_dict() for i in infos], tun.as_dict()
+
+
+def clear_tuning():
+    C.check(lib().mfipm_clear_tuning())

@@ -40,6 +40,15 @@ class Info(ctypes.Structure):
         return d
 
 
+class Tuning(ctypes.Structure):
+    _fields_ = [("path", ctypes.c_int32), ("candidates", ctypes.c_int32), ("cluster_size", ctypes.c_int32),
+                ("splits1", ctypes.c_int32), ("splits2", ctypes.c_int32), ("cta_max_n", ctypes.c_int64),
+                ("best_ms", ctypes.c_double), ("default_ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
 # Every function the header declares, with its ctypes signature.
 _P = ctypes.c_void_p
 _PP = ctypes.POINTER(ctypes.c_void_p)
@@ -66,6 +75,10 @@ SIGNATURES = {
                                        ctypes.c_int32, _P]),
     "mfipm_set_gemm_mode": (ctypes.c_int, [ctypes.c_int32]),
     "mfipm_set_large_dct_threshold": (ctypes.c_int, [ctypes.c_int64]),
+    "mfipm_autotune": (ctypes.c_int, [ctypes.c_int32, ctypes.POINTER(Operator), _PP, ctypes.POINTER(ctypes.c_double),
+                                      ctypes.POINTER(Params), _PP, _P, ctypes.c_size_t, ctypes.POINTER(Info),
+                                      ctypes.POINTER(Tuning), _P]),
+    "mfipm_clear_tuning": (ctypes.c_int, []),
     "mfipm_last_operator_stats": (ctypes.c_int, [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                                                  ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
     "mfipm_set_timing": (ctypes.c_int, [ctypes.c_int32]),

@@ -7,7 +7,9 @@
 #include <string.h>
 
 #include <algorithm>
+#include <map>
 #include <mutex>
+#include <tuple>
 #include <numeric>
 #include <string>
 #include <vector>
@@ -25,6 +27,25 @@ thread_local std::string g_err;
 
 // Plain CUDA-core GEMM instead of tcgen05 in the bf16 solver (mfipm_set_gemm_mode; for tests).
 bool g_force_simple_gemm = false;
+
+// Autotuner results (mfipm_autotune), process-wide.  Persistent partial-DCT kernel: keyed by
+// the batch's largest n and ceil(log2 batch) -> cluster size G and the largest n solved by a
+// single CTA.  Shared bf16 A: keyed by (m, n, right-hand sides) -> split-K of the two GEMMs.
+struct TuneDct {
+  int G;
+  int64_t cta_max_n;
+};
+struct TuneGemm {
+  int s1, s2;
+};
+std::mutex g_tune_mu;
+std::map<std::pair<int64_t, int>, TuneDct> g_tune_dct;
+std::map<std::tuple<int64_t, int64_t, int>, TuneGemm> g_tune_gemm;
+int ceil_log2i(int64_t v) {
+  int l = 0;
+  while (((int64_t)1 << l) < v) ++l;
+  return l;
+}
 
 // Optional timing of the solver kernel (mfipm_set_timing / mfipm_last_kernel_ms).
 thread_local bool g_timing = false;
@@ -236,6 +257,7 @@ struct Prepared {
   int G;
   bool dct, pcg64;
   int64_t max_n, max_m;
+  int64_t cta_max_n = 0;  // > 0: largest n solved by a single CTA (tuned), else the default rule
   char* ws;
 };
 
@@ -280,6 +302,18 @@ int prepare(int batch, const mfipm_operator* ops, const double* const* b, const 
     P.max_m = std::max<int64_t>(P.max_m, o.m);
   }
   P.G = pick_G(vops, p, batch);
+  if (P.dct && p->cluster_size == 0) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune_dct.find({P.max_n, ceil_log2i(batch)});
+    if (it != g_tune_dct.end()) {
+      int64_t min_n = INT64_MAX;
+      for (auto& o : vops) min_n = std::min<int64_t>(min_n, o.n);
+      if (it->second.G >= dct_min_G(P.max_n) && it->second.G <= dct_max_G(min_n)) {
+        P.G = it->second.G;
+        P.cta_max_n = it->second.cta_max_n;
+      }
+    }
+  }
   if (P.dct) {
     int64_t min_n = INT64_MAX;
     for (auto& o : vops) min_n = std::min<int64_t>(min_n, o.n);
@@ -371,7 +405,8 @@ int run(Prepared& P, cudaStream_t st, int batch, mfipm_info* infos, const std::v
   if (P.G == 1) {
     nbig = 0;
   } else if (P.dct) {
-    const int64_t small_max = std::min<int64_t>(16384, P.max_n / P.G);
+    int64_t small_max = std::min<int64_t>(16384, P.max_n / P.G);  // shared memory of one CTA
+    if (P.cta_max_n > 0) small_max = std::min<int64_t>(small_max, P.cta_max_n);
     nbig = 0;
     for (int i = 0; i < batch; ++i) nbig += sorted[i].n > small_max;
   }
@@ -571,6 +606,12 @@ int solve_shared_bf16(int batch, const mfipm_operator* ops, const double* const*
     call.gemm_ctx = err_dev;
     call.splits1 = std::min(kMaxSplits, tc_gemm_splits(m32, n32, sms));
     call.splits2 = std::min(kMaxSplits, tc_gemm_splits(n32, m32, sms));
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune_gemm.find({ops[0].m, ops[0].n, batch});
+    if (it != g_tune_gemm.end()) {
+      call.splits1 = it->second.s1;
+      call.splits2 = it->second.s2;
+    }
   } else {
     call.gemm = gemm_simple;
     call.gemm_ctx = nullptr;
@@ -746,6 +787,148 @@ int apply_checked(int what, const mfipm_operator* op, const double* in, const do
   std::string msg;
   rc = apply_operator(what, *op, in, b, tau, out, kkt, workspace, ws_bytes, static_cast<cudaStream_t>(stream), &msg);
   return rc ? fail(rc, "%s", msg.c_str()) : MFIPM_OK;
+}
+
+// ------------------------------------------------------------------ autotuner
+// Persistent partial-DCT kernel: every (G, single-CTA limit) that fits the batch, timed by the
+// solver kernel's CUDA events on the caller's problems (second of two runs).
+int tune_dct(int batch, const mfipm_operator* ops, const double* const* b, const double* tau, const mfipm_params* p,
+             double* const* x, void* workspace, size_t ws_bytes, mfipm_info* infos, cudaStream_t st,
+             mfipm_tuning* t) {
+  int64_t max_n = 0, min_n = INT64_MAX;
+  for (int i = 0; i < batch; ++i) {
+    max_n = std::max<int64_t>(max_n, ops[i].n);
+    min_n = std::min<int64_t>(min_n, ops[i].n);
+  }
+  mfipm_params q = *p;
+  q.cluster_size = 0;
+  std::vector<mfipm_operator> vops(ops, ops + batch);
+  const int G0 = pick_G(vops, &q, batch);
+  const int64_t cm0 = std::min<int64_t>(16384, max_n / G0);
+  std::vector<std::pair<int, int64_t>> cands{{G0, cm0}};
+  for (int G = 1; G <= 16; G *= 2) {
+    if (G < dct_min_G(max_n) || G > dct_max_G(min_n)) continue;
+    for (int64_t cm : {2048, 4096, 8192, 16384}) {
+      if (cm > std::min<int64_t>(16384, max_n / G) || (G == G0 && cm == cm0)) continue;
+      if (G == 1 && cm != std::min<int64_t>(16384, max_n)) continue;  // one CTA each: the limit plays no part
+      cands.push_back({G, cm});
+    }
+  }
+  const std::vector<int> ord = cost_order(ops, batch);
+  auto run_cfg = [&](int G, int64_t cm, int reps, double* ms) -> int {
+    q.cluster_size = G;
+    Prepared P;
+    int rc = prepare(batch, ops, b, tau, &q, x, nullptr, workspace, ws_bytes, P);
+    if (rc) return rc;
+    P.cta_max_n = cm;
+    const bool saved = g_timing;
+    g_timing = true;
+    for (int r = 0; r < reps && !rc; ++r) rc = run(P, st, batch, infos, &ord);
+    g_timing = saved;
+    *ms = g_last_ms;
+    return rc;
+  };
+  double best = 1e300, dflt = -1.0;
+  std::pair<int, int64_t> pick = cands[0];
+  int timed = 0;
+  for (size_t c = 0; c < cands.size(); ++c) {
+    double ms = 0.0;
+    if (run_cfg(cands[c].first, cands[c].second, 2, &ms) != MFIPM_OK) continue;  // skipped: did not solve
+    ++timed;
+    if (c == 0) dflt = ms;
+    if (ms < best) {
+      best = ms;
+      pick = cands[c];
+    }
+  }
+  if (!timed) return fail(MFIPM_NOT_CONVERGED, "autotune: no configuration solved the batch");
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune_dct[{max_n, ceil_log2i(batch)}] = TuneDct{pick.first, pick.second};
+  }
+  double ms = 0.0;
+  const int rc = run_cfg(pick.first, pick.second, 1, &ms);  // x and infos from the chosen configuration
+  if (t) {
+    t->path = 1;
+    t->candidates = timed;
+    t->cluster_size = pick.first;
+    t->cta_max_n = pick.second;
+    t->best_ms = best;
+    t->default_ms = dflt;
+  }
+  return rc;
+}
+
+// Shared bf16 A: split-K of T = A W and of Y = A^T T, each timed alone on its real shapes
+// (median of 5), scratch operands carved from the caller's workspace.
+int tune_gemm(int batch, const mfipm_operator* ops, void* workspace, size_t ws_bytes, cudaStream_t st,
+              mfipm_tuning* t, int* s1_out, int* s2_out) {
+  const int m = (int)ops[0].m, n = (int)ops[0].n, N = 2 * batch;
+  *s1_out = *s2_out = 0;
+  if (!tc_gemm_supported(m, N, n) || !tc_gemm_supported(n, N, m) || g_force_simple_gemm) return MFIPM_OK;
+  char* ws = static_cast<char*>(workspace);
+  const size_t wb = align256((size_t)N * n * 2), tb = align256((size_t)N * m * 2);
+  const size_t cb = align256((size_t)kMaxSplits * N * std::max(m, n) * 4);
+  if (wb + tb + cb > ws_bytes) return fail(MFIPM_INVALID_ARG, "autotune: workspace too small");
+  void* W = ws;
+  void* T = ws + wb;
+  float* Cb = reinterpret_cast<float*>(ws + wb + tb);
+  int* err = g_gemm_err_ptr();
+  if (!err) return fail(MFIPM_CUDA, "no device error word");
+  cudaError_t e;
+  if ((e = cudaMemsetAsync(W, 0, wb + tb, st)) || (e = cudaMemsetAsync(err, 0, 4, st))) return cuda_fail(e, "autotune");
+  cudaEvent_t ev[2];
+  if ((e = cudaEventCreate(&ev[0])) || (e = cudaEventCreate(&ev[1]))) return cuda_fail(e, "autotune events");
+  // the second GEMM reads A^T (n x m, K-major); A's own bytes viewed with that shape time the same
+  auto time_one = [&](int rows, int K, const void* Bop, int s, double* ms) -> cudaError_t {
+    std::vector<float> v;
+    for (int r = 0; r < 6; ++r) {
+      cudaError_t r2;
+      if ((r2 = cudaEventRecord(ev[0], st)) || (r2 = tc_gemm(ops[0].A, Bop, Cb, rows, N, K, s, err, st)) ||
+          (r2 = cudaEventRecord(ev[1], st)) || (r2 = cudaEventSynchronize(ev[1])))
+        return r2;
+      float x = 0.f;
+      cudaEventElapsedTime(&x, ev[0], ev[1]);
+      if (r) v.push_back(x);
+    }
+    std::sort(v.begin(), v.end());
+    *ms = v[v.size() / 2];
+    return cudaSuccess;
+  };
+  double b1 = 1e300, b2 = 1e300, d1 = 0, d2 = 0;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int s1d = std::min(kMaxSplits, tc_gemm_splits(m, n, sms)), s2d = std::min(kMaxSplits, tc_gemm_splits(n, m, sms));
+  int timed = 0;
+  for (int s = 1; s <= kMaxSplits; s *= 2) {
+    double ms1 = 0, ms2 = 0;
+    if ((e = time_one(m, n, W, s, &ms1)) || (e = time_one(n, m, T, s, &ms2))) break;
+    timed += 2;
+    if (s == s1d) d1 = ms1;
+    if (s == s2d) d2 = ms2;
+    if (ms1 < b1) { b1 = ms1; *s1_out = s; }
+    if (ms2 < b2) { b2 = ms2; *s2_out = s; }
+  }
+  cudaEventDestroy(ev[0]);
+  cudaEventDestroy(ev[1]);
+  if (e) return cuda_fail(e, "autotune GEMM");
+  int herr = 0;
+  if ((e = cudaMemcpy(&herr, err, 4, cudaMemcpyDeviceToHost))) return cuda_fail(e, "autotune GEMM status");
+  if (herr) return fail(herr, "tensor-core GEMM: a bounded mbarrier wait expired");
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune_gemm[{ops[0].m, ops[0].n, batch}] = TuneGemm{*s1_out, *s2_out};
+  }
+  if (t) {
+    t->path = 2;
+    t->candidates = timed;
+    t->splits1 = *s1_out;
+    t->splits2 = *s2_out;
+    t->best_ms = b1 + b2;
+    t->default_ms = d1 + d2;
+  }
+  return MFIPM_OK;
 }
 }  // namespace
 
@@ -933,6 +1116,46 @@ int mfipm_apply_At(const mfipm_operator* op, const double* y, double* x, void* w
 int mfipm_kkt_residual(const mfipm_operator* op, const double* b, double tau, const double* x, void* workspace,
                        size_t ws_bytes, double* out, void* stream) {
   return apply_checked(2, op, x, b, tau, nullptr, out, workspace, ws_bytes, stream);
+}
+
+int mfipm_autotune(int32_t batch, const mfipm_operator* ops, const double* const* b, const double* tau,
+                   const mfipm_params* p, double* const* x, void* workspace, size_t ws_bytes, mfipm_info* infos,
+                   mfipm_tuning* tuning, void* stream) {
+  g_err.clear();
+  if (tuning) memset(tuning, 0, sizeof(*tuning));
+  int rc = validate_params(p);
+  if (rc) return rc;
+  if (batch < 1 || !ops || !b || !tau || !x) return fail(MFIPM_INVALID_ARG, "NULL argument array or batch < 1");
+  for (int i = 0; i < batch; ++i)
+    if ((rc = validate_op(&ops[i], i))) return rc;
+  if (!workspace || ((uintptr_t)workspace & 255)) return fail(MFIPM_INVALID_ARG, "workspace NULL or not 256-byte aligned");
+  size_t need = 0;
+  if ((rc = mfipm_workspace_size(ops, batch, p, &need))) return rc;
+  if (ws_bytes < need) return fail(MFIPM_INVALID_ARG, "workspace too small: %zu < %zu bytes", ws_bytes, need);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  std::vector<mfipm_info> tmp;
+  if (!infos) {
+    tmp.resize(batch);
+    infos = tmp.data();
+  }
+  bool shared = false;
+  if ((rc = check_shared_bf16(ops, batch, p, &shared))) return rc;
+  if (shared) {
+    int s1 = 0, s2 = 0;
+    if ((rc = tune_gemm(batch, ops, workspace, ws_bytes, st, tuning, &s1, &s2))) return rc;
+    return solve_shared_bf16(batch, ops, b, tau, p, x, nullptr, workspace, ws_bytes, infos, stream);
+  }
+  const Split sp = split_batch(ops, batch);
+  if (ops[0].kind != MFIPM_OP_PARTIAL_DCT || sp.any_large() || p->cluster_size != 0)
+    return mfipm_solve_batched(batch, ops, b, tau, p, x, nullptr, workspace, ws_bytes, infos, stream);
+  return tune_dct(batch, ops, b, tau, p, x, workspace, ws_bytes, infos, st, tuning);
+}
+
+int mfipm_clear_tuning(void) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune_dct.clear();
+  g_tune_gemm.clear();
+  return MFIPM_OK;
 }
 
 const char* mfipm_last_error(void) { return g_err.c_str(); }

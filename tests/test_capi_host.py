@@ -175,3 +175,22 @@ def test_operator_products_rejected_before_launch(L, fn, case):
         rc = L.mfipm_kkt_residual(ctypes.byref(op), ctypes.c_void_p(0x5000), tau, vin, ws, wsb, ctypes.byref(out), None)
     assert rc == C.MFIPM_INVALID_ARG, (fn, case, rc)
     assert len(L.mfipm_last_error()) > 5
+
+
+def test_autotune_rejected_before_launch(L):
+    from paper_1208_5435_gb300 import _capi as C
+    p = C.Params()
+    L.mfipm_params_default(ctypes.byref(p))
+    ops = (C.Operator * 2)(_dct_op(C, 4096, 1024), _dct_op(C, 2048, 512))
+    P = ctypes.c_void_p
+    arr = (P * 2)(P(0x3000), P(0x3100))
+    taus = (ctypes.c_double * 2)(0.1, 0.1)
+    t = C.Tuning()
+    assert L.mfipm_autotune(2, ops, arr, taus, ctypes.byref(p), arr, None, 1 << 40, None, ctypes.byref(t), None) \
+        == C.MFIPM_INVALID_ARG  # no workspace
+    assert L.mfipm_autotune(2, ops, arr, taus, ctypes.byref(p), arr, ctypes.c_void_p(0x10000), 4096, None,
+                            ctypes.byref(t), None) == C.MFIPM_INVALID_ARG  # small workspace
+    assert L.mfipm_autotune(0, ops, arr, taus, ctypes.byref(p), arr, ctypes.c_void_p(0x10000), 1 << 40, None,
+                            ctypes.byref(t), None) == C.MFIPM_INVALID_ARG
+    assert t.path == 0
+    assert L.mfipm_clear_tuning() == 0
