@@ -238,8 +238,8 @@ def run_ours(args, rank, world, local_rank):
         return run_bf16(args, rank, world, local_rank, probs)
     if args.workload == "dct_adjoint_32x1M":
         return run_adjoint(args, rank, world, local_rank, probs)
-    if probs[0].kind != "dct":
-        raise SystemExit("bench.py times the partial-DCT and the shared-A bf16 workloads")
+    if probs[0].kind == "dense":
+        return run_dense(args, rank, world, local_rank, probs)
     ops = [M.PartialDCT(p.n, torch.from_numpy(p.rows).to(dev)) for p in probs]
     bs = [torch.from_numpy(p.b).to(dev) for p in probs]
     taus = [p.tau for p in probs]
@@ -370,6 +370,95 @@ def run_ours(args, rank, world, local_rank):
     print(json.dumps(line), flush=True)
 
 
+def run_dense(args, rank, world, local_rank, probs):
+    """Plain float64 mfIPM on one dense Gaussian problem (256 x 1024): one step = one mfipm_solve
+    (the persistent kernel on one cluster; float64 PCG).  A (2 MiB) stays in L2, so the
+    roofline's algorithmic bytes (A read once per product with A or A^T) are an L2-resident
+    stream reported against HBM for comparability."""
+    import torch
+    import paper_1208_5435_gb300 as M
+
+    dev = torch.device("cuda", local_rank)
+    L = M.lib()
+    p0 = probs[0]
+    op = M.Dense(torch.from_numpy(p0.A).to(dev))
+    b = torch.from_numpy(p0.b).to(dev)
+    params = M.SolverParams()
+    ws = torch.empty(M.workspace_bytes([op], params), dtype=torch.uint8, device=dev)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        M.solve(op, b, p0.tau, params, ws=ws)
+    torch.cuda.synchronize()
+    L.mfipm_set_timing(1)
+    step_ms, kern_ms = [], []
+    with ClockSampler(local_rank) as clk:
+        for _ in range(args.steps):
+            flush.fill_(1)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            x, info = M.solve(op, b, p0.tau, params, ws=ws)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            step_ms.append(e0.elapsed_time(e1))
+            kern_ms.append(L.mfipm_last_kernel_ms())
+    L.mfipm_set_timing(0)
+    ok = 1 if info["status"] == 0 and info["kkt_rel"] <= KKT_GATE else 0
+    value, total_ms = job_throughput(ok, sum(step_ms), args.steps, world, dev)
+    ms_per_step = total_ms / args.steps
+    kms = statistics.mean(kern_ms)
+    abytes = info["n_mat"] * p0.m * p0.n * 8
+    peak, peak_kind = measured_peaks()
+    # e2e: A and b from pinned host memory, x read back
+    hA = torch.from_numpy(p0.A).pin_memory()
+    hb = torch.from_numpy(p0.b).pin_memory()
+    hx = torch.empty(p0.n, dtype=torch.float64).pin_memory()
+    e2e_ms = []
+    for it in range(1 + args.steps):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        eop = M.Dense(hA.to(dev, non_blocking=True))
+        xe, ie = M.solve(eop, hb.to(dev, non_blocking=True), p0.tau, params, ws=ws)
+        hx.copy_(xe, non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if it >= 1:
+            e2e_ms.append(e0.elapsed_time(e1))
+    e2e_ok = 1 if ie["status"] == 0 and ie["kkt_rel"] <= KKT_GATE else 0
+    e2e_value = sum_over_ranks(e2e_ok, world, dev) / (max_over_ranks(sum(e2e_ms), world, dev) / args.steps / 1e3)
+    if rank != 0:
+        return
+    cpu = None
+    if not args.no_cpu and world == 1:
+        from oracle import mfipm_oracle as O
+        t0 = time.perf_counter()
+        done = 0
+        while time.perf_counter() - t0 < 10.0:
+            O.ipm(O.Operator.from_dense(p0.A), p0.b, p0.tau, O.OracleParams(tol=1e-10))
+            done += 1
+        secs = time.perf_counter() - t0
+        cpu = {"value": done / secs, "unit": UNIT, "cores": cpu_threads(), "kind": "oracle",
+               "sample": f"{done} solve(s) of the same problem in {secs:.1f} s: direct-solve float64 IPM"}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "m": p0.m, "n": p0.n, "tol": params.tol,
+                   "l2": "flushed (512 MiB write) before each step", "solved_at_kkt_1e-6": ok},
+        "roofline": {"bound": "hbm", "achieved": abytes / (kms / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
+                     "frac": abytes / (kms / 1e3) / 1e9 / peak, "traffic": None, "peak_kind": peak_kind,
+                     "kernel": "ipm_kernel (dense float64, one cluster)", "kernel_ms": kms,
+                     "algorithmic_bytes": abytes},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": (p0.A.size + p0.m) * 8,
+                "d2h_bytes_per_step": p0.n * 8},
+        "cpu_baseline": cpu, "gpu_launches": args.steps,  # one persistent launch per solve
+        "clocks": clk.summary(),
+        "iterations": {"ipm": info["ipm_iters"], "pcg": info["pcg_iters"], "kkt": info["kkt_rel"]},
+    }
+    print(json.dumps(line), flush=True)
+
+
 def run_bf16(args, rank, world, local_rank, probs):
     """Shared-A bf16 workload: one step = one mfipm_solve_batched over all right-hand sides."""
     import ctypes
@@ -404,6 +493,35 @@ def run_bf16(args, rank, world, local_rank, probs):
     ok = sum(1 for i in infos if i["status"] == 0 and i["kkt_rel"] <= KKT_GATE)
     value, total_ms = job_throughput(ok, sum(step_ms), args.steps, world, dev)
     ms_per_step = total_ms / args.steps
+    ms_, by_, pr_, la_ = ctypes.c_double(), ctypes.c_double(), ctypes.c_int64(), ctypes.c_int64()
+    assert L.mfipm_last_operator_stats(ctypes.byref(ms_), ctypes.byref(by_), ctypes.byref(pr_), ctypes.byref(la_)) == 0
+    launches = int(la_.value) + 1  # the lockstep solve's kernels + the norm of A before it
+
+    # e2e: A and the right-hand sides from pinned host memory, x read back, every step
+    hA = torch.from_numpy(probs[0].a_bf16.view(np.int16)).pin_memory()
+    hb = [torch.from_numpy(p.b).pin_memory() for p in probs]
+    hx = [torch.empty(p.n, dtype=torch.float64).pin_memory() for p in probs]
+    dA = torch.empty(hA.shape, dtype=torch.int16, device=dev)
+    h2d = hA.numel() * 2 + sum(t.numel() * 8 for t in hb)
+    d2h = sum(t.numel() * 8 for t in hx)
+    e2e_ms = []
+    for it in range(1 + args.steps):
+        flush.fill_(1)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        dA.copy_(hA, non_blocking=True)
+        eop = M.DenseBF16(dA.view(torch.bfloat16), probs[0].a_scale)
+        xs_, inf_ = M.solve_batched([eop] * len(probs), [b_.to(dev, non_blocking=True) for b_ in hb], taus, params,
+                                    ws=ws)
+        for h, d_ in zip(hx, xs_):
+            h.copy_(d_, non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if it >= 1:
+            e2e_ms.append(e0.elapsed_time(e1))
+    e2e_ok = sum(1 for i in inf_ if i["status"] == 0 and i["kkt_rel"] <= KKT_GATE)
+    e2e_value, _ = job_throughput(e2e_ok, sum(e2e_ms), args.steps, world, dev)
     # the tensor-core GEMMs of one PCG operator product, timed alone on their real shapes
     m, n, R = probs[0].m, probs[0].n, len(probs)
     W_ = torch.randn(2 * R, n, device=dev).to(torch.bfloat16)
@@ -455,6 +573,8 @@ def run_bf16(args, rank, world, local_rank, probs):
                      "frac": gbytes / (gms / 1e3) / 1e9 / peak, "traffic": None, "peak_kind": peak_kind,
                      "kernel": "tc_gemm_kernel pair (T = A W, Y = A^T T), timed alone", "kernel_ms": gms,
                      "algorithmic_bytes": gbytes, "tensor_tflops": gflop / (gms / 1e3) / 1e12},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches * args.steps,
         "cpu_baseline": cpu, "clocks": clk.summary(),
         "iterations": {"ipm_mean": statistics.mean(i["ipm_iters"] for i in infos),
                        "pcg_mean": statistics.mean(i["pcg_iters"] for i in infos),

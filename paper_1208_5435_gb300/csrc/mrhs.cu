@@ -673,7 +673,9 @@ __global__ void k_alpha(Dev d, int first, const double* part2) {
   if (c.active) c.nmat += 2;
 }
 
-__global__ void k_pcg_D(Dev d, float2* __restrict__ Xo, int first) {
+// at most 64 registers: four blocks per SM for this memory-bound pass (measured faster than
+// its unbounded 128 registers and than three blocks, despite a small spill)
+__global__ void __launch_bounds__(kT, 4) k_pcg_D(Dev d, float2* __restrict__ Xo, int first) {
   const int j = blockIdx.y, blk = blockIdx.x;
   const Col& c = d.col[j];
   const float alpha = c.alpha, rho = (float)c.rho, sc = (float)d.a_scale;
@@ -1045,6 +1047,7 @@ int lockstep_run(mr::Dev& d, double* part2, const double* taus, const double* rh
 
 int mrhs_solve(const MrhsCall& call, std::string* msg) {
   using namespace mr;
+  g_nlaunch = 0;
   const int64_t m = call.m, n = call.n;
   const int R = call.R;
   cudaStream_t st = call.stream;
@@ -1132,6 +1135,7 @@ int mrhs_solve(const MrhsCall& call, std::string* msg) {
   const bool vecA2 = m % 8 == 0;
   k_rowpow<<<(unsigned)(((int64_t)m * S1 * 32 + 255) / 256), 256, 0, st>>>(d.A, d.lda, (int)m, (int)n, S1, rp1);
   k_rowpow<<<(unsigned)(((int64_t)n * S2 * 32 + 255) / 256), 256, 0, st>>>(At, m, (int)n, (int)m, S2, rp2);
+  g_nlaunch += 4;  // transpose, gather of b, two row-bound passes
   if ((e = cudaGetLastError())) return mr_fail(e, msg, "row bounds");
 
   auto residual = [&]() -> cudaError_t {
@@ -1145,9 +1149,11 @@ int mrhs_solve(const MrhsCall& call, std::string* msg) {
     k_fin2<<<(unsigned)std::min<int64_t>(((int64_t)R * n + 255) / 256, 4096), 256, 0, st>>>(Part, S2, d.a_scale,
                                                                                            d.Gr, (int)n, R);
     k_colnorm2<<<dim3(nb, R), kT, 0, st>>>(d.Rr, (int)m, part2, nb);
+    g_nlaunch += 6;
     return cudaGetLastError();
   };
   auto normal = [&](int, int) -> cudaError_t {
+    g_nlaunch += 3;
     e = call.gemm(call.gemm_ctx, d.A, d.W, d.C1, (int)m, 2 * R, (int)n, d.s1, st);
     if (e) return e;
     k_split_t<<<dim3(nb, R), kT, 0, st>>>(d, part2);
