@@ -235,6 +235,11 @@ int mfipm_gemm_bf16(const void* Aop, const void* Bop, float* C, int32_t rows, in
                     int32_t tensor_cores, void* stream);
 /* Use (1, default) or bypass (0) the tensor-core GEMM inside the bf16 solver on this process. */
 int mfipm_set_gemm_mode(int32_t tensor_cores);
+/* Outer residual A^T(A x - b) of the bf16 solver on this process (not in the paper; both are
+ * float64-grade, below 1e-10 of ||a|| ||x|| per entry): 1 (default) = exact integer digit
+ * slices of A and x on the tcgen05 GEMM (error-free splitting: float32 accumulation of integer
+ * products over chunks of 1024 is exact), 0 = a biased float32 accumulator on the CUDA cores. */
+int mfipm_set_residual_mode(int32_t tensor_cores);
 /* Partial-DCT problems with n >= threshold (a power of two, default 131072 = twice the
  * cluster solver's largest n; accepted range [1024, 131072]) are solved by the lockstep
  * multi-pass solver, whose operator is the same chain of Sec. 2 (Eq. eq:orthonormality) as

@@ -75,6 +75,7 @@ SIGNATURES = {
                                        ctypes.c_int32, _P]),
     "mfipm_set_gemm_mode": (ctypes.c_int, [ctypes.c_int32]),
     "mfipm_set_large_dct_threshold": (ctypes.c_int, [ctypes.c_int64]),
+    "mfipm_set_residual_mode": (ctypes.c_int, [ctypes.c_int32]),
     "mfipm_autotune": (ctypes.c_int, [ctypes.c_int32, ctypes.POINTER(Operator), _PP, ctypes.POINTER(ctypes.c_double),
                                       ctypes.POINTER(Params), _PP, _P, ctypes.c_size_t, ctypes.POINTER(Info),
                                       ctypes.POINTER(Tuning), _P]),

@@ -27,6 +27,9 @@ thread_local std::string g_err;
 
 // Plain CUDA-core GEMM instead of tcgen05 in the bf16 solver (mfipm_set_gemm_mode; for tests).
 bool g_force_simple_gemm = false;
+// Residual of the bf16 solver: exact digit slices on the tensor cores (1) or the biased float32
+// accumulator on the CUDA cores (0) (mfipm_set_residual_mode).
+int g_resid_tc = 1;
 
 // Autotuner results (mfipm_autotune), process-wide.  Persistent partial-DCT kernel: keyed by
 // the batch's largest n and ceil(log2 batch) -> cluster size G and the largest n solved by a
@@ -596,6 +599,7 @@ int solve_shared_bf16(int batch, const mfipm_operator* ops, const double* const*
   int* err_dev = reinterpret_cast<int*>(ws + 64);
   if ((e = cudaMemsetAsync(err_dev, 0, 4, st))) return cuda_fail(e, "clear error word");
   call.err_dev = err_dev;
+  call.resid_tc = g_resid_tc && !g_force_simple_gemm;
   const int m32 = (int)ops[0].m, n32 = (int)ops[0].n;
   if (tc_gemm_supported(m32, 2 * batch, n32) && tc_gemm_supported(n32, 2 * batch, m32) && !g_force_simple_gemm) {
     int dev = 0, sms = 0;
@@ -1177,6 +1181,11 @@ int mfipm_last_operator_stats(double* ms, double* bytes, int64_t* products, int6
 
 int mfipm_set_gemm_mode(int32_t tensor_cores) {
   g_force_simple_gemm = tensor_cores == 0;
+  return MFIPM_OK;
+}
+
+int mfipm_set_residual_mode(int32_t tensor_cores) {
+  g_resid_tc = tensor_cores != 0;
   return MFIPM_OK;
 }
 

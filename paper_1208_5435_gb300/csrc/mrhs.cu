@@ -420,6 +420,124 @@ __global__ void k_fin2(const float2* __restrict__ Part, int S2, double scale, fl
   }
 }
 
+// ------------------------------------------------------------------ residual on the tensor cores
+// The same float64-grade products A x and A^T r on the tcgen05 GEMM by error-free splitting
+// into integer digit slices (the splitting of Ozaki et al. for accurate products on
+// low-precision units): per row r of A and per column j of x, with 2^E bounding the largest
+// magnitude,
+//     a = 2^(Er - 7) sum_t D_t 2^(-7t),   x = 2^(Ej - 7) sum_s X_s 2^(-7s),
+// digits |D_0|, |X_0| <= 128 and |D_t|, |X_s| <= 65 after the first: every digit is an integer
+// exact in bf16, every product of two digits is below 2^14 and a sum of 1024 of them below
+// 2^24, so the GEMM's float32 accumulation over a split-K chunk of 1024 is exact.  The integer
+// chunk sums are combined in double-float with the weights 2^(Er + Ej - 14 - 7(t + s)) for all
+// pairs t + s <= kPairMax.  kSlA = 5 slices carry 35 bits of A (bf16 A needs 8 bits within
+// 2^-27 of the row maximum: exact but for entries below that), kSlX = 6 carry 42 bits of x.
+constexpr int kSlA = 5, kSlX = 6, kPairMax = 6, kChunkK = 1024;
+
+__device__ __forceinline__ int exp_above(float mx) {  // 2^E > mx (frexp: mx = f 2^E, f in [0.5, 1))
+  if (!(mx > 0.f)) return -60;
+  int e;
+  frexpf(mx, &e);
+  return e;
+}
+__device__ __forceinline__ float block_max(float v, float* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float t = 0.f;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t = fmaxf(t, red[w]);
+    red[32] = t;
+  }
+  __syncthreads();
+  return red[32];
+}
+
+// A (rows x K, lda) -> digit slices S[t][r][k] and row exponents E[r]; one block per row
+__global__ void k_slice_rows(const __nv_bfloat16* __restrict__ A, int64_t lda, int rows, int K,
+                             __nv_bfloat16* __restrict__ S, int* __restrict__ E) {
+  __shared__ float red[33];
+  const int r = blockIdx.x;
+  const __nv_bfloat16* a = A + (int64_t)r * lda;
+  float mx = 0.f;
+  for (int k = threadIdx.x; k < K; k += blockDim.x) mx = fmaxf(mx, fabsf(bf(a[k])));
+  const int e = exp_above(block_max(mx, red));
+  if (threadIdx.x == 0) E[r] = e;
+  const float sc = ldexpf(1.f, 7 - e);
+  for (int k = threadIdx.x; k < K; k += blockDim.x) {
+    float v = bf(a[k]) * sc;  // |v| < 128, exact
+#pragma unroll
+    for (int t = 0; t < kSlA; ++t) {
+      const float dg = rintf(v);
+      S[((int64_t)t * rows + r) * K + k] = __float2bfloat16_rn(dg);
+      v = (v - dg) * 128.f;  // exact
+    }
+  }
+}
+
+__device__ __forceinline__ df load_dfv(const float2* X, int64_t i) { return df(X[i].x, X[i].y); }
+__device__ __forceinline__ df load_dfv(const double* X, int64_t i) { return to_df(X[i]); }
+__device__ __forceinline__ df scale2(df v, float p2) { return df(v.hi * p2, v.lo * p2); }  // exact: power of two
+
+// X (R x K, double-float or float64) -> digit slices S[s][j][k] and column exponents E[j];
+// one block per column
+template <class T>
+__global__ void k_slice_cols(const T* __restrict__ X, int R, int K, __nv_bfloat16* __restrict__ S,
+                             int* __restrict__ E) {
+  __shared__ float red[33];
+  const int j = blockIdx.x;
+  float mx = 0.f;
+  for (int k = threadIdx.x; k < K; k += blockDim.x) mx = fmaxf(mx, fabsf(load_dfv(X, (int64_t)j * K + k).hi));
+  // |x| <= |hi| (1 + 2^-24): a bound just above the largest hi covers it
+  const int e = exp_above(block_max(mx, red) * 1.0001f);
+  if (threadIdx.x == 0) E[j] = e;
+  const float sc = ldexpf(1.f, 7 - e);
+  for (int k = threadIdx.x; k < K; k += blockDim.x) {
+    df v = scale2(load_dfv(X, (int64_t)j * K + k), sc);
+#pragma unroll
+    for (int s = 0; s < kSlX; ++s) {
+      const float dg = rintf(v.hi);
+      S[((int64_t)s * R + j) * K + k] = __float2bfloat16_rn(dg);
+      v = scale2(v - df(dg), 128.f);
+    }
+  }
+}
+
+// Acc[j][r] (+)= sum over the c slices s0.. of one GEMM call: weight(t, s) * (integer chunk sums)
+__global__ void k_slice_acc(const float* __restrict__ C, int splits, int c, int R, int rows, int t, int s0,
+                            const int* __restrict__ Er, const int* __restrict__ Ej, float2* __restrict__ Acc,
+                            int first) {
+  const int64_t total = (int64_t)R * rows, N = (int64_t)c * R;
+  for (int64_t gi = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; gi < total;
+       gi += (int64_t)gridDim.x * blockDim.x) {
+    const int j = (int)(gi / rows), r = (int)(gi % rows);
+    df acc = first ? df(0.f) : df(Acc[gi].x, Acc[gi].y);
+    for (int sl = 0; sl < c; ++sl) {
+      int isum = 0;  // exact: chunk sums are integers below 2^24, their sum below 2^28
+      for (int sp = 0; sp < splits; ++sp) isum += __float2int_rn(C[((int64_t)sp * N + sl * R + j) * rows + r]);
+      const float hi = __int2float_rn(isum);
+      const df term(hi, __int2float_rn(isum - __float2int_rn(hi)));
+      acc = acc + scale2(term, ldexpf(1.f, Er[r] + Ej[j] - 14 - 7 * (t + s0 + sl)));
+    }
+    Acc[gi] = make_float2(acc.hi, acc.lo);
+  }
+}
+// Rr = scale Acc - Bm (float64), first product of the residual
+__global__ void k_fin1_tc(const float2* __restrict__ Acc, const double* __restrict__ Bm, double scale,
+                          double* __restrict__ Rr, int64_t total) {
+  for (int64_t gi = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; gi < total; gi += (int64_t)gridDim.x * blockDim.x)
+    Rr[gi] = scale * ((double)Acc[gi].x + (double)Acc[gi].y) - Bm[gi];
+}
+// Gr = scale Acc (double-float)
+__global__ void k_fin2_tc(const float2* __restrict__ Acc, double scale, float2* __restrict__ Gr, int64_t total) {
+  const df sc = to_df(scale);
+  for (int64_t gi = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; gi < total; gi += (int64_t)gridDim.x * blockDim.x) {
+    const df g = sc * df(Acc[gi].x, Acc[gi].y);
+    Gr[gi] = make_float2(g.hi, g.lo);
+  }
+}
+
 // ------------------------------------------------------------------ per-column state
 struct Dev {
   int m, n, R, nb;                 // nb: blocks per column of the index passes
@@ -911,6 +1029,24 @@ __global__ void k_info(Dev d, mfipm_info* infos) {
 }  // namespace mr
 
 // ------------------------------------------------------------------ host orchestration
+namespace {
+int slice_splits(int64_t K) { return (int)(((K + 63) / 64 + 15) / 16); }  // chunks of <= 1024 = 16 x 64
+size_t tc_resid_cbuf(int64_t m, int64_t n) {
+  return (size_t)std::max<int64_t>(slice_splits(n) * m, slice_splits(m) * n) * 256 * 4;
+}
+size_t tc_resid_bytes(int64_t m, int64_t n, int R) {
+  auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  const int64_t mx = std::max(m, n);
+  return al((size_t)mr::kSlA * m * n * 2) * 2 + al((size_t)mr::kSlX * R * mx * 2) + al(tc_resid_cbuf(m, n)) +
+         al((size_t)R * mx * 8) + al((size_t)(m + n) * 4) + al((size_t)R * 8);
+}
+}  // namespace
+
+bool mrhs_resid_tc_supported(int64_t m, int64_t n, int R) {
+  return R >= 1 && R <= 256 && m % 8 == 0 && n % 8 == 0 && tc_gemm_supported((int)m, R, (int)n) &&
+         tc_gemm_supported((int)n, R, (int)m);
+}
+
 size_t mrhs_workspace_bytes(int64_t m, int64_t n, int R) {
   auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
   const int nb = (int)((n + mr::kIdx - 1) / mr::kIdx);
@@ -932,6 +1068,7 @@ size_t mrhs_workspace_bytes(int64_t m, int64_t n, int R) {
   b += al((size_t)R * m * 8);                                              // Rf
   b += al((size_t)mr::kMaxRsplit * m * 4) + al((size_t)mr::kMaxRsplit * n * 4);  // row bounds
   b += al((size_t)mr::kMaxRsplit * R * 4) * 2;                             // column bounds
+  if (mrhs_resid_tc_supported(m, n, R)) b += tc_resid_bytes(m, n, R);
   return b;
 }
 
@@ -1098,6 +1235,23 @@ int mrhs_solve(const MrhsCall& call, std::string* msg) {
   float* rp2 = reinterpret_cast<float*>(take((size_t)kMaxRsplit * n * 4));
   float* cp1 = reinterpret_cast<float*>(take((size_t)kMaxRsplit * R * 4));
   float* cp2 = reinterpret_cast<float*>(take((size_t)kMaxRsplit * R * 4));
+  const bool rtc = call.resid_tc && mrhs_resid_tc_supported(m, n, R);
+  __nv_bfloat16 *SA = nullptr, *SAt = nullptr, *XS = nullptr;
+  float* Cb = nullptr;
+  float2* Acc = nullptr;
+  int *EA = nullptr, *EAt = nullptr, *Ex1 = nullptr, *Ex2 = nullptr;
+  if (rtc) {
+    const int64_t mx = std::max(m, n);
+    SA = reinterpret_cast<__nv_bfloat16*>(take((size_t)kSlA * m * n * 2));
+    SAt = reinterpret_cast<__nv_bfloat16*>(take((size_t)kSlA * m * n * 2));
+    XS = reinterpret_cast<__nv_bfloat16*>(take((size_t)kSlX * R * mx * 2));
+    Cb = reinterpret_cast<float*>(take(tc_resid_cbuf(m, n)));
+    Acc = reinterpret_cast<float2*>(take((size_t)R * mx * 8));
+    EA = reinterpret_cast<int*>(take((size_t)(m + n) * 4));
+    EAt = EA + m;
+    Ex1 = reinterpret_cast<int*>(take((size_t)R * 8));
+    Ex2 = Ex1 + R;
+  }
   if (o > call.ws_bytes) {
     *msg = "workspace too small for the shared-A solver";
     return MFIPM_INVALID_ARG;
@@ -1161,7 +1315,47 @@ int mrhs_solve(const MrhsCall& call, std::string* msg) {
     if (e) return e;
     return cudaGetLastError();
   };
-  auto resid = [&](int) -> cudaError_t { return residual(); };
+  // the same residual by exact digit slices on the tensor cores (slices of A and A^T once)
+  if (rtc) {
+    k_slice_rows<<<(unsigned)m, 256, 0, st>>>(d.A, d.lda, (int)m, (int)n, SA, EA);
+    k_slice_rows<<<(unsigned)n, 256, 0, st>>>(At, m, (int)n, (int)m, SAt, EAt);
+    g_nlaunch += 2;
+    if ((e = cudaGetLastError())) return mr_fail(e, msg, "digit slices of A");
+  }
+  const int per_call = std::max(1, 256 / R);  // x slices per GEMM (N = slices x R <= 256)
+  auto slice_product = [&](const __nv_bfloat16* S, const int* Er, int rows, int K, const int* Ej) -> cudaError_t {
+    const int splits = slice_splits(K);
+    const unsigned ga = (unsigned)std::min<int64_t>(((int64_t)R * rows + 255) / 256, 4096);
+    bool first = true;
+    for (int t = 0; t < kSlA; ++t) {
+      const int smax = std::min(kSlX - 1, kPairMax - t);
+      for (int s0 = 0; s0 <= smax; s0 += per_call) {
+        const int c = std::min(per_call, smax - s0 + 1);
+        cudaError_t r = tc_gemm(S + (size_t)t * rows * K, XS + (size_t)s0 * R * K, Cb, rows, c * R, K, splits,
+                                call.err_dev, st);
+        if (r) return r;
+        k_slice_acc<<<ga, 256, 0, st>>>(Cb, splits, c, R, rows, t, s0, Er, Ej, Acc, first ? 1 : 0);
+        first = false;
+        g_nlaunch += 2;
+      }
+    }
+    return cudaGetLastError();
+  };
+  auto residual_tc = [&]() -> cudaError_t {
+    const unsigned g1 = (unsigned)std::min<int64_t>(((int64_t)R * m + 255) / 256, 4096);
+    const unsigned g2 = (unsigned)std::min<int64_t>(((int64_t)R * n + 255) / 256, 4096);
+    cudaError_t r;
+    k_slice_cols<float2><<<R, 256, 0, st>>>(d.X, R, (int)n, XS, Ex1);
+    if ((r = slice_product(SA, EA, (int)m, (int)n, Ex1))) return r;
+    k_fin1_tc<<<g1, 256, 0, st>>>(Acc, d.Bm, d.a_scale, d.Rr, (int64_t)R * m);
+    k_slice_cols<double><<<R, 256, 0, st>>>(d.Rr, R, (int)m, XS, Ex2);
+    if ((r = slice_product(SAt, EAt, (int)n, (int)m, Ex2))) return r;
+    k_fin2_tc<<<g2, 256, 0, st>>>(Acc, d.a_scale, d.Gr, (int64_t)R * n);
+    k_colnorm2<<<dim3(nb, R), kT, 0, st>>>(d.Rr, (int)m, part2, nb);
+    g_nlaunch += 5;
+    return cudaGetLastError();
+  };
+  auto resid = [&](int) -> cudaError_t { return rtc ? residual_tc() : residual(); };
   return lockstep_run(d, part2, taus, nullptr, resid, normal, xptr, zptr, call.infos_dev, st, msg);
 }
 

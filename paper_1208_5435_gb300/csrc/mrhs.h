@@ -34,11 +34,14 @@ struct MrhsCall {
   void* gemm_ctx;
   int splits1, splits2;   // split-K slices of T = A W and Y = A^T T
   int* err_dev;           // DEVICE error word of the GEMMs (MFIPM_TIMEOUT)
+  int resid_tc;           // residual by exact digit slices on the tcgen05 GEMM (else FP32 pipes)
 };
 
 constexpr int kMaxSplits = 8;
 
 size_t mrhs_workspace_bytes(int64_t m, int64_t n, int R);
+// whether the tensor-core residual can run for these shapes (GEMM N = R <= 256, K % 8 == 0)
+bool mrhs_resid_tc_supported(int64_t m, int64_t n, int R);
 
 // Partial-DCT problems of one length n above the cluster solver's reach: the same lockstep
 // IPM with the multi-pass operator of large_dct.cu.

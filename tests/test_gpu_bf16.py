@@ -73,3 +73,22 @@ def test_shared_bf16_full_size_certificates():
         assert k <= 1e-6
         P, D = O.dual_gap_certificate(op, probs[j].b, probs[j].tau, xs[j])
         assert 0 <= P - D <= 1e-5 * (1 + abs(P))  # certificate slack at the default gap tolerance
+
+
+def test_residual_modes_agree():
+    """The residual by exact digit slices on the tensor cores (default) and by the biased
+    float32 accumulator on the CUDA cores reach the same minimisers, both at the oracle's."""
+    import paper_1208_5435_gb300 as M
+    probs = W.bf16_dense_problems(256, 1024, 10, 6, seed=2004)
+    op = O.Operator.from_dense(probs[0].A)
+    xt, it = _solve(probs, tol=1e-12)
+    M.lib().mfipm_set_residual_mode(0)
+    try:
+        xc, ic = _solve(probs, tol=1e-12)
+    finally:
+        M.lib().mfipm_set_residual_mode(1)
+    for p, a, b, i1, i2 in zip(probs, xt, xc, it, ic):
+        assert i1["status"] == 0 and i2["status"] == 0
+        xo = O.ipm(op, p.b, p.tau).x
+        assert np.linalg.norm(a - xo) <= 1e-6 * np.linalg.norm(xo)
+        assert np.linalg.norm(a - b) <= 1e-7 * np.linalg.norm(b)

@@ -40,3 +40,27 @@ def test_tensor_core_gemm_matches_fp32_reference(L, rows, N, K, splits):
     if splits == 1:
         Cs = _run(L, A, B, 1, 0)
         assert (Cs - ref).abs().max().item() / ref.abs().max().item() <= 1e-5
+
+
+def test_integer_digit_products_are_exact(L):
+    """Integer bf16 digits |d| <= 128, as in the residual's slices: each split-K chunk of 1024
+    products sums exactly in the float32 accumulator, up to the edge |sum| = 2^24."""
+    rows, N, K, splits = 512, 64, 4096, 4  # chunks of 1024
+    g = torch.Generator(device="cuda").manual_seed(5)
+    A = torch.randint(-128, 129, (rows, K), generator=g, device="cuda")
+    B = torch.randint(-128, 129, (N, K), generator=g, device="cuda")
+    A[:8] = 128
+    B[:4] = 128
+    B[4:8] = -128  # chunk sums of exactly +-2^24
+    Ab, Bb = A.to(torch.bfloat16), B.to(torch.bfloat16)
+    assert torch.equal(Ab.long(), A) and torch.equal(Bb.long(), B)
+    C = torch.full((splits, N, rows), float("nan"), dtype=torch.float32, device="cuda")
+    rc = L.mfipm_gemm_bf16(Ab.data_ptr(), Bb.data_ptr(), C.data_ptr(), rows, N, K, splits, 1,
+                           ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert rc == 0, L.mfipm_last_error()
+    torch.cuda.synchronize()
+    for sp in range(splits):
+        k0, k1 = sp * 1024, (sp + 1) * 1024
+        ref = (B[:, k0:k1].cpu() @ A[:, k0:k1].cpu().T)  # int64, N x rows
+        assert torch.equal(C[sp].double().cpu(), ref.double()), sp
+    assert C[0, 0, 0].item() == 2.0 ** 24
