@@ -254,8 +254,8 @@ int mfipm_set_large_dct_threshold(int64_t n);
  *     distributed exchange step; every G that fits the batch's n) and the largest n a single
  *     CTA solves alone (2048 .. 16384), keyed by the batch's largest n and ceil(log2 batch);
  *     each candidate is timed by the solver kernel's CUDA events over the real solve;
- *   path 2, shared bf16 A (MFIPM_PREC_BF16_A): the split-K counts of the two tcgen05 GEMMs
- *     of the PCG product, each timed alone on its real shapes, keyed by (m, n, batch).
+ *   path 2, shared bf16 A (MFIPM_PREC_BF16_A): the split-K counts (1 .. 8) of the two tcgen05
+ *     GEMMs of the PCG product, each timed alone on its real shapes, keyed by (m, n, batch).
  * Other batches are solved without tuning (path 0).  Arguments as for mfipm_solve_batched;
  * x and infos receive a solve with the chosen configuration.  *tuning (HOST, nullable):
  * the choice, the number of timed candidates, and the device times (ms) of the best and of

@@ -905,7 +905,7 @@ int tune_gemm(int batch, const mfipm_operator* ops, void* workspace, size_t ws_b
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int s1d = std::min(kMaxSplits, tc_gemm_splits(m, n, sms)), s2d = std::min(kMaxSplits, tc_gemm_splits(n, m, sms));
   int timed = 0;
-  for (int s = 1; s <= kMaxSplits; s *= 2) {
+  for (int s = 1; s <= kMaxSplits; ++s) {  // every count: grid fill is not monotone in s
     double ms1 = 0, ms2 = 0;
     if ((e = time_one(m, n, W, s, &ms1)) || (e = time_one(n, m, T, s, &ms2))) break;
     timed += 2;
