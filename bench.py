@@ -528,12 +528,13 @@ def run_bf16(args, rank, world, local_rank, probs):
     T_ = torch.randn(2 * R, m, device=dev).to(torch.bfloat16)
     At = bits.T.contiguous()
     s1, s2 = max(1, tuning["splits1"]), max(1, tuning["splits2"])  # the split-K the solve uses
+    g1, g2 = tuning["stages1"] or 4, tuning["stages2"] or 4         # and its ring stages
     C1 = torch.empty(s1, 2 * R, m, device=dev)
     C2 = torch.empty(s2, 2 * R, n, device=dev)
     sh = ctypes.c_void_p(stream.cuda_stream)
     def gemm_pair():
-        assert L.mfipm_gemm_bf16(bits.data_ptr(), W_.data_ptr(), C1.data_ptr(), m, 2 * R, n, s1, 1, sh) == 0
-        assert L.mfipm_gemm_bf16(At.data_ptr(), T_.data_ptr(), C2.data_ptr(), n, 2 * R, m, s2, 1, sh) == 0
+        assert L.mfipm_gemm_bf16(bits.data_ptr(), W_.data_ptr(), C1.data_ptr(), m, 2 * R, n, s1, g1, sh) == 0
+        assert L.mfipm_gemm_bf16(At.data_ptr(), T_.data_ptr(), C2.data_ptr(), n, 2 * R, m, s2, g2, sh) == 0
     for _ in range(3):
         gemm_pair()
     reps = 20
@@ -547,7 +548,9 @@ def run_bf16(args, rank, world, local_rank, probs):
         torch.cuda.synchronize()
         g_ms.append(e0.elapsed_time(e1))
     gms = statistics.median(g_ms)
-    gbytes = 2 * (m * n * 2) + 2 * R * (n + m) * 2 + (s1 * 2 * R * m + s2 * 2 * R * n) * 4
+    # algorithmic: A read by both GEMMs, W and T in, one float32 product out each (split-K
+    # partial slices are the implementation's extra traffic, not counted)
+    gbytes = 2 * (m * n * 2) + 2 * R * (n + m) * 2 + (2 * R * m + 2 * R * n) * 4
     gflop = 2 * 2 * m * n * 2 * R
     peak, peak_kind = measured_peaks()
     if rank != 0:
@@ -568,6 +571,7 @@ def run_bf16(args, rank, world, local_rank, probs):
         "config": {"workload": args.workload, "m": m, "n": n, "rhs": R, "l2": "flushed (512 MiB write) before each step",
                    "solved_at_kkt_1e-6": ok,
                    "tuned": {"splits1": tuning["splits1"], "splits2": tuning["splits2"],
+                             "stages1": tuning["stages1"], "stages2": tuning["stages2"],
                              "best_ms": tuning["best_ms"], "default_ms": tuning["default_ms"]}},
         "roofline": {"bound": "hbm", "achieved": gbytes / (gms / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
                      "frac": gbytes / (gms / 1e3) / 1e9 / peak, "traffic": None, "peak_kind": peak_kind,

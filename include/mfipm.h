@@ -228,8 +228,8 @@ int mfipm_last_operator_stats(double* ms, double* bytes, int64_t* products, int6
  * in the paper):  C_s[c][r] = sum_{k in slice s} Aop[r][k] * Bop[c][k]  for s < splits, with
  * Aop (rows x K) and Bop (N x K) bf16 row-major DEVICE arrays and C a DEVICE array of
  * splits x N x rows float32 (the sum of the slices is the product; split-K).  tensor_cores = 1
- * runs the tcgen05/TMA kernel (N <= 256, K % 8 == 0, 16-byte aligned operands), 0 a plain
- * CUDA-core kernel (splits = 1).  Synchronises `stream`; MFIPM_TIMEOUT if a bounded device
+ * or 4 runs the tcgen05/TMA kernel with a four-stage shared-memory ring, 3 with three stages
+ * (N <= 256, K % 8 == 0, 16-byte aligned operands), 0 a plain CUDA-core kernel (splits = 1).  Synchronises `stream`; MFIPM_TIMEOUT if a bounded device
  * wait expired. */
 int mfipm_gemm_bf16(const void* Aop, const void* Bop, float* C, int32_t rows, int32_t N, int32_t K, int32_t splits,
                     int32_t tensor_cores, void* stream);
@@ -254,8 +254,9 @@ int mfipm_set_large_dct_threshold(int64_t n);
  *     distributed exchange step; every G that fits the batch's n) and the largest n a single
  *     CTA solves alone (2048 .. 16384), keyed by the batch's largest n and ceil(log2 batch);
  *     each candidate is timed by the solver kernel's CUDA events over the real solve;
- *   path 2, shared bf16 A (MFIPM_PREC_BF16_A): the split-K counts (1 .. 8) of the two tcgen05
- *     GEMMs of the PCG product, each timed alone on its real shapes, keyed by (m, n, batch).
+ *   path 2, shared bf16 A (MFIPM_PREC_BF16_A): the split-K count (1 .. 8) and the number of
+ *     shared-memory ring stages (4, or 3 to fit two CTAs per SM) of each of the two tcgen05
+ *     GEMMs of the PCG product, timed alone on their real shapes, keyed by (m, n, batch).
  * Other batches are solved without tuning (path 0).  Arguments as for mfipm_solve_batched;
  * x and infos receive a solve with the chosen configuration.  *tuning (HOST, nullable):
  * the choice, the number of timed candidates, and the device times (ms) of the best and of
@@ -267,6 +268,7 @@ typedef struct {
   int32_t splits1, splits2; /* path 2 */
   int64_t cta_max_n;        /* path 1 */
   double best_ms, default_ms;
+  int32_t stages1, stages2; /* path 2: tcgen05 ring stages (3 or 4) of the two GEMMs */
 } mfipm_tuning;
 int mfipm_autotune(int32_t batch, const mfipm_operator* ops, const double* const* b,
                    const double* tau, const mfipm_params* p, double* const* x, void* workspace,

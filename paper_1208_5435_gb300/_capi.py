@@ -43,7 +43,8 @@ class Info(ctypes.Structure):
 class Tuning(ctypes.Structure):
     _fields_ = [("path", ctypes.c_int32), ("candidates", ctypes.c_int32), ("cluster_size", ctypes.c_int32),
                 ("splits1", ctypes.c_int32), ("splits2", ctypes.c_int32), ("cta_max_n", ctypes.c_int64),
-                ("best_ms", ctypes.c_double), ("default_ms", ctypes.c_double)]
+                ("best_ms", ctypes.c_double), ("default_ms", ctypes.c_double), ("stages1", ctypes.c_int32),
+                ("stages2", ctypes.c_int32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

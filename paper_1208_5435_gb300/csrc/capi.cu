@@ -39,7 +39,7 @@ struct TuneDct {
   int64_t cta_max_n;
 };
 struct TuneGemm {
-  int s1, s2;
+  int s1, s2, st1, st2;  // split-K and ring stages of T = A W and Y = A^T T
 };
 std::mutex g_tune_mu;
 std::map<std::pair<int64_t, int>, TuneDct> g_tune_dct;
@@ -606,15 +606,20 @@ int solve_shared_bf16(int batch, const mfipm_operator* ops, const double* const*
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     call.gemm = [](void* ctx, const void* Aop, const void* Bop, float* C, int rows, int N, int K, int splits,
-                   cudaStream_t s2) { return tc_gemm(Aop, Bop, C, rows, N, K, splits, static_cast<int*>(ctx), s2); };
+                   cudaStream_t s2, int stages) {
+      return tc_gemm(Aop, Bop, C, rows, N, K, splits, static_cast<int*>(ctx), s2, stages);
+    };
     call.gemm_ctx = err_dev;
     call.splits1 = std::min(kMaxSplits, tc_gemm_splits(m32, n32, sms));
     call.splits2 = std::min(kMaxSplits, tc_gemm_splits(n32, m32, sms));
     std::lock_guard<std::mutex> lk(g_tune_mu);
+    call.stages1 = call.stages2 = 4;
     auto it = g_tune_gemm.find({ops[0].m, ops[0].n, batch});
     if (it != g_tune_gemm.end()) {
       call.splits1 = it->second.s1;
       call.splits2 = it->second.s2;
+      call.stages1 = it->second.st1;
+      call.stages2 = it->second.st2;
     }
   } else {
     call.gemm = gemm_simple;
@@ -884,11 +889,11 @@ int tune_gemm(int batch, const mfipm_operator* ops, void* workspace, size_t ws_b
   cudaEvent_t ev[2];
   if ((e = cudaEventCreate(&ev[0])) || (e = cudaEventCreate(&ev[1]))) return cuda_fail(e, "autotune events");
   // the second GEMM reads A^T (n x m, K-major); A's own bytes viewed with that shape time the same
-  auto time_one = [&](int rows, int K, const void* Bop, int s, double* ms) -> cudaError_t {
+  auto time_one = [&](int rows, int K, const void* Bop, int s, int stg, double* ms) -> cudaError_t {
     std::vector<float> v;
     for (int r = 0; r < 6; ++r) {
       cudaError_t r2;
-      if ((r2 = cudaEventRecord(ev[0], st)) || (r2 = tc_gemm(ops[0].A, Bop, Cb, rows, N, K, s, err, st)) ||
+      if ((r2 = cudaEventRecord(ev[0], st)) || (r2 = tc_gemm(ops[0].A, Bop, Cb, rows, N, K, s, err, st, stg)) ||
           (r2 = cudaEventRecord(ev[1], st)) || (r2 = cudaEventSynchronize(ev[1])))
         return r2;
       float x = 0.f;
@@ -904,15 +909,17 @@ int tune_gemm(int batch, const mfipm_operator* ops, void* workspace, size_t ws_b
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int s1d = std::min(kMaxSplits, tc_gemm_splits(m, n, sms)), s2d = std::min(kMaxSplits, tc_gemm_splits(n, m, sms));
-  int timed = 0;
-  for (int s = 1; s <= kMaxSplits; ++s) {  // every count: grid fill is not monotone in s
-    double ms1 = 0, ms2 = 0;
-    if ((e = time_one(m, n, W, s, &ms1)) || (e = time_one(n, m, T, s, &ms2))) break;
-    timed += 2;
-    if (s == s1d) d1 = ms1;
-    if (s == s2d) d2 = ms2;
-    if (ms1 < b1) { b1 = ms1; *s1_out = s; }
-    if (ms2 < b2) { b2 = ms2; *s2_out = s; }
+  int timed = 0, st1 = 4, st2 = 4;
+  for (int stg = 4; stg >= 3 && !e; --stg) {  // 3 stages: two CTAs per SM at N <= 128
+    for (int s = 1; s <= kMaxSplits; ++s) {  // every count: grid fill is not monotone in s
+      double ms1 = 0, ms2 = 0;
+      if ((e = time_one(m, n, W, s, stg, &ms1)) || (e = time_one(n, m, T, s, stg, &ms2))) break;
+      timed += 2;
+      if (stg == 4 && s == s1d) d1 = ms1;
+      if (stg == 4 && s == s2d) d2 = ms2;
+      if (ms1 < b1) { b1 = ms1; *s1_out = s; st1 = stg; }
+      if (ms2 < b2) { b2 = ms2; *s2_out = s; st2 = stg; }
+    }
   }
   cudaEventDestroy(ev[0]);
   cudaEventDestroy(ev[1]);
@@ -922,13 +929,15 @@ int tune_gemm(int batch, const mfipm_operator* ops, void* workspace, size_t ws_b
   if (herr) return fail(herr, "tensor-core GEMM: a bounded mbarrier wait expired");
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
-    g_tune_gemm[{ops[0].m, ops[0].n, batch}] = TuneGemm{*s1_out, *s2_out};
+    g_tune_gemm[{ops[0].m, ops[0].n, batch}] = TuneGemm{*s1_out, *s2_out, st1, st2};
   }
   if (t) {
     t->path = 2;
     t->candidates = timed;
     t->splits1 = *s1_out;
     t->splits2 = *s2_out;
+    t->stages1 = st1;
+    t->stages2 = st2;
     t->best_ms = b1 + b2;
     t->default_ms = d1 + d2;
   }
@@ -1204,12 +1213,13 @@ int mfipm_gemm_bf16(const void* Aop, const void* Bop, float* C, int32_t rows, in
   cudaError_t e;
   if (tensor_cores) {
     if (!tc_gemm_supported(rows, N, K)) return fail(MFIPM_UNSUPPORTED, "tensor-core GEMM needs N <= 256, K % 8 == 0");
-    int* err_dev = nullptr;
-    // the error word lives in the caller's C buffer tail? no: use a tiny static device flag
-    err_dev = g_gemm_err_ptr();
+    if (tensor_cores != 1 && tensor_cores != 3 && tensor_cores != 4)
+      return fail(MFIPM_INVALID_ARG, "mfipm_gemm_bf16: tensor_cores must be 0, 1, 3 or 4");
+    int* err_dev = g_gemm_err_ptr();  // a static device word: the call allocates nothing
     if (!err_dev) return fail(MFIPM_CUDA, "no device error word");
     if ((e = cudaMemsetAsync(err_dev, 0, 4, st))) return cuda_fail(e, "clear error word");
-    if ((e = tc_gemm(Aop, Bop, C, rows, N, K, splits, err_dev, st))) return cuda_fail(e, "tc_gemm");
+    if ((e = tc_gemm(Aop, Bop, C, rows, N, K, splits, err_dev, st, tensor_cores == 3 ? 3 : 4)))
+      return cuda_fail(e, "tc_gemm");
     int herr = 0;
     if ((e = cudaMemcpyAsync(&herr, err_dev, 4, cudaMemcpyDeviceToHost, st)) || (e = cudaStreamSynchronize(st)))
       return cuda_fail(e, "tc_gemm status");
@@ -1217,7 +1227,7 @@ int mfipm_gemm_bf16(const void* Aop, const void* Bop, float* C, int32_t rows, in
     return MFIPM_OK;
   }
   if (splits != 1) return fail(MFIPM_INVALID_ARG, "the CUDA-core GEMM has no split-K");
-  if ((e = gemm_simple(nullptr, Aop, Bop, C, rows, N, K, 1, st))) return cuda_fail(e, "gemm_simple");
+  if ((e = gemm_simple(nullptr, Aop, Bop, C, rows, N, K, 1, st, 0))) return cuda_fail(e, "gemm_simple");
   if ((e = cudaStreamSynchronize(st))) return cuda_fail(e, "gemm_simple");
   return MFIPM_OK;
 }

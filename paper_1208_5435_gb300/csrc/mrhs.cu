@@ -1308,10 +1308,10 @@ int mrhs_solve(const MrhsCall& call, std::string* msg) {
   };
   auto normal = [&](int, int) -> cudaError_t {
     g_nlaunch += 3;
-    e = call.gemm(call.gemm_ctx, d.A, d.W, d.C1, (int)m, 2 * R, (int)n, d.s1, st);
+    e = call.gemm(call.gemm_ctx, d.A, d.W, d.C1, (int)m, 2 * R, (int)n, d.s1, st, call.stages1);
     if (e) return e;
     k_split_t<<<dim3(nb, R), kT, 0, st>>>(d, part2);
-    e = call.gemm(call.gemm_ctx, At, d.Tb, d.C2, (int)n, 2 * R, (int)m, d.s2, st);
+    e = call.gemm(call.gemm_ctx, At, d.Tb, d.C2, (int)n, 2 * R, (int)m, d.s2, st, call.stages2);
     if (e) return e;
     return cudaGetLastError();
   };
@@ -1800,7 +1800,7 @@ cudaError_t bf16_fro2(const void* A, int64_t m, int64_t n, int64_t lda, double* 
 }
 
 cudaError_t gemm_simple(void*, const void* Aop, const void* Bop, float* C, int rows, int N, int K, int splits,
-                        cudaStream_t st) {
+                        cudaStream_t st, int) {
   if (splits != 1) return cudaErrorInvalidValue;
   mr::gemm_bf16_simple<<<dim3((unsigned)((rows + 63) / 64), (unsigned)((N + 63) / 64)), mr::kT, 0, st>>>(
       static_cast<const __nv_bfloat16*>(Aop), static_cast<const __nv_bfloat16*>(Bop), C, rows, N, K);

@@ -14,7 +14,7 @@ namespace mfipm {
 // (K-major); C is N x rows float32.
 // With split-K the result is `splits` slices of N x rows (their sum is the product).
 using GemmFn = cudaError_t (*)(void* ctx, const void* Aop, const void* Bop, float* C, int rows, int N, int K,
-                               int splits, cudaStream_t st);
+                               int splits, cudaStream_t st, int stages);
 
 struct MrhsCall {
   int64_t m, n, lda;
@@ -33,6 +33,7 @@ struct MrhsCall {
   GemmFn gemm;
   void* gemm_ctx;
   int splits1, splits2;   // split-K slices of T = A W and Y = A^T T
+  int stages1, stages2;   // their tcgen05 ring stages (3 or 4)
   int* err_dev;           // DEVICE error word of the GEMMs (MFIPM_TIMEOUT)
   int resid_tc;           // residual by exact digit slices on the tcgen05 GEMM (else FP32 pipes)
 };
@@ -74,12 +75,12 @@ void large_dct_set_timing(bool on);
 void large_dct_timing(double* ms, double* bytes, int64_t* products, int64_t* launches);
 int mrhs_solve(const MrhsCall& call, std::string* msg);
 cudaError_t gemm_simple(void*, const void* Aop, const void* Bop, float* C, int rows, int N, int K, int splits,
-                        cudaStream_t st);
+                        cudaStream_t st, int stages);
 // tensor-core GEMM (tc_gemm.cu)
 bool tc_gemm_supported(int rows, int N, int K);
 int tc_gemm_splits(int rows, int K, int num_sms);
 cudaError_t tc_gemm(const void* Aop, const void* Bop, float* C, int rows, int N, int K, int splits, int* err,
-                    cudaStream_t st);
+                    cudaStream_t st, int stages = 4);
 // ||A||_F^2 of a bf16 matrix (device result in *out)
 cudaError_t bf16_fro2(const void* A, int64_t m, int64_t n, int64_t lda, double* out, cudaStream_t st);
 

@@ -4,7 +4,7 @@
 // slices of N x rows float32 (the consumer adds them, which keeps the sum deterministic).
 //
 // One CTA computes a 128-row x BN tile: one thread issues TMA loads (128-byte swizzle) into a
-// four-stage shared-memory ring, one thread issues tcgen05.mma (M = 128, N = BN, K = 16, bf16
+// three- or four-stage shared-memory ring, one thread issues tcgen05.mma (M = 128, N = BN, K = 16, bf16
 // in, float32 accumulators in tensor memory), and all four warps read the accumulators back
 // with tcgen05.ld and store them.  Stages are handed over with mbarriers; every wait is
 // bounded and, on expiry, records an error code and abandons the tile (no hang).
@@ -20,7 +20,7 @@
 namespace mfipm {
 namespace tc {
 
-constexpr int kBM = 128, kBK = 64, kStages = 4, kThreadsTc = 128;
+constexpr int kBM = 128, kBK = 64, kThreadsTc = 128;
 constexpr uint32_t kTileA = kBM * kBK * 2;  // 16 KiB
 constexpr long long kSpinLimit = 1ll << 22;  // polls of an mbarrier before giving up (well above 1 s)
 
@@ -71,7 +71,8 @@ __host__ __device__ constexpr uint32_t idesc_bf16(int bn) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(bn >> 3) << 17) | ((uint32_t)(kBM >> 4) << 24);
 }
 
-template <int BN>
+// ST ring stages: 4 by default; 3 leaves room for two CTAs per SM at BN = 128 (autotuned)
+template <int BN, int ST>
 __global__ void __launch_bounds__(kThreadsTc, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, float* C,
                    int rows, int N, int K, int kt_per_split, int* err) {
@@ -80,8 +81,8 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
   unsigned char* sA = smem;
-  unsigned char* sB = smem + kStages * kTileA;
-  __shared__ __align__(8) uint64_t full_bar[kStages], empty_bar[kStages], done_bar;
+  unsigned char* sB = smem + ST * kTileA;
+  __shared__ __align__(8) uint64_t full_bar[ST], empty_bar[ST], done_bar;
   __shared__ uint32_t tmem_base;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m0 = blockIdx.x * kBM, split = blockIdx.y;
@@ -94,7 +95,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   if (threadIdx.x == 0) {
-    for (int s = 0; s < kStages; ++s) {
+    for (int s = 0; s < ST; ++s) {
       mbar_init(&full_bar[s], 1);
       mbar_init(&empty_bar[s], 1);
     }
@@ -111,9 +112,9 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
       // producer: TMA loads of the A and B tiles of each k-step
       int issued = 0;
       for (int kt = 0; kt < ktiles; ++kt) {
-        const int s = kt % kStages;
-        const uint32_t ph = (uint32_t)(kt / kStages) & 1u;
-        if (kt >= kStages && !mbar_wait(&empty_bar[s], ph ^ 1u)) {
+        const int s = kt % ST;
+        const uint32_t ph = (uint32_t)(kt / ST) & 1u;
+        if (kt >= ST && !mbar_wait(&empty_bar[s], ph ^ 1u)) {
           atomicCAS(err, 0, MFIPM_TIMEOUT);
           break;
         }
@@ -125,15 +126,15 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
       }
       // no copy may still be in flight when the CTA leaves: wait (bounded) for the last load
       // of every stage (phases of one stage complete in order)
-      for (int kt = (issued > kStages ? issued - kStages : 0); kt < issued; ++kt)
-        if (!mbar_wait(&full_bar[kt % kStages], (uint32_t)(kt / kStages) & 1u)) atomicCAS(err, 0, MFIPM_TIMEOUT);
+      for (int kt = (issued > ST ? issued - ST : 0); kt < issued; ++kt)
+        if (!mbar_wait(&full_bar[kt % ST], (uint32_t)(kt / ST) & 1u)) atomicCAS(err, 0, MFIPM_TIMEOUT);
     } else if (warp == 1 && lane == 0) {
       // MMA issuer: four K=16 steps per stage, accumulate in tensor memory
       constexpr uint32_t idesc = idesc_bf16(BN);
       bool ok = true;
       for (int kt = 0; kt < ktiles && ok; ++kt) {
-        const int s = kt % kStages;
-        const uint32_t ph = (uint32_t)(kt / kStages) & 1u;
+        const int s = kt % ST;
+        const uint32_t ph = (uint32_t)(kt / ST) & 1u;
         if (!mbar_wait(&full_bar[s], ph)) {
           atomicCAS(err, 0, MFIPM_TIMEOUT);
           ok = false;
@@ -235,11 +236,11 @@ bool make_map(CUtensorMap* map, const void* base, int64_t rows, int64_t K, int b
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <int BN>
+template <int BN, int ST>
 cudaError_t launch_bn(const CUtensorMap& ma, const CUtensorMap& mb, float* C, int rows, int N, int K, int splits,
                       int kt_per, int* err, cudaStream_t st) {
-  const size_t smem = 1024 + (size_t)kStages * (kTileA + BN * kBK * 2);
-  auto kern = tc_gemm_kernel<BN>;
+  const size_t smem = 1024 + (size_t)ST * (kTileA + BN * kBK * 2);
+  auto kern = tc_gemm_kernel<BN, ST>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e) return e;
   kern<<<dim3((unsigned)((rows + kBM - 1) / kBM), (unsigned)splits), kThreadsTc, smem, st>>>(ma, mb, C, rows, N, K,
@@ -260,17 +261,25 @@ int tc_gemm_splits(int rows, int K, int num_sms) {
 }
 
 cudaError_t tc_gemm(const void* Aop, const void* Bop, float* C, int rows, int N, int K, int splits, int* err,
-                    cudaStream_t st) {
+                    cudaStream_t st, int stages) {
   const int bn = N <= 32 ? 32 : N <= 64 ? 64 : N <= 128 ? 128 : 256;
   CUtensorMap ma, mb;
   if (!tc::make_map(&ma, Aop, rows, K, tc::kBM) || !tc::make_map(&mb, Bop, N, K, bn)) return cudaErrorInvalidValue;
   const int kt = (K + tc::kBK - 1) / tc::kBK;
   const int kt_per = (kt + splits - 1) / splits;
+  if (stages == 3) {
+    switch (bn) {
+      case 32: return tc::launch_bn<32, 3>(ma, mb, C, rows, N, K, splits, kt_per, err, st);
+      case 64: return tc::launch_bn<64, 3>(ma, mb, C, rows, N, K, splits, kt_per, err, st);
+      case 128: return tc::launch_bn<128, 3>(ma, mb, C, rows, N, K, splits, kt_per, err, st);
+      default: return tc::launch_bn<256, 3>(ma, mb, C, rows, N, K, splits, kt_per, err, st);
+    }
+  }
   switch (bn) {
-    case 32: return tc::launch_bn<32>(ma, mb, C, rows, N, K, splits, kt_per, err, st);
-    case 64: return tc::launch_bn<64>(ma, mb, C, rows, N, K, splits, kt_per, err, st);
-    case 128: return tc::launch_bn<128>(ma, mb, C, rows, N, K, splits, kt_per, err, st);
-    default: return tc::launch_bn<256>(ma, mb, C, rows, N, K, splits, kt_per, err, st);
+    case 32: return tc::launch_bn<32, 4>(ma, mb, C, rows, N, K, splits, kt_per, err, st);
+    case 64: return tc::launch_bn<64, 4>(ma, mb, C, rows, N, K, splits, kt_per, err, st);
+    case 128: return tc::launch_bn<128, 4>(ma, mb, C, rows, N, K, splits, kt_per, err, st);
+    default: return tc::launch_bn<256, 4>(ma, mb, C, rows, N, K, splits, kt_per, err, st);
   }
 }
 
