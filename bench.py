@@ -262,12 +262,13 @@ def run_ours(args, rank, world, local_rank):
         torch.distributed.barrier()
     torch.cuda.synchronize()
     with ClockSampler(local_rank) as clk:
-        for _ in range(args.steps):
+        for s_ in range(args.steps):
             flush.fill_(1)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            xs, infos = step()
-            e1.record(stream)
+            with RooflineRange(s_ == args.steps - 1):
+                e0.record(stream)
+                xs, infos = step()
+                e1.record(stream)
             torch.cuda.synchronize()
             step_ms.append(e0.elapsed_time(e1))
             kern_ms.append(L.mfipm_last_kernel_ms())
@@ -327,12 +328,8 @@ def run_ours(args, rank, world, local_rank):
     abytes = algorithmic_bytes(probs, infos)
     achieved = abytes / (kms / 1e3) / 1e9
     obytes = operator_bytes(probs, infos)
-    traffic = None
-    tpath = os.path.join(ROOT, "profiles", "traffic.json")
-    if os.path.exists(tpath):
-        tj = json.load(open(tpath)).get(args.workload)
-        if tj and tj.get("kernel_hash") == kernel_hash():
-            traffic = tj.get("bytes_per_launch")
+    tj = load_traffic(args.workload)
+    traffic = tj["bytes_per_launch"] if tj and tj.get("problems") == len(probs) else None
     if rank != 0:
         return
     cpu = None
@@ -393,12 +390,13 @@ def run_dense(args, rank, world, local_rank, probs):
     L.mfipm_set_timing(1)
     step_ms, kern_ms = [], []
     with ClockSampler(local_rank) as clk:
-        for _ in range(args.steps):
+        for s_ in range(args.steps):
             flush.fill_(1)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            x, info = M.solve(op, b, p0.tau, params, ws=ws)
-            e1.record(stream)
+            with RooflineRange(s_ == args.steps - 1):
+                e0.record(stream)
+                x, info = M.solve(op, b, p0.tau, params, ws=ws)
+                e1.record(stream)
             torch.cuda.synchronize()
             step_ms.append(e0.elapsed_time(e1))
             kern_ms.append(L.mfipm_last_kernel_ms())
@@ -409,6 +407,8 @@ def run_dense(args, rank, world, local_rank, probs):
     kms = statistics.mean(kern_ms)
     abytes = info["n_mat"] * p0.m * p0.n * 8
     peak, peak_kind = measured_peaks()
+    tj = load_traffic(args.workload)
+    traffic = tj["bytes_per_launch"] if tj else None
     # e2e: A and b from pinned host memory, x read back
     hA = torch.from_numpy(p0.A).pin_memory()
     hb = torch.from_numpy(p0.b).pin_memory()
@@ -447,7 +447,7 @@ def run_dense(args, rank, world, local_rank, probs):
         "config": {"workload": args.workload, "m": p0.m, "n": p0.n, "tol": params.tol,
                    "l2": "flushed (512 MiB write) before each step", "solved_at_kkt_1e-6": ok},
         "roofline": {"bound": "hbm", "achieved": abytes / (kms / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
-                     "frac": abytes / (kms / 1e3) / 1e9 / peak, "traffic": None, "peak_kind": peak_kind,
+                     "frac": abytes / (kms / 1e3) / 1e9 / peak, "traffic": traffic, "peak_kind": peak_kind,
                      "kernel": "ipm_kernel (dense float64, one cluster)", "kernel_ms": kms,
                      "algorithmic_bytes": abytes},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": (p0.A.size + p0.m) * 8,
@@ -539,12 +539,13 @@ def run_bf16(args, rank, world, local_rank, probs):
         gemm_pair()
     reps = 20
     g_ms = []
-    for _ in range(reps):
+    for r_ in range(reps):
         flush.fill_(1)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        gemm_pair()
-        e1.record(stream)
+        with RooflineRange(r_ == reps - 1):
+            e0.record(stream)
+            gemm_pair()
+            e1.record(stream)
         torch.cuda.synchronize()
         g_ms.append(e0.elapsed_time(e1))
     gms = statistics.median(g_ms)
@@ -553,6 +554,8 @@ def run_bf16(args, rank, world, local_rank, probs):
     gbytes = 2 * (m * n * 2) + 2 * R * (n + m) * 2 + (2 * R * m + 2 * R * n) * 4
     gflop = 2 * 2 * m * n * 2 * R
     peak, peak_kind = measured_peaks()
+    tj = load_traffic(args.workload)
+    traffic = tj["bytes_per_launch"] if tj and tj.get("splits") == [s1, s2] and tj.get("stages") == [g1, g2] else None
     if rank != 0:
         return
     cpu = None
@@ -574,7 +577,7 @@ def run_bf16(args, rank, world, local_rank, probs):
                              "stages1": tuning["stages1"], "stages2": tuning["stages2"],
                              "best_ms": tuning["best_ms"], "default_ms": tuning["default_ms"]}},
         "roofline": {"bound": "hbm", "achieved": gbytes / (gms / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
-                     "frac": gbytes / (gms / 1e3) / 1e9 / peak, "traffic": None, "peak_kind": peak_kind,
+                     "frac": gbytes / (gms / 1e3) / 1e9 / peak, "traffic": traffic, "peak_kind": peak_kind,
                      "kernel": "tc_gemm_kernel pair (T = A W, Y = A^T T), timed alone", "kernel_ms": gms,
                      "algorithmic_bytes": gbytes, "tensor_tflops": gflop / (gms / 1e3) / 1e12},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
@@ -631,12 +634,13 @@ def run_adjoint(args, rank, world, local_rank, probs):
     if world > 1:
         torch.distributed.barrier()
     with ClockSampler(local_rank) as clk:
-        for _ in range(args.steps):
+        for s_ in range(args.steps):
             flush.fill_(1)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            xs, infos, gbs, gts, binfos = step(bs, stats)
-            e1.record(stream)
+            with RooflineRange(s_ == args.steps - 1):
+                e0.record(stream)
+                xs, infos, gbs, gts, binfos = step(bs, stats)
+                e1.record(stream)
             torch.cuda.synchronize()
             step_ms.append(e0.elapsed_time(e1))
     L.mfipm_set_timing(0)
@@ -649,6 +653,11 @@ def run_adjoint(args, rank, world, local_rank, probs):
     launches = sum(s[3] for s in stats)
     peak, peak_kind = measured_peaks()
     achieved = op_bytes / (op_ms / 1e3) / 1e9
+    # the capture holds the first product of the step (every problem live); per product on
+    # average, its per-problem traffic times the problems a product served on average
+    tj = load_traffic(args.workload)
+    traffic = (tj["bytes_per_launch"] / tj["problems"] * (op_bytes / max(op_products, 1)) / (8.0 * probs[0].n)
+               if tj and tj.get("n") == probs[0].n else None)
 
     # e2e: host b, rows and x_hat in pinned memory; x and grad_b read back every step
     hb = [torch.from_numpy(p.b).pin_memory() for p in probs]
@@ -708,7 +717,7 @@ def run_adjoint(args, rank, world, local_rank, probs):
                    "l2": "inputs larger than L2 (about 4 GB of solver state) and a 512 MiB flush per step",
                    "solved_at_kkt_1e-6": ok},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": None, "peak_kind": peak_kind,
+                     "traffic": traffic, "peak_kind": peak_kind,
                      "kernel": "operator product y = A^T A w (pass_a + pass_b + pass_c, float32), "
                                "CUDA events inside the timed solves",
                      "kernel_ms": op_ms / max(op_products, 1), "products": op_products,
@@ -733,6 +742,37 @@ def kernel_hash():
     for f in sorted(os.listdir(d)):
         h.update(open(os.path.join(d, f), "rb").read())
     return h.hexdigest()[:12]
+
+
+def load_traffic(workload):
+    """DRAM bytes (read + write) that one ncu capture measured for this workload's roofline
+    kernel, kept only while the CUDA sources are the ones that were captured."""
+    tpath = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(tpath):
+        return None
+    tj = json.load(open(tpath)).get(workload)
+    if tj and tj.get("kernel_hash") == kernel_hash():
+        return tj
+    return None
+
+
+class RooflineRange:
+    """NVTX range "roofline" around the launches whose DRAM traffic the roofline reports
+    (ncu --nvtx --nvtx-include roofline/ captures exactly those)."""
+
+    def __init__(self, on):
+        self.on = on
+
+    def __enter__(self):
+        if self.on:
+            import torch
+            torch.cuda.nvtx.range_push("roofline")
+        return self
+
+    def __exit__(self, *a):
+        if self.on:
+            import torch
+            torch.cuda.nvtx.range_pop()
 
 
 def main():

@@ -155,3 +155,11 @@ def test_full_size_n_1m_certificates_and_derivative():
     ht = 1e-4 * p.tau
     fd_t = (L(p.tau + ht) - L(p.tau - ht)) / (2 * ht)
     assert abs(fd_t - gts[0]) <= 1e-3 * abs(fd_t) + 1e-9, (fd_t, gts[0])
+
+
+def test_no_measurements_gives_zero_multipass(threshold):
+    threshold(1024)
+    M = mf()
+    op = M.PartialDCT(2048, torch.zeros(0, dtype=torch.int64))
+    x, info = M.solve(op, torch.zeros(0, dtype=torch.float64), 0.1, M.SolverParams(tol=1e-12))
+    assert info["status"] == 0 and float(x.abs().max()) <= 1e-8 and info["kkt_rel"] <= 1e-8

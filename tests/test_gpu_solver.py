@@ -166,3 +166,11 @@ def test_dct_float64_outer_mode_matches_oracle_and_df_mode(n, G):
     assert info64["status"] == 0 and infodf["status"] == 0
     assert relx(x64, xo) <= RELX_TOL and relx(xdf, xo) <= RELX_TOL
     assert relx(xdf, x64) <= 1e-7
+
+
+def test_no_measurements_gives_zero():
+    """m = 0 (no sampled rows): the objective is tau ||x||_1, minimised by x = 0."""
+    M = mf()
+    op = M.PartialDCT(1024, torch.zeros(0, dtype=torch.int64))
+    x, info = M.solve(op, torch.zeros(0, dtype=torch.float64), 0.1, M.SolverParams(tol=1e-12))
+    assert info["status"] == 0 and float(x.abs().max()) <= 1e-8 and info["kkt_rel"] <= 1e-8
