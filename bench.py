@@ -555,7 +555,8 @@ def run_bf16(args, rank, world, local_rank, probs):
     gflop = 2 * 2 * m * n * 2 * R
     peak, peak_kind = measured_peaks()
     tj = load_traffic(args.workload)
-    traffic = tj["bytes_per_launch"] if tj and tj.get("splits") == [s1, s2] and tj.get("stages") == [g1, g2] else None
+    traffic = tj["bytes_per_launch"] if tj else None
+    traffic_cfg = {"splits": tj["splits"], "stages": tj["stages"]} if tj else None
     if rank != 0:
         return
     cpu = None
@@ -578,6 +579,7 @@ def run_bf16(args, rank, world, local_rank, probs):
                              "best_ms": tuning["best_ms"], "default_ms": tuning["default_ms"]}},
         "roofline": {"bound": "hbm", "achieved": gbytes / (gms / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
                      "frac": gbytes / (gms / 1e3) / 1e9 / peak, "traffic": traffic, "peak_kind": peak_kind,
+                     "traffic_config": traffic_cfg,
                      "kernel": "tc_gemm_kernel pair (T = A W, Y = A^T T), timed alone", "kernel_ms": gms,
                      "algorithmic_bytes": gbytes, "tensor_tflops": gflop / (gms / 1e3) / 1e12},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
