@@ -311,10 +311,12 @@ __global__ void __launch_bounds__(kThrB) pass_b(LdArgs a) {
     if (MODE != MODE_FORWARD) buf[it.pA] = nA;
   }
   if (MODE == MODE_FORWARD) return;
-  // block total of the masked energy (||A w||^2 or ||A x - b||^2)
-  double v = to_double(acc);
-  v = warp_sum(v);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  // block total of the masked energy (||A w||^2 or ||A x - b||^2): warp sums in the
+  // accumulator's own type (float32 or double-float, no float64 instruction per thread)
+  R wsum = acc;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) wsum = wsum + shfl_xor(wsum, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = to_double(wsum);
   __syncthreads();
   if (threadIdx.x == 0) {
     double t = 0.0;

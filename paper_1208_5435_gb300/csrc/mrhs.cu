@@ -42,14 +42,17 @@ __device__ __forceinline__ float2 precond2(float2 d, float2 r, float rho) {
 }
 
 // block sum of up to kPart values; thread 0 writes part[(col * nb + blk) * kPart + k]
-template <int K>
-__device__ __forceinline__ void block_partials(const double (&v)[K], double* part, int col, int nb, int blk) {
+// Per-block totals of K per-thread values: warp sums in the values' own type (float32 for
+// the positive sums of the float32 passes, so that no float64 instruction runs per thread),
+// the warps' totals in float64.
+template <int K, class V>
+__device__ __forceinline__ void block_partials(const V (&v)[K], double* part, int col, int nb, int blk) {
   __shared__ double red[kT / 32][K];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
   for (int k = 0; k < K; ++k) {
-    double w = warp_sum(v[k]);
-    if (lane == 0) red[warp][k] = w;
+    const V w = warp_sum(v[k]);
+    if (lane == 0) red[warp][k] = (double)w;
   }
   __syncthreads();
   if (threadIdx.x < K) {
@@ -58,16 +61,19 @@ __device__ __forceinline__ void block_partials(const double (&v)[K], double* par
     part[((int64_t)col * nb + blk) * kPart + threadIdx.x] = s;
   }
 }
-template <int K>
-__device__ __forceinline__ void block_minima(const double (&v)[K], double* part, int col, int nb, int blk) {
+__device__ __forceinline__ float vmin(float a, float b) { return fminf(a, b); }
+__device__ __forceinline__ double vmin(double a, double b) { return fmin(a, b); }
+// per-block minima (exact in any precision: the warp minima stay in the values' type)
+template <int K, class V>
+__device__ __forceinline__ void block_minima(const V (&v)[K], double* part, int col, int nb, int blk) {
   __shared__ double red[kT / 32][K];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
   for (int k = 0; k < K; ++k) {
-    double w = v[k];
+    V w = v[k];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) w = fmin(w, __shfl_xor_sync(0xffffffffu, w, o));
-    if (lane == 0) red[warp][k] = w;
+    for (int o = 16; o > 0; o >>= 1) w = vmin(w, __shfl_xor_sync(0xffffffffu, w, o));
+    if (lane == 0) red[warp][k] = (double)w;
   }
   __syncthreads();
   if (threadIdx.x < K) {
@@ -650,8 +656,7 @@ __global__ void k_update(Dev d, int first) {
     a[1] += st.u.hi + st.v.hi;
     a[2] += x.hi * x.hi;
   }
-  const double v[3] = {a[0], a[1], a[2]};
-  block_partials<3>(v, d.part, j, d.nb, blk);
+  block_partials<3>(a, d.part, j, d.nb, blk);
 }
 
 // sum of squares of a double-float vector, per block
@@ -663,7 +668,7 @@ __global__ void k_colnorm2_df(const float2* __restrict__ V, int len, double* par
     const float t = V[(int64_t)j * len + i].x;
     a = fmaf(t, t, a);
   }
-  const double v[1] = {a};
+  const float v[1] = {a};
   block_partials<1>(v, part, j, nb, blk);
 }
 
@@ -711,7 +716,7 @@ __global__ void k_pcg_init(Dev d, int corr) {
   const Steer sc = steer(c, d.prm.sigma3, false);
   const df tau = to_df(c.tau), ap1 = to_df(c.alpha_p1), ad1 = to_df(c.alpha_d1);
   const float s3mu = (float)(d.prm.sigma3 * c.mu_t);
-  double v[2] = {0, 0};
+  float v[2] = {0.f, 0.f};
   for (int i = blk * kIdx + threadIdx.x; i < min(d.n, (blk + 1) * kIdx); i += kT) {
     const int64_t gi = (int64_t)j * d.n + i;
     const St st = load_st(d.zs, gi);
@@ -749,8 +754,8 @@ __global__ void k_pcg_init(Dev d, int corr) {
       d.W[(int64_t)j * d.n + i] = wh;
       d.W[(int64_t)(d.R + j) * d.n + i] = __float2bfloat16_rn(w - __bfloat162float(wh));
     }
-    v[0] += (double)(r.x * p.x + r.y * p.y);
-    v[1] += (double)(dd.x * p.x * p.x + dd.y * p.y * p.y);
+    v[0] += r.x * p.x + r.y * p.y;
+    v[1] += dd.x * p.x * p.x + dd.y * p.y * p.y;
   }
   block_partials<2>(v, d.part, j, d.nb, blk);
 }
@@ -758,7 +763,7 @@ __global__ void k_pcg_init(Dev d, int corr) {
 // T = a_scale (C1_hi + C1_lo) -> bf16 hi/lo halves; partial ||T_j||^2 = ||A w_j||^2
 __global__ void k_split_t(Dev d, double* part2) {
   const int j = blockIdx.y, blk = blockIdx.x;
-  double v[1] = {0.0};
+  float v[1] = {0.f};
   const int per = (d.m + d.nb - 1) / d.nb;
   for (int i = blk * per + threadIdx.x; i < min(d.m, (blk + 1) * per); i += kT) {
     float acc = 0.f;
@@ -770,7 +775,7 @@ __global__ void k_split_t(Dev d, double* part2) {
     const __nv_bfloat16 th = __float2bfloat16_rn(t);
     d.Tb[(int64_t)j * d.m + i] = th;
     d.Tb[(int64_t)(d.R + j) * d.m + i] = __float2bfloat16_rn(t - __bfloat162float(th));
-    v[0] += (double)t * t;
+    v[0] += t * t;
   }
   block_partials<1>(v, part2, j, d.nb, blk);
 }
@@ -796,8 +801,11 @@ __global__ void k_alpha(Dev d, int first, const double* part2) {
 __global__ void __launch_bounds__(kT, 4) k_pcg_D(Dev d, float2* __restrict__ Xo, int first) {
   const int j = blockIdx.y, blk = blockIdx.x;
   const Col& c = d.col[j];
+  // a column whose PCG has stopped has alpha = 0: nothing would change (its partial is not
+  // read); on the first iteration every column writes its x = 0
+  if (!first && !c.active) return;
   const float alpha = c.alpha, rho = (float)c.rho, sc = (float)d.a_scale;
-  double v[1] = {0.0};
+  float v[1] = {0.f};
   for (int i = blk * kIdx + threadIdx.x; i < min(d.n, (blk + 1) * kIdx); i += kT) {
     const int64_t gi = (int64_t)j * d.n + i;
     float2 x = first ? make_float2(0.f, 0.f) : Xo[gi];
@@ -819,7 +827,7 @@ __global__ void __launch_bounds__(kT, 4) k_pcg_D(Dev d, float2* __restrict__ Xo,
     r.x -= alpha * (dd.x * p.x + y);
     r.y -= alpha * (dd.y * p.y - y);
     const float2 zz = precond2(dd, r, rho);
-    v[0] += (double)(r.x * zz.x + r.y * zz.y);
+    v[0] += r.x * zz.x + r.y * zz.y;
     Xo[gi] = x;
     d.Rv[gi] = r;
   }
@@ -847,8 +855,11 @@ __global__ void k_beta(Dev d, int k) {
 __global__ void k_pcg_E(Dev d) {
   const int j = blockIdx.y, blk = blockIdx.x;
   const Col& c = d.col[j];
+  // a stopped column keeps its direction and its partials go unread; the bf16 path still
+  // zeroes its GEMM input below
+  if (!c.active && d.op != OP_SHARED_BF16) return;
   const float beta = c.beta, rho = (float)c.rho;
-  double v[2] = {0, 0};
+  float v[2] = {0.f, 0.f};
   for (int i = blk * kIdx + threadIdx.x; i < min(d.n, (blk + 1) * kIdx); i += kT) {
     const int64_t gi = (int64_t)j * d.n + i;
     const float2 dd = d.Dv[gi], r = d.Rv[gi];
@@ -867,7 +878,7 @@ __global__ void k_pcg_E(Dev d) {
       d.W[(int64_t)j * d.n + i] = wh;
       d.W[(int64_t)(d.R + j) * d.n + i] = __float2bfloat16_rn(w - __bfloat162float(wh));
     }
-    v[1] += (double)(dd.x * p.x * p.x + dd.y * p.y * p.y);
+    v[1] += dd.x * p.x * p.x + dd.y * p.y * p.y;
   }
   block_partials<2>(v, d.part, j, d.nb, blk);
 }
@@ -891,8 +902,7 @@ __global__ void k_steps(Dev d, int corr) {
     if (du.ds < 0.f) v[1] = fminf(v[1], -st.su.hi * __frcp_rn(du.ds));
     if (dv.ds < 0.f) v[1] = fminf(v[1], -st.sv.hi * __frcp_rn(dv.ds));
   }
-  const double vd[2] = {v[0], v[1]};
-  block_minima<2>(vd, d.part, j, d.nb, blk);
+  block_minima<2>(v, d.part, j, d.nb, blk);
 }
 
 // one block of kT threads per column
@@ -947,7 +957,7 @@ __global__ void k_trial(Dev d) {
     d.X[gi] = f2(zu - zv);
     a += zu.hi * su.hi + zv.hi * sv.hi;
   }
-  const double v[1] = {a};
+  const float v[1] = {a};
   block_partials<1>(v, d.part, j, d.nb, blk);
 }
 

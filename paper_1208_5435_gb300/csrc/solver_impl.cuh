@@ -83,15 +83,30 @@ template <class R> __device__ __forceinline__ R cst(double v);
 template <> __device__ __forceinline__ float cst<float>(double v) { return (float)v; }
 template <> __device__ __forceinline__ double cst<double>(double v) { return v; }
 template <> __device__ __forceinline__ df cst<df>(double v) { return to_df(v); }
+// 2^e built from its exponent bits (|e| small), and 1/sqrt(2): exact or correctly rounded
+// constants without float64 arithmetic (a float64 division costs more here than the
+// float32 work of a pointwise block: the float64 pipe runs at a small fraction of FP32)
+template <class R> __device__ __forceinline__ R pow2(int e);
+template <> __device__ __forceinline__ float pow2<float>(int e) { return __int_as_float((127 + e) << 23); }
+template <> __device__ __forceinline__ double pow2<double>(int e) {
+  return __longlong_as_double((long long)(1023 + e) << 52);
+}
+template <> __device__ __forceinline__ df pow2<df>(int e) { return df(pow2<float>(e), 0.f); }
+template <class R> __device__ __forceinline__ R rsqrt2();
+template <> __device__ __forceinline__ float rsqrt2<float>() { return 0x1.6a09e6p-1f; }
+template <> __device__ __forceinline__ double rsqrt2<double>() { return 0.70710678118654752440; }
+template <> __device__ __forceinline__ df rsqrt2<df>() { return df(0x1.6a09e6p-1f, 0x1.9fcef4p-27f); }
+
+// N = 2^logN and L = N/2 are powers of two, so 1/L, 1/N and 2/N are exact
 template <class R> struct PwConst {
   R half, invL, a2_0, a2_j, rs2, zero;
   __device__ explicit PwConst(const DctGeom& geo)
-      : half(cst<R>(0.5)),
-        invL(cst<R>(1.0 / (double)((int64_t)1 << geo.logL))),
-        a2_0(cst<R>(1.0 / (double)geo.N)),
-        a2_j(cst<R>(2.0 / (double)geo.N)),
-        rs2(cst<R>(0.70710678118654752440)),
-        zero(cst<R>(0.0)) {}
+      : half(pow2<R>(-1)),
+        invL(pow2<R>(-geo.logL)),
+        a2_0(pow2<R>(-geo.logN)),
+        a2_j(pow2<R>(1 - geo.logN)),
+        rs2(rsqrt2<R>()),
+        zero() {}
 };
 __device__ __forceinline__ float load_bsu(const DctGeom&, int64_t, float) { return 0.f; }
 __device__ __forceinline__ double load_bsu(const DctGeom& g, int64_t i, double) { return g.bsu[i]; }
