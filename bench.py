@@ -155,6 +155,11 @@ def oracle_sample_problems(args):
     if args.workload == "dct_batch_256":
         probs = [p for p in W.make_workload("dct_batch_256") if p.n == 4096]
         return probs, "partial-DCT problems of the n=4096, m=1024 class of the 256-problem batch"
+    if W.WORKLOADS[args.workload]["kind"] == "phase":
+        cells = W.phase_cells()
+        probs = W.make_workload(args.workload)
+        pick = [j for j, (m, k) in enumerate(cells) if k == max(1, m // 10)]
+        return [probs[j] for j in pick], "trial 0 of the cells k = m/10 (m = 100..900) of the phase-transition grid"
     probs = W.make_workload(args.workload, count=2)
     return probs, f"first problems of {args.workload}"
 
@@ -233,6 +238,8 @@ def run_ours(args, rank, world, local_rank):
     B.build()
     L = M.lib()
     dev = torch.device("cuda", local_rank)
+    if W.WORKLOADS[args.workload]["kind"] == "phase":
+        return run_phase(args, rank, world, local_rank)
     probs = rank_problems(args.workload, rank, count=args.count)
     if probs[0].a_bf16 is not None:
         return run_bf16(args, rank, world, local_rank, probs)
@@ -363,6 +370,151 @@ def run_ours(args, rank, world, local_rank):
         "iterations": {"ipm_mean": statistics.mean(i["ipm_iters"] for i in infos),
                        "pcg_mean": statistics.mean(i["pcg_iters"] for i in infos),
                        "kkt_max": max(i["kkt_rel"] for i in infos)},
+    }
+    print(json.dumps(line), flush=True)
+
+
+PHASE_RE = 1e-5  # reconstruction counted as a success when ||x - x_hat|| / ||x_hat|| <= 1e-5 (Sec. 5.8)
+
+
+def phase_curve(cells, success):
+    """Per m: the largest k/m whose success fraction over the trials is >= 1/2 (Sec. 5.8)."""
+    out = {}
+    for (m, k), s in zip(cells, success):
+        if s >= 0.5:
+            out[m] = max(out.get(m, 0.0), k / m)
+    return {str(m): round(out.get(m, 0.0), 4) for m in sorted({m for m, _ in cells})}
+
+
+def run_phase(args, rank, world, local_rank):
+    """The phase-transition workload: one step = one mfipm_solve_batched call over one trial of
+    every (m, k) cell (4500 noiseless partial-DCT problems, n = 1024).  Each timed step solves
+    another trial (all trials resident in HBM before timing), so the steps also give the
+    empirical phase transition: per m, the largest k/m solved to r.e. <= 1e-5 in at least
+    half of the trials."""
+    import torch
+    import paper_1208_5435_gb300 as M
+
+    dev = torch.device("cuda", local_rank)
+    L = M.lib()
+    w = W.WORKLOADS[args.workload]
+    cells = W.phase_cells()[: args.count or None]
+    base = rank * RANK_STRIDE
+    trials = [W.make_workload(args.workload, count=args.count, offset=base + t) for t in range(args.steps)]
+    dev_trials = []
+    for probs in trials:
+        ops = [M.PartialDCT(p.n, torch.from_numpy(p.rows).to(dev)) for p in probs]
+        bs = [torch.from_numpy(p.b).to(dev) for p in probs]
+        dev_trials.append((ops, bs, [p.tau for p in probs]))
+    params = M.SolverParams()
+    ws = torch.empty(M.workspace_bytes(dev_trials[0][0], params), dtype=torch.uint8, device=dev)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+    ops0, bs0, taus0 = dev_trials[0]
+    tuning = M.autotune(ops0, bs0, taus0, params, ws=ws)[2]
+    for _ in range(args.warmup):
+        M.solve_batched(ops0, bs0, taus0, params, ws=ws)
+    torch.cuda.synchronize()
+    L.mfipm_set_timing(1)
+    step_ms, kern_ms, results = [], [], []
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local_rank) as clk:
+        for s_, (ops, bs, taus) in enumerate(dev_trials):
+            flush.fill_(1)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            with RooflineRange(s_ == args.steps - 1):
+                e0.record(stream)
+                xs, infos = M.solve_batched(ops, bs, taus, params, ws=ws)
+                e1.record(stream)
+            torch.cuda.synchronize()
+            step_ms.append(e0.elapsed_time(e1))
+            kern_ms.append(L.mfipm_last_kernel_ms())
+            results.append((xs, infos))
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    L.mfipm_set_timing(0)
+    ok = sum(1 for _, infos in results for i in infos if i["status"] == 0 and i["kkt_rel"] <= KKT_GATE)
+    value, total_ms = job_throughput(ok / args.steps, sum(step_ms), args.steps, world, dev)
+    ms_per_step = total_ms / args.steps
+    # reconstruction success per cell over this rank's trials (after the timed region)
+    succ = np.zeros(len(cells))
+    for probs, (xs, _) in zip(trials, results):
+        for j, (p, x) in enumerate(zip(probs, xs)):
+            xh = x.cpu().numpy()
+            succ[j] += np.linalg.norm(xh - p.x_hat) <= PHASE_RE * np.linalg.norm(p.x_hat)
+    succ_all = succ.copy()
+    if world > 1:
+        t = torch.from_numpy(succ_all).to(dev)
+        torch.distributed.all_reduce(t)
+        succ_all = t.cpu().numpy()
+    frac = succ_all / (args.steps * world)
+
+    # e2e: trial 0 through the public API from pinned host buffers, x read back
+    probs0 = trials[0]
+    hb = [torch.from_numpy(p.b).pin_memory() for p in probs0]
+    hr = [torch.from_numpy(p.rows).pin_memory() for p in probs0]
+    hx = [torch.empty(p.n, dtype=torch.float64).pin_memory() for p in probs0]
+    h2d = sum(t.numel() * 8 for t in hb) + sum(t.numel() * 8 for t in hr)
+    d2h = sum(t.numel() * 8 for t in hx)
+    e2e_ms = []
+    for it in range(1 + args.steps):
+        flush.fill_(1)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        dops = [M.PartialDCT(p.n, r.to(dev, non_blocking=True)) for p, r in zip(probs0, hr)]
+        dbs = [b_.to(dev, non_blocking=True) for b_ in hb]
+        xs_, inf_ = M.solve_batched(dops, dbs, taus0, params, ws=ws)
+        for h, d in zip(hx, xs_):
+            h.copy_(d, non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if it >= 1:
+            e2e_ms.append(e0.elapsed_time(e1))
+    e2e_ok = sum(1 for i in inf_ if i["status"] == 0 and i["kkt_rel"] <= KKT_GATE)
+    e2e_value, _ = job_throughput(e2e_ok, sum(e2e_ms), args.steps, world, dev)
+
+    peak, peak_kind = measured_peaks()
+    infos_last = results[-1][1]
+    kms = kern_ms[-1]
+    abytes = algorithmic_bytes(trials[-1], infos_last)
+    tj = load_traffic(args.workload)
+    traffic = tj["bytes_per_launch"] if tj and tj.get("problems") == len(cells) else None
+    if rank != 0:
+        return
+    cpu = None
+    if not args.no_cpu and world == 1:
+        sp, desc = oracle_sample_problems(args)
+        d, s = time_oracle(sp, 15.0)
+        cpu = {"value": d / s, "unit": UNIT, "cores": cpu_threads(), "kind": "oracle",
+               "sample": f"{d} problem(s) in {s:.1f} s: {desc}; direct-solve float64 IPM, tol 1e-10"}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32 PCG / f64 IPM", "data": "synthetic",
+        "config": {"workload": args.workload, "problems": len(cells), "n": w["n"],
+                   "cells": "m = 100..900 step 100, k = 1..m", "tau": "1e-6 ||A^T b||_inf, noiseless b",
+                   "trials": args.steps * world, "tol": params.tol,
+                   "l2": "flushed (512 MiB write) before each step", "solved_at_kkt_1e-6": ok,
+                   "tuned": {"cluster_size": tuning["cluster_size"], "cta_max_n": tuning["cta_max_n"],
+                             "candidates": tuning["candidates"]}},
+        "roofline": {"bound": "hbm", "achieved": abytes / (kms / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
+                     "frac": abytes / (kms / 1e3) / 1e9 / peak, "traffic": traffic, "peak_kind": peak_kind,
+                     "kernel": "ipm_kernel (persistent, one CTA per problem)", "kernel_ms": kms,
+                     "algorithmic_bytes": abytes},
+        "phase_transition": {"success_re": PHASE_RE, "k_over_m_at_50pct": phase_curve(cells, frac),
+                             "successes": int(succ_all.sum()), "solves": len(cells) * args.steps * world,
+                             "processed_per_s": len(cells) * world / (ms_per_step / 1e3)},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "cpu_baseline": cpu,
+        "gpu_launches": 4 * args.steps,
+        "clocks": clk.summary(),
+        "iterations": {"ipm_mean": statistics.mean(i["ipm_iters"] for i in infos_last),
+                       "pcg_mean": statistics.mean(i["pcg_iters"] for i in infos_last),
+                       "kkt_max": max(i["kkt_rel"] for i in infos_last)},
     }
     print(json.dumps(line), flush=True)
 

@@ -16,7 +16,7 @@ Operators:
   * the dense ensemble quantised to bf16 with one per-tensor scale: the problem's matrix is
     exactly  a_scale * bf16(A / a_scale)
 
-The named workloads mirror the five benchmark configurations of this project
+The named workloads mirror the benchmark configurations of this project
 (sizes in the docstrings of ``WORKLOADS``).  Random streams: numpy PCG64 seeded
 with the SeedSequence ``[seed, j]`` for problem ``j`` of a workload.
 """
@@ -30,7 +30,7 @@ import scipy.fft
 
 __all__ = [
     "Problem", "dense_problem", "dct_problem", "bf16_dense_problems", "WORKLOADS",
-    "make_workload", "bf16_round", "dct_apply", "dct_apply_t",
+    "make_workload", "bf16_round", "dct_apply", "dct_apply_t", "phase_cells", "phase_problems",
 ]
 
 
@@ -145,7 +145,27 @@ WORKLOADS = {
     # 32 partial-DCT problems n=2^20, m=2^18, k=n/100 N(0,1)
     "dct_adjoint_32x1M": dict(kind="dct", n=1 << 20, m=1 << 18, k=(1 << 20) // 100, values="normal",
                               seed=1005, count=32),
+    # the empirical phase transition of Sec. 5.8: noiseless partial DCT, m = 100..900 step 100,
+    # k = 1..m step 1, +-1 spikes; one problem per (m, k) cell per trial (4500 per trial), n =
+    # 1024 in place of the paper's 1000 (a power of two for the radix-2 DCT), tau = 1e-6
+    # ||A^T b||_inf (the paper states no tau for this experiment; see phase_problems)
+    "phase_transition_1024": dict(kind="phase", n=1024, seed=1006, trials=100, tau_frac=1e-6),
 }
+
+
+def phase_cells():
+    """(m, k) of every cell of the phase-transition grid, m-major."""
+    return [(m, k) for m in range(100, 901, 100) for k in range(1, m + 1)]
+
+
+def phase_problems(n: int, seed: int, trial: int, tau_frac: float, count: Optional[int] = None):
+    """Trial ``trial`` of every phase-transition cell: m random rows of the orthonormal n-point
+    DCT-II, k-sparse +-1 x_hat at random positions, b = A x_hat exactly (no noise).  Problem j
+    of trial t draws from the stream [seed, t * 4500 + j]."""
+    cells = phase_cells()[: count or None]
+    base = trial * len(phase_cells())
+    return [dct_problem(n, m, k, seed, base + j, sigma=0.0, tau_frac=tau_frac, values="pm1")
+            for j, (m, k) in enumerate(cells)]
 
 
 def batch_sizes(count: int, seed: int):
@@ -182,4 +202,7 @@ def make_workload(name: str, count: Optional[int] = None, scale_n: Optional[int]
         return [dct_problem(n, m, k, w["seed"], offset + j) for j, (n, m, k) in enumerate(sizes)]
     if w["kind"] == "bf16":
         return bf16_dense_problems(w["m"], w["n"], w["k"], count or w["nrhs"], w["seed"], first=offset)
+    if w["kind"] == "phase":
+        # offset selects the trial (another GPU's shard is another set of trials)
+        return phase_problems(w["n"], w["seed"], offset, w["tau_frac"], count)
     raise KeyError(name)
