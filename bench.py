@@ -164,13 +164,13 @@ def oracle_sample_problems(args):
     return probs, f"first problems of {args.workload}"
 
 
-def time_oracle(probs, budget_s):
+def time_oracle(probs, budget_s, tol=1e-10):
     from oracle import mfipm_oracle as O
     t0 = time.perf_counter()
     done = 0
     for p in probs:
         op = O.Operator.from_dense(p.A) if p.kind == "dense" else O.Operator.from_dct_rows(p.n, p.rows)
-        O.ipm(op, p.b, p.tau, O.OracleParams(tol=1e-10))
+        O.ipm(op, p.b, p.tau, O.OracleParams(tol=tol))
         done += 1
         if time.perf_counter() - t0 > budget_s:
             break
@@ -189,11 +189,12 @@ def run_reference(args, rank, world):
     if rank != 0:
         return
     probs, desc = oracle_sample_problems(args)
+    tol = W.WORKLOADS[args.workload].get("tol", 1e-10)
     for _ in range(args.warmup):
-        time_oracle(probs[:1], 1e9)
+        time_oracle(probs[:1], 1e9, tol)
     done, secs = 0, 0.0
     for _ in range(args.steps):
-        d, s = time_oracle(probs[:1], 1e9)
+        d, s = time_oracle(probs[:1], 1e9, tol)
         done += d
         secs += s
     value = done / secs
@@ -202,7 +203,7 @@ def run_reference(args, rank, world):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": args.workload, "sample": desc},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cpu_threads(), "kind": "oracle",
-                             "sample": f"1 problem per step: {desc}; direct-solve float64 IPM, tol 1e-10"},
+                             "sample": f"1 problem per step: {desc}; direct-solve float64 IPM, tol {tol:g}"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -406,7 +407,7 @@ def run_phase(args, rank, world, local_rank):
         ops = [M.PartialDCT(p.n, torch.from_numpy(p.rows).to(dev)) for p in probs]
         bs = [torch.from_numpy(p.b).to(dev) for p in probs]
         dev_trials.append((ops, bs, [p.tau for p in probs]))
-    params = M.SolverParams()
+    params = M.SolverParams(tol=w["tol"])
     ws = torch.empty(M.workspace_bytes(dev_trials[0][0], params), dtype=torch.uint8, device=dev)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
@@ -488,9 +489,9 @@ def run_phase(args, rank, world, local_rank):
     cpu = None
     if not args.no_cpu and world == 1:
         sp, desc = oracle_sample_problems(args)
-        d, s = time_oracle(sp, 15.0)
+        d, s = time_oracle(sp, 15.0, w["tol"])
         cpu = {"value": d / s, "unit": UNIT, "cores": cpu_threads(), "kind": "oracle",
-               "sample": f"{d} problem(s) in {s:.1f} s: {desc}; direct-solve float64 IPM, tol 1e-10"}
+               "sample": f"{d} problem(s) in {s:.1f} s: {desc}; direct-solve float64 IPM, tol {w['tol']:g}"}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",

@@ -42,7 +42,8 @@ extern "C" {
 typedef enum {
   MFIPM_OK = 0,
   MFIPM_INVALID_ARG = 1,    /* null pointer, m > n, bad DCT size or rows, tau <= 0, small workspace */
-  MFIPM_NOT_CONVERGED = 2,  /* max_iter reached; x and info are still written */
+  MFIPM_NOT_CONVERGED = 2,  /* max_iter reached, or the gap test passed while the KKT residual
+                               of x (info.kkt_rel) exceeds sqrt(tol); x and info are written */
   MFIPM_NUMERIC = 3,        /* NaN/Inf met in the data or during the iteration */
   MFIPM_CUDA = 4,           /* CUDA runtime error (message in mfipm_last_error) */
   MFIPM_TIMEOUT = 5,        /* a bounded device-side wait expired */
@@ -94,7 +95,8 @@ typedef struct {
 } mfipm_operator;
 
 typedef struct {
-  double tol;            /* relative duality gap z^T s / (1 + |P(z)|) to stop at (Sec. 5.4 "tol"); 1e-10 */
+  double tol;            /* relative duality gap z^T s / (1 + |P(z)|) to stop at (Sec. 5.4 "tol"); 1e-10.
+                            MFIPM_OK also needs kkt_rel <= sqrt(tol) at the stop */
   int32_t max_iter;      /* IPM iteration cap (Sec. 5.4 "maxiters"); 100 */
   double tol_pcg;        /* PCG tolerance (Sec. 5.4 "tolpcg") on the preconditioned residual norm
                             sqrt(r^T P^-1 r) relative to its initial value; 1e-2 */

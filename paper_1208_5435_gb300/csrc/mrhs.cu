@@ -1024,7 +1024,6 @@ __global__ void k_info(Dev d, mfipm_info* infos) {
                x2 = block_col_total(d.part, j, d.nb, 2);
   if (threadIdx.x) return;
   mfipm_info info{};
-  info.status = c.done ? c.stop : MFIPM_NOT_CONVERGED;
   info.ipm_iters = c.ipm_iters;
   info.correctors = c.correctors;
   info.pcg_iters = c.pcg_iters;
@@ -1032,6 +1031,9 @@ __global__ void k_info(Dev d, mfipm_info* infos) {
   info.rel_gap = c.rel_gap;
   info.dual_res = sqrt(fz2) / (1.0 + c.cn);
   info.kkt_rel = sqrt(kk2) / (1.0 + sqrt(x2));
+  // converged: the gap test (reading R7) and a KKT residual of x within sqrt(tol)
+  info.status = c.done ? c.stop : MFIPM_NOT_CONVERGED;
+  if (info.status == MFIPM_OK && !(info.kkt_rel <= sqrt(d.prm.tol))) info.status = MFIPM_NOT_CONVERGED;
   info.primal_obj = c.P_obj;
   infos[j] = info;
 }

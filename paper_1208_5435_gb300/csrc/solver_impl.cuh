@@ -982,7 +982,6 @@ __device__ void solve_one(const ProbDesc& pd, const KernelArgs& a, Op& op, RedSm
   cluster_reduce<G, 3>(rs, par, fin, [&](const double (&t)[3]) {
     if (op.rank == 0) {
       mfipm_info info{};
-      info.status = sh.stop == -1 ? MFIPM_OK : sh.stop;
       info.ipm_iters = its - 1;
       info.correctors = sh.correctors;
       info.pcg_iters = pcg_total;
@@ -990,6 +989,9 @@ __device__ void solve_one(const ProbDesc& pd, const KernelArgs& a, Op& op, RedSm
       info.rel_gap = sh.rel_gap;
       info.dual_res = sqrt(t[0]) / (1.0 + sh.cn);
       info.kkt_rel = sqrt(t[1]) / (1.0 + sqrt(t[2]));
+      // converged: the gap test (reading R7) and a KKT residual of x within sqrt(tol); the
+      // complementarity gap alone also shrinks on an iterate that has run away (|P| huge)
+      info.status = sh.stop != -1 ? sh.stop : (info.kkt_rel <= sqrt(prm.tol) ? MFIPM_OK : MFIPM_NOT_CONVERGED);
       info.primal_obj = sh.P_obj;
       *pd.info = info;
       if (info.status != MFIPM_OK) atomicCAS(a.err, 0, info.status);

@@ -37,7 +37,7 @@ def test_phase_cells_match_oracle():
     probs = _sample()
     ops = [M.PartialDCT(p.n, torch.from_numpy(p.rows)) for p in probs]
     xs, infos = M.solve_batched(ops, [torch.from_numpy(p.b) for p in probs], [p.tau for p in probs],
-                                M.SolverParams())
+                                M.SolverParams(tol=W.WORKLOADS["phase_transition_1024"]["tol"]))
     for p, x, info in zip(probs, xs, infos):
         op = O.Operator.from_dct_rows(p.n, p.rows)
         ref = O.ipm(op, p.b, p.tau, O.OracleParams(tol=1e-12)).x
@@ -50,9 +50,9 @@ def test_phase_cells_match_oracle():
             assert info["status"] == 0, (cell, info)
         if info["status"] == 0:
             assert O.kkt_rel(op, p.b, p.tau, xg) <= 1e-6, cell
-            # the solver stops at duality gap <= tol (1 + |P|), tol = 1e-10: a bound on the
-            # primal suboptimality (doubled for rounding)
+            # the solver stops at duality gap <= tol (1 + |P|), tol = 1e-12: a bound on the
+            # primal suboptimality (with room for the float64 rounding of both objectives)
             f_ref, f_gpu = O.objective(op, p.b, p.tau, ref), O.objective(op, p.b, p.tau, xg)
-            assert f_gpu - f_ref <= 2e-10 * (1 + abs(f_ref)), (cell, f_gpu, f_ref)
+            assert f_gpu - f_ref <= 1e-11 * (1 + abs(f_ref)), (cell, f_gpu, f_ref)
         else:
             assert info["status"] == 2, (cell, info)  # MFIPM_NOT_CONVERGED
