@@ -241,6 +241,8 @@ def run_ours(args, rank, world, local_rank):
     dev = torch.device("cuda", local_rank)
     if W.WORKLOADS[args.workload]["kind"] == "phase":
         return run_phase(args, rank, world, local_rank)
+    if W.WORKLOADS[args.workload]["kind"] == "scaling":
+        return run_scaling(args, rank, world, local_rank)
     probs = rank_problems(args.workload, rank, count=args.count)
     if probs[0].a_bf16 is not None:
         return run_bf16(args, rank, world, local_rank, probs)
@@ -516,6 +518,123 @@ def run_phase(args, rank, world, local_rank):
         "iterations": {"ipm_mean": statistics.mean(i["ipm_iters"] for i in infos_last),
                        "pcg_mean": statistics.mean(i["pcg_iters"] for i in infos_last),
                        "kkt_max": max(i["kkt_rel"] for i in infos_last)},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_scaling(args, rank, world, local_rank):
+    """PCG against a direct solver (Sec. 5.7): one Gaussian problem per n = 2^5..2^12 (m = n/4,
+    tau = 1e-3, noiseless).  One step = one mfipm_solve per size, in turn (float64 PCG in the
+    persistent kernel).  Beside each size: the IPM iterations of the oracle's float64 IPM with
+    exact (direct) Newton directions and its host time, the paper's comparison of iteration
+    counts and of time growth."""
+    import torch
+    import paper_1208_5435_gb300 as M
+
+    dev = torch.device("cuda", local_rank)
+    L = M.lib()
+    probs = rank_problems(args.workload, rank, count=args.count)
+    params = M.SolverParams()
+    ops = [M.Dense(torch.from_numpy(p.A).to(dev)) for p in probs]
+    bs = [torch.from_numpy(p.b).to(dev) for p in probs]
+    ws = torch.empty(max(M.workspace_bytes([o], params) for o in ops), dtype=torch.uint8, device=dev)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        for o, b_, p in zip(ops, bs, probs):
+            M.solve(o, b_, p.tau, params, ws=ws)
+    torch.cuda.synchronize()
+    L.mfipm_set_timing(1)
+    per = [[] for _ in probs]
+    kern_last, infos = [0.0] * len(probs), [None] * len(probs)
+    step_ms = []
+    if world > 1:
+        torch.distributed.barrier()
+    with ClockSampler(local_rank) as clk:
+        for s_ in range(args.steps):
+            flush.fill_(1)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            with RooflineRange(s_ == args.steps - 1):
+                e0.record(stream)
+                for j, (o, b_, p) in enumerate(zip(ops, bs, probs)):
+                    ej = torch.cuda.Event(enable_timing=True)
+                    ej.record(stream)
+                    x, infos[j] = M.solve(o, b_, p.tau, params, ws=ws)
+                    kern_last[j] = L.mfipm_last_kernel_ms()
+                    per[j].append((ej, torch.cuda.Event(enable_timing=True)))
+                    per[j][-1][1].record(stream)
+                e1.record(stream)
+            torch.cuda.synchronize()
+            step_ms.append(e0.elapsed_time(e1))
+    L.mfipm_set_timing(0)
+    ok = sum(1 for i in infos if i["status"] == 0 and i["kkt_rel"] <= KKT_GATE)
+    value, total_ms = job_throughput(ok, sum(step_ms), args.steps, world, dev)
+    ms_per_step = total_ms / args.steps
+    gpu_ms = [statistics.median(a.elapsed_time(b_) for a, b_ in ev) for ev in per]
+
+    # e2e: A and b of every size from pinned host memory, x read back
+    hA = [torch.from_numpy(p.A).pin_memory() for p in probs]
+    hb = [torch.from_numpy(p.b).pin_memory() for p in probs]
+    hx = [torch.empty(p.n, dtype=torch.float64).pin_memory() for p in probs]
+    e2e_ms = []
+    for it in range(1 + args.steps):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        e2e_ok = 0
+        for a_, b_, h, p in zip(hA, hb, hx, probs):
+            xe, ie = M.solve(M.Dense(a_.to(dev, non_blocking=True)), b_.to(dev, non_blocking=True), p.tau, params, ws=ws)
+            h.copy_(xe, non_blocking=True)
+            e2e_ok += ie["status"] == 0 and ie["kkt_rel"] <= KKT_GATE
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if it >= 1:
+            e2e_ms.append(e0.elapsed_time(e1))
+    e2e_value, _ = job_throughput(e2e_ok, sum(e2e_ms), args.steps, world, dev)
+    peak, peak_kind = measured_peaks()
+    big = len(probs) - 1
+    abytes = infos[big]["n_mat"] * probs[big].m * probs[big].n * 8
+    tj = load_traffic(args.workload)
+    traffic = tj["bytes_per_launch"] if tj else None
+    if rank != 0:
+        return
+    # the oracle with direct Newton solves, per size (host), within a bounded budget
+    rows, cpu = [], None
+    from oracle import mfipm_oracle as O
+    t_all, done = 0.0, 0
+    for j, p in enumerate(probs):
+        row = {"n": p.n, "m": p.m, "k": int(np.count_nonzero(p.x_hat)), "gpu_ms": gpu_ms[j],
+               "gpu_ipm_iters": infos[j]["ipm_iters"], "gpu_pcg_iters": infos[j]["pcg_iters"],
+               "gpu_kkt_rel": infos[j]["kkt_rel"]}
+        if not args.no_cpu and t_all < 20.0:
+            t0 = time.perf_counter()
+            r = O.ipm(O.Operator.from_dense(p.A), p.b, p.tau, O.OracleParams(tol=params.tol))
+            dt = time.perf_counter() - t0
+            t_all += dt
+            done += 1
+            # Newton directions taken (the oracle counts its gap checks, one more)
+            row.update({"direct_ipm_iters": r.iters - 1, "direct_host_ms": 1e3 * dt})
+        rows.append(row)
+    if done:
+        cpu = {"value": done / t_all, "unit": UNIT, "cores": cpu_threads(), "kind": "oracle",
+               "sample": f"{done} of the {len(probs)} sizes (smallest first) in {t_all:.1f} s: float64 IPM "
+                         f"with direct Newton solves, tol {params.tol:g}"}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "sizes": [p.n for p in probs], "m": "n/4", "k": "ceil(m/20)",
+                   "tau": probs[0].tau, "tol": params.tol, "l2": "flushed (512 MiB write) before each step",
+                   "solved_at_kkt_1e-6": ok},
+        "roofline": {"bound": "hbm", "achieved": abytes / (kern_last[big] / 1e3) / 1e9, "peak": peak,
+                     "unit": "GB/s", "frac": abytes / (kern_last[big] / 1e3) / 1e9 / peak, "traffic": traffic,
+                     "peak_kind": peak_kind, "kernel": f"ipm_kernel (dense float64), n = {probs[big].n}",
+                     "kernel_ms": kern_last[big], "algorithmic_bytes": abytes},
+        "pcg_vs_direct": rows,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": sum((p.A.size + p.m) * 8 for p in probs),
+                "d2h_bytes_per_step": sum(p.n * 8 for p in probs)},
+        "cpu_baseline": cpu, "gpu_launches": len(probs) * args.steps,  # one persistent launch per solve
+        "clocks": clk.summary(),
     }
     print(json.dumps(line), flush=True)
 

@@ -1,0 +1,30 @@
+"""The PCG-against-direct workload (Sec. 5.7) on the CPU: its generator, and the paper's
+observation on it at small sizes, checked with the oracle's two Newton solvers: PCG
+directions need about as many IPM iterations as exact (direct) ones."""
+import math
+
+import numpy as np
+
+import workloads as W
+from oracle import mfipm_oracle as O
+
+
+def test_sizes_and_problems():
+    probs = W.make_workload("pcg_vs_direct")
+    assert [p.n for p in probs] == [1 << e for e in range(5, 13)]
+    for p in probs:
+        assert p.m == p.n // 4 and p.A.shape == (p.m, p.n)
+        assert np.count_nonzero(p.x_hat) == math.ceil(p.m / 20)
+        assert p.tau == 1e-3
+        assert np.array_equal(p.A @ p.x_hat, p.b)  # noiseless
+        assert abs(p.A.var() * p.m - 1.0) < 0.2   # N(0, 1/m) entries
+
+
+def test_pcg_iterations_match_direct_at_small_sizes():
+    for p in W.make_workload("pcg_vs_direct", count=4):
+        op = O.Operator.from_dense(p.A)
+        direct = O.ipm(op, p.b, p.tau, O.OracleParams(tol=1e-10, solver="cholesky"))
+        pcg = O.ipm(op, p.b, p.tau, O.OracleParams(tol=1e-10, solver="pcg"))
+        assert direct.converged and pcg.converged
+        assert abs(direct.iters - pcg.iters) <= 2, (p.n, direct.iters, pcg.iters)
+        assert np.linalg.norm(direct.x - pcg.x) <= 1e-5 * np.linalg.norm(direct.x)

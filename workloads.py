@@ -31,6 +31,7 @@ import scipy.fft
 __all__ = [
     "Problem", "dense_problem", "dct_problem", "bf16_dense_problems", "WORKLOADS",
     "make_workload", "bf16_round", "dct_apply", "dct_apply_t", "phase_cells", "phase_problems",
+    "scaling_problems",
 ]
 
 
@@ -152,7 +153,24 @@ WORKLOADS = {
     # tolerance 1e-12: with objectives near tau ||x_hat||_1 ~ 1e-5, a relative gap of 1e-10
     # against 1 + |P| leaves x errors close to the 1e-5 success radius
     "phase_transition_1024": dict(kind="phase", n=1024, seed=1006, trials=100, tau_frac=1e-6, tol=1e-12),
+    # PCG against a direct solver (Sec. 5.7): Gaussian A, n = 2^5..2^12, m = n/4, k = ceil(m/20)
+    # N(0,1) values, noiseless b, tau = 1e-3; one problem per size
+    "pcg_vs_direct": dict(kind="scaling", seed=1007, log2n=(5, 12), tau=1e-3),
 }
+
+
+def scaling_problems(seed: int, log2n=(5, 12), tau: float = 1e-3, trial: int = 0):
+    """One Gaussian problem per n = 2^e (e in log2n, inclusive): A ~ N(0, 1/m), m = n/4,
+    k = ceil(m/20) N(0,1) spikes, b = A x_hat exactly, tau fixed.  Problem e of trial t draws
+    from the stream [seed, 100 t + e]."""
+    out = []
+    for e in range(log2n[0], log2n[1] + 1):
+        n = 1 << e
+        m = n // 4
+        k = -(-m // 20)
+        p = dense_problem(m, n, k, seed, 100 * trial + e, sigma=0.0, values="normal")
+        out.append(dataclasses.replace(p, tau=float(tau)))
+    return out
 
 
 def phase_cells():
@@ -204,6 +222,8 @@ def make_workload(name: str, count: Optional[int] = None, scale_n: Optional[int]
         return [dct_problem(n, m, k, w["seed"], offset + j) for j, (n, m, k) in enumerate(sizes)]
     if w["kind"] == "bf16":
         return bf16_dense_problems(w["m"], w["n"], w["k"], count or w["nrhs"], w["seed"], first=offset)
+    if w["kind"] == "scaling":
+        return scaling_problems(w["seed"], w["log2n"], w["tau"], offset)[: count or None]
     if w["kind"] == "phase":
         # offset selects the trial (another GPU's shard is another set of trials)
         return phase_problems(w["n"], w["seed"], offset, w["tau_frac"], count)
