@@ -28,3 +28,15 @@ def test_pcg_iterations_match_direct_at_small_sizes():
         assert direct.converged and pcg.converged
         assert abs(direct.iters - pcg.iters) <= 2, (p.n, direct.iters, pcg.iters)
         assert np.linalg.norm(direct.x - pcg.x) <= 1e-5 * np.linalg.norm(direct.x)
+
+
+def test_bp_limit_pcg_with_noiseless_settings():
+    """Tiny tau (Table regparams) with the paper's noiseless settings: the PCG variant of the
+    oracle agrees with its direct variant, and the solution approaches the sparse signal."""
+    p = W.dct_problem(1024, 256, 10, 1008, 0, sigma=0.0, values="pm1")
+    op = O.Operator.from_dct_rows(p.n, p.rows)
+    direct = O.ipm(op, p.b, 1e-10, O.OracleParams(tol=1e-14))
+    pcg = O.ipm(op, p.b, 1e-10, O.OracleParams(tol=1e-14, solver="pcg", tol_pcg=1e-6))
+    assert direct.converged and pcg.converged
+    assert np.linalg.norm(pcg.x - direct.x) <= 1e-6 * np.linalg.norm(direct.x)
+    assert np.linalg.norm(direct.x - p.x_hat) <= 1e-5 * np.linalg.norm(p.x_hat)
