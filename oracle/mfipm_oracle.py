@@ -29,6 +29,9 @@ library DCT):
   solve itself never uses PCG.
 * certificates: the prox (KKT) residual of the l1 problem and an l1 duality-gap
   certificate.
+* the operators: dense A, m rows of the orthonormal DCT-II (Sec. 2, Eq.
+  eq:orthonormality) and m rows of the orthonormal Haar matrix (Sec. 2), each
+  written out from its definition.
 
 Readings where the paper is silent or ambiguous (each also listed in the design doc):
   R1 objective has the 1/2 factor (the QP of Eq. wrightBPDN) although Eq.
@@ -81,6 +84,28 @@ def dct_matrix_rows(n: int, rows) -> np.ndarray:
     return alpha * np.cos(np.pi * arg.astype(np.float64) / (2.0 * n))
 
 
+def haar_matrix_rows(n: int, rows) -> np.ndarray:
+    """Rows of the orthonormal n x n Haar matrix (n a power of two), from its definition:
+    row 0 is the constant 1/sqrt(n); row 2^j + k (0 <= j < log2 n, 0 <= k < 2^j) is the
+    wavelet of scale j and position k, +2^(j/2)/sqrt(n) on [k n/2^j, (k + 1/2) n/2^j) and
+    -2^(j/2)/sqrt(n) on [(k + 1/2) n/2^j, (k + 1) n/2^j), zero elsewhere.  Sec. 2 names
+    Haar wavelets among the orthonormal systems whose random rows form CS matrices with
+    orthonormal rows (A A^T = I) and O(n) products."""
+    rows = np.asarray(rows, dtype=np.int64)
+    H = np.zeros((len(rows), n))
+    for r, i in enumerate(rows):
+        if i == 0:
+            H[r, :] = 1.0 / math.sqrt(n)
+            continue
+        j = int(i).bit_length() - 1
+        k = int(i) - (1 << j)
+        w = n >> j                      # support length n / 2^j
+        h = 2.0 ** (j / 2.0) / math.sqrt(n)
+        H[r, k * w: k * w + w // 2] = h
+        H[r, k * w + w // 2: (k + 1) * w] = -h
+    return H
+
+
 def dct_rows_apply(x: np.ndarray, rows: np.ndarray) -> np.ndarray:
     """A x for the partial DCT via the library DCT (large-n certificates only)."""
     return scipy.fft.dct(np.asarray(x, dtype=np.float64), type=2, norm="ortho")[rows]
@@ -102,6 +127,10 @@ class Operator:
     def from_dense(A: np.ndarray) -> "Operator":
         A = np.asarray(A, dtype=np.float64)
         return Operator(A.shape[0], A.shape[1], lambda x: A @ x, lambda y: A.T @ y, A)
+
+    @staticmethod
+    def from_haar_rows(n: int, rows) -> "Operator":
+        return Operator.from_dense(haar_matrix_rows(n, rows))
 
     @staticmethod
     def from_dct_rows(n: int, rows, explicit: bool = True) -> "Operator":

@@ -31,7 +31,7 @@ import scipy.fft
 __all__ = [
     "Problem", "dense_problem", "dct_problem", "bf16_dense_problems", "WORKLOADS",
     "make_workload", "bf16_round", "dct_apply", "dct_apply_t", "phase_cells", "phase_problems",
-    "scaling_problems",
+    "scaling_problems", "haar_apply", "haar_problem",
 ]
 
 
@@ -39,14 +39,14 @@ __all__ = [
 class Problem:
     """One seeded l1-LS instance.  ``A`` (dense, row-major m x n float64) or
     ``rows`` (partial DCT, sorted int64 row indices) describes the operator."""
-    kind: str                      # "dense" | "dct"
+    kind: str                      # "dense" | "dct" | "haar"
     m: int
     n: int
     b: np.ndarray                  # (m,) float64
     tau: float
     x_hat: np.ndarray              # (n,) float64, the sparse signal b was made from
     A: Optional[np.ndarray] = None     # dense: (m, n) float64 (already the exact problem matrix)
-    rows: Optional[np.ndarray] = None  # dct: (m,) int64 ascending
+    rows: Optional[np.ndarray] = None  # dct, haar: (m,) int64 ascending
     a_bf16: Optional[np.ndarray] = None  # bf16-quantised dense: (m, n) uint16 bit patterns
     a_scale: float = 1.0
     seed: tuple = ()
@@ -99,6 +99,48 @@ def dct_problem(n: int, m: int, k: int, seed: int, j: int = 0, sigma: float = 1e
     b = dct_apply(x_hat, rows) + sigma * rng.standard_normal(m)
     tau = tau_frac * float(np.abs(dct_apply_t(b, rows, n)).max())
     return Problem("dct", m, n, b, tau, x_hat, rows=rows, seed=(seed, j))
+
+
+def haar_apply(x: np.ndarray) -> np.ndarray:
+    """Orthonormal Haar coefficients of x (n a power of two), in the order: scaling
+    coefficient, then scale j = 0, 1, ... with positions k = 0 .. 2^j - 1 (index 2^j + k).
+    Pyramid of pairwise sums and differences / sqrt(2); used only to synthesise b."""
+    a = np.asarray(x, dtype=np.float64).copy()
+    details = []
+    while a.size > 1:
+        even, odd = a[0::2], a[1::2]
+        details.append((even - odd) / np.sqrt(2.0))
+        a = (even + odd) / np.sqrt(2.0)
+    return np.concatenate([a] + details[::-1])
+
+
+def haar_problem(n: int, m: int, k: int, seed: int, j: int = 0, sigma: float = 1e-3,
+                 tau_frac: float = 0.01, values: str = "normal") -> Problem:
+    """m random rows of the orthonormal n x n Haar matrix (uniform without replacement,
+    sorted), k-sparse x_hat, b = A x_hat + N(0, sigma^2), tau = tau_frac ||A^T b||_inf."""
+    rng = _rng(seed, j)
+    rows = np.sort(rng.choice(n, size=m, replace=False)).astype(np.int64)
+    x_hat = _sparse_signal(rng, n, k, values)
+    b = haar_apply(x_hat)[rows] + sigma * rng.standard_normal(m)
+    # A^T b: coefficients b at the sampled rows, inverse transform
+    full = np.zeros(n)
+    full[rows] = b
+    atb = _haar_inverse(full)
+    tau = tau_frac * float(np.abs(atb).max())
+    return Problem("haar", m, n, b, tau, x_hat, rows=rows, seed=(seed, j))
+
+
+def _haar_inverse(c: np.ndarray) -> np.ndarray:
+    a = c[:1].copy()
+    pos = 1
+    while pos < c.size:
+        d = c[pos: 2 * pos]
+        out = np.empty(2 * pos)
+        out[0::2] = (a + d) / np.sqrt(2.0)
+        out[1::2] = (a - d) / np.sqrt(2.0)
+        a = out
+        pos *= 2
+    return a
 
 
 def bf16_round(a: np.ndarray) -> np.ndarray:
