@@ -58,8 +58,15 @@ typedef enum {
  *                         two with 64 <= n <= 1048576: up to 65536 one thread-block
  *                         cluster holds a problem's FFT in shared memory; from 131072 the
  *                         problems of one length run in lockstep with a three-pass FFT
- *                         through device memory (see mfipm_set_large_dct_threshold). */
-typedef enum { MFIPM_OP_DENSE = 0, MFIPM_OP_PARTIAL_DCT = 1 } mfipm_op_kind;
+ *                         through device memory (see mfipm_set_large_dct_threshold).
+ *   MFIPM_OP_PARTIAL_HAAR: A = the rows `rows` of the orthonormal n x n Haar matrix (Sec. 2
+ *                         names Haar wavelets among the orthonormal systems with O(n)
+ *                         products): row 0 = 1/sqrt(n); row 2^j + k (0 <= j < log2 n,
+ *                         0 <= k < 2^j) = +-2^(j/2)/sqrt(n) on the two halves of
+ *                         [k n/2^j, (k+1) n/2^j).  A A^T = I_m.  n a power of two with
+ *                         64 <= n <= 65536 (one cluster); solve and solve_batched only, with
+ *                         precision MFIPM_PREC_FP32_PCG and the double-float outer loop. */
+typedef enum { MFIPM_OP_DENSE = 0, MFIPM_OP_PARTIAL_DCT = 1, MFIPM_OP_PARTIAL_HAAR = 2 } mfipm_op_kind;
 
 /* Storage type of a dense A. */
 typedef enum { MFIPM_A_F64 = 0, MFIPM_A_F32 = 1, MFIPM_A_BF16 = 2 } mfipm_a_dtype;
@@ -91,7 +98,7 @@ typedef struct {
   const void* A;         /* DEVICE, dense only: row-major, entry (i,j) = a_scale * A[i*lda + j] */
   double a_scale;        /* dense only; 1.0 for plain storage */
   int64_t lda;           /* dense only; >= n */
-  const int64_t* rows;   /* DEVICE, partial DCT only: m distinct row indices in [0, n), ascending */
+  const int64_t* rows;   /* DEVICE, partial DCT and Haar: m distinct row indices in [0, n), ascending */
 } mfipm_operator;
 
 typedef struct {

@@ -11,7 +11,7 @@ from typing import List, Optional, Sequence
 from . import _capi as C
 from ._capi import MfipmError, lib
 
-__all__ = ["Dense", "DenseBF16", "PartialDCT", "SolverParams", "solve", "solve_batched", "workspace_bytes",
+__all__ = ["Dense", "DenseBF16", "PartialDCT", "PartialHaar", "SolverParams", "solve", "solve_batched", "workspace_bytes",
            "apply_A", "apply_At", "kkt_residual", "autotune", "clear_tuning", "MfipmError", "lib"]
 
 
@@ -62,6 +62,25 @@ class PartialDCT:
     def c_op(self) -> C.Operator:
         op = C.Operator()
         op.kind, op.a_dtype, op.m, op.n = C.OP_PARTIAL_DCT, 0, self.m, self.n
+        op.A, op.a_scale, op.lda = None, 1.0, 0
+        op.rows = self.rows.data_ptr() if self.m else None
+        return op
+
+
+class PartialHaar:
+    """A = the sampled rows `rows` (int64, ascending, distinct) of the orthonormal n x n Haar
+    matrix: row 0 the constant 1/sqrt(n), row 2^j + k the wavelet of scale j, position k."""
+
+    def __init__(self, n: int, rows):
+        torch = _torch()
+        self.n = int(n)
+        self.rows = rows.to(device="cuda", dtype=torch.int64).contiguous()
+        self.m = int(self.rows.numel())
+        self.default_precision = C.PREC_FP32_PCG
+
+    def c_op(self) -> C.Operator:
+        op = C.Operator()
+        op.kind, op.a_dtype, op.m, op.n = C.OP_PARTIAL_HAAR, 0, self.m, self.n
         op.A, op.a_scale, op.lda = None, 1.0, 0
         op.rows = self.rows.data_ptr() if self.m else None
         return op

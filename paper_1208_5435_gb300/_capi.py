@@ -9,7 +9,7 @@ LIB_PATH = os.path.join(_PKG, "libmfipm.so")
 
 MFIPM_OK, MFIPM_INVALID_ARG, MFIPM_NOT_CONVERGED, MFIPM_NUMERIC, MFIPM_CUDA, MFIPM_TIMEOUT, MFIPM_UNSUPPORTED = range(7)
 STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "NOT_CONVERGED", 3: "NUMERIC", 4: "CUDA", 5: "TIMEOUT", 6: "UNSUPPORTED"}
-OP_DENSE, OP_PARTIAL_DCT = 0, 1
+OP_DENSE, OP_PARTIAL_DCT, OP_PARTIAL_HAAR = 0, 1, 2
 A_F64, A_F32, A_BF16 = 0, 1, 2
 PREC_FP64, PREC_FP32_PCG, PREC_BF16_A = 0, 1, 2
 OUTER_DF, OUTER_FP64 = 0, 1

@@ -77,6 +77,56 @@ __global__ void dct_rows_t_direct(const double* __restrict__ y, const int64_t* _
   for (int64_t i = 0; i < m; ++i) s = fma(dct_entry(rows[i], k, n), y[i], s);
   x[k] = s;
 }
+// Partial orthonormal Haar (row 0 = 1/sqrt(n); row 2^j + k = +-2^(j/2)/sqrt(n) on the halves
+// of [k n/2^j, (k+1) n/2^j)), evaluated directly from its definition: one warp per row for
+// A x; for A^T y each column sums its log2(n) + 1 rows, found by binary search in rows.
+__device__ __forceinline__ int ilog2_64(int64_t v) { return 63 - __clzll((unsigned long long)v); }
+__global__ void haar_rows_direct(const double* __restrict__ x, const int64_t* __restrict__ rows,
+                                 double* __restrict__ y, int64_t m, int64_t n) {
+  const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (i >= m) return;
+  const int64_t r = rows[i];
+  const double rn = rsqrt((double)n);
+  double s = 0.0;
+  if (r == 0) {
+    for (int64_t k = lane; k < n; k += 32) s += x[k];
+    s = warp_sum(s) * rn;
+  } else {
+    const int j = ilog2_64(r);
+    const int64_t w = n >> j, k0 = (r - ((int64_t)1 << j)) * w, h = w >> 1;
+    for (int64_t k = lane; k < w; k += 32) s += k < h ? x[k0 + k] : -x[k0 + k];
+    s = warp_sum(s) * rn * exp2(0.5 * j);
+  }
+  if (lane == 0) y[i] = s;
+}
+__global__ void haar_rows_t_direct(const double* __restrict__ y, const int64_t* __restrict__ rows,
+                                   double* __restrict__ x, int64_t m, int64_t n) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n) return;
+  const int logn = ilog2_64(n);
+  const double rn = rsqrt((double)n);
+  auto find = [&](int64_t idx) -> int64_t {  // position of idx in the ascending rows, or -1
+    int64_t lo = 0, hi = m;
+    while (lo < hi) {
+      const int64_t mid = (lo + hi) >> 1;
+      if (rows[mid] < idx) lo = mid + 1; else hi = mid;
+    }
+    return (lo < m && rows[lo] == idx) ? lo : -1;
+  };
+  double s = 0.0;
+  int64_t p = find(0);
+  if (p >= 0) s += y[p] * rn;
+  for (int j = 0; j < logn; ++j) {
+    const int64_t k = c >> (logn - j);
+    p = find(((int64_t)1 << j) + k);
+    if (p < 0) continue;
+    const bool upper = (c >> (logn - j - 1)) & 1;
+    const double v = rn * exp2(0.5 * j);
+    s += upper ? -y[p] * v : y[p] * v;
+  }
+  x[c] = s;
+}
 // rows ascending, distinct, inside [0, n): err = -1 otherwise
 __global__ void check_rows(const int64_t* __restrict__ rows, int64_t m, int64_t n, int* err) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
@@ -197,7 +247,7 @@ int apply_operator(int what, const mfipm_operator& op, const double* in, const d
   double* ybuf = static_cast<double*>(c.take((size_t)8 * (m > n ? m : n)));
   cudaError_t e;
   if ((e = cudaMemsetAsync(err, 0, 4, st))) return cu_fail(e, msg, "clear error word");
-  const bool dct = op.kind == MFIPM_OP_PARTIAL_DCT;
+  const bool dct = op.kind == MFIPM_OP_PARTIAL_DCT, haar = op.kind == MFIPM_OP_PARTIAL_HAAR;
   if (dct && n >= kLdMinN) {
     const LdShape s = ld_shape(n);
     const int log2_tw = s.logN + 2;
@@ -270,6 +320,8 @@ int apply_operator(int what, const mfipm_operator& op, const double* in, const d
     auto Ax = [&](const double* x, double* y) {
       if (dct) {
         ap::dct_rows_direct<<<grid_for(32 * m), ap::kT, 0, st>>>(x, op.rows, y, m, n);
+      } else if (haar) {
+        ap::haar_rows_direct<<<grid_for(32 * m), ap::kT, 0, st>>>(x, op.rows, y, m, n);
       } else {
         ap::gemv_rows<<<grid_for(32 * m), ap::kT, 0, st>>>(op.A, op.a_dtype, op.a_scale, op.lda, x, y, m, n);
       }
@@ -277,11 +329,13 @@ int apply_operator(int what, const mfipm_operator& op, const double* in, const d
     auto Aty = [&](const double* y, double* x) {
       if (dct) {
         ap::dct_rows_t_direct<<<grid_for(n), ap::kT, 0, st>>>(y, op.rows, x, m, n);
+      } else if (haar) {
+        ap::haar_rows_t_direct<<<grid_for(n), ap::kT, 0, st>>>(y, op.rows, x, m, n);
       } else {
         ap::gemv_cols<<<grid_for(n), ap::kT, 0, st>>>(op.A, op.a_dtype, op.a_scale, op.lda, y, x, m, n);
       }
     };
-    if (dct && m > 0) ap::check_rows<<<grid_for(m), ap::kT, 0, st>>>(op.rows, m, n, err);
+    if ((dct || haar) && m > 0) ap::check_rows<<<grid_for(m), ap::kT, 0, st>>>(op.rows, m, n, err);
     if (what == 0) {
       Ax(in, out);
     } else if (what == 1) {

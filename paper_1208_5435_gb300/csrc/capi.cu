@@ -100,6 +100,13 @@ int validate_op(const mfipm_operator* op, int idx) {
     if (op->m > 0 && !op->rows) return fail(MFIPM_INVALID_ARG, "operator %d: rows is NULL", idx);
     return MFIPM_OK;
   }
+  if (op->kind == MFIPM_OP_PARTIAL_HAAR) {
+    if (!is_pow2(op->n) || op->n < kDctMinN || op->n > kDctMaxN)
+      return fail(MFIPM_INVALID_ARG, "operator %d: partial Haar needs n a power of two in [%lld, %lld] (n=%lld)",
+                  idx, (long long)kDctMinN, (long long)kDctMaxN, (long long)op->n);
+    if (op->m > 0 && !op->rows) return fail(MFIPM_INVALID_ARG, "operator %d: rows is NULL", idx);
+    return MFIPM_OK;
+  }
   if (op->kind == MFIPM_OP_DENSE) {
     if (op->m > 0 && !op->A) return fail(MFIPM_INVALID_ARG, "operator %d: A is NULL", idx);
     if (op->lda < op->n) return fail(MFIPM_INVALID_ARG, "operator %d: lda < n", idx);
@@ -162,7 +169,8 @@ int dct_max_G(int64_t n) {
 size_t problem_bytes(const mfipm_operator& op, bool pcg64) {
   const size_t n = (size_t)op.n;
   size_t b = 0;
-  if (op.kind == MFIPM_OP_PARTIAL_DCT) b += align256(n) + 2 * align256(8 * n);  // mask, bsu, bsu_df
+  if (op.kind == MFIPM_OP_PARTIAL_DCT || op.kind == MFIPM_OP_PARTIAL_HAAR)
+    b += align256(n) + 2 * align256(8 * n);  // mask, bsu, bsu_df
   b += align256(32 * n);                                                     // z, s
   b += align256(5 * n * (pcg64 ? 16 : 8));                                   // x1 x2 r p d
   b += align256(8 * n);                                                      // scratch (apply)
@@ -206,7 +214,8 @@ bool pcg_in_fp64(const mfipm_operator& op, const mfipm_params* p) {
 }
 
 int pick_G(const std::vector<mfipm_operator>& ops, const mfipm_params* p, int batch) {
-  const bool dct = ops[0].kind == MFIPM_OP_PARTIAL_DCT;
+  // the Haar chain follows the DCT's rule: the same shared memory per value and cluster sizes
+  const bool dct = ops[0].kind == MFIPM_OP_PARTIAL_DCT || ops[0].kind == MFIPM_OP_PARTIAL_HAAR;
   int64_t max_n = 0, min_n = INT64_MAX;
   for (auto& o : ops) {
     max_n = std::max<int64_t>(max_n, o.n);
@@ -258,7 +267,7 @@ struct Prepared {
   std::vector<ProbDesc> desc;
   KernelArgs args;
   int G;
-  bool dct, pcg64;
+  bool dct, haar, pcg64;  // dct: a masked orthonormal operator (partial DCT or partial Haar)
   int64_t max_n, max_m;
   int64_t cta_max_n = 0;  // > 0: largest n solved by a single CTA (tuned), else the default rule
   char* ws;
@@ -283,13 +292,16 @@ int prepare(int batch, const mfipm_operator* ops, const double* const* b, const 
   for (int i = 0; i < batch; ++i)
     if (ops[i].kind == MFIPM_OP_DENSE && ops[i].a_dtype == MFIPM_A_BF16)
       return fail(MFIPM_UNSUPPORTED, "bf16 A is solved by the shared-A multi-RHS solver (precision MFIPM_PREC_BF16_A)");
-  P.dct = kind == MFIPM_OP_PARTIAL_DCT;
+  P.haar = kind == MFIPM_OP_PARTIAL_HAAR;
+  P.dct = kind == MFIPM_OP_PARTIAL_DCT || P.haar;
   for (int i = 0; i < batch; ++i)
     if (P.dct && ops[i].n > kDctMaxN)
       return fail(MFIPM_UNSUPPORTED, "operator %d: n=%lld above the cluster solver's %lld", i, (long long)ops[i].n,
                   (long long)kDctMaxN);
   if (P.dct && p->precision != MFIPM_PREC_FP32_PCG)
     return fail(MFIPM_UNSUPPORTED, "the partial-DCT solver runs its PCG in float32 (precision=%d)", p->precision);
+  if (P.haar && p->outer != MFIPM_OUTER_DF)
+    return fail(MFIPM_UNSUPPORTED, "the partial-Haar solver keeps its iterate in double-float (outer=%d)", p->outer);
   if (!P.dct && p->precision == MFIPM_PREC_BF16_A)
     return fail(MFIPM_UNSUPPORTED, "bf16 dense A goes through the shared-A multi-RHS solver");
   P.pcg64 = pcg_in_fp64(ops[0], p);
@@ -305,7 +317,7 @@ int prepare(int batch, const mfipm_operator* ops, const double* const* b, const 
     P.max_m = std::max<int64_t>(P.max_m, o.m);
   }
   P.G = pick_G(vops, p, batch);
-  if (P.dct && p->cluster_size == 0) {
+  if (P.dct && !P.haar && p->cluster_size == 0) {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tune_dct.find({P.max_n, ceil_log2i(batch)});
     if (it != g_tune_dct.end()) {
@@ -415,8 +427,9 @@ int run(Prepared& P, cudaStream_t st, int batch, mfipm_info* infos, const std::v
   }
   P.args.nbig = nbig;
   const bool f64 = P.args.prm.resid_fp64 != 0;
-  int maxc = P.dct ? (f64 ? max_active_clusters_dct_f64(P.G, P.max_n) : max_active_clusters_dct_df(P.G, P.max_n))
-                   : max_active_clusters_dense(P.G, P.pcg64, P.max_n, P.max_m);
+  int maxc = P.haar  ? max_active_clusters_haar(P.G, P.max_n)
+             : P.dct ? (f64 ? max_active_clusters_dct_f64(P.G, P.max_n) : max_active_clusters_dct_df(P.G, P.max_n))
+                     : max_active_clusters_dense(P.G, P.pcg64, P.max_n, P.max_m);
   if (maxc < 1) return fail(MFIPM_UNSUPPORTED, "no resident cluster of size %d fits this problem", P.G);
   const int clusters = std::min(maxc, std::max(nbig, (batch + P.G - 1) / P.G));
   if (timing) {
@@ -424,9 +437,10 @@ int run(Prepared& P, cudaStream_t st, int batch, mfipm_info* infos, const std::v
       if (!ev && (e = cudaEventCreate(&ev)) != cudaSuccess) return cuda_fail(e, "timing event");
     cudaEventRecord(g_ev[0], st);
   }
-  e = P.dct ? (f64 ? launch_dct_solver_f64(P.G, P.args, P.max_n, clusters, st)
-                   : launch_dct_solver_df(P.G, P.args, P.max_n, clusters, st))
-            : launch_dense_solver(P.G, P.pcg64, P.args, P.max_n, P.max_m, clusters, st);
+  e = P.haar  ? launch_haar_solver(P.G, P.args, P.max_n, clusters, st)
+      : P.dct ? (f64 ? launch_dct_solver_f64(P.G, P.args, P.max_n, clusters, st)
+                     : launch_dct_solver_df(P.G, P.args, P.max_n, clusters, st))
+              : launch_dense_solver(P.G, P.pcg64, P.args, P.max_n, P.max_m, clusters, st);
   if (e != cudaSuccess) return cuda_fail(e, "solver launch");
   if (timing) cudaEventRecord(g_ev[1], st);
   int err = 0;
@@ -732,6 +746,7 @@ int backward_persistent(int32_t batch, const mfipm_operator* ops, const double* 
   Prepared P;
   int rc = prepare(batch, ops, b, tau, p, const_cast<double* const*>(x), nullptr, workspace, ws_bytes, P);
   if (rc) return rc;
+  if (P.haar) return fail(MFIPM_UNSUPPORTED, "mfipm_backward is not built for the partial Haar operator");
   for (int i = 0; i < batch; ++i) {
     if (!zs[i] || !grad_x[i]) return fail(MFIPM_INVALID_ARG, "zs[%d] or grad_x[%d] is NULL", i, i);
     if (grad_A && grad_A[i] && ops[i].kind != MFIPM_OP_DENSE)

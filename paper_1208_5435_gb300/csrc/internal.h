@@ -76,6 +76,9 @@ size_t apply_workspace_bytes(const mfipm_operator& op);
 int apply_operator(int what, const mfipm_operator& op, const double* in, const double* b, double tau, double* out,
                    double* kkt, void* workspace, size_t ws_bytes, cudaStream_t st, std::string* msg);
 cudaError_t launch_dct_solver_df(int G, const KernelArgs& a, int64_t max_n, int grid_clusters, cudaStream_t st);
+cudaError_t launch_haar_solver(int G, const KernelArgs& a, int64_t max_n, int grid_clusters, cudaStream_t st);
+int max_active_clusters_haar(int G, int64_t max_n);
+size_t haar_smem_bytes(int G, int64_t max_n);
 cudaError_t launch_dct_solver_f64(int G, const KernelArgs& a, int64_t max_n, int grid_clusters, cudaStream_t st);
 cudaError_t launch_dense_solver(int G, bool fp64_pcg, const KernelArgs& a, int64_t max_n, int64_t max_m,
                                 int grid_clusters, cudaStream_t st);

@@ -21,7 +21,7 @@ __global__ void twiddle_kernel(double2* tw64, float2* tw32, float4* twdf, int lo
   }
 }
 
-// mask[j] = 1 and bsu[j] = b_i / alpha_j for j = rows[i]; validates rows.
+// mask[j] = 1 and bsu[j] = b_i / alpha_j (DCT) or b_i (Haar) for j = rows[i]; validates rows.
 __global__ void dct_setup_kernel(const ProbDesc* probs, int batch, int* err) {
   const ProbDesc pd = probs[blockIdx.y];
   const int64_t n = pd.n;
@@ -45,7 +45,9 @@ __global__ void dct_scatter_kernel(const ProbDesc* probs, int batch, int* err) {
     const double bi = pd.b ? pd.b[i] : 0.0;  // no b: the mask alone
     if (!isfinite(bi)) atomicCAS(err, 0, -2);
     pd.mask[r] = 1;
-    const double v = bi * (r == 0 ? sc0 : scj);
+    // the DCT chain works on the unnormalised transform (b over the row's scale); the Haar
+    // chain on the orthonormal coefficients themselves
+    const double v = pd.kind == MFIPM_OP_PARTIAL_HAAR ? bi : bi * (r == 0 ? sc0 : scj);
     pd.bsu[r] = v;
     const df vd = to_df(v);
     pd.bsu_df[r] = make_float2(vd.hi, vd.lo);

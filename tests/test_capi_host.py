@@ -194,3 +194,38 @@ def test_autotune_rejected_before_launch(L):
                             ctypes.byref(t), None) == C.MFIPM_INVALID_ARG
     assert t.path == 0
     assert L.mfipm_clear_tuning() == 0
+
+
+@pytest.mark.parametrize("case", ["n_not_pow2", "n_too_big", "n_too_small", "fp64_outer", "fp64_pcg", "null_rows",
+                                  "backward"])
+def test_partial_haar_rejected_before_launch(L, case):
+    from paper_1208_5435_gb300 import _capi as C
+    p = C.Params()
+    L.mfipm_params_default(ctypes.byref(p))
+    op = _dct_op(C, 4096, 1024)
+    op.kind = C.OP_PARTIAL_HAAR
+    ws, wsb = ctypes.c_void_p(0x10000), 1 << 40
+    if case == "n_not_pow2":
+        op.n = 3000
+    elif case == "n_too_big":
+        op.n, op.m = 1 << 17, 1 << 15
+    elif case == "n_too_small":
+        op.n, op.m = 32, 8
+    elif case == "fp64_outer":
+        p.outer = 1
+    elif case == "fp64_pcg":
+        p.precision = C.PREC_FP64
+    elif case == "null_rows":
+        op.rows = None
+    info = C.Info()
+    if case == "backward":
+        one = lambda v: (ctypes.c_void_p * 1)(v)
+        rc = L.mfipm_backward(1, ctypes.byref(op), one(0x3000), (ctypes.c_double * 1)(0.1), one(0x4000), one(0x5000),
+                              one(0x6000), one(0x7000), (ctypes.c_double * 1)(), None, ctypes.byref(p), ws, wsb,
+                              ctypes.byref(info), None)
+        assert rc == C.MFIPM_UNSUPPORTED, rc
+    else:
+        rc = L.mfipm_solve(ctypes.byref(op), ctypes.c_void_p(0x3000), 0.1, ctypes.byref(p), ctypes.c_void_p(0x4000),
+                           None, ws, wsb, ctypes.byref(info), None)
+        assert rc in (C.MFIPM_INVALID_ARG, C.MFIPM_UNSUPPORTED), (case, rc)
+    assert L.mfipm_last_error() and len(L.mfipm_last_error()) > 5

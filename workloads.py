@@ -31,7 +31,7 @@ import scipy.fft
 __all__ = [
     "Problem", "dense_problem", "dct_problem", "bf16_dense_problems", "WORKLOADS",
     "make_workload", "bf16_round", "dct_apply", "dct_apply_t", "phase_cells", "phase_problems",
-    "scaling_problems", "haar_apply", "haar_problem",
+    "scaling_problems", "haar_apply", "haar_apply_t", "haar_problem",
 ]
 
 
@@ -125,12 +125,13 @@ def haar_problem(n: int, m: int, k: int, seed: int, j: int = 0, sigma: float = 1
     # A^T b: coefficients b at the sampled rows, inverse transform
     full = np.zeros(n)
     full[rows] = b
-    atb = _haar_inverse(full)
+    atb = haar_apply_t(full)
     tau = tau_frac * float(np.abs(atb).max())
     return Problem("haar", m, n, b, tau, x_hat, rows=rows, seed=(seed, j))
 
 
-def _haar_inverse(c: np.ndarray) -> np.ndarray:
+def haar_apply_t(c: np.ndarray) -> np.ndarray:
+    """Inverse of haar_apply (the synthesis pyramid; the orthonormal Haar matrix transposed)."""
     a = c[:1].copy()
     pos = 1
     while pos < c.size:
