@@ -152,9 +152,9 @@ class ClockSampler:
 # ----------------------------------------------------------------------------- reference arm
 def oracle_sample_problems(args):
     """Smallest-class problems of the workload: the oracle's direct Newton solves grow with m^3."""
-    if args.workload == "dct_batch_256":
-        probs = [p for p in W.make_workload("dct_batch_256") if p.n == 4096]
-        return probs, "partial-DCT problems of the n=4096, m=1024 class of the 256-problem batch"
+    if args.workload in ("dct_batch_256", "haar_batch_256"):
+        probs = [p for p in W.make_workload(args.workload) if p.n == 4096]
+        return probs, f"problems of the n=4096, m=1024 class of {args.workload}"
     if W.WORKLOADS[args.workload]["kind"] == "phase":
         cells = W.phase_cells()
         probs = W.make_workload(args.workload)
@@ -169,7 +169,8 @@ def time_oracle(probs, budget_s, tol=1e-10):
     t0 = time.perf_counter()
     done = 0
     for p in probs:
-        op = O.Operator.from_dense(p.A) if p.kind == "dense" else O.Operator.from_dct_rows(p.n, p.rows)
+        op = (O.Operator.from_dense(p.A) if p.kind == "dense" else
+              O.Operator.from_haar_rows(p.n, p.rows) if p.kind == "haar" else O.Operator.from_dct_rows(p.n, p.rows))
         O.ipm(op, p.b, p.tau, O.OracleParams(tol=tol))
         done += 1
         if time.perf_counter() - t0 > budget_s:
@@ -250,7 +251,8 @@ def run_ours(args, rank, world, local_rank):
         return run_adjoint(args, rank, world, local_rank, probs)
     if probs[0].kind == "dense":
         return run_dense(args, rank, world, local_rank, probs)
-    ops = [M.PartialDCT(p.n, torch.from_numpy(p.rows).to(dev)) for p in probs]
+    Op = M.PartialHaar if probs[0].kind == "haar" else M.PartialDCT
+    ops = [Op(p.n, torch.from_numpy(p.rows).to(dev)) for p in probs]
     bs = [torch.from_numpy(p.b).to(dev) for p in probs]
     taus = [p.tau for p in probs]
     params = M.SolverParams()
@@ -320,7 +322,7 @@ def run_ours(args, rank, world, local_rank):
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        dops = [M.PartialDCT(p.n, r.to(dev, non_blocking=True)) for p, r in zip(probs, hr)]
+        dops = [Op(p.n, r.to(dev, non_blocking=True)) for p, r in zip(probs, hr)]
         dbs = [b_.to(dev, non_blocking=True) for b_ in hb]
         xs_, inf_ = M.solve_batched(dops, dbs, taus, params, ws=ws)
         for h, d in zip(hx, xs_):

@@ -196,6 +196,8 @@ WORKLOADS = {
     # tolerance 1e-12: with objectives near tau ||x_hat||_1 ~ 1e-5, a relative gap of 1e-10
     # against 1 + |P| leaves x errors close to the 1e-5 success radius
     "phase_transition_1024": dict(kind="phase", n=1024, seed=1006, trials=100, tau_frac=1e-6, tol=1e-12),
+    # the uneven batch of dct_batch_256 (same sizes and spikes) on partial Haar rows (Sec. 2)
+    "haar_batch_256": dict(kind="haar_batch", count=256, seed=1003),
     # PCG against a direct solver (Sec. 5.7): Gaussian A, n = 2^5..2^12, m = n/4, k = ceil(m/20)
     # N(0,1) values, noiseless b, tau = 1e-3; one problem per size
     "pcg_vs_direct": dict(kind="scaling", seed=1007, log2n=(5, 12), tau=1e-3),
@@ -263,6 +265,9 @@ def make_workload(name: str, count: Optional[int] = None, scale_n: Optional[int]
     if w["kind"] == "dct_batch":
         sizes = batch_sizes(w["count"], w["seed"])[: (count or w["count"])]
         return [dct_problem(n, m, k, w["seed"], offset + j) for j, (n, m, k) in enumerate(sizes)]
+    if w["kind"] == "haar_batch":
+        sizes = batch_sizes(w["count"], w["seed"])[: (count or w["count"])]
+        return [haar_problem(n, m, k, w["seed"], offset + j) for j, (n, m, k) in enumerate(sizes)]
     if w["kind"] == "bf16":
         return bf16_dense_problems(w["m"], w["n"], w["k"], count or w["nrhs"], w["seed"], first=offset)
     if w["kind"] == "scaling":
