@@ -192,9 +192,12 @@ def solve_batched(ops: Sequence, bs: Sequence, taus: Sequence[float], params: Op
     infos = (C.Info * B)()
     rc = lib().mfipm_solve_batched(B, arr, bp, tp, ctypes.byref(p), xp, zp, ws.data_ptr(), ws.numel(), infos,
                                    _stream_handle(stream))
-    if raise_on_failure:
-        C.check(rc, allow=(C.MFIPM_OK, C.MFIPM_NOT_CONVERGED))
     out = [i.as_dict() for i in infos]
+    # a problem of the batch that ended MFIPM_NUMERIC is reported in its info, like one that
+    # did not converge; anything else (bad arguments, CUDA errors, non-finite b) raises
+    per_problem = rc == C.MFIPM_NUMERIC and any(i["status"] == rc for i in out)
+    if raise_on_failure and not per_problem:
+        C.check(rc, allow=(C.MFIPM_OK, C.MFIPM_NOT_CONVERGED))
     return (xs, out, zss) if return_zs else (xs, out)
 
 
