@@ -89,3 +89,11 @@ def test_rank_zero_shard_is_the_single_gpu_workload():
     a = bench.rank_problems("dct_batch_256", 0, count=2)
     b = W.make_workload("dct_batch_256", count=2)
     assert all(np.array_equal(x.b, y.b) and np.array_equal(x.rows, y.rows) for x, y in zip(a, b))
+
+
+def test_phase_curve_takes_the_largest_half_successful_ratio():
+    import bench
+    cells = [(100, k) for k in range(1, 6)] + [(200, k) for k in range(1, 4)]
+    succ = [1.0, 1.0, 0.5, 0.25, 0.75, 1.0, 0.0, 0.0]
+    # per m: the largest k/m with a success fraction >= 1/2 (k = 5 for m = 100, k = 1 for m = 200)
+    assert bench.phase_curve(cells, succ) == {"100": 0.05, "200": 0.005}
