@@ -33,7 +33,7 @@ library DCT):
   eq:orthonormality) and m rows of the orthonormal Haar matrix (Sec. 2), each
   written out from its definition.
 
-Readings where the paper is silent or ambiguous (each also listed in the design doc):
+Readings where the paper is silent or ambiguous:
   R1 objective has the 1/2 factor (the QP of Eq. wrightBPDN) although Eq.
      formulationsnoisy1 prints it without;
   R2 rho = ||A||_F^2 / n (the Frobenius-closest multiple of I to A^T A; equals
