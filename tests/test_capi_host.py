@@ -229,3 +229,18 @@ def test_partial_haar_rejected_before_launch(L, case):
                            None, ws, wsb, ctypes.byref(info), None)
         assert rc in (C.MFIPM_INVALID_ARG, C.MFIPM_UNSUPPORTED), (case, rc)
     assert L.mfipm_last_error() and len(L.mfipm_last_error()) > 5
+
+
+def test_partial_haar_workspace_matches_dct(L):
+    """The Haar operator keeps the DCT's per-problem state (row mask, scattered b) and no more."""
+    from paper_1208_5435_gb300 import _capi as C
+    p = C.Params()
+    L.mfipm_params_default(ctypes.byref(p))
+    sizes = {}
+    for kind in (C.OP_PARTIAL_DCT, C.OP_PARTIAL_HAAR):
+        op = _dct_op(C, 8192, 2048)
+        op.kind = kind
+        nb = ctypes.c_size_t()
+        assert L.mfipm_workspace_size(ctypes.byref(op), 1, ctypes.byref(p), ctypes.byref(nb)) == 0
+        sizes[kind] = nb.value
+    assert sizes[C.OP_PARTIAL_HAAR] == sizes[C.OP_PARTIAL_DCT]
