@@ -232,7 +232,8 @@ def test_partial_haar_rejected_before_launch(L, case):
 
 
 def test_partial_haar_workspace_matches_dct(L):
-    """The Haar operator keeps the DCT's per-problem state (row mask, scattered b) and no more."""
+    """The Haar operator keeps the DCT's per-problem state (row mask 1 B, scattered b 16 B,
+    iterate 32 B, five PCG pairs 40 B, scratch 8 B per index) but needs no twiddle tables."""
     from paper_1208_5435_gb300 import _capi as C
     p = C.Params()
     L.mfipm_params_default(ctypes.byref(p))
@@ -243,4 +244,4 @@ def test_partial_haar_workspace_matches_dct(L):
         nb = ctypes.c_size_t()
         assert L.mfipm_workspace_size(ctypes.byref(op), 1, ctypes.byref(p), ctypes.byref(nb)) == 0
         sizes[kind] = nb.value
-    assert sizes[C.OP_PARTIAL_HAAR] == sizes[C.OP_PARTIAL_DCT]
+    assert 97 * 8192 <= sizes[C.OP_PARTIAL_HAAR] < sizes[C.OP_PARTIAL_DCT]
