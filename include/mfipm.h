@@ -191,7 +191,8 @@ int mfipm_solve_batched(int32_t batch, const mfipm_operator* ops, const double* 
  *   grad_x    DEVICE n.   grad_b DEVICE m or NULL.   grad_tau HOST (batch) or NULL.
  *   grad_A    DEVICE m x n row-major or NULL (dense operators only; MFIPM_UNSUPPORTED otherwise).
  * Arrays are HOST arrays of DEVICE pointers, as in mfipm_solve_batched; infos[i].pcg_iters and
- * n_mat count the work of each derivative. */
+ * n_mat count the work of each derivative.  Dense and partial-DCT operators; MFIPM_UNSUPPORTED
+ * for the partial Haar operator. */
 int mfipm_backward(int32_t batch, const mfipm_operator* ops, const double* const* b,
                    const double* tau, const double* const* x, const double* const* zs,
                    const double* const* grad_x, double* const* grad_b, double* grad_tau,
@@ -203,7 +204,8 @@ int mfipm_backward(int32_t batch, const mfipm_operator* ops, const double* const
  *   mfipm_apply_At:  x (DEVICE, n) = A^T y (y DEVICE, m)
  * float64 in and out (input and output must not overlap).  Partial DCT with n >= 1024: the
  * multi-pass FFT chain in double-float (about 2^-44 relative, Sec. 2's A = rows of the
- * orthonormal DCT-II); n < 1024 and dense A: direct float64 sums.  `workspace`: DEVICE,
+ * orthonormal DCT-II); n < 1024, partial Haar and dense A: direct float64 sums (a Haar row
+ * touches its support only; a column sums its log2(n) + 1 rows).  `workspace`: DEVICE,
  * 256-byte aligned, at least the bytes mfipm_workspace_size reports for this operator with
  * batch 1 (a bf16 A: with precision MFIPM_PREC_BF16_A); the caller owns it.  Synchronises
  * `stream`.  MFIPM_INVALID_ARG for NULL vectors, a small workspace or bad rows. */
