@@ -1027,23 +1027,25 @@ def run_adjoint(args, rank, world, local_rank, probs):
     print(json.dumps(line), flush=True)
 
 
-def kernel_hash():
+def kernel_hash(files=None):
+    """Hash of the CUDA sources (all of them, or the listed files that define one kernel)."""
     import hashlib
     h = hashlib.sha1()
     d = os.path.join(ROOT, "paper_1208_5435_gb300", "csrc")
-    for f in sorted(os.listdir(d)):
+    for f in sorted(files or os.listdir(d)):
         h.update(open(os.path.join(d, f), "rb").read())
     return h.hexdigest()[:12]
 
 
 def load_traffic(workload):
     """DRAM bytes (read + write) that one ncu capture measured for this workload's roofline
-    kernel, kept only while the CUDA sources are the ones that were captured."""
+    kernel, kept only while the CUDA sources are the ones that were captured (all of them, or
+    the entry's `sources`: the files that define the captured kernel)."""
     tpath = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(tpath):
         return None
     tj = json.load(open(tpath)).get(workload)
-    if tj and tj.get("kernel_hash") == kernel_hash():
+    if tj and tj.get("kernel_hash") == kernel_hash(tj.get("sources")):
         return tj
     return None
 
