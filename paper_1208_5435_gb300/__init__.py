@@ -194,8 +194,9 @@ def solve_batched(ops: Sequence, bs: Sequence, taus: Sequence[float], params: Op
                                    _stream_handle(stream))
     out = [i.as_dict() for i in infos]
     # a problem of the batch that ended MFIPM_NUMERIC is reported in its info, like one that
-    # did not converge; anything else (bad arguments, CUDA errors, non-finite b) raises
-    per_problem = rc == C.MFIPM_NUMERIC and any(i["status"] == rc for i in out)
+    # did not converge; anything else (bad arguments, CUDA errors, non-finite b: the calls
+    # that leave a message in mfipm_last_error) raises
+    per_problem = rc == C.MFIPM_NUMERIC and not C.last_error() and any(i["status"] == rc for i in out)
     if raise_on_failure and not per_problem:
         C.check(rc, allow=(C.MFIPM_OK, C.MFIPM_NOT_CONVERGED))
     return (xs, out, zss) if return_zs else (xs, out)
