@@ -97,3 +97,15 @@ def test_phase_curve_takes_the_largest_half_successful_ratio():
     succ = [1.0, 1.0, 0.5, 0.25, 0.75, 1.0, 0.0, 0.0]
     # per m: the largest k/m with a success fraction >= 1/2 (k = 5 for m = 100, k = 1 for m = 200)
     assert bench.phase_curve(cells, succ) == {"100": 0.05, "200": 0.005}
+
+
+@pytest.mark.parametrize("workload", sorted(__import__("workloads").WORKLOADS))
+def test_oracle_samples_stay_small(workload):
+    """The CPU-baseline and reference legs time the oracle's direct solve (an m x m Woodbury
+    factorisation per iteration): every workload's sample keeps m <= 4096 and n <= 16384 (a
+    full-size m = 16384 sample ran ~20 min)."""
+    import argparse
+    import bench
+    probs, desc = bench.oracle_sample_problems(argparse.Namespace(workload=workload))
+    assert probs and desc
+    assert max(p.m for p in probs) <= 4096 and max(p.n for p in probs) <= 16384, workload
