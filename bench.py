@@ -156,6 +156,8 @@ def oracle_sample_problems(args):
     if args.workload in ("dct_batch_256", "haar_batch_256"):
         probs = [p for p in W.make_workload(args.workload) if p.n == 4096]
         return probs, f"problems of the n=4096, m=1024 class of {args.workload}"
+    if W.WORKLOADS[args.workload]["kind"] == "scaling":
+        return W.make_workload(args.workload), "the whole size sweep n = 2^5 .. 2^12"
     if W.WORKLOADS[args.workload]["kind"] == "phase":
         cells = W.phase_cells()
         probs = W.make_workload(args.workload)
@@ -196,11 +198,13 @@ def run_reference(args, rank, world):
         return
     probs, desc = oracle_sample_problems(args)
     tol = W.WORKLOADS[args.workload].get("tol", 1e-10)
+    # one problem per step; the size sweep of pcg_vs_direct is one step as in the GPU leg
+    step = probs if W.WORKLOADS[args.workload]["kind"] == "scaling" else probs[:1]
     for _ in range(args.warmup):
-        time_oracle(probs[:1], 1e9, tol)
+        time_oracle(step, 1e9, tol)
     done, secs = 0, 0.0
     for _ in range(args.steps):
-        d, s = time_oracle(probs[:1], 1e9, tol)
+        d, s = time_oracle(step, 1e9, tol)
         done += d
         secs += s
     value = done / secs
@@ -209,7 +213,7 @@ def run_reference(args, rank, world):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": args.workload, "sample": desc},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cpu_threads(), "kind": "oracle",
-                             "sample": f"1 problem per step: {desc}; direct-solve float64 IPM, tol {tol:g}"},
+                             "sample": f"{len(step)} problem(s) per step: {desc}; direct-solve float64 IPM, tol {tol:g}"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
