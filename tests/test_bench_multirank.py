@@ -109,3 +109,21 @@ def test_oracle_samples_stay_small(workload):
     probs, desc = bench.oracle_sample_problems(argparse.Namespace(workload=workload))
     assert probs and desc
     assert max(p.m for p in probs) <= 4096 and max(p.n for p in probs) <= 16384, workload
+
+
+def test_reference_arm_line():
+    """bench.py --impl reference: the oracle on the host cores, one JSON line with the
+    contract's keys (impl, metric, value, unit, cpu_baseline, e2e with zero copies)."""
+    import json
+    import subprocess
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference", "--workload",
+                          "dense_fp64_256x1024", "--steps", "1", "--warmup", "0"], capture_output=True, text=True,
+                         timeout=300, cwd=root)
+    assert out.returncode == 0, out.stderr[-2000:]
+    line = json.loads(out.stdout.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["value"] > 0 and line["higher_is_better"] is True
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["value"] == line["value"]
+    assert line["e2e"] == {"value": line["value"], "unit": line["unit"], "h2d_bytes_per_step": 0,
+                           "d2h_bytes_per_step": 0}
+    assert line["config"]["workload"] == "dense_fp64_256x1024"
