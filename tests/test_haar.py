@@ -71,3 +71,37 @@ def test_haar_problem_generator():
     H = O.haar_matrix_rows(p.n, p.rows)
     assert np.abs(H @ p.x_hat - p.b).max() < 1e-12
     assert p.tau == pytest.approx(0.01 * np.abs(H.T @ p.b).max())
+
+
+def _mutant(kind):
+    """haar_matrix_rows with one plausible mistake planted."""
+    def rows_fn(n, rows):
+        H = np.zeros((len(rows), n))
+        for r, i in enumerate(rows):
+            if i == 0:
+                H[r, :] = 1.0 / math.sqrt(n)
+                continue
+            j = int(i).bit_length() - 1
+            k = int(i) - (1 << j)
+            if kind == "position" and j > 0:
+                k = (k + 1) % (1 << j)
+            w = n >> j
+            h = (2.0 ** j if kind == "scale" else 2.0 ** (j / 2.0)) / math.sqrt(n)
+            sgn = -1.0 if (kind == "sign" and j == 2) else 1.0
+            H[r, k * w: k * w + w // 2] = sgn * h
+            H[r, k * w + w // 2: (k + 1) * w] = -sgn * h
+        return H
+    return rows_fn
+
+
+@pytest.mark.parametrize("kind", ["scale", "sign", "position"])
+def test_pins_catch_planted_mistakes(kind, monkeypatch):
+    """Each planted mistake in the Haar rows fails at least one of the pins above."""
+    monkeypatch.setattr(O, "haar_matrix_rows", _mutant(kind))
+    caught = 0
+    for pin in (lambda: test_orthonormal_rows(64), test_closed_forms, lambda: test_pyramid_equals_matrix(32)):
+        try:
+            pin()
+        except AssertionError:
+            caught += 1
+    assert caught >= 1, kind
