@@ -197,6 +197,21 @@ def recover_ds(fs, z, d, dz):
     return fs / z - d * dz
 
 
+def corrector_direction(op: "Operator", b, tau, c, z, s, d, zt, st, sigma3, solve):
+    """The corrector of the Algorithm (Sec. 5.1), reading R6: the right-hand side of
+    Eq. fzfs is evaluated at the trial point (zt, st) = (z + alpha_P dz, s + alpha_D ds) with
+    sigma3 and the trial point's mu,
+        f_z~ = st - c - F F^T zt,   f_s~ = sigma3 mu~ e - Zt St e,   mu~ = zt^T st / (2n),
+    while the Newton matrix (through d = Theta^-1 = s / z) and the Z^-1 of Eqs.
+    redNewtonA/B stay those of the current iterate (z, s).  Returns (dz~, ds~); the Algorithm adds them to
+    the predictor and steps the sum from (z, s)."""
+    fzt, mut = residuals(op, b, tau, zt, st, c)
+    fst = complementarity_rhs(zt, st, sigma3, mut)
+    dz2 = solve(d, newton_rhs(fzt, fst, z))
+    ds2 = recover_ds(fst, z, d, dz2)
+    return dz2, ds2
+
+
 # --------------------------------------------------------------------------------------
 # Exact solves of (Theta^-1 + F F^T) dz = r   (Sec. 5.7 direct variant)
 # --------------------------------------------------------------------------------------
@@ -388,12 +403,7 @@ def ipm(op: Operator, b, tau, params: Optional[OracleParams] = None) -> OracleRe
         # corrector (R6)
         if aP <= p.alpha_tilde or aD <= p.alpha_tilde:
             corr += 1
-            zt = z + aP * dz
-            st = s + aD * ds
-            fzt, mut = residuals(op, b, tau, zt, st, c)
-            fst = complementarity_rhs(zt, st, p.sigma3, mut)
-            dz2 = solve(d, newton_rhs(fzt, fst, z))
-            ds2 = recover_ds(fst, z, d, dz2)
+            dz2, ds2 = corrector_direction(op, b, tau, c, z, s, d, z + aP * dz, s + aD * ds, p.sigma3, solve)
             dz = dz + dz2
             ds = ds + ds2
             aP, aD = steps(dz, ds)
@@ -430,14 +440,21 @@ def optimality_violation(op: Operator, b, tau, x, support_tol: float):
     return v_on, v_off
 
 
-def dual_gap_certificate(op: Operator, b, tau, x):
-    """Duality gap of the l1 problem at a dual-feasible point built from x:
-    nu = (A x - b) * min(1, tau / ||A^T(Ax-b)||_inf), D(nu) = -1/2||nu||^2 - b^T nu,
-    and 0 <= P(x) - P* <= P(x) - D(nu).  Returns (P(x), D(nu))."""
+def dual_point(op: Operator, b, tau, x):
+    """A dual-feasible point of the l1 problem built from x (the construction of the l1_ls
+    method the paper cites in Sec. 1): the residual r = A x - b scaled into the dual
+    feasible set {nu : ||A^T nu||_inf <= tau},  nu = r * min(1, tau / ||A^T r||_inf)."""
     r = op.mv(x) - b
-    g = op.rmv(r)
-    gi = float(np.abs(g).max())
-    nu = r * (min(1.0, tau / gi) if gi > 0 else 1.0)
+    gi = float(np.abs(op.rmv(r)).max()) if r.size else 0.0
+    return r * (min(1.0, tau / gi) if gi > 0 else 1.0)
+
+
+def dual_gap_certificate(op: Operator, b, tau, x):
+    """Duality gap of the l1 problem at the dual-feasible point nu = dual_point(x):
+    D(nu) = -1/2||nu||^2 - b^T nu is a lower bound on P* (weak duality), so
+    0 <= P(x) - P* <= P(x) - D(nu).  Returns (P(x), D(nu))."""
+    r = op.mv(x) - b
+    nu = dual_point(op, b, tau, x)
     P = tau * float(np.abs(x).sum()) + 0.5 * float(r @ r)
     D = -0.5 * float(nu @ nu) - float(b @ nu)
     return P, D

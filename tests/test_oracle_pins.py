@@ -2,6 +2,7 @@
 (a closed form, brute force, a textbook linear solve, a theorem of the paper, a library
 routine, or a value the paper prints).  The last group plants mistakes in the oracle and
 checks that some pin catches each one."""
+import dataclasses
 import itertools
 import json
 import math
@@ -169,6 +170,94 @@ def pin_pcg_one_iteration(seed=13, n=32):
     return it, float(np.abs(x - xd).max() / np.abs(xd).max()), abs(rho - 1.0)
 
 
+def pin_corrector_error(seed=19, m=3, n=6, aP=0.07, aD=0.04):
+    """One corrector step of the Algorithm (Sec. 5.1) at a fixed interior (z, s), against the
+    4n x 4n block system of Eq. sepregaugeq solved by a textbook dense solver.  The predictor
+    solves K [dz; ds] = [f_z; f_s] with K = [[F F^T, -I], [S, Z]] at (z, s); under reading R6
+    the corrector solves the same K for the residuals of Eq. fzfs at the trial point
+    (z + aP dz, s + aD ds) with sigma3 and the trial point's mu; the combined direction is
+    the sum.  Every quantity here is written out from Eqs. sepregaugeq and fzfs, not taken
+    from the oracle."""
+    rng = _rng(seed)
+    A = rng.standard_normal((m, n))
+    b = rng.standard_normal(m)
+    tau, sigma = 0.3, 0.1
+    z = rng.uniform(0.1, 2.0, 2 * n)
+    s = rng.uniform(0.1, 2.0, 2 * n)
+    Ft = np.hstack([A, -A])
+    FFt = Ft.T @ Ft
+    atb = A.T @ b
+    c_def = np.concatenate([tau * np.ones(n) - atb, tau * np.ones(n) + atb])
+    K = np.block([[FFt, -np.eye(2 * n)], [np.diag(s), np.diag(z)]])
+    mu = float(z @ s) / (2 * n)
+    pred = np.linalg.solve(K, np.concatenate([s - c_def - FFt @ z, sigma * mu - z * s]))
+    zt, st = z + aP * pred[:2 * n], s + aD * pred[2 * n:]
+    mut = float(zt @ st) / (2 * n)
+    corr = np.linalg.solve(K, np.concatenate([st - c_def - FFt @ zt, 0.8 * mut - zt * st]))
+    want = pred + corr
+    # the oracle's predictor and corrector (Eqs. redNewtonA/B, exact solves)
+    op = O.Operator.from_dense(A)
+    c = O.c_vector(op, b, tau)
+    fz, mu_o = O.residuals(op, b, tau, z, s, c)
+    fs = O.complementarity_rhs(z, s, sigma, mu_o)
+    d = s / z
+    dz = O.solve_full_cholesky(op, d, O.newton_rhs(fz, fs, z))
+    ds = O.recover_ds(fs, z, d, dz)
+    dz2, ds2 = O.corrector_direction(op, b, tau, c, z, s, d, z + aP * dz, s + aD * ds, O.SIGMA3,
+                                     lambda dd, r: O.solve_full_cholesky(op, dd, r))
+    got = np.concatenate([dz + dz2, ds + ds2])
+    return float(np.abs(got - want).max() / np.abs(want).max())
+
+
+def _orthonormal_problem(seed, n=40):
+    rng = _rng(seed)
+    Q, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    b = rng.standard_normal(n)
+    tau = 0.3 * np.abs(Q.T @ b).max()
+    return Q, b, tau, rng
+
+
+def pin_kkt_off_optimum_error(seed=23, n=40):
+    """For orthonormal square Q, x - g(x) = x - Q^T (Q x - b) = Q^T b for EVERY x, so the prox
+    residual has the closed form kkt_rel(x) = ||x - S_tau(Q^T b)|| / (1 + ||x||) at any x,
+    not only at the minimiser."""
+    Q, b, tau, rng = _orthonormal_problem(seed, n)
+    op = O.Operator.from_dense(Q)
+    xs = np.sign(Q.T @ b) * np.maximum(np.abs(Q.T @ b) - tau, 0.0)
+    errs = []
+    for scale in (1e-8, 1e-4, 1e-1, 1.0, 10.0):
+        x = xs + scale * rng.standard_normal(n)
+        want = np.linalg.norm(x - xs) / (1.0 + np.linalg.norm(x))
+        # rounding of x - Q^T (Q x - b) is ~1e-16 |Q^T b|, so compare against a floor of 1e-7
+        errs.append(abs(O.kkt_rel(op, b, tau, x) - want) / max(want, 1e-7))
+    return max(errs)
+
+
+def pin_certificate_chain_violation(seed=29, n=40):
+    """For orthonormal square Q the minimum is known in closed form, P* = P(S_tau(Q^T b)).
+    At perturbed x (several magnitudes) the certificate must satisfy weak duality,
+    P(x) - D(nu) >= P(x) - P* >= 0, with nu dual-feasible (||Q^T nu||_inf <= tau).
+    Returns the largest violation (0 when every inequality holds)."""
+    Q, b, tau, rng = _orthonormal_problem(seed, n)
+    op = O.Operator.from_dense(Q)
+    xs = np.sign(Q.T @ b) * np.maximum(np.abs(Q.T @ b) - tau, 0.0)
+    Pstar = tau * np.abs(xs).sum() + 0.5 * np.sum((Q @ xs - b) ** 2)
+    viol = 0.0
+    for scale in (0.0, 1e-6, 1e-3, 1e-1, 1.0, 10.0):
+        x = xs + scale * rng.standard_normal(n)
+        Px = tau * np.abs(x).sum() + 0.5 * np.sum((Q @ x - b) ** 2)
+        P, D = O.dual_gap_certificate(op, b, tau, x)
+        nu = O.dual_point(op, b, tau, x)
+        tol = 1e-12 * (1.0 + abs(Pstar))
+        viol = max(viol, abs(P - Px) - tol, D - Pstar - tol, Pstar - Px - tol,
+                   float(np.abs(Q.T @ nu).max()) - tau * (1 + 1e-12))
+    # x = 0 with tau < ||Q^T b||_inf: the unscaled residual -b is infeasible; the scaled
+    # point must still bound P* from below
+    P0, D0 = O.dual_gap_certificate(op, b, tau, np.zeros(n))
+    viol = max(viol, D0 - Pstar - 1e-12 * (1.0 + abs(Pstar)))
+    return max(viol, 0.0)
+
+
 # ---------------------------------------------------------------- tests
 def test_dct_rows_orthonormal_and_match_library():
     n = 256
@@ -225,6 +314,55 @@ def test_l1_optimality_and_dual_gap_certificate(kind):
     P, D = O.dual_gap_certificate(op, p.b, p.tau, res.x)
     assert P - D >= -1e-12 and (P - D) / (1 + abs(P)) < 1e-10
     assert O.kkt_rel(op, p.b, p.tau, res.x) < 1e-10
+
+
+def test_corrector_step_matches_block_system():
+    assert pin_corrector_error() < 1e-10
+    assert pin_corrector_error(seed=20, m=4, n=9, aP=0.01, aD=0.09) < 1e-10
+
+
+@pytest.mark.parametrize("pin,bar", [(pin_closed_form_error, 1e-9), (pin_brute_force_error, 1e-8)])
+def test_ipm_with_a_corrector_every_iteration(pin, bar, monkeypatch):
+    """alpha_tilde = 1 makes the corrector test of the Algorithm true at every iteration
+    (alpha <= 1 always): the closed-form and brute-force pins still hold, and every
+    iteration that computed a direction also took a corrector."""
+    seen = []
+    orig = O.ipm
+
+    def ipm_every(op, b, tau, params=None):
+        q = dataclasses.replace(params or O.OracleParams(), alpha_tilde=1.0)
+        r = orig(op, b, tau, q)
+        seen.append(r)
+        return r
+
+    monkeypatch.setattr(O, "ipm", ipm_every)
+    assert pin() < bar
+    r = seen[-1]
+    assert r.converged and r.correctors == r.iters - 1 > 0
+
+
+def test_ipm_corrector_optimality_dense():
+    A, b, tau = _gauss_problem(30, 90, 5, 61)
+    op = O.Operator.from_dense(A)
+    r = O.ipm(op, b, tau, O.OracleParams(alpha_tilde=1.0))
+    r0 = O.ipm(op, b, tau)
+    assert r.converged and r.correctors == r.iters - 1 > 0
+    v_on, v_off = O.optimality_violation(op, b, tau, r.x, support_tol=1e-7)
+    assert v_on < 1e-8 and v_off < 1e-10
+    assert np.linalg.norm(r.x - r0.x) / np.linalg.norm(r0.x) < 1e-8
+
+
+def test_kkt_rel_closed_form_away_from_optimum():
+    assert pin_kkt_off_optimum_error() < 1e-9
+
+
+def test_certificate_weak_duality_chain_away_from_optimum():
+    assert pin_certificate_chain_violation() == 0.0
+    # and the bound is tight at the optimum (gap ~ 0)
+    Q, b, tau, _ = _orthonormal_problem(29)
+    xs = O.soft_threshold(Q.T @ b, tau)
+    P, D = O.dual_gap_certificate(O.Operator.from_dense(Q), b, tau, xs)
+    assert abs(P - D) <= 1e-12 * (1 + abs(P))
 
 
 def test_central_path_fixed_point():
@@ -305,10 +443,11 @@ def test_workload_generators_deterministic():
 
 # ---------------------------------------------------------------- planted mistakes
 @pytest.mark.parametrize("mutation", ["c_sign", "drop_sigma_mu", "ds_sign", "precond_offdiag",
-                                      "rho_sign", "rhs_no_zinv", "step_eta"])
+                                      "rho_sign", "rhs_no_zinv", "step_eta", "corr_sigma1", "corr_zinv_trial",
+                                      "corr_rhs_at_current", "corr_dropped"])
 def test_planted_mistake_is_caught(monkeypatch, mutation):
     orig = {k: getattr(O, k) for k in ("c_vector", "residuals", "recover_ds", "precond_apply",
-                                       "newton_rhs", "step_to_boundary", "ipm")}
+                                       "newton_rhs", "step_to_boundary", "ipm", "corrector_direction")}
     if mutation == "c_sign":
         monkeypatch.setattr(O, "c_vector", lambda op, b, tau: -orig["c_vector"](op, b, tau) + 2 * tau)
     elif mutation == "drop_sigma_mu":
@@ -328,13 +467,30 @@ def test_planted_mistake_is_caught(monkeypatch, mutation):
         monkeypatch.setattr(O, "newton_rhs", lambda fz, fs, z: fz + fs)
     elif mutation == "step_eta":
         monkeypatch.setattr(O, "step_to_boundary", lambda v, dv, eta: orig["step_to_boundary"](v, dv, 1.2))
+    elif mutation == "corr_sigma1":          # predictor's centring in the corrector
+        monkeypatch.setattr(O, "corrector_direction", lambda op, b, tau, c, z, s, d, zt, st, sigma3, solve:
+                            orig["corrector_direction"](op, b, tau, c, z, s, d, zt, st, O.SIGMA1, solve))
+    elif mutation == "corr_zinv_trial":      # Z^-1 of the trial point instead of the current one
+        def cd(op, b, tau, c, z, s, d, zt, st, sigma3, solve):
+            fzt, mut = O.residuals(op, b, tau, zt, st, c)
+            fst = O.complementarity_rhs(zt, st, sigma3, mut)
+            dz2 = solve(d, O.newton_rhs(fzt, fst, zt))
+            return dz2, O.recover_ds(fst, zt, d, dz2)
+        monkeypatch.setattr(O, "corrector_direction", cd)
+    elif mutation == "corr_rhs_at_current":  # residuals of the current point, not the trial point
+        monkeypatch.setattr(O, "corrector_direction", lambda op, b, tau, c, z, s, d, zt, st, sigma3, solve:
+                            orig["corrector_direction"](op, b, tau, c, z, s, d, z, s, sigma3, solve))
+    elif mutation == "corr_dropped":         # the predictor alone
+        monkeypatch.setattr(O, "corrector_direction", lambda op, b, tau, c, z, s, d, zt, st, sigma3, solve:
+                            (np.zeros_like(z), np.zeros_like(s)))
 
     caught = []
     for pin, ok in ((pin_closed_form_error, lambda e: e < 1e-9),
                     (pin_brute_force_error, lambda e: e < 1e-8),
                     (pin_full_kkt_error, lambda e: e < 1e-10),
                     (pin_theorem_error, lambda e: e < 1e-6),
-                    (pin_central_path_error, lambda e: e < 1e-14)):
+                    (pin_central_path_error, lambda e: e < 1e-14),
+                    (pin_corrector_error, lambda e: e < 1e-10)):
         try:
             with np.errstate(all="ignore"):
                 e = pin()
@@ -347,3 +503,29 @@ def test_planted_mistake_is_caught(monkeypatch, mutation):
     except Exception:
         caught.append(True)
     assert any(caught), f"mutation {mutation} slipped through every pin"
+
+
+@pytest.mark.parametrize("mutation", ["kkt_zero", "kkt_no_prox", "nu_unscaled", "nu_zero_gap"])
+def test_planted_certificate_mistake_is_caught(monkeypatch, mutation):
+    """The certificates (the prox residual and the l1 dual-gap bound) are the only parity
+    evidence at sizes beyond the oracle's direct solve; a mistake in either must fail a pin
+    that holds away from the optimum."""
+    orig_kkt, orig_dual = O.kkt_rel, O.dual_point
+    if mutation == "kkt_zero":
+        monkeypatch.setattr(O, "kkt_rel", lambda op, b, tau, x: 0.0)
+    elif mutation == "kkt_no_prox":          # ||g|| instead of the prox residual
+        monkeypatch.setattr(O, "kkt_rel", lambda op, b, tau, x: float(np.linalg.norm(O.gradient(op, b, x)))
+                            / (1.0 + float(np.linalg.norm(x))))
+    elif mutation == "nu_unscaled":          # residual not scaled into the dual feasible set
+        monkeypatch.setattr(O, "dual_point", lambda op, b, tau, x: op.mv(x) - b)
+    elif mutation == "nu_zero_gap":          # scaled by tau / ||g||_2 instead of the inf-norm
+        def dp(op, b, tau, x):
+            r = op.mv(x) - b
+            g = float(np.linalg.norm(op.rmv(r)))
+            return r * min(1.0, tau / g) * 4.0
+        monkeypatch.setattr(O, "dual_point", dp)
+    caught = []
+    with np.errstate(all="ignore"):
+        caught.append(not (pin_kkt_off_optimum_error() < 1e-9))
+        caught.append(pin_certificate_chain_violation() != 0.0)
+    assert any(caught), f"mutation {mutation} slipped through every certificate pin"
