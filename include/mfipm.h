@@ -71,8 +71,10 @@ typedef enum { MFIPM_OP_DENSE = 0, MFIPM_OP_PARTIAL_DCT = 1, MFIPM_OP_PARTIAL_HA
 /* Storage type of a dense A. */
 typedef enum { MFIPM_A_F64 = 0, MFIPM_A_F32 = 1, MFIPM_A_BF16 = 2 } mfipm_a_dtype;
 
-/* Arithmetic of the PCG solve.  The IPM residuals, duality gap, step lengths and
- * iterate updates are always float64.
+/* Arithmetic of the PCG solve.  The outer loop (IPM residuals, duality gap, step lengths and
+ * iterate updates) is float64 for dense operators; for the partial-DCT and partial-Haar
+ * operators its per-index arithmetic follows mfipm_outer below (double-float by default),
+ * while its scalar reductions and every output stay float64.
  *   MFIPM_PREC_FP64      PCG vectors and operator products in float64.
  *   MFIPM_PREC_FP32_PCG  PCG vectors and operator products in float32 (the inexact Newton
  *                        direction is corrected by the float64 residuals of the outer loop).
@@ -234,6 +236,14 @@ double mfipm_last_kernel_ms(void);
  * the product covers), *products = how many products, *launches = how many kernels the
  * whole call launched.  Not in the paper. */
 int mfipm_last_operator_stats(double* ms, double* bytes, int64_t* products, int64_t* launches);
+
+/* Measured float32 FMA throughput of the current device, in TFLOP/s (*tflops, HOST): the
+ * best of three timed launches of a plain fused-multiply-add loop on every SM (8 independent
+ * chains per thread, 32 warps per SM), timed with CUDA events on `stream` after one warm-up
+ * launch.  The denominator of the float32 ALU roofline of the shared-memory FFT chain (the
+ * partial-DCT operator), which runs near the float32 ridge.  Synchronises `stream`.  Not in
+ * the paper. */
+int mfipm_fp32_fma_peak(double* tflops, void* stream);
 
 /* The bf16 GEMM of the shared-A solver (MFIPM_PREC_BF16_A), exposed for testing and reuse (not
  * in the paper):  C_s[c][r] = sum_{k in slice s} Aop[r][k] * Bop[c][k]  for s < splits, with

@@ -75,6 +75,7 @@ SIGNATURES = {
     "mfipm_gemm_bf16": (ctypes.c_int, [_P, _P, _P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                        ctypes.c_int32, _P]),
     "mfipm_set_gemm_mode": (ctypes.c_int, [ctypes.c_int32]),
+    "mfipm_fp32_fma_peak": (ctypes.c_int, [ctypes.POINTER(ctypes.c_double), _P]),
     "mfipm_set_large_dct_threshold": (ctypes.c_int, [ctypes.c_int64]),
     "mfipm_set_residual_mode": (ctypes.c_int, [ctypes.c_int32]),
     "mfipm_autotune": (ctypes.c_int, [ctypes.c_int32, ctypes.POINTER(Operator), _PP, ctypes.POINTER(ctypes.c_double),

@@ -1203,6 +1203,13 @@ int mfipm_last_operator_stats(double* ms, double* bytes, int64_t* products, int6
   return MFIPM_OK;
 }
 
+int mfipm_fp32_fma_peak(double* tflops, void* stream) {
+  g_err.clear();
+  if (!tflops) return fail(MFIPM_INVALID_ARG, "tflops is NULL");
+  const cudaError_t e = measure_fp32_fma_peak(tflops, static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? MFIPM_OK : cuda_fail(e, "fp32 FMA probe");
+}
+
 int mfipm_set_gemm_mode(int32_t tensor_cores) {
   g_force_simple_gemm = tensor_cores == 0;
   return MFIPM_OK;

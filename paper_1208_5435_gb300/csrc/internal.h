@@ -99,4 +99,7 @@ int max_active_clusters_bwd_dense(int G, bool fp64_pcg, int64_t max_n, int64_t m
 cudaError_t launch_apply(int mode, int G, const KernelArgs& a, const double* in, double* out,
                          cudaStream_t st);
 
+// Measured FP32 FMA rate of the current device in TFLOP/s (probe.cu).
+cudaError_t measure_fp32_fma_peak(double* tflops, cudaStream_t st);
+
 }  // namespace mfipm

@@ -127,3 +127,33 @@ def test_reference_arm_line():
     assert line["e2e"] == {"value": line["value"], "unit": line["unit"], "h2d_bytes_per_step": 0,
                            "d2h_bytes_per_step": 0}
     assert line["config"]["workload"] == "dense_fp64_256x1024"
+
+
+def test_oracle_extrapolation_to_the_batch():
+    """The CPU baseline of the 256 batch: per-class times fitted by a power law in n and summed
+    over every problem of the batch (measured classes at their mean time)."""
+    import types
+    import bench
+    tf, a = bench.fit_class_times({4096: [1.0, 1.0], 8192: [8.0]})
+    assert abs(a - 3.0) < 1e-12 and abs(tf(16384) - 64.0) < 1e-9 and abs(tf(65536) - 4096.0) < 1e-6
+    probs = [types.SimpleNamespace(n=n) for n in (4096, 8192, 16384, 65536)]
+    rate, a2, total = bench.extrapolated_batch_rate(probs, {4096: [1.0], 8192: [8.0]})
+    assert abs(total - (1 + 8 + 64 + 4096)) < 1e-6 and abs(rate - 4 / total) < 1e-12
+    # one measured class: the direct solve's cost model n^3
+    _, a1 = bench.fit_class_times({4096: [2.0]})
+    assert a1 == 3.0
+
+
+def test_reference_arm_batch_line():
+    """--impl reference on the 256 batch: one problem per step, extrapolated to the batch."""
+    import json
+    import subprocess
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference", "--workload",
+                          "dct_batch_256", "--steps", "1", "--warmup", "0"], capture_output=True, text=True,
+                         timeout=600, cwd=root)
+    assert out.returncode == 0, out.stderr[-2000:]
+    line = json.loads(out.stdout.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and 0 < line["value"] < 1.0
+    assert line["cpu_baseline"]["extrapolated"] is True and line["cpu_baseline"]["value"] == line["value"]
+    assert "n^3.00" in line["cpu_baseline"]["sample"]
