@@ -117,6 +117,11 @@ typedef struct {
   int32_t equal_steps;   /* 0: separate primal and dual steps as in Sec. 5.1; 1: common step */
   int32_t cluster_size;  /* CTAs that cooperate on one problem (1,2,4,8,16); 0 = automatic */
   int32_t outer;         /* mfipm_outer; MFIPM_OUTER_DF */
+  double outer_f32_gap;  /* partial DCT: while the relative duality gap exceeds this value the
+                            outer residual A^T(Ax - b) runs through the float32 FFT chain; at the
+                            first iterate at or below it, and before any stop, it is recomputed
+                            in the outer loop's precision (mfipm_outer), which every later
+                            iteration keeps.  0 = always the outer precision.  1e-2 */
 } mfipm_params;
 
 typedef struct {

@@ -133,6 +133,8 @@ int validate_params(const mfipm_params* p) {
   if (p->precision < 0 || p->precision > 2) return fail(MFIPM_INVALID_ARG, "params: bad precision %d", p->precision);
   if (p->outer != MFIPM_OUTER_DF && p->outer != MFIPM_OUTER_FP64)
     return fail(MFIPM_INVALID_ARG, "params: bad outer-loop arithmetic %d", p->outer);
+  if (!(p->outer_f32_gap >= 0) || !isfinite(p->outer_f32_gap))
+    return fail(MFIPM_INVALID_ARG, "params: outer_f32_gap must be finite and >= 0");
   const int cs = p->cluster_size;
   if (!(cs == 0 || cs == 1 || cs == 2 || cs == 4 || cs == 8 || cs == 16))
     return fail(MFIPM_INVALID_ARG, "params: cluster_size must be 0,1,2,4,8,16");
@@ -153,6 +155,7 @@ SolveParams to_solve(const mfipm_params* p) {
   s.max_iter_pcg = p->max_iter_pcg;
   s.equal_steps = p->equal_steps;
   s.resid_fp64 = p->outer == MFIPM_OUTER_FP64;
+  s.f32_gap = p->outer_f32_gap;
   return s;
 }
 
@@ -171,6 +174,7 @@ size_t problem_bytes(const mfipm_operator& op, bool pcg64) {
   size_t b = 0;
   if (op.kind == MFIPM_OP_PARTIAL_DCT || op.kind == MFIPM_OP_PARTIAL_HAAR)
     b += align256(n) + 2 * align256(8 * n);  // mask, bsu, bsu_df
+  if (op.kind == MFIPM_OP_PARTIAL_DCT) b += align256(n / 2) + align256(16 * n);  // mcode, bpk
   b += align256(32 * n);                                                     // z, s
   b += align256(5 * n * (pcg64 ? 16 : 8));                                   // x1 x2 r p d
   b += align256(8 * n);                                                      // scratch (apply)
@@ -369,6 +373,12 @@ int prepare(int batch, const mfipm_operator* ops, const double* const* b, const 
       q += align256(8 * n);
       d.bsu_df = reinterpret_cast<float2*>(ws + q);
       q += align256(8 * n);
+      if (!P.haar) {
+        d.mcode = reinterpret_cast<uint8_t*>(ws + q);
+        q += align256(n / 2);
+        d.bpk = ws + q;
+        q += align256(16 * n);
+      }
     }
     d.zs = reinterpret_cast<double*>(ws + q);
     q += align256(32 * n);
@@ -411,7 +421,8 @@ int run(Prepared& P, cudaStream_t st, int batch, mfipm_info* infos, const std::v
     if ((e = launch_twiddles(const_cast<double2*>(P.args.tw64), const_cast<float2*>(P.args.tw32),
                              const_cast<float4*>(P.args.twdf), P.args.log2_tw, st)) != cudaSuccess)
       return cuda_fail(e, "twiddle kernel");
-    if ((e = launch_dct_setup(P.args.probs, batch, P.max_n, P.args.err, st)) != cudaSuccess)
+    if ((e = launch_dct_setup(P.args.probs, batch, P.max_n, P.args.err, st, P.args.prm.resid_fp64 != 0)) !=
+        cudaSuccess)
       return cuda_fail(e, "setup kernel");
   }
   // problems small enough for one CTA's shared memory go to the per-CTA phase of the kernel
@@ -978,6 +989,8 @@ int mfipm_params_default(mfipm_params* p) {
   p->precision = MFIPM_PREC_FP32_PCG;
   p->equal_steps = 0;
   p->cluster_size = 0;
+  p->outer = MFIPM_OUTER_DF;
+  p->outer_f32_gap = 1e-2;
   return MFIPM_OK;
 }
 

@@ -195,9 +195,22 @@ template <int G> __device__ __forceinline__ void cluster_barrier() {
 }
 
 // ------------------------------------------------------------------ shared-memory FFT
+// Shared-memory slot of complex element p of an M = 2^logM point buffer: the low four bits
+// of p are XORed with four higher bits (bits max(logM - 4, 4) and up).  An involution that
+// keeps every aligned run of 16 consecutive p on 16 distinct slots of one 16-slot group (the
+// FFT stages and the per-index passes stay conflict-free), and spreads the bit-reversed
+// column accesses of the DCT exchange step over distinct banks: consecutive columns k2 sit
+// at positions bitrev(k2) that differ only in their top bits, which without the XOR all
+// fall into one bank.
+__device__ __forceinline__ int swz(int p, int logM) {
+  const int sh = logM > 8 ? logM - 4 : 4;
+  return p ^ ((p >> sh) & 15);
+}
+
 // In-place radix-4 decimation-in-frequency FFT of M = 2^logM points held in shared
-// memory: natural-order input, bit-reversed output, forward sign exp(-2 pi i jk/M).
-// Each radix-4 group is two radix-2 stages, so the output order is plain bit reversal.
+// memory (element p in slot swz(p)): natural-order input, bit-reversed output, forward sign
+// exp(-2 pi i jk/M).  Each radix-4 group is two radix-2 stages, so the output order is
+// plain bit reversal.
 template <class C, class R>
 __device__ void fft_dif(C* buf, int logM, const Twiddle<C>& tw) {
   const int M = 1 << logM;
@@ -206,38 +219,41 @@ __device__ void fft_dif(C* buf, int logM, const Twiddle<C>& tw) {
     const int logS = logB - 2, S = 1 << logS;
     for (int gi = threadIdx.x; gi < (M >> 2); gi += kThreads) {
       const int blk = gi >> logS, t = gi & (S - 1);
-      C* p = buf + (blk << logB) + t;
-      C a0 = p[0], a1 = p[S], a2 = p[2 * S], a3 = p[3 * S];
+      const int p = (blk << logB) + t;
+      const int q0 = swz(p, logM), q1 = swz(p + S, logM), q2 = swz(p + 2 * S, logM), q3 = swz(p + 3 * S, logM);
+      C a0 = buf[q0], a1 = buf[q1], a2 = buf[q2], a3 = buf[q3];
       C w1 = tw.root(t, logB), w2 = tw.root(2 * t, logB), w3 = tw.root(3 * t, logB);
       C s02 = cadd(a0, a2), d02 = csub(a0, a2), s13 = cadd(a1, a3), d13 = csub(a1, a3);
-      p[0] = cadd(s02, s13);
-      p[S] = cmul(csub(s02, s13), w2);
-      p[2 * S] = cmul(cadd(d02, cmul_mi(d13)), w1);
-      p[3 * S] = cmul(cadd(d02, cmul_i(d13)), w3);
+      buf[q0] = cadd(s02, s13);
+      buf[q1] = cmul(csub(s02, s13), w2);
+      buf[q2] = cmul(cadd(d02, cmul_mi(d13)), w1);
+      buf[q3] = cmul(cadd(d02, cmul_i(d13)), w3);
     }
     __syncthreads();
   }
   if (logB == 1) {
     for (int gi = threadIdx.x; gi < (M >> 1); gi += kThreads) {
-      C a0 = buf[2 * gi], a1 = buf[2 * gi + 1];
-      buf[2 * gi] = cadd(a0, a1);
-      buf[2 * gi + 1] = csub(a0, a1);
+      const int q0 = swz(2 * gi, logM), q1 = swz(2 * gi + 1, logM);
+      C a0 = buf[q0], a1 = buf[q1];
+      buf[q0] = cadd(a0, a1);
+      buf[q1] = csub(a0, a1);
     }
     __syncthreads();
   }
 }
 
 // Unnormalised inverse of fft_dif: bit-reversed input, natural output, sign +,
-// result = M * IDFT.
+// result = M * IDFT (same slot layout).
 template <class C, class R>
 __device__ void fft_dit_inv(C* buf, int logM, const Twiddle<C>& tw) {
   const int M = 1 << logM;
   int logB = 2;
   if (logM & 1) {
     for (int gi = threadIdx.x; gi < (M >> 1); gi += kThreads) {
-      C a0 = buf[2 * gi], a1 = buf[2 * gi + 1];
-      buf[2 * gi] = cadd(a0, a1);
-      buf[2 * gi + 1] = csub(a0, a1);
+      const int q0 = swz(2 * gi, logM), q1 = swz(2 * gi + 1, logM);
+      C a0 = buf[q0], a1 = buf[q1];
+      buf[q0] = cadd(a0, a1);
+      buf[q1] = csub(a0, a1);
     }
     __syncthreads();
     logB = 3;
@@ -246,16 +262,17 @@ __device__ void fft_dit_inv(C* buf, int logM, const Twiddle<C>& tw) {
     const int logS = logB - 2, S = 1 << logS;
     for (int gi = threadIdx.x; gi < (M >> 2); gi += kThreads) {
       const int blk = gi >> logS, t = gi & (S - 1);
-      C* p = buf + (blk << logB) + t;
-      C o0 = p[0];
-      C b1 = cmulc(p[S], tw.root(2 * t, logB));
-      C b2 = cmulc(p[2 * S], tw.root(t, logB));
-      C b3 = cmulc(p[3 * S], tw.root(3 * t, logB));
+      const int p = (blk << logB) + t;
+      const int q0 = swz(p, logM), q1 = swz(p + S, logM), q2 = swz(p + 2 * S, logM), q3 = swz(p + 3 * S, logM);
+      C o0 = buf[q0];
+      C b1 = cmulc(buf[q1], tw.root(2 * t, logB));
+      C b2 = cmulc(buf[q2], tw.root(t, logB));
+      C b3 = cmulc(buf[q3], tw.root(3 * t, logB));
       C Ss = cadd(o0, b1), D = csub(o0, b1), E = cadd(b2, b3), F = csub(b3, b2);
-      p[0] = cadd(Ss, E);
-      p[S] = cadd(D, cmul_mi(F));
-      p[2 * S] = csub(Ss, E);
-      p[3 * S] = cadd(D, cmul_i(F));
+      buf[q0] = cadd(Ss, E);
+      buf[q1] = cadd(D, cmul_mi(F));
+      buf[q2] = csub(Ss, E);
+      buf[q3] = cadd(D, cmul_i(F));
     }
     __syncthreads();
   }

@@ -13,6 +13,7 @@ namespace mfipm {
 // Parameters of the IPM as the kernels read them (copied from mfipm_params).
 struct SolveParams {
   double tol, tol_pcg, sigma1, sigma2, sigma3, alpha_bar, alpha_tilde, eta;
+  double f32_gap;  // relative gap above which the partial-DCT outer residual runs in float32
   int32_t max_iter, max_iter_pcg, equal_steps, resid_fp64;
 };
 
@@ -32,6 +33,12 @@ struct ProbDesc {
   uint8_t* mask;          // DEVICE n: 1 where the DCT row is sampled
   double* bsu;            // DEVICE n: b scattered to its rows, divided by the row's DCT scale
   float2* bsu_df;         // DEVICE n: bsu as double-float (hi, lo)
+  // partial DCT, persistent kernel: per frequency k < n/2 of the half-length FFT, the row-mask
+  // bits of the four DCT rows k, n-k (k > 0), n/2-k, n/2+k (bits 0..3), and their four b_u
+  // values as one 32-byte record (double-float: hi[4] then lo[4] as float32; float64: the
+  // four values); the exchange step reads one code and at most one record per frequency
+  uint8_t* mcode;         // DEVICE n/2 or null
+  void* bpk;              // DEVICE n/2 records of 32 bytes or null
   // dense
   const void* A;
   int32_t a_dtype;
@@ -68,7 +75,8 @@ struct KernelArgs {
 
 // Launchers implemented in solver.cu.  Return cudaError_t of the launch.
 cudaError_t launch_twiddles(double2* tw64, float2* tw32, float4* twdf, int log2_tw, cudaStream_t st);
-cudaError_t launch_dct_setup(const ProbDesc* probs_dev, int batch, int64_t max_n, int* err, cudaStream_t st);
+cudaError_t launch_dct_setup(const ProbDesc* probs_dev, int batch, int64_t max_n, int* err, cudaStream_t st,
+                             bool pack_fp64 = false);
 
 // Products with A and the KKT residual of a candidate x (apply.cu): what = 0: out = A in,
 // 1: out = A^T in, 2: *kkt = kkt_rel(in) for (b, tau).  Synchronises st.

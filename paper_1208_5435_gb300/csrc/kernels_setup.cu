@@ -54,6 +54,31 @@ __global__ void dct_scatter_kernel(const ProbDesc* probs, int batch, int* err) {
   }
 }
 
+// Per-frequency packing for the persistent kernel's exchange step (problems with mcode set):
+// code[k] = mask bits of rows k, N-k (k > 0), L-k, L+k; bpk[k] = their b_u values.
+__global__ void dct_pack_kernel(const ProbDesc* probs, int batch, bool fp64) {
+  const ProbDesc pd = probs[blockIdx.y];
+  if (!pd.mcode) return;
+  const int64_t N = pd.n, L = N >> 1;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < L; k += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i2 = k > 0 ? N - k : 0;
+    const bool m1 = pd.mask[k], m2 = k > 0 && pd.mask[i2], m3 = pd.mask[L - k], m4 = pd.mask[L + k];
+    pd.mcode[k] = (uint8_t)((m1 ? 1u : 0u) | (m2 ? 2u : 0u) | (m3 ? 4u : 0u) | (m4 ? 8u : 0u));
+    const double b1 = m1 ? pd.bsu[k] : 0.0, b2 = m2 ? pd.bsu[i2] : 0.0;
+    const double b3 = m3 ? pd.bsu[L - k] : 0.0, b4 = m4 ? pd.bsu[L + k] : 0.0;
+    if (fp64) {
+      double2* r = static_cast<double2*>(pd.bpk) + 2 * k;
+      r[0] = make_double2(b1, b2);
+      r[1] = make_double2(b3, b4);
+    } else {
+      const df d1 = to_df(b1), d2 = to_df(b2), d3 = to_df(b3), d4 = to_df(b4);
+      float4* r = static_cast<float4*>(pd.bpk) + 2 * k;
+      r[0] = make_float4(d1.hi, d2.hi, d3.hi, d4.hi);
+      r[1] = make_float4(d1.lo, d2.lo, d3.lo, d4.lo);
+    }
+  }
+}
+
 // ------------------------------------------------------------------ launchers
 size_t dct_smem_bytes(int G, int64_t max_n) {
   const int64_t M = max_n / 2 / G;
@@ -72,12 +97,15 @@ cudaError_t launch_twiddles(double2* tw64, float2* tw32, float4* twdf, int log2_
   return cudaGetLastError();
 }
 
-cudaError_t launch_dct_setup(const ProbDesc* probs_dev, int batch, int64_t max_n, int* err, cudaStream_t st) {
+cudaError_t launch_dct_setup(const ProbDesc* probs_dev, int batch, int64_t max_n, int* err, cudaStream_t st,
+                             bool pack_fp64) {
   const int bx = (int)((max_n + 255) / 256 < 64 ? (max_n + 255) / 256 : 64);
   dct_setup_kernel<<<dim3(bx, batch), 256, 0, st>>>(probs_dev, batch, err);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   dct_scatter_kernel<<<dim3(bx, batch), 256, 0, st>>>(probs_dev, batch, err);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  dct_pack_kernel<<<dim3(bx, batch), 256, 0, st>>>(probs_dev, batch, pack_fp64);
   return cudaGetLastError();
 }
 

@@ -54,6 +54,8 @@ template <int G> struct HaarOp {
   template <class T> __device__ __forceinline__ T* rbuf() const { return reinterpret_cast<T*>(rb); }
   template <class PS> __device__ __forceinline__ PS* wbuf() const { return reinterpret_cast<PS*>(wb); }
   template <class T> __device__ double resid_t() { return chain<T, MODE_RESID>(rbuf<T>()); }
+  static constexpr bool kLowpResid = false;
+  template <class T> __device__ double resid_lowp() { return resid_t<T>(); }
   template <class PS> __device__ double normal(PS* w) { return chain<PS, MODE_NORMAL>(w); }
   __device__ void apply_A_out(const ProbDesc&) {}
   __device__ void grad_A_out(const ProbDesc&, const void*) {}

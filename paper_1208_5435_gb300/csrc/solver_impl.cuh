@@ -51,6 +51,12 @@ __device__ __forceinline__ double rcp64(double z) {
   return fma(r, e, r);
 }
 
+__device__ __forceinline__ float to_float(df v) { return __fadd_rn(v.hi, v.lo); }
+__device__ __forceinline__ float to_float(double v) { return (float)v; }
+template <class T> __device__ __forceinline__ T from_float(float f);
+template <> __device__ __forceinline__ df from_float<df>(float f) { return df(f, 0.f); }
+template <> __device__ __forceinline__ double from_float<double>(float f) { return (double)f; }
+
 template <class PS> struct V2;
 template <> struct V2<float> { using T = float2; };
 template <> struct V2<double> { using T = double2; };
@@ -76,7 +82,34 @@ struct DctGeom {
   const uint8_t* mask;
   const double* bsu;      // b scattered to its rows / DCT scale (float64)
   const float2* bsu_df;   // the same as double-float (hi, lo)
+  // per frequency k < L (persistent kernel; null elsewhere): mask bits of rows k, N-k, L-k,
+  // L+k and their four b_u values as one 32-byte record in the residual's arithmetic
+  const uint8_t* mcode = nullptr;
+  const void* bpk = nullptr;
+  bool bpk_f64 = false;   // records hold float64 values (else double-float hi[4], lo[4])
 };
+
+// The four b_u values of frequency k from its packed record (loaded only when a row is sampled).
+template <class R> struct B4 { R b1, b2, b3, b4; };
+__device__ __forceinline__ B4<float> load_b4(const DctGeom& g, int64_t k, float) {
+  if (g.bpk_f64) {
+    const double2* r = static_cast<const double2*>(g.bpk) + 2 * k;
+    const double2 u = __ldg(r), v = __ldg(r + 1);
+    return B4<float>{(float)u.x, (float)u.y, (float)v.x, (float)v.y};
+  }
+  const float4 h = __ldg(static_cast<const float4*>(g.bpk) + 2 * k);
+  return B4<float>{h.x, h.y, h.z, h.w};
+}
+__device__ __forceinline__ B4<double> load_b4(const DctGeom& g, int64_t k, double) {
+  const double2* r = static_cast<const double2*>(g.bpk) + 2 * k;
+  const double2 u = __ldg(r), v = __ldg(r + 1);
+  return B4<double>{u.x, u.y, v.x, v.y};
+}
+__device__ __forceinline__ B4<df> load_b4(const DctGeom& g, int64_t k, df) {
+  const float4* r = static_cast<const float4*>(g.bpk) + 2 * k;
+  const float4 h = __ldg(r), l = __ldg(r + 1);
+  return B4<df>{df(h.x, l.x), df(h.y, l.y), df(h.z, l.z), df(h.w, l.w)};
+}
 
 // Constants of the pointwise step in the chain's arithmetic, built once per exchange step.
 template <class R> __device__ __forceinline__ R cst(double v);
@@ -108,7 +141,7 @@ template <class R> struct PwConst {
         rs2(rsqrt2<R>()),
         zero() {}
 };
-__device__ __forceinline__ float load_bsu(const DctGeom&, int64_t, float) { return 0.f; }
+__device__ __forceinline__ float load_bsu(const DctGeom& g, int64_t i, float) { return g.bsu_df[i].x; }
 __device__ __forceinline__ double load_bsu(const DctGeom& g, int64_t i, double) { return g.bsu[i]; }
 __device__ __forceinline__ df load_bsu(const DctGeom& g, int64_t i, df) {
   const float2 v = g.bsu_df[i];
@@ -146,10 +179,22 @@ __device__ __forceinline__ C dct_pointwise_w(int64_t k, C a, C b, C wN, C eps, u
   } else {
     const bool m1 = mb & 1u, m2 = mb & 2u, m3 = mb & 4u, m4 = mb & 8u;
     if constexpr (MODE == MODE_RESID) {
-      X1 = m1 ? X1 - load_bsu(geo, i1, R()) : pc.zero;
-      X2 = m2 ? X2 - load_bsu(geo, i2, R()) : pc.zero;
-      X3 = m3 ? X3 - load_bsu(geo, i3, R()) : pc.zero;
-      X4 = m4 ? X4 - load_bsu(geo, i4, R()) : pc.zero;
+      if (geo.bpk) {
+        if (mb) {
+          const B4<R> bq = load_b4(geo, k, R());
+          X1 = m1 ? X1 - bq.b1 : pc.zero;
+          X2 = m2 ? X2 - bq.b2 : pc.zero;
+          X3 = m3 ? X3 - bq.b3 : pc.zero;
+          X4 = m4 ? X4 - bq.b4 : pc.zero;
+        } else {
+          X1 = X2 = X3 = X4 = pc.zero;
+        }
+      } else {
+        X1 = m1 ? X1 - load_bsu(geo, i1, R()) : pc.zero;
+        X2 = m2 ? X2 - load_bsu(geo, i2, R()) : pc.zero;
+        X3 = m3 ? X3 - load_bsu(geo, i3, R()) : pc.zero;
+        X4 = m4 ? X4 - load_bsu(geo, i4, R()) : pc.zero;
+      }
     } else {
       X1 = m1 ? X1 : pc.zero;
       X2 = m2 ? X2 : pc.zero;
@@ -171,20 +216,6 @@ __device__ __forceinline__ C dct_pointwise_w(int64_t k, C a, C b, C wN, C eps, u
   }
 }
 
-// Twiddles from the level-ordered table and mask bits from geo.mask.
-template <class C, int MODE, class R = decltype(C().x)>
-__device__ __forceinline__ C dct_pointwise(int64_t k, C a, C b, const DctGeom& geo, const Twiddle<C>& tw,
-                                           const PwConst<R>& pc, bool valid, R& acc, double* fwd_out) {
-  unsigned mb = 0;
-  if constexpr (MODE != MODE_FORWARD) {
-    const int64_t L = (int64_t)1 << geo.logL, N = geo.N;
-    mb = (geo.mask[k] ? 1u : 0u) | ((k > 0 && geo.mask[N - k]) ? 2u : 0u) | (geo.mask[L - k] ? 4u : 0u) |
-         (geo.mask[L + k] ? 8u : 0u);
-  }
-  return dct_pointwise_w<C, MODE, R>(k, a, b, tw.root(k, geo.logN), tw.root(k, geo.logN + 2), mb, geo, pc, valid,
-                                     acc, fwd_out);
-}
-
 // The exchange step of the distributed DCT chain (see the file comment).  Returns this
 // CTA's share of sum_j alpha_j^2 X'_j^2 (||A w||^2 or ||A x - b||^2).  MODE_FORWARD
 // writes alpha_j X_j (the full orthonormal DCT-II) to fwd_out[j] and stops there.
@@ -193,6 +224,7 @@ __device__ __noinline__ double dct_slot_step(C* buf, const DctGeom& geo, const T
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int M = 1 << geo.logM;
   const int spc = (M >> 1) / G;  // slots per CTA (>= 1 by the host's choice of G)
+  constexpr int kLogG = G == 1 ? 0 : G == 2 ? 1 : G == 4 ? 2 : G == 8 ? 3 : 4;
   using R = decltype(C().x);
   const PwConst<R> pc(geo);
   R acc = pc.zero;
@@ -205,7 +237,30 @@ __device__ __noinline__ double dct_slot_step(C* buf, const DctGeom& geo, const T
     // paired with itself)
     const int k2 = (lane < 16) ? s : (s == 0 ? (M >> 1) : M - s);
     const bool self0 = (k2 == 0), selfh = (k2 == (M >> 1));
-    const int pos = bitrev(k2, geo.logM);
+    const int pos = swz(bitrev(k2, geo.logM), geo.logM);
+    // twiddles of frequency k = k2 + M k1 as products of this lane's k2 part and a root of
+    // order 2G (resp. 8G) shared by all lanes: w_N^k = w_N^k2 exp(-i pi k1 / G) and
+    // eps^k = eps^k2 exp(-i pi k1 / (4G)) (N = 2 M G)
+    const C wk2 = tw.root(k2, geo.logN), ek2 = tw.root(k2, geo.logN + 2);
+    auto pw = [&](int k1, C a, C b, R& accr) -> C {
+      const int64_t k = (int64_t)k2 + (int64_t)M * k1;
+      C wN = wk2, eps = ek2;
+      if (k1 != 0) {
+        wN = cmul(wk2, tw.root(k1, kLogG + 1));
+        eps = cmul(ek2, tw.root(k1, kLogG + 3));
+      }
+      unsigned mb = 0;
+      if constexpr (MODE != MODE_FORWARD) {
+        if (geo.mcode) {
+          mb = __ldg(&geo.mcode[k]);
+        } else {
+          const int64_t L = (int64_t)1 << geo.logL, N = geo.N;
+          mb = (geo.mask[k] ? 1u : 0u) | ((k > 0 && geo.mask[N - k]) ? 2u : 0u) | (geo.mask[L - k] ? 4u : 0u) |
+               (geo.mask[L + k] ? 8u : 0u);
+        }
+      }
+      return dct_pointwise_w<C, MODE, R>(k, a, b, wN, eps, mb, geo, pc, valid, accr, fwd_out);
+    };
     C Z[G];
 #pragma unroll
     for (int g = 0; g < G; ++g) {
@@ -224,8 +279,7 @@ __device__ __noinline__ double dct_slot_step(C* buf, const DctGeom& geo, const T
 #pragma unroll
       for (int k1 = 0; k1 < G; ++k1) T[k1] = Z[k1];
 #pragma unroll
-      for (int k1 = 0; k1 < G; ++k1)
-        Z[k1] = dct_pointwise<C, MODE>((int64_t)M * k1, T[k1], T[(G - k1) % G], geo, tw, pc, valid, acc, fwd_out);
+      for (int k1 = 0; k1 < G; ++k1) Z[k1] = pw(k1, T[k1], T[(G - k1) % G], acc);
     }
     // other columns: H[k2 + M k1] pairs with H[(M - k2) + M (G-1-k1)], held by lane^16
     // (column M/2 pairs with itself the same way); update k1 and G-1-k1 together so
@@ -243,9 +297,9 @@ __device__ __noinline__ double dct_slot_step(C* buf, const DctGeom& geo, const T
         bB = Z[kA];
       }
       if (!self0) {
-        const C nA = dct_pointwise<C, MODE>((int64_t)k2 + (int64_t)M * kA, Z[kA], bA, geo, tw, pc, valid, acc, fwd_out);
+        const C nA = pw(kA, Z[kA], bA, acc);
         if (kB != kA) {
-          const C nB = dct_pointwise<C, MODE>((int64_t)k2 + (int64_t)M * kB, Z[kB], bB, geo, tw, pc, valid, acc, fwd_out);
+          const C nB = pw(kB, Z[kB], bB, acc);
           Z[kB] = nB;
         }
         Z[kA] = nA;
@@ -282,10 +336,12 @@ __device__ double dct_chain(C* buf, const DctGeom& geo, const Twiddle<C>& tw, do
   return acc;
 }
 
-// natural index of storage position q (global over the cluster)
+// natural index of storage position q (global over the cluster): CTA g = q / 2M holds the
+// real q % 2M in shared-memory slot q' = (q % 2M) >> 1 as part q & 1, and slot q' holds complex
+// element n2 = swz(q') of its M-point FFT input
 __device__ __forceinline__ int64_t dct_natural_index(int64_t q, int logM, int G) {
   const int64_t M = (int64_t)1 << logM;
-  const int64_t g = q / (2 * M), n2 = (q % (2 * M)) >> 1, part = q & 1;
+  const int64_t g = q / (2 * M), n2 = swz((int)((q % (2 * M)) >> 1), logM), part = q & 1;
   const int64_t j = g + (int64_t)G * n2;
   const int64_t N = 2 * M * G;
   const int64_t i = 2 * j + part;
@@ -313,6 +369,9 @@ template <int G> struct DctOp {
     geo.mask = pd.mask;
     geo.bsu = pd.bsu;
     geo.bsu_df = pd.bsu_df;
+    geo.mcode = pd.mcode;
+    geo.bpk = pd.bpk;
+    geo.bpk_f64 = a.prm.resid_fp64 != 0;
     const int64_t M = (int64_t)1 << geo.logM;
     buf64 = reinterpret_cast<double2*>(smem);
     buf32 = reinterpret_cast<float2*>(smem + (size_t)16 * M);
@@ -336,7 +395,22 @@ template <int G> struct DctOp {
       return dct_chain<G, double2, MODE_RESID>(buf64, geo, tw64);
     }
   }
-  template <class PS> __device__ double normal(PS*) { return dct_chain<G, float2, MODE_NORMAL>(buf32, geo, tw32); }
+  template <class PS> __device__ double normal(PS*) {
+    return dct_chain<G, float2, MODE_NORMAL>(buf32, geo, tw32);
+  }
+  // The same residual through the float32 chain on the operator buffer (the outer loop's
+  // large-gap iterations): rbuf holds x on entry and A^T(Ax - b) on exit.
+  static constexpr bool kLowpResid = true;
+  template <class T> __device__ double resid_lowp() {
+    T* rb = rbuf<T>();
+    float* wb = wbuf<float>();
+    for (int64_t q = threadIdx.x; q < chunk; q += kThreads) wb[q] = to_float(rb[q]);
+    __syncthreads();
+    const double acc = dct_chain<G, float2, MODE_RESID>(buf32, geo, tw32);
+    for (int64_t q = threadIdx.x; q < chunk; q += kThreads) rb[q] = from_float<T>(wb[q]);
+    __syncthreads();
+    return acc;
+  }
   // grad_b = A w for w in rbuf<double>() (float64 chain): all n DCT coefficients go to
   // pd.scratch, then the sampled rows are gathered.  Overwrites rbuf.
   __device__ void apply_A_out(const ProbDesc& pd) {
@@ -435,6 +509,8 @@ template <int G> struct DenseOp {
     return acc;
   }
   template <class T> __device__ double resid_t() { return chain<double, MODE_RESID>(buf64); }
+  static constexpr bool kLowpResid = false;
+  template <class T> __device__ double resid_lowp() { return resid_t<T>(); }
   // grad_b = A w for w in rbuf<double>(); keeps A w in aw for grad_A_out
   __device__ void apply_A_out(const ProbDesc& pd) {
     chain<double, MODE_FORWARD>(buf64);
@@ -574,6 +650,7 @@ template <class H, class T> struct IpmShared {
   T apT, adT, ap1T, ad1T, tauT, keepT;  // step lengths etc. in the iterate's arithmetic
   H smu, ap1, ad1, s3mut, apH, adH, alpha, beta;
   int corr, corr_next, stop, pcg_stop, correctors;
+  int lowp, redo;  // outer residual in float32 (large gap); recompute it in full precision
 };
 
 template <class H, class T>
@@ -728,6 +805,8 @@ __device__ void solve_one(const ProbDesc& pd, const KernelArgs& a, Op& op, RedSm
       sh.corr = sh.corr_next = 0;
       sh.correctors = 0;
       sh.stop = 0;
+      sh.lowp = Op::kLowpResid && prm.f32_gap > 0.0;
+      sh.redo = 0;
       sh.rel_gap = INFINITY;
       sh.P_obj = 0.0;
     });
@@ -866,10 +945,15 @@ __device__ void solve_one(const ProbDesc& pd, const KernelArgs& a, Op& op, RedSm
       }
     }
     __syncthreads();
-    // ---- residual g = A^T (A x - b)  (f_z of Eq. fzfs needs F F^T z + c)
-    const double res2 = op.template resid_t<T>();
-    nmat += 2;
-    {
+    // ---- residual g = A^T (A x - b)  (f_z of Eq. fzfs needs F F^T z + c).  While the relative
+    // gap exceeds f32_gap the chain runs in float32: the Newton directions of those iterations
+    // are inexact to ~tol_pcg anyway, and each iteration recomputes the residual from scratch,
+    // so its rounding does not carry over.  At the first iteration whose gap falls to f32_gap,
+    // and before any stop, the residual of that iterate is recomputed in the outer loop's
+    // precision, which every later iteration keeps.
+    for (;;) {
+      const double res2 = sh.lowp ? op.template resid_lowp<T>() : op.template resid_t<T>();
+      nmat += 2;
       double v[4] = {(double)part[0], (double)part[1], (double)part[2], res2};
       const int itc = it;
       cluster_reduce<G, 4>(rs, par, v, [&](const double (&t)[4]) {
@@ -880,10 +964,23 @@ __device__ void solve_one(const ProbDesc& pd, const KernelArgs& a, Op& op, RedSm
         if (!isfinite(sh.rel_gap)) sh.stop = MFIPM_NUMERIC;
         else if (sh.rel_gap <= prm.tol) sh.stop = -1;                       // converged (reading R7)
         else if (itc > prm.max_iter) sh.stop = MFIPM_NOT_CONVERGED;
+        sh.redo = sh.lowp && (sh.stop != 0 || !(sh.rel_gap > prm.f32_gap));
+        if (sh.redo) {
+          sh.lowp = 0;
+          sh.stop = 0;
+        }
         // predictor centering (Algorithm; reading R8)
         sh.sigma = (itc != 1 && (sh.prev_ap <= prm.alpha_bar || sh.prev_ad <= prm.alpha_bar)) ? prm.sigma2 : prm.sigma1;
         sh.smu = (H)(sh.sigma * sh.mu);
       });
+      if (!sh.redo) break;
+      // x = u - v of the iterate again (the chain replaced it by the residual)
+      for (int64_t q = tid; q < chunk; q += kThreads) {
+        if (!op.valid(q)) { gbuf[q] = zeroT; continue; }
+        const Q st = S::load(zs, gb + q);
+        gbuf[q] = S::sub(st.u, st.v);
+      }
+      __syncthreads();
     }
     if (sh.stop) break;
     // ---- predictor
@@ -921,7 +1018,8 @@ __device__ void solve_one(const ProbDesc& pd, const KernelArgs& a, Op& op, RedSm
         }
       }
       __syncthreads();
-      op.template resid_t<T>();
+      if (sh.lowp) op.template resid_lowp<T>();
+      else op.template resid_t<T>();
       nmat += 2;
       {
         PS v[1] = {zts_t};

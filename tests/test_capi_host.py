@@ -39,6 +39,26 @@ def test_param_defaults_are_the_papers(L):
     assert L.mfipm_params_default(None) == C.MFIPM_INVALID_ARG
 
 
+def test_python_params_mirror_the_c_defaults(L):
+    """SolverParams() (the binding's defaults) equals mfipm_params_default field by field."""
+    import paper_1208_5435_gb300 as M
+    from paper_1208_5435_gb300 import _capi as C
+    p = C.Params()
+    assert L.mfipm_params_default(ctypes.byref(p)) == 0
+    q = M.SolverParams().to_c(C.PREC_FP32_PCG)
+    for name, _ in C.Params._fields_:
+        assert getattr(p, name) == getattr(q, name), name
+    assert p.outer_f32_gap == 1e-2
+    p.outer_f32_gap = -1.0
+    op = _dct_op(C, 1024, 256)
+    nb = ctypes.c_size_t()
+    ws = ctypes.c_void_p(0x100000)
+    info = C.Info()
+    assert L.mfipm_solve(ctypes.byref(op), ctypes.c_void_p(0x3000), 0.1, ctypes.byref(p), ctypes.c_void_p(0x4000),
+                         None, ws, 1 << 30, ctypes.byref(info), None) == C.MFIPM_INVALID_ARG
+    assert b"outer_f32_gap" in L.mfipm_last_error()
+
+
 def _dct_op(C, n, m, rows_ptr=0x1000):
     op = C.Operator()
     op.kind, op.a_dtype, op.m, op.n, op.A, op.a_scale, op.lda, op.rows = C.OP_PARTIAL_DCT, 0, m, n, None, 1.0, 0, rows_ptr
