@@ -161,15 +161,17 @@ int mfipm_solve(const mfipm_operator* op, const double* b, double tau, const mfi
  * loop that must not enter the allocator).  The paper has no counterpart; this is a
  * deployment convenience.
  * Scratch comes from one 8 MiB array in device memory that every GPU loading this library
- * holds until the process exits; the library allocates nothing.  Problems whose
- * mfipm_workspace_size exceeds 8 MiB (partial DCT up to n = 16384, small dense problems fit)
+ * holds until the process exits; the library allocates nothing.  The call takes the same
+ * path as mfipm_solve would for the same arguments (the persistent kernel, the multi-pass
+ * partial DCT when its threshold has been lowered, the shared-A bf16 solver for a dense bf16
+ * A with MFIPM_PREC_BF16_A) and needs the scratch that mfipm_workspace_size reports for it:
+ * problems above 8 MiB (partial DCT up to n = 16384 fits, small dense and bf16 problems fit)
  * are rejected with MFIPM_INVALID_ARG before any launch.  All calls share the array and it
  * keeps the last call's contents: each call re-initialises everything it reads, and calls
  * that may overlap on the GPU (other streams, other host threads) race on it and must be
  * serialised by the caller.  The first call on a device looks up the array's device address
  * (cudaGetSymbolAddress) with that device current; make that first call before any stream
- * capture.  Kernel timing (mfipm_set_timing) is not recorded by this entry point.
- * Arguments and results as for mfipm_solve. */
+ * capture.  Arguments and results as for mfipm_solve. */
 int mfipm_solve_noalloc(const mfipm_operator* op, const double* b, double tau, const mfipm_params* p,
                         double* x, double* zs_out, mfipm_info* info, void* stream);
 

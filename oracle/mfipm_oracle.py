@@ -286,7 +286,11 @@ def H_apply(op: Operator, d, p):
 
 def pcg(op: Operator, d, rhs, rho, tol, maxiter=MXITERPCG):
     """Textbook preconditioned conjugate gradients on H dz = rhs from dz = 0 (Sec. 4).
-    Stops when sqrt(r^T P^-1 r) <= tol * sqrt(rhs^T P^-1 rhs).  Returns (dz, iterations)."""
+    Stops when sqrt(r^T P^-1 r) <= tol * sqrt(rhs^T P^-1 rhs).  Breakdown guard (the paper
+    does not say what PCG does when rounding destroys positive definiteness, which happens
+    when Theta^-1 spans ~30 orders of magnitude): a search direction with p^T H p not
+    positive and finite, or a step alpha that is not finite, ends the solve with the last
+    iterate.  Returns (dz, iterations)."""
     x = np.zeros_like(rhs)
     r = rhs.copy()
     zz = precond_apply(d, rho, r)
@@ -296,7 +300,10 @@ def pcg(op: Operator, d, rhs, rho, tol, maxiter=MXITERPCG):
     it = 0
     while it < maxiter and rz > tol * tol * rz0:
         q = H_apply(op, d, p)
-        alpha = rz / float(p @ q)
+        pq = float(p @ q)
+        if not (pq > 0.0 and math.isfinite(pq) and math.isfinite(rz / pq)):
+            break
+        alpha = rz / pq
         x += alpha * p
         r -= alpha * q
         zz = precond_apply(d, rho, r)

@@ -1053,14 +1053,9 @@ int mfipm_solve_noalloc(const mfipm_operator* op, const double* b, double tau, c
                 need, kNoallocScratchBytes);
   void* ws = nullptr;
   if ((rc = noalloc_scratch(&ws))) return rc;
-  const double* bb[1] = {b};
-  double* xx[1] = {x};
-  double* zz[1] = {zs_out};
-  double tt[1] = {tau};
-  Prepared P;
-  if ((rc = prepare(1, op, bb, tt, p, xx, zs_out ? zz : nullptr, ws, kNoallocScratchBytes, P))) return rc;
-  mfipm_info tmp;
-  return run(P, static_cast<cudaStream_t>(stream), 1, info ? info : &tmp, nullptr, /*allow_timing=*/false);
+  // the same dispatch as mfipm_solve (shared-A bf16, multi-pass partial DCT, persistent kernel),
+  // whose workspace need is the one checked above
+  return mfipm_solve(op, b, tau, p, x, zs_out, ws, kNoallocScratchBytes, info, stream);
 }
 
 int mfipm_solve_batched(int32_t batch, const mfipm_operator* ops, const double* const* b, const double* tau,

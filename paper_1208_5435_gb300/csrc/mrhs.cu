@@ -792,7 +792,11 @@ __global__ void k_alpha(Dev d, int first, const double* part2) {
     c.rz0 = c.rz = rz;
     c.active = rz > 0.0 && isfinite(rz);
   }
-  c.alpha = c.active ? (float)(c.rz / (pdp + aw2)) : 0.f;
+  // breakdown guard: p^T H p not positive and finite ends this column's solve with its last
+  // iterate (on the first iteration: zero)
+  const double php = pdp + aw2, a = c.rz / php;
+  if (c.active && (!(php > 0.0) || !isfinite(php) || !isfinite(a) || !isfinite((double)(float)a))) c.active = 0;
+  c.alpha = c.active ? (float)a : 0.f;
   if (c.active) c.nmat += 2;
 }
 

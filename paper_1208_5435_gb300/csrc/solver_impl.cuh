@@ -241,7 +241,26 @@ __device__ __noinline__ double dct_slot_step(C* buf, const DctGeom& geo, const T
     // twiddles of frequency k = k2 + M k1 as products of this lane's k2 part and a root of
     // order 2G (resp. 8G) shared by all lanes: w_N^k = w_N^k2 exp(-i pi k1 / G) and
     // eps^k = eps^k2 exp(-i pi k1 / (4G)) (N = 2 M G)
+    // every global load of the slot (twiddles of this column, the G four-step twiddles kept
+    // for the scatter, the G mask codes) is issued before the exchange's shared-memory reads
     const C wk2 = tw.root(k2, geo.logN), ek2 = tw.root(k2, geo.logN + 2);
+    C t4[G];
+    unsigned mcs[G];
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+      t4[g] = g == 0 ? wk2 : tw.root((int64_t)g * k2, geo.logL);
+      mcs[g] = 0;
+      if constexpr (MODE != MODE_FORWARD) {
+        const int64_t k = (int64_t)k2 + (int64_t)M * g;
+        if (geo.mcode) {
+          mcs[g] = __ldg(&geo.mcode[k]);
+        } else {
+          const int64_t L = (int64_t)1 << geo.logL, N = geo.N;
+          mcs[g] = (geo.mask[k] ? 1u : 0u) | ((k > 0 && geo.mask[N - k]) ? 2u : 0u) | (geo.mask[L - k] ? 4u : 0u) |
+                   (geo.mask[L + k] ? 8u : 0u);
+        }
+      }
+    }
     auto pw = [&](int k1, C a, C b, R& accr) -> C {
       const int64_t k = (int64_t)k2 + (int64_t)M * k1;
       C wN = wk2, eps = ek2;
@@ -249,17 +268,7 @@ __device__ __noinline__ double dct_slot_step(C* buf, const DctGeom& geo, const T
         wN = cmul(wk2, tw.root(k1, kLogG + 1));
         eps = cmul(ek2, tw.root(k1, kLogG + 3));
       }
-      unsigned mb = 0;
-      if constexpr (MODE != MODE_FORWARD) {
-        if (geo.mcode) {
-          mb = __ldg(&geo.mcode[k]);
-        } else {
-          const int64_t L = (int64_t)1 << geo.logL, N = geo.N;
-          mb = (geo.mask[k] ? 1u : 0u) | ((k > 0 && geo.mask[N - k]) ? 2u : 0u) | (geo.mask[L - k] ? 4u : 0u) |
-               (geo.mask[L + k] ? 8u : 0u);
-        }
-      }
-      return dct_pointwise_w<C, MODE, R>(k, a, b, wN, eps, mb, geo, pc, valid, accr, fwd_out);
+      return dct_pointwise_w<C, MODE, R>(k, a, b, wN, eps, mcs[k1], geo, pc, valid, accr, fwd_out);
     };
     C Z[G];
 #pragma unroll
@@ -270,7 +279,7 @@ __device__ __noinline__ double dct_slot_step(C* buf, const DctGeom& geo, const T
       } else {
         y = cl.map_shared_rank(buf, g)[pos];
       }
-      Z[g] = (g == 0) ? y : cmul(y, tw.root((int64_t)g * k2, geo.logL));
+      Z[g] = (g == 0) ? y : cmul(y, t4[g]);
     }
     small_dft<G>(Z, false, tw);  // Z[k1] = H[k2 + M k1]
     // column 0: H[M k1] pairs with H[M ((G - k1) mod G)] of the same column
@@ -310,7 +319,7 @@ __device__ __noinline__ double dct_slot_step(C* buf, const DctGeom& geo, const T
       if (valid) {
 #pragma unroll
         for (int g = 0; g < G; ++g) {
-          const C y = (g == 0) ? Z[g] : cmulc(Z[g], tw.root((int64_t)g * k2, geo.logL));
+          const C y = (g == 0) ? Z[g] : cmulc(Z[g], t4[g]);
           if constexpr (G == 1) {
             buf[pos] = y;
           } else {
@@ -649,7 +658,7 @@ template <class H, class T> struct IpmShared {
   double rel_gap, P_obj, cn, rz0, rz;
   T apT, adT, ap1T, ad1T, tauT, keepT;  // step lengths etc. in the iterate's arithmetic
   H smu, ap1, ad1, s3mut, apH, adH, alpha, beta;
-  int corr, corr_next, stop, pcg_stop, correctors;
+  int corr, corr_next, stop, pcg_stop, pcg_brk, correctors;
   int lowp, redo;  // outer residual in float32 (large gap); recompute it in full precision
 };
 
@@ -689,10 +698,15 @@ __device__ int pcg_solve(Op& op, RedSmem& rs, SH& sh, int& par, typename V2<PS>:
           sh.rz0 = sh.rz = t[1];
           sh.pcg_stop = !(t[1] > 0.0) || !isfinite(t[1]);
         }
-        sh.alpha = (PS)(sh.rz / t[0]);
+        // breakdown guard: a direction with p^T H p not positive and finite (rounding when
+        // Theta^-1 spans many orders of magnitude) ends the solve with the last iterate
+        const double a_ = sh.rz / t[0];
+        sh.pcg_brk = !(t[0] > 0.0) || !isfinite(t[0]) || !isfinite(a_) || !isfinite((double)(PS)a_);
+        sh.alpha = (PS)a_;
       });
     }
-    if (sh.pcg_stop) {  // zero right-hand side: y = 0
+    if (sh.pcg_brk && !sh.pcg_stop && k > 0) break;  // keep the iterate of the last step
+    if (sh.pcg_stop || sh.pcg_brk) {  // zero right-hand side (or breakdown at once): y = 0
       P2 zero;
       zero.x = (PS)0;
       zero.y = (PS)0;

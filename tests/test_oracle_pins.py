@@ -529,3 +529,18 @@ def test_planted_certificate_mistake_is_caught(monkeypatch, mutation):
         caught.append(not (pin_kkt_off_optimum_error() < 1e-9))
         caught.append(pin_certificate_chain_violation() != 0.0)
     assert any(caught), f"mutation {mutation} slipped through every certificate pin"
+
+
+def test_pcg_breakdown_guard_returns_the_last_finite_iterate():
+    """A matrix that is not positive definite (negative Theta^-1 here) makes p^T H p <= 0 on
+    the first direction: the guarded PCG stops there with x = 0 instead of dividing by it."""
+    A, b, tau = _gauss_problem(8, 24, 2, 71)
+    op = O.Operator.from_dense(A)
+    d = -1e3 * np.ones(48)
+    x, it = O.pcg(op, d, _rng(72).standard_normal(48), O.rho_of(op), 1e-8)
+    assert it == 0 and np.all(x == 0.0)
+    # positive definite systems are untouched: the guarded PCG still solves them
+    d = np.exp(_rng(73).uniform(-3, 3, 48))
+    r = _rng(74).standard_normal(48)
+    x, it = O.pcg(op, d, r, O.rho_of(op), 1e-12, maxiter=500)
+    assert np.abs(x - O.solve_full_cholesky(op, d, r)).max() <= 1e-8 * np.abs(x).max()
