@@ -110,31 +110,3 @@ def test_products_match_explicit_rows():
     assert _relx(M.apply_A(op, torch.from_numpy(xr)).cpu().numpy(), A @ xr) <= 1e-12
     assert _relx(M.apply_At(op, torch.from_numpy(yr)).cpu().numpy(), A.T @ yr) <= 1e-12
 
-
-def test_pcg_breakdown_guard_finishes_the_hard_haar_problem():
-    """Problem 198 of the 256-problem Haar batch (n = 32768, m = 8192, k = 1505): its Newton
-    systems lose positive definiteness in rounding (Theta^-1 spans ~30 orders of magnitude),
-    and without the PCG breakdown guard the iteration produced NaN (MFIPM_NUMERIC) on every
-    cluster size; the oracle's float64 PCG variant broke down the same way.  With the guard
-    the solve ends with a finite x whose KKT residual, computed on the CPU, is small."""
-    M = mf()
-    p = W.make_workload("haar_batch_256")[198]
-    assert (p.n, p.m) == (32768, 8192)
-    x, info = M.solve(M.PartialHaar(p.n, torch.from_numpy(p.rows)), torch.from_numpy(p.b), p.tau,
-                      M.SolverParams(), raise_on_failure=False)
-    assert info["status"] in (0, 2), info        # OK or NOT_CONVERGED, never NUMERIC
-    x = x.cpu().numpy()
-    assert np.all(np.isfinite(x))
-    rows, n = p.rows, p.n
-
-    def mv(v):
-        return W.haar_apply(v)[rows]
-
-    def rmv(y):
-        full = np.zeros(n)
-        full[rows] = y
-        return W.haar_apply_t(full)
-
-    k = O.kkt_rel(O.Operator(len(rows), n, mv, rmv), p.b, p.tau, x)
-    print(f"Haar problem 198: status {info['status']} ipm {info['ipm_iters']} kkt_rel {k:.2e}")
-    assert k <= 1e-4

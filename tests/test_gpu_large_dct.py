@@ -120,8 +120,9 @@ def test_multipass_backward_matches_oracle_adjoint(threshold):
     res = _oracle(p)
     rb, rt, _ = O.adjoint_kkt(O.Operator.from_dct_rows(p.n, p.rows), p.b, p.tau, res.z, res.s, gx)
     gb = gbs[0].cpu().numpy()
-    assert np.abs(gb - rb).max() <= 2e-4 * np.abs(rb).max()
-    assert abs(gts[0] - rt) <= 2e-4 * max(1.0, abs(rt))
+    # float32 adjoint PCG to min(tol_pcg, 1e-6): measured 3.2e-7 (grad_b), 1.4e-7 (grad_tau)
+    assert np.abs(gb - rb).max() <= 5e-6 * np.abs(rb).max()
+    assert abs(gts[0] - rt) <= 5e-6 * max(1.0, abs(rt))
     assert infos[0]["status"] == 0 and infos[0]["pcg_iters"] > 0
 
 
