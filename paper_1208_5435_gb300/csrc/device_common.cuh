@@ -207,6 +207,82 @@ __device__ __forceinline__ int swz(int p, int logM) {
   return p ^ ((p >> sh) & 15);
 }
 
+// Radix-4 butterflies of the two transforms, in registers: the forward (DIF) one takes a0..a3
+// at stride S of a block and twiddles w, w^2, w^3 of the block's order; the inverse (DIT) one
+// undoes it with the conjugate twiddles.
+template <class C>
+__device__ __forceinline__ void bfly4_dif(C& a0, C& a1, C& a2, C& a3, C w1, C w2, C w3) {
+  const C s02 = cadd(a0, a2), d02 = csub(a0, a2), s13 = cadd(a1, a3), d13 = csub(a1, a3);
+  a0 = cadd(s02, s13);
+  a1 = cmul(csub(s02, s13), w2);
+  a2 = cmul(cadd(d02, cmul_mi(d13)), w1);
+  a3 = cmul(cadd(d02, cmul_i(d13)), w3);
+}
+template <class C>
+__device__ __forceinline__ void bfly4_dit(C& a0, C& a1, C& a2, C& a3, C w1, C w2, C w3) {
+  const C b1 = cmulc(a1, w2), b2 = cmulc(a2, w1), b3 = cmulc(a3, w3);
+  const C Ss = cadd(a0, b1), D = csub(a0, b1), E = cadd(b2, b3), F = csub(b3, b2);
+  a0 = cadd(Ss, E);
+  a1 = cadd(D, cmul_mi(F));
+  a2 = csub(Ss, E);
+  a3 = cadd(D, cmul_i(F));
+}
+
+// Two consecutive radix-4 stages of the forward transform (blocks of 2^logB, then of
+// 2^(logB-2)) in one pass over shared memory: each group of 16 points (stride 2^(logB-4) in
+// one block) is loaded once, both stages run in registers, and it is stored once -- half the
+// barriers and shared-memory traffic of two single stages, and 16 independent loads per
+// thread to cover their latency.
+template <class C>
+__device__ __forceinline__ void fft_dif_pass16(C* buf, int logM, int logB, const Twiddle<C>& tw) {
+  const int logS2 = logB - 4, S2 = 1 << logS2, S1 = S2 << 2;
+  for (int g = threadIdx.x; g < (1 << (logM - 4)); g += kThreads) {
+    const int blk = g >> logS2, t2 = g & (S2 - 1);
+    const int base = (blk << logB) + t2;
+    C x[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) x[j] = buf[swz(base + j * S2, logM)];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int t = t2 + i * S2;
+      bfly4_dif(x[i], x[i + 4], x[i + 8], x[i + 12], tw.root(t, logB), tw.root(2 * t, logB), tw.root(3 * t, logB));
+    }
+    const C v1 = tw.root(t2, logB - 2), v2 = tw.root(2 * t2, logB - 2), v3 = tw.root(3 * t2, logB - 2);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) bfly4_dif(x[4 * q], x[4 * q + 1], x[4 * q + 2], x[4 * q + 3], v1, v2, v3);
+#pragma unroll
+    for (int j = 0; j < 16; ++j) buf[swz(base + j * S2, logM)] = x[j];
+    (void)S1;
+  }
+}
+// The inverse of two consecutive forward stages: blocks of 2^(logB-2), then of 2^logB.
+template <class C>
+__device__ __forceinline__ void fft_dit_pass16(C* buf, int logM, int logB, const Twiddle<C>& tw) {
+  const int logS2 = logB - 4, S2 = 1 << logS2;
+  for (int g = threadIdx.x; g < (1 << (logM - 4)); g += kThreads) {
+    const int blk = g >> logS2, t2 = g & (S2 - 1);
+    const int base = (blk << logB) + t2;
+    C x[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) x[j] = buf[swz(base + j * S2, logM)];
+    const C v1 = tw.root(t2, logB - 2), v2 = tw.root(2 * t2, logB - 2), v3 = tw.root(3 * t2, logB - 2);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) bfly4_dit(x[4 * q], x[4 * q + 1], x[4 * q + 2], x[4 * q + 3], v1, v2, v3);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int t = t2 + i * S2;
+      bfly4_dit(x[i], x[i + 4], x[i + 8], x[i + 12], tw.root(t, logB), tw.root(2 * t, logB), tw.root(3 * t, logB));
+    }
+#pragma unroll
+    for (int j = 0; j < 16; ++j) buf[swz(base + j * S2, logM)] = x[j];
+  }
+}
+// The fused passes are used for 8-byte complex values (float32 chains) when every thread has a
+// group of 16 points; 16-byte values (double-float, float64) keep single stages (register room).
+template <class C> __device__ __forceinline__ bool use_pass16(int logM) {
+  return sizeof(C) == 8 && (1 << (logM - 4)) >= kThreads;
+}
+
 // In-place radix-4 decimation-in-frequency FFT of M = 2^logM points held in shared
 // memory (element p in slot swz(p)): natural-order input, bit-reversed output, forward sign
 // exp(-2 pi i jk/M).  Each radix-4 group is two radix-2 stages, so the output order is
@@ -215,6 +291,12 @@ template <class C, class R>
 __device__ void fft_dif(C* buf, int logM, const Twiddle<C>& tw) {
   const int M = 1 << logM;
   int logB = logM;
+  if (use_pass16<C>(logM)) {
+    for (; logB >= 4; logB -= 4) {
+      fft_dif_pass16(buf, logM, logB, tw);
+      __syncthreads();
+    }
+  }
   for (; logB >= 2; logB -= 2) {
     const int logS = logB - 2, S = 1 << logS;
     for (int gi = threadIdx.x; gi < (M >> 2); gi += kThreads) {
@@ -257,6 +339,32 @@ __device__ void fft_dit_inv(C* buf, int logM, const Twiddle<C>& tw) {
     }
     __syncthreads();
     logB = 3;
+  }
+  // the forward transform fused its first stages in pairs from the top: the single stages
+  // it ran last (the small blocks) are undone first, then the fused pairs
+  if (use_pass16<C>(logM)) {
+    const int fused = (logM - (logM & 1)) / 4;  // pairs the forward transform fused
+    const int single_top = logM - 4 * fused;    // largest block size of its single stages
+    for (; logB <= single_top; logB += 2) {
+      const int logS = logB - 2, S = 1 << logS;
+      for (int gi = threadIdx.x; gi < (M >> 2); gi += kThreads) {
+        const int blk = gi >> logS, t = gi & (S - 1);
+        const int p = (blk << logB) + t;
+        const int q0 = swz(p, logM), q1 = swz(p + S, logM), q2 = swz(p + 2 * S, logM), q3 = swz(p + 3 * S, logM);
+        C a0 = buf[q0], a1 = buf[q1], a2 = buf[q2], a3 = buf[q3];
+        bfly4_dit(a0, a1, a2, a3, tw.root(t, logB), tw.root(2 * t, logB), tw.root(3 * t, logB));
+        buf[q0] = a0;
+        buf[q1] = a1;
+        buf[q2] = a2;
+        buf[q3] = a3;
+      }
+      __syncthreads();
+    }
+    for (logB = single_top + 4; logB <= logM; logB += 4) {
+      fft_dit_pass16(buf, logM, logB, tw);
+      __syncthreads();
+    }
+    return;
   }
   for (; logB <= logM; logB += 2) {
     const int logS = logB - 2, S = 1 << logS;
