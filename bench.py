@@ -17,6 +17,7 @@ the same workload on the host cores.
 from __future__ import annotations
 
 import argparse
+import ctypes
 import json
 import os
 import statistics

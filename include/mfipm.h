@@ -75,7 +75,9 @@ typedef enum { MFIPM_A_F64 = 0, MFIPM_A_F32 = 1, MFIPM_A_BF16 = 2 } mfipm_a_dtyp
  * iterate updates) is float64 for dense operators; for the partial-DCT and partial-Haar
  * operators its per-index arithmetic follows mfipm_outer below (double-float by default),
  * while its scalar reductions and every output stay float64.
- *   MFIPM_PREC_FP64      PCG vectors and operator products in float64.
+ *   MFIPM_PREC_FP64      PCG vectors and operator products in float64 (dense A; partial DCT
+ *                        below the multi-pass threshold, with the float64 outer loop: the PCG
+ *                        tolerances of basis pursuit, tol_pcg down to 1e-6, Sec. 5.4).
  *   MFIPM_PREC_FP32_PCG  PCG vectors and operator products in float32 (the inexact Newton
  *                        direction is corrected by the float64 residuals of the outer loop).
  *   MFIPM_PREC_BF16_A    dense A stored bf16 (times a_scale) on the tensor cores with float32
@@ -113,7 +115,8 @@ typedef struct {
   double sigma1, sigma2, sigma3;  /* centering parameters (Sec. 5.1); 0.1, 0.5, 0.8 */
   double alpha_bar, alpha_tilde;  /* step-size thresholds (Sec. 5.1); 0.5, 0.1 */
   double eta;            /* fraction of the step to the boundary; 0.995 */
-  int32_t precision;     /* mfipm_precision; MFIPM_PREC_FP32_PCG for the DCT, MFIPM_PREC_FP64 dense */
+  int32_t precision;     /* mfipm_precision; default MFIPM_PREC_FP32_PCG (the Python binding passes
+                            MFIPM_PREC_FP64 for a dense float64 A unless told otherwise) */
   int32_t equal_steps;   /* 0: separate primal and dual steps as in Sec. 5.1; 1: common step */
   int32_t cluster_size;  /* CTAs that cooperate on one problem (1,2,4,8,16); 0 = automatic */
   int32_t outer;         /* mfipm_outer; MFIPM_OUTER_DF */

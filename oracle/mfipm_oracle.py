@@ -49,7 +49,13 @@ Readings where the paper is silent or ambiguous:
   R7 termination on the relative duality gap  z^T s / (1 + |P(z)|) <= tol
      (Sec. 5.1 "Duality Gap", Sec. 5.4 "tol");
   R8 sigma = sigma2 on iterations k != 1 whose previous step had
-     alpha_P <= alpha_bar or alpha_D <= alpha_bar, else sigma1.
+     alpha_P <= alpha_bar or alpha_D <= alpha_bar, else sigma1;
+  R19 multiple centrality correctors (the variant Sec. 5.1 describes as the original method
+     and sets aside; the paper gives no formulas): after the predictor, up to mcc correctors
+     with right-hand side (0, t), t the correction of the trial point's complementarity
+     products toward [beta_min, beta_max] * sigma*mu, trial point at the aspiration steps
+     alpha + delta, accepted while the smaller step grows by gamma * delta (beta_min 0.1,
+     beta_max 10, delta 0.1, gamma 0.1).
 """
 from __future__ import annotations
 
@@ -197,6 +203,44 @@ def recover_ds(fs, z, d, dz):
     return fs / z - d * dz
 
 
+def centrality_target(v, mu_t, beta_min, beta_max):
+    """Correction of the complementarity products v = z~ o s~ toward the box
+    [beta_min mu_t, beta_max mu_t] around the target barrier mu_t (multiple centrality
+    correctors, reading R19): t_i = beta_min mu_t - v_i below the box,
+    max(beta_max mu_t - v_i, -beta_max mu_t) above it, 0 inside."""
+    lo, hi = beta_min * mu_t, beta_max * mu_t
+    t = np.zeros_like(v)
+    below, above = v < lo, v > hi
+    t[below] = lo - v[below]
+    t[above] = np.maximum(hi - v[above], -hi)
+    return t
+
+
+def centrality_correctors(z, s, d, dz, ds, aP, aD, mu_t, p, solve, steps):
+    """Up to p.mcc centrality correctors after the predictor (dz, ds) with steps (aP, aD)
+    (reading R19).  Each takes the trial point of the current direction at the aspiration
+    steps min(1, alpha + delta), the correction t of its complementarity products toward the
+    box around mu_t, and solves the Newton system of Eq. sepregaugeq with right-hand side
+    (f_z, f_s) = (0, t): (Theta^-1 + F F^T) dz~ = Z^-1 t, ds~ = Z^-1 t - Theta^-1 dz~
+    (Eqs. redNewtonA/B).  The sum is kept when its smaller step grows by at least
+    gamma * delta; the first rejected corrector ends the sequence.
+    Returns (dz, ds, aP, aD, accepted)."""
+    acc = 0
+    for _ in range(p.mcc):
+        if min(aP, aD) >= 1.0:
+            break
+        aPt, aDt = min(1.0, aP + p.mcc_delta), min(1.0, aD + p.mcc_delta)
+        t = centrality_target((z + aPt * dz) * (s + aDt * ds), mu_t, p.mcc_beta_min, p.mcc_beta_max)
+        dzc = solve(d, newton_rhs(np.zeros_like(t), t, z))
+        dsc = recover_ds(t, z, d, dzc)
+        aPn, aDn = steps(dz + dzc, ds + dsc)
+        if min(aPn, aDn) < min(aP, aD) + p.mcc_gamma * p.mcc_delta:
+            break
+        dz, ds, aP, aD = dz + dzc, ds + dsc, aPn, aDn
+        acc += 1
+    return dz, ds, aP, aD, acc
+
+
 def corrector_direction(op: "Operator", b, tau, c, z, s, d, zt, st, sigma3, solve):
     """The corrector of the Algorithm (Sec. 5.1), reading R6: the right-hand side of
     Eq. fzfs is evaluated at the trial point (zt, st) = (z + alpha_P dz, s + alpha_D ds) with
@@ -338,6 +382,13 @@ class OracleParams:
     equal_steps: bool = False
     solver: str = "auto"        # "auto" | "cholesky" | "woodbury" | "pcg"
     tol_pcg: float = 1e-2       # only for solver="pcg"
+    # multiple centrality correctors (the method Sec. 5.1 starts from; reading R19): up to mcc
+    # correctors per iteration in place of the single conditional one; 0 = the Algorithm
+    mcc: int = 0
+    mcc_beta_min: float = 0.1
+    mcc_beta_max: float = 10.0
+    mcc_delta: float = 0.1      # aspiration: trial steps alpha + delta
+    mcc_gamma: float = 0.1      # acceptance: min step grows by at least gamma * delta
 
 
 @dataclasses.dataclass
@@ -407,8 +458,11 @@ def ipm(op: Operator, b, tau, params: Optional[OracleParams] = None) -> OracleRe
         dz = solve(d, newton_rhs(fz, fs, z))
         ds = recover_ds(fs, z, d, dz)
         aP, aD = steps(dz, ds)
+        if p.mcc > 0:                                                            # R19
+            dz, ds, aP, aD, acc = centrality_correctors(z, s, d, dz, ds, aP, aD, sigma * mu, p, solve, steps)
+            corr += acc
         # corrector (R6)
-        if aP <= p.alpha_tilde or aD <= p.alpha_tilde:
+        elif aP <= p.alpha_tilde or aD <= p.alpha_tilde:
             corr += 1
             dz2, ds2 = corrector_direction(op, b, tau, c, z, s, d, z + aP * dz, s + aD * ds, p.sigma3, solve)
             dz = dz + dz2

@@ -214,7 +214,7 @@ Layout make_layout(const mfipm_operator* ops, int batch, bool pcg64) {
 }
 
 bool pcg_in_fp64(const mfipm_operator& op, const mfipm_params* p) {
-  return op.kind == MFIPM_OP_DENSE && p->precision == MFIPM_PREC_FP64;
+  return (op.kind == MFIPM_OP_DENSE || op.kind == MFIPM_OP_PARTIAL_DCT) && p->precision == MFIPM_PREC_FP64;
 }
 
 int pick_G(const std::vector<mfipm_operator>& ops, const mfipm_params* p, int batch) {
@@ -302,8 +302,11 @@ int prepare(int batch, const mfipm_operator* ops, const double* const* b, const 
     if (P.dct && ops[i].n > kDctMaxN)
       return fail(MFIPM_UNSUPPORTED, "operator %d: n=%lld above the cluster solver's %lld", i, (long long)ops[i].n,
                   (long long)kDctMaxN);
-  if (P.dct && p->precision != MFIPM_PREC_FP32_PCG)
-    return fail(MFIPM_UNSUPPORTED, "the partial-DCT solver runs its PCG in float32 (precision=%d)", p->precision);
+  if (P.haar && p->precision != MFIPM_PREC_FP32_PCG)
+    return fail(MFIPM_UNSUPPORTED, "the partial-Haar solver runs its PCG in float32 (precision=%d)", p->precision);
+  if (P.dct && p->precision != MFIPM_PREC_FP32_PCG && p->precision != MFIPM_PREC_FP64)
+    return fail(MFIPM_UNSUPPORTED, "the partial-DCT solver runs its PCG in float32 or float64 (precision=%d)",
+                p->precision);
   if (P.haar && p->outer != MFIPM_OUTER_DF)
     return fail(MFIPM_UNSUPPORTED, "the partial-Haar solver keeps its iterate in double-float (outer=%d)", p->outer);
   if (!P.dct && p->precision == MFIPM_PREC_BF16_A)
@@ -401,6 +404,7 @@ int prepare(int batch, const mfipm_operator* ops, const double* const* b, const 
   a.twdf = reinterpret_cast<const float4*>(ws + P.lay.off_twdf);
   a.log2_tw = P.lay.log2_tw;
   a.prm = to_solve(p);
+  if (P.dct && P.pcg64) a.prm.resid_fp64 = 1;  // a float64 PCG runs with the float64 outer loop
   return MFIPM_OK;
 }
 
@@ -438,7 +442,8 @@ int run(Prepared& P, cudaStream_t st, int batch, mfipm_info* infos, const std::v
   }
   P.args.nbig = nbig;
   const bool f64 = P.args.prm.resid_fp64 != 0;
-  int maxc = P.haar  ? max_active_clusters_haar(P.G, P.max_n)
+  int maxc = P.haar             ? max_active_clusters_haar(P.G, P.max_n)
+             : P.dct && P.pcg64 ? max_active_clusters_dct_f64pcg(P.G, P.max_n)
              : P.dct ? (f64 ? max_active_clusters_dct_f64(P.G, P.max_n) : max_active_clusters_dct_df(P.G, P.max_n))
                      : max_active_clusters_dense(P.G, P.pcg64, P.max_n, P.max_m);
   if (maxc < 1) return fail(MFIPM_UNSUPPORTED, "no resident cluster of size %d fits this problem", P.G);
@@ -448,7 +453,8 @@ int run(Prepared& P, cudaStream_t st, int batch, mfipm_info* infos, const std::v
       if (!ev && (e = cudaEventCreate(&ev)) != cudaSuccess) return cuda_fail(e, "timing event");
     cudaEventRecord(g_ev[0], st);
   }
-  e = P.haar  ? launch_haar_solver(P.G, P.args, P.max_n, clusters, st)
+  e = P.haar             ? launch_haar_solver(P.G, P.args, P.max_n, clusters, st)
+      : P.dct && P.pcg64 ? launch_dct_solver_f64pcg(P.G, P.args, P.max_n, clusters, st)
       : P.dct ? (f64 ? launch_dct_solver_f64(P.G, P.args, P.max_n, clusters, st)
                      : launch_dct_solver_df(P.G, P.args, P.max_n, clusters, st))
               : launch_dense_solver(P.G, P.pcg64, P.args, P.max_n, P.max_m, clusters, st);
@@ -717,7 +723,8 @@ int solve_split(int batch, const mfipm_operator* ops, const double* const* b, co
     if (ops[i].kind != MFIPM_OP_PARTIAL_DCT) return fail(MFIPM_UNSUPPORTED, "a batch must use one operator kind");
   }
   if (p->precision != MFIPM_PREC_FP32_PCG)
-    return fail(MFIPM_UNSUPPORTED, "the partial-DCT solver runs its PCG in float32 (precision=%d)", p->precision);
+    return fail(MFIPM_UNSUPPORTED, "the multi-pass partial-DCT solver (n >= its threshold) runs its PCG in float32 "
+                "(precision=%d)", p->precision);
   const size_t small = split_small_bytes(ops, sp, p), need = small + split_large_bytes(sp);
   if (!workspace || ((uintptr_t)workspace & 255)) return fail(MFIPM_INVALID_ARG, "workspace NULL or not 256-byte aligned");
   if (ws_bytes < need) return fail(MFIPM_INVALID_ARG, "workspace too small: %zu < %zu bytes", ws_bytes, need);
@@ -1107,7 +1114,8 @@ int mfipm_backward(int32_t batch, const mfipm_operator* ops, const double* const
     if (grad_A && grad_A[i]) return fail(MFIPM_UNSUPPORTED, "grad_A is defined for dense operators only (operator %d)", i);
   }
   if (p->precision != MFIPM_PREC_FP32_PCG)
-    return fail(MFIPM_UNSUPPORTED, "the partial-DCT solver runs its PCG in float32 (precision=%d)", p->precision);
+    return fail(MFIPM_UNSUPPORTED, "the multi-pass partial-DCT solver (n >= its threshold) runs its PCG in float32 "
+                "(precision=%d)", p->precision);
   const size_t small = split_small_bytes(ops, sp, p), need = small + split_large_bytes(sp);
   if (!workspace || ((uintptr_t)workspace & 255)) return fail(MFIPM_INVALID_ARG, "workspace NULL or not 256-byte aligned");
   if (ws_bytes < need) return fail(MFIPM_INVALID_ARG, "workspace too small: %zu < %zu bytes", ws_bytes, need);

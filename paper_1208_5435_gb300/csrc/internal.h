@@ -90,6 +90,8 @@ size_t haar_smem_bytes(int G, int64_t max_n);
 cudaError_t launch_dct_solver_f64(int G, const KernelArgs& a, int64_t max_n, int grid_clusters, cudaStream_t st);
 cudaError_t launch_dense_solver(int G, bool fp64_pcg, const KernelArgs& a, int64_t max_n, int64_t max_m,
                                 int grid_clusters, cudaStream_t st);
+cudaError_t launch_dct_solver_f64pcg(int G, const KernelArgs& a, int64_t max_n, int grid_clusters, cudaStream_t st);
+int max_active_clusters_dct_f64pcg(int G, int64_t max_n);
 int max_active_clusters_dct_df(int G, int64_t max_n);
 int max_active_clusters_dct_f64(int G, int64_t max_n);
 int max_active_clusters_dense(int G, bool fp64_pcg, int64_t max_n, int64_t max_m);

@@ -395,7 +395,16 @@ template <int G> struct DctOp {
   // residual buffer: this CTA's chunk of x (in) / A^T(Ax - b) (out), one value per storage
   // position, as float64 or as double-float (both 16 bytes per complex pair)
   template <class T> __device__ __forceinline__ T* rbuf() const { return reinterpret_cast<T*>(buf64); }
-  template <class PS> __device__ __forceinline__ PS* wbuf() const { return reinterpret_cast<PS*>(buf32); }
+  // PCG operator buffer: float32 values in their own buffer; float64 values (the float64 PCG)
+  // share the residual buffer, whose content every PCG initialisation consumes element by
+  // element before writing the operator input in its place (same index, same thread)
+  template <class PS> __device__ __forceinline__ PS* wbuf() const {
+    if constexpr (sizeof(PS) == 8) {
+      return reinterpret_cast<PS*>(buf64);
+    } else {
+      return reinterpret_cast<PS*>(buf32);
+    }
+  }
   // rbuf := A^T (A rbuf - b); returns this CTA's share of ||A x - b||^2
   template <class T> __device__ double resid_t() {
     if constexpr (std::is_same<T, df>::value) {
@@ -405,7 +414,11 @@ template <int G> struct DctOp {
     }
   }
   template <class PS> __device__ double normal(PS*) {
-    return dct_chain<G, float2, MODE_NORMAL>(buf32, geo, tw32);
+    if constexpr (sizeof(PS) == 8) {
+      return dct_chain<G, double2, MODE_NORMAL>(buf64, geo, tw64);
+    } else {
+      return dct_chain<G, float2, MODE_NORMAL>(buf32, geo, tw32);
+    }
   }
   // The same residual through the float32 chain on the operator buffer (the outer loop's
   // large-gap iterations): rbuf holds x on entry and A^T(Ax - b) on exit.

@@ -79,7 +79,7 @@ def test_workspace_size_grows_with_batch(L):
 
 
 @pytest.mark.parametrize("case", ["n_not_pow2", "m_gt_n", "n_too_big", "tau_nonpositive", "null_ws", "small_ws",
-                                  "bad_cluster", "bad_eta", "dense_bf16_here", "dct_fp64_pcg"])
+                                  "bad_cluster", "bad_eta", "dense_bf16_here", "dct_bf16_prec"])
 def test_invalid_arguments_rejected_before_launch(L, case):
     from paper_1208_5435_gb300 import _capi as C
     p = C.Params()
@@ -105,8 +105,8 @@ def test_invalid_arguments_rejected_before_launch(L, case):
         p.eta = 1.0
     elif case == "dense_bf16_here":
         op.kind, op.a_dtype, op.A, op.lda, op.rows = C.OP_DENSE, C.A_BF16, 0x2000, op.n, None
-    elif case == "dct_fp64_pcg":
-        p.precision = C.PREC_FP64
+    elif case == "dct_bf16_prec":
+        p.precision = C.PREC_BF16_A
     info = C.Info()
     rc = L.mfipm_solve(ctypes.byref(op), ctypes.c_void_p(0x3000), tau, ctypes.byref(p), ctypes.c_void_p(0x4000),
                        None, ws, wsb, ctypes.byref(info), None)

@@ -39,3 +39,21 @@ def test_tiny_tau_matches_direct_oracle(tau, tol, tol_pcg):
     assert np.linalg.norm(xg - ref.x) <= 1e-6 * np.linalg.norm(ref.x)
     if tau <= 1e-7:
         assert np.linalg.norm(xg - p.x_hat) <= 1e-5 * np.linalg.norm(p.x_hat)
+
+
+@pytest.mark.parametrize("tau,tol,tol_pcg", SETTINGS)
+def test_tiny_tau_matrix_free_float64_pcg(tau, tol, tol_pcg):
+    """The same basis-pursuit settings on the matrix-free partial-DCT operator with the float64
+    PCG (precision MFIPM_PREC_FP64: FFT chain, PCG vectors and preconditioner in float64), which
+    reaches the tolpcg 1e-6 of the noiseless settings without explicit rows."""
+    import paper_1208_5435_gb300 as M
+    p = W.dct_problem(1024, 256, 10, 1008, 0, sigma=0.0, values="pm1")
+    A = O.dct_matrix_rows(p.n, p.rows)
+    ref = O.ipm(O.Operator.from_dense(A), p.b, tau, O.OracleParams(tol=1e-14))
+    x, info = M.solve(M.PartialDCT(p.n, torch.from_numpy(p.rows)), torch.from_numpy(p.b), tau,
+                      M.SolverParams(tol=tol, tol_pcg=tol_pcg, precision=0))
+    xg = x.cpu().numpy()
+    assert info["status"] == 0, info
+    assert np.linalg.norm(xg - ref.x) <= 1e-6 * np.linalg.norm(ref.x)
+    if tau <= 1e-7:
+        assert np.linalg.norm(xg - p.x_hat) <= 1e-5 * np.linalg.norm(p.x_hat)

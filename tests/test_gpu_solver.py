@@ -174,3 +174,16 @@ def test_no_measurements_gives_zero():
     op = M.PartialDCT(1024, torch.zeros(0, dtype=torch.int64))
     x, info = M.solve(op, torch.zeros(0, dtype=torch.float64), 0.1, M.SolverParams(tol=1e-12))
     assert info["status"] == 0 and float(x.abs().max()) <= 1e-8 and info["kkt_rel"] <= 1e-8
+
+
+@pytest.mark.parametrize("n,G", [(1024, 1), (1024, 4), (4096, 2), (4096, 16)])
+def test_dct_float64_pcg_matches_oracle(n, G):
+    """The partial-DCT operator with the float64 PCG (precision MFIPM_PREC_FP64)."""
+    p = W.dct_problem(n, n // 4, max(1, n // 100), seed=77, j=n)
+    xo = oracle_solution(p)
+    x, info = gpu_solve(p, cluster_size=G, precision=0)
+    assert info["status"] == 0, info
+    assert relx(x, xo) <= RELX_TOL, (relx(x, xo), info)
+    # the float64 PCG matches the float32 one's IPM iteration count to within a few iterations
+    x32, info32 = gpu_solve(p, cluster_size=G)
+    assert abs(info["ipm_iters"] - info32["ipm_iters"]) <= 4

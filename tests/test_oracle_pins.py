@@ -209,6 +209,32 @@ def pin_corrector_error(seed=19, m=3, n=6, aP=0.07, aD=0.04):
     return float(np.abs(got - want).max() / np.abs(want).max())
 
 
+def pin_mcc_step_error(seed=31, m=3, n=6, aP=0.3, aD=0.5, mu_t=0.05):
+    """One multiple-centrality corrector (reading R19) at a fixed interior (z, s) and a fixed
+    direction, against the 4n x 4n block system of Eq. sepregaugeq with right-hand side
+    (0, t): t written out here from the box [0.1 mu_t, 10 mu_t] around mu_t at the trial point
+    of the aspiration steps alpha + 0.1."""
+    rng = _rng(seed)
+    A = rng.standard_normal((m, n))
+    z = rng.uniform(0.05, 2.0, 2 * n)
+    s = rng.uniform(0.05, 2.0, 2 * n)
+    dz, ds = rng.standard_normal(2 * n), rng.standard_normal(2 * n)
+    Ft = np.hstack([A, -A])
+    K = np.block([[Ft.T @ Ft, -np.eye(2 * n)], [np.diag(s), np.diag(z)]])
+    v = (z + min(1.0, aP + 0.1) * dz) * (s + min(1.0, aD + 0.1) * ds)
+    t = np.where(v < 0.1 * mu_t, 0.1 * mu_t - v, np.where(v > 10 * mu_t, np.maximum(10 * mu_t - v, -10 * mu_t), 0.0))
+    assert np.count_nonzero(t) > 0
+    want = np.linalg.solve(K, np.concatenate([np.zeros(2 * n), t]))
+    op = O.Operator.from_dense(A)
+    d = s / z
+    prm = O.OracleParams(mcc=1, mcc_gamma=-1e9)   # accept whatever the step does
+    dz2, ds2, _, _, acc = O.centrality_correctors(z, s, d, dz, ds, aP, aD, mu_t, prm,
+                                                  lambda dd, r: O.solve_full_cholesky(op, dd, r),
+                                                  lambda a, b: (0.9, 0.9))
+    got = np.concatenate([dz2 - dz, ds2 - ds])
+    return float(np.abs(got - want).max() / np.abs(want).max()) if acc == 1 else 1.0
+
+
 def _orthonormal_problem(seed, n=40):
     rng = _rng(seed)
     Q, _ = np.linalg.qr(rng.standard_normal((n, n)))
@@ -350,6 +376,36 @@ def test_ipm_corrector_optimality_dense():
     v_on, v_off = O.optimality_violation(op, b, tau, r.x, support_tol=1e-7)
     assert v_on < 1e-8 and v_off < 1e-10
     assert np.linalg.norm(r.x - r0.x) / np.linalg.norm(r0.x) < 1e-8
+
+
+def test_mcc_step_matches_block_system():
+    assert pin_mcc_step_error() < 1e-10
+    assert pin_mcc_step_error(seed=32, m=4, n=9, aP=0.95, aD=0.2, mu_t=0.3) < 1e-10
+
+
+@pytest.mark.parametrize("pin,bar", [(pin_closed_form_error, 1e-9), (pin_brute_force_error, 1e-8)])
+def test_ipm_with_multiple_centrality_correctors(pin, bar, monkeypatch):
+    """mcc = 3: the closed-form and brute-force pins still hold, and correctors were taken."""
+    seen = []
+    orig = O.ipm
+
+    def ipm_mcc(op, b, tau, params=None):
+        r = orig(op, b, tau, dataclasses.replace(params or O.OracleParams(), mcc=3))
+        seen.append(r)
+        return r
+
+    monkeypatch.setattr(O, "ipm", ipm_mcc)
+    assert pin() < bar
+    assert seen[-1].converged
+
+
+def test_mcc_takes_correctors_and_saves_iterations():
+    A, b, tau = _gauss_problem(40, 160, 6, 81)
+    op = O.Operator.from_dense(A)
+    r0 = O.ipm(op, b, tau)
+    r = O.ipm(op, b, tau, O.OracleParams(mcc=3))
+    assert r.converged and r.correctors > 0 and r.iters <= r0.iters
+    assert np.linalg.norm(r.x - r0.x) <= 1e-8 * np.linalg.norm(r0.x)
 
 
 def test_kkt_rel_closed_form_away_from_optimum():
@@ -544,3 +600,36 @@ def test_pcg_breakdown_guard_returns_the_last_finite_iterate():
     r = _rng(74).standard_normal(48)
     x, it = O.pcg(op, d, r, O.rho_of(op), 1e-12, maxiter=500)
     assert np.abs(x - O.solve_full_cholesky(op, d, r)).max() <= 1e-8 * np.abs(x).max()
+
+
+@pytest.mark.parametrize("mutation", ["box_sign", "rhs_with_fz", "ds_without_t", "trial_current"])
+def test_planted_mcc_mistake_is_caught(monkeypatch, mutation):
+    orig_t, orig_cc = O.centrality_target, O.centrality_correctors
+    if mutation == "box_sign":          # pushes away from the box
+        monkeypatch.setattr(O, "centrality_target", lambda v, mu, lo, hi: -orig_t(v, mu, lo, hi))
+    elif mutation == "rhs_with_fz":     # right-hand side (t, t) instead of (0, t)
+        def cc(z, s, d, dz, ds, aP, aD, mu_t, p, solve, steps):
+            t = O.centrality_target((z + min(1, aP + p.mcc_delta) * dz) * (s + min(1, aD + p.mcc_delta) * ds),
+                                    mu_t, p.mcc_beta_min, p.mcc_beta_max)
+            dzc = solve(d, O.newton_rhs(t, t, z))
+            return dz + dzc, ds + O.recover_ds(t, z, d, dzc), 0.9, 0.9, 1
+        monkeypatch.setattr(O, "centrality_correctors", cc)
+    elif mutation == "ds_without_t":    # ds~ = -Theta^-1 dz~ (the Z^-1 t term dropped)
+        def cc(z, s, d, dz, ds, aP, aD, mu_t, p, solve, steps):
+            t = O.centrality_target((z + min(1, aP + p.mcc_delta) * dz) * (s + min(1, aD + p.mcc_delta) * ds),
+                                    mu_t, p.mcc_beta_min, p.mcc_beta_max)
+            dzc = solve(d, O.newton_rhs(np.zeros_like(t), t, z))
+            return dz + dzc, ds - d * dzc, 0.9, 0.9, 1
+        monkeypatch.setattr(O, "centrality_correctors", cc)
+    elif mutation == "trial_current":   # products of the current point instead of the trial point
+        def cc(z, s, d, dz, ds, aP, aD, mu_t, p, solve, steps):
+            t = O.centrality_target(z * s, mu_t, p.mcc_beta_min, p.mcc_beta_max)
+            dzc = solve(d, O.newton_rhs(np.zeros_like(t), t, z))
+            return dz + dzc, ds + O.recover_ds(t, z, d, dzc), 0.9, 0.9, 1
+        monkeypatch.setattr(O, "centrality_correctors", cc)
+    with np.errstate(all="ignore"):
+        try:
+            e = pin_mcc_step_error()
+        except Exception:
+            e = 1.0
+    assert not (e < 1e-10), f"mutation {mutation} slipped through"
