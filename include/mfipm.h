@@ -124,7 +124,20 @@ typedef struct {
                             outer residual A^T(Ax - b) runs through the float32 FFT chain; at the
                             first iterate at or below it, and before any stop, it is recomputed
                             in the outer loop's precision (mfipm_outer), which every later
-                            iteration keeps.  0 = always the outer precision.  1e-2 */
+                            iteration keeps.  Applied only when tau >= 1e-3 ||A^T b||_inf (the
+                            float32 chain errs by ~1e-6 ||A^T b||_inf); smaller tau (basis
+                            pursuit, the phase-transition workload) always use the outer
+                            precision.  0 = always the outer precision.  1e-2 */
+  int32_t centrality_correctors;  /* 0 (default): the single conditional corrector of the
+                            Algorithm (Sec. 5.1).  K in 1..16: the multiple-centrality-corrector
+                            variant that Sec. 5.1 names as the method's origin: after each
+                            predictor, up to K correctors, each one more PCG solve with
+                            right-hand side (0, t) of Eq. sepregaugeq, t moving the trial
+                            point's products z_i s_i (at the steps alpha + 0.1) into
+                            [0.1, 10] * sigma * mu; a corrector is kept while the smaller step
+                            grows by at least 0.01.  Persistent-kernel paths only (partial DCT
+                            and Haar below the multi-pass threshold, dense float64 A);
+                            MFIPM_UNSUPPORTED elsewhere.  info.correctors counts the kept ones. */
 } mfipm_params;
 
 typedef struct {

@@ -26,7 +26,8 @@ class Params(ctypes.Structure):
                 ("max_iter_pcg", ctypes.c_int32), ("sigma1", ctypes.c_double), ("sigma2", ctypes.c_double),
                 ("sigma3", ctypes.c_double), ("alpha_bar", ctypes.c_double), ("alpha_tilde", ctypes.c_double),
                 ("eta", ctypes.c_double), ("precision", ctypes.c_int32), ("equal_steps", ctypes.c_int32),
-                ("cluster_size", ctypes.c_int32), ("outer", ctypes.c_int32), ("outer_f32_gap", ctypes.c_double)]
+                ("cluster_size", ctypes.c_int32), ("outer", ctypes.c_int32), ("outer_f32_gap", ctypes.c_double),
+                ("centrality_correctors", ctypes.c_int32)]
 
 
 class Info(ctypes.Structure):

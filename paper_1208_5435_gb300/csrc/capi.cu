@@ -135,6 +135,8 @@ int validate_params(const mfipm_params* p) {
     return fail(MFIPM_INVALID_ARG, "params: bad outer-loop arithmetic %d", p->outer);
   if (!(p->outer_f32_gap >= 0) || !isfinite(p->outer_f32_gap))
     return fail(MFIPM_INVALID_ARG, "params: outer_f32_gap must be finite and >= 0");
+  if (p->centrality_correctors < 0 || p->centrality_correctors > 16)
+    return fail(MFIPM_INVALID_ARG, "params: centrality_correctors must lie in [0, 16]");
   const int cs = p->cluster_size;
   if (!(cs == 0 || cs == 1 || cs == 2 || cs == 4 || cs == 8 || cs == 16))
     return fail(MFIPM_INVALID_ARG, "params: cluster_size must be 0,1,2,4,8,16");
@@ -156,6 +158,11 @@ SolveParams to_solve(const mfipm_params* p) {
   s.equal_steps = p->equal_steps;
   s.resid_fp64 = p->outer == MFIPM_OUTER_FP64;
   s.f32_gap = p->outer_f32_gap;
+  s.mcc = p->centrality_correctors;
+  s.mcc_beta_min = 0.1;
+  s.mcc_beta_max = 10.0;
+  s.mcc_delta = 0.1;
+  s.mcc_gamma = 0.1;
   return s;
 }
 
@@ -176,7 +183,7 @@ size_t problem_bytes(const mfipm_operator& op, bool pcg64) {
     b += align256(n) + 2 * align256(8 * n);  // mask, bsu, bsu_df
   if (op.kind == MFIPM_OP_PARTIAL_DCT) b += align256(n / 2) + align256(16 * n);  // mcode, bpk
   b += align256(32 * n);                                                     // z, s
-  b += align256(5 * n * (pcg64 ? 16 : 8));                                   // x1 x2 r p d
+  b += align256(6 * n * (pcg64 ? 16 : 8));                                   // x1 x2 r p d xc
   b += align256(8 * n);                                                      // scratch (apply)
   return b;
 }
@@ -386,7 +393,7 @@ int prepare(int batch, const mfipm_operator* ops, const double* const* b, const 
     d.zs = reinterpret_cast<double*>(ws + q);
     q += align256(32 * n);
     d.pcg = ws + q;
-    q += align256(5 * n * (P.pcg64 ? 16 : 8));
+    q += align256(6 * n * (P.pcg64 ? 16 : 8));
     d.scratch = reinterpret_cast<double*>(ws + q);
     q += align256(8 * n);
     d.grad_tau = reinterpret_cast<double*>(ws + P.lay.off_gtau) + i;
@@ -594,6 +601,9 @@ int solve_shared_bf16(int batch, const mfipm_operator* ops, const double* const*
     if (!(tau[i] > 0.0) || !isfinite(tau[i])) return fail(MFIPM_INVALID_ARG, "tau[%d] must be positive and finite", i);
     if (!b[i] || !x[i]) return fail(MFIPM_INVALID_ARG, "b[%d] or x[%d] is NULL", i, i);
   }
+  if (p->centrality_correctors > 0)
+    return fail(MFIPM_UNSUPPORTED, "multiple centrality correctors run on the persistent kernel only, not on the "
+                "shared-A bf16 solver");
   size_t need = 0;
   int rc = mfipm_workspace_size(ops, batch, p, &need);
   if (rc) return rc;
@@ -725,6 +735,9 @@ int solve_split(int batch, const mfipm_operator* ops, const double* const* b, co
   if (p->precision != MFIPM_PREC_FP32_PCG)
     return fail(MFIPM_UNSUPPORTED, "the multi-pass partial-DCT solver (n >= its threshold) runs its PCG in float32 "
                 "(precision=%d)", p->precision);
+  if (p->centrality_correctors > 0 && !sp.groups.empty())
+    return fail(MFIPM_UNSUPPORTED, "multiple centrality correctors run on the persistent kernel only, not on the "
+                "multi-pass partial-DCT solver");
   const size_t small = split_small_bytes(ops, sp, p), need = small + split_large_bytes(sp);
   if (!workspace || ((uintptr_t)workspace & 255)) return fail(MFIPM_INVALID_ARG, "workspace NULL or not 256-byte aligned");
   if (ws_bytes < need) return fail(MFIPM_INVALID_ARG, "workspace too small: %zu < %zu bytes", ws_bytes, need);
@@ -1116,6 +1129,9 @@ int mfipm_backward(int32_t batch, const mfipm_operator* ops, const double* const
   if (p->precision != MFIPM_PREC_FP32_PCG)
     return fail(MFIPM_UNSUPPORTED, "the multi-pass partial-DCT solver (n >= its threshold) runs its PCG in float32 "
                 "(precision=%d)", p->precision);
+  if (p->centrality_correctors > 0 && !sp.groups.empty())
+    return fail(MFIPM_UNSUPPORTED, "multiple centrality correctors run on the persistent kernel only, not on the "
+                "multi-pass partial-DCT solver");
   const size_t small = split_small_bytes(ops, sp, p), need = small + split_large_bytes(sp);
   if (!workspace || ((uintptr_t)workspace & 255)) return fail(MFIPM_INVALID_ARG, "workspace NULL or not 256-byte aligned");
   if (ws_bytes < need) return fail(MFIPM_INVALID_ARG, "workspace too small: %zu < %zu bytes", ws_bytes, need);

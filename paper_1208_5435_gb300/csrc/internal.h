@@ -14,7 +14,9 @@ namespace mfipm {
 struct SolveParams {
   double tol, tol_pcg, sigma1, sigma2, sigma3, alpha_bar, alpha_tilde, eta;
   double f32_gap;  // relative gap above which the partial-DCT outer residual runs in float32
+  double mcc_beta_min, mcc_beta_max, mcc_delta, mcc_gamma;  // centrality correctors (reading R19)
   int32_t max_iter, max_iter_pcg, equal_steps, resid_fp64;
+  int32_t mcc;     // multiple centrality correctors per iteration (0: the single corrector)
 };
 
 // One problem of a launch.  Vectors of length n live in the caller's workspace, in the
@@ -55,7 +57,7 @@ struct ProbDesc {
   double* grad_b;         // DEVICE m or null
   double* grad_A;         // DEVICE m x n or null (dense)
   double* grad_tau;       // DEVICE 1
-  void* pcg;              // DEVICE 5 vectors of n pairs (x1, x2, r, p, d), float or double pairs
+  void* pcg;              // DEVICE 6 vectors of n pairs (x1, x2, r, p, d, xc), float or double pairs
   mfipm_info* info;       // DEVICE
 };
 

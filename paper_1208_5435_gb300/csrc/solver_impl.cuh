@@ -585,6 +585,7 @@ template <int G> struct DenseOp {
 template <class H> struct ScH {
   H smu, ap1, ad1, s3mut;
   bool corr;
+  bool mcc;  // multiple centrality correctors: the second vector holds the summed targets t
 };
 
 __device__ __forceinline__ float rcpH(float z) { return __frcp_rn(z); }
@@ -602,7 +603,9 @@ template <class H>
 __device__ __forceinline__ Dir<H> direction(H z, H s, H dz1, H dz2, const ScH<H>& c) {
   const H rz = rcpH(z);
   const H d = s * rz;
-  const H ds1 = (c.smu * rz - s) - d * dz1;
+  // with centrality correctors (reading R19) dz1 is the summed direction and dz2 the summed
+  // targets T: ds = Z^-1 (f_s + T) - Theta^-1 dz (Eq. redNewtonB, right-hand side f_s + T)
+  const H ds1 = ((c.mcc ? c.smu + dz2 : c.smu) * rz - s) - d * dz1;
   Dir<H> r{dz1, ds1};
   if (c.corr) {
     const H zt = z + c.ap1 * dz1;
@@ -673,6 +676,7 @@ template <class H, class T> struct IpmShared {
   H smu, ap1, ad1, s3mut, apH, adH, alpha, beta;
   int corr, corr_next, stop, pcg_stop, pcg_brk, correctors;
   int lowp, redo;  // outer residual in float32 (large gap); recompute it in full precision
+  int mcc_on, mcc_acc;  // centrality correctors enabled; the last one was accepted
 };
 
 template <class H, class T>
@@ -683,7 +687,16 @@ __device__ __forceinline__ ScH<H> steering(const IpmShared<H, T>& sh, bool corr)
   c.ad1 = sh.ad1;
   c.s3mut = sh.s3mut;
   c.corr = corr;
+  c.mcc = sh.mcc_on != 0;
   return c;
+}
+
+// Correction of one complementarity product v = z~ s~ toward [beta_min mu_t, beta_max mu_t]
+// (multiple centrality correctors, reading R19).
+template <class H> __device__ __forceinline__ H centrality_t(H v, H lo, H hi) {
+  if (v < lo) return lo - v;
+  if (v > hi) return fmax(hi - v, -hi);
+  return (H)0;
 }
 
 // PCG on (Theta^-1 + F F^T) y = rhs (Sec. 4, preconditioner of Eq. eq:ne2_P).  On entry
@@ -799,6 +812,7 @@ __device__ void solve_one(const ProbDesc& pd, const KernelArgs& a, Op& op, RedSm
   P2* __restrict__ Rv = X2 + n;
   P2* __restrict__ Pv = Rv + n;
   P2* __restrict__ Dv = Pv + n;
+  P2* __restrict__ Xc = Dv + n;  // a centrality corrector's direction before it is accepted
   T* __restrict__ gbuf = op.template rbuf<T>();
   PS* __restrict__ w = op.template wbuf<PS>();
   const T zeroT = S::from_d(0.0);
@@ -814,12 +828,21 @@ __device__ void solve_one(const ProbDesc& pd, const KernelArgs& a, Op& op, RedSm
   {
     const double bb = op.template resid_t<T>();
     ++nmat;
-    double atb2 = 0.0;
+    double atb2 = 0.0, atbmax = 0.0;
     for (int64_t q = tid; q < chunk; q += kThreads)
       if (op.valid(q)) {
         const double g = S::to_d(gbuf[q]);
         atb2 += g * g;
+        atbmax = fmax(atbmax, fabs(g));
       }
+    {
+      // the float32 residual chain errs by ~1e-6 ||A^T b||_inf; it is used only while that
+      // stays three orders below tau, the scale of the dual residual f_z = s - tau -+ g
+      double vm[1] = {-atbmax};
+      cluster_reduce<G, 1, true>(rs, par, vm, [&](const double (&t)[1]) {
+        sh.lowp = Op::kLowpResid && prm.f32_gap > 0.0 && tau >= 1e-3 * (-t[0]);
+      });
+    }
     double v[2] = {atb2, bb};
     cluster_reduce<G, 2>(rs, par, v, [&](const double (&t)[2]) {
       sh.cn = sqrt(2.0 * (double)n * tau * tau + 2.0 * t[0]);
@@ -832,8 +855,9 @@ __device__ void solve_one(const ProbDesc& pd, const KernelArgs& a, Op& op, RedSm
       sh.corr = sh.corr_next = 0;
       sh.correctors = 0;
       sh.stop = 0;
-      sh.lowp = Op::kLowpResid && prm.f32_gap > 0.0;
       sh.redo = 0;
+      sh.mcc_on = prm.mcc > 0;
+      sh.mcc_acc = 0;
       sh.rel_gap = INFINITY;
       sh.P_obj = 0.0;
     });
@@ -879,7 +903,7 @@ __device__ void solve_one(const ProbDesc& pd, const KernelArgs& a, Op& op, RedSm
     P2 x2;
     x2.x = (PS)0;
     x2.y = (PS)0;
-    if (c.corr) x2 = X2[gi];
+    if (c.corr || c.mcc) x2 = X2[gi];
     du = direction<H>((H)S::hf(st.u), (H)S::hf(st.su), x1.x, x2.x, c);
     dv = direction<H>((H)S::hf(st.v), (H)S::hf(st.sv), x1.y, x2.y, c);
   };
@@ -912,7 +936,7 @@ __device__ void solve_one(const ProbDesc& pd, const KernelArgs& a, Op& op, RedSm
       sh.adH = (H)ad;
       sh.apT = S::from_d(ap);
       sh.adT = S::from_d(ad);
-      sh.corr_next = corr ? 0 : (ap <= prm.alpha_tilde || ad <= prm.alpha_tilde);
+      sh.corr_next = (corr || sh.mcc_on) ? 0 : (ap <= prm.alpha_tilde || ad <= prm.alpha_tilde);
       if (sh.corr_next) {
         sh.alpha_p1 = ap;
         sh.alpha_d1 = ad;
@@ -1015,18 +1039,105 @@ __device__ void solve_one(const ProbDesc& pd, const KernelArgs& a, Op& op, RedSm
     {
       const H smuH = sh.smu;
       // rhs = f_z + Z^-1 f_s = sigma mu / z - (c + F F^T z) = sigma mu / z - [tau + g; tau - g]
-      pcg_init([&](int64_t q, int64_t, const Q& st) {
+      const bool mcc = sh.mcc_on != 0;
+      pcg_init([&](int64_t q, int64_t gi, const Q& st) {
                  const T g = gbuf[q];
                  P2 r;
                  r.x = smuH * rcpH((H)S::hf(st.u)) - (H)S::hf(S::add(tauT, g));
                  r.y = smuH * rcpH((H)S::hf(st.v)) - (H)S::hf(S::sub(tauT, g));
+                 if (mcc) {  // no centrality targets yet
+                   P2 zero;
+                   zero.x = (PS)0;
+                   zero.y = (PS)0;
+                   X2[gi] = zero;
+                 }
                  return r;
                }, true, rzp, pdpp);
     }
     pcg(X1, rzp, pdpp);
     step_lengths(false);
+    // ---- multiple centrality correctors (reading R19), in place of the single corrector
+    for (int kc = 0; sh.mcc_on && kc < prm.mcc; ++kc) {
+      if (sh.alpha_p >= 1.0 && sh.alpha_d >= 1.0) break;
+      const ScH<H> c = steering(sh, false);
+      const H apt = (H)fmin(1.0, sh.alpha_p + prm.mcc_delta), adt = (H)fmin(1.0, sh.alpha_d + prm.mcc_delta);
+      const H lo = (H)(prm.mcc_beta_min * sh.sigma * sh.mu), hi = (H)(prm.mcc_beta_max * sh.sigma * sh.mu);
+      // targets of this corrector from the current summed direction, at the aspiration steps
+      auto targets = [&](int64_t gi, const Q& st, P2& tv) {
+        Dir<H> du, dv;
+        load_dir(gi, st, c, du, dv);
+        const H zu = (H)S::hf(st.u), zv = (H)S::hf(st.v);
+        tv.x = centrality_t<H>((zu + apt * du.dz) * ((H)S::hf(st.su) + adt * du.ds), lo, hi);
+        tv.y = centrality_t<H>((zv + apt * dv.dz) * ((H)S::hf(st.sv) + adt * dv.ds), lo, hi);
+      };
+      // (Theta^-1 + F F^T) dz~ = Z^-1 t  (right-hand side (f_z, f_s) = (0, t))
+      pcg_init([&](int64_t, int64_t gi, const Q& st) {
+                 P2 tv;
+                 targets(gi, st, tv);
+                 P2 r;
+                 r.x = tv.x * rcpH((H)S::hf(st.u));
+                 r.y = tv.y * rcpH((H)S::hf(st.v));
+                 return r;
+               }, false, rzp, pdpp);
+      pcg(Xc, rzp, pdpp);
+      // step lengths of the sum (dz + dz~, T + t); keep it when the smaller step grows by
+      // at least gamma * delta
+      {
+        H mp = (H)INFINITY, md = (H)INFINITY;
+        for (int64_t q = tid; q < chunk; q += kThreads) {
+          if (!op.valid(q)) continue;
+          const int64_t gi = gb + q;
+          const Q st = S::load(zs, gi);
+          P2 tv;
+          targets(gi, st, tv);
+          const P2 x1 = X1[gi], xc = Xc[gi], x2 = X2[gi];
+          const Dir<H> du = direction<H>((H)S::hf(st.u), (H)S::hf(st.su), x1.x + xc.x, x2.x + tv.x, c);
+          const Dir<H> dv = direction<H>((H)S::hf(st.v), (H)S::hf(st.sv), x1.y + xc.y, x2.y + tv.y, c);
+          if (du.dz < (H)0) mp = fmin(mp, (H)S::hf(st.u) * rcpH(-du.dz));
+          if (dv.dz < (H)0) mp = fmin(mp, (H)S::hf(st.v) * rcpH(-dv.dz));
+          if (du.ds < (H)0) md = fmin(md, (H)S::hf(st.su) * rcpH(-du.ds));
+          if (dv.ds < (H)0) md = fmin(md, (H)S::hf(st.sv) * rcpH(-dv.ds));
+        }
+        H v[2] = {mp, md};
+        cluster_reduce<G, 2, true>(rs, par, v, [&](const double (&t)[2]) {
+          double ap = fmin(1.0, prm.eta * t[0]);
+          double ad = fmin(1.0, prm.eta * t[1]);
+          if (prm.equal_steps) ap = ad = fmin(ap, ad);
+          sh.mcc_acc = fmin(ap, ad) >= fmin(sh.alpha_p, sh.alpha_d) + prm.mcc_gamma * prm.mcc_delta;
+          if (sh.mcc_acc) {
+            sh.alpha_p = ap;
+            sh.alpha_d = ad;
+            sh.apH = (H)ap;
+            sh.adH = (H)ad;
+            sh.apT = S::from_d(ap);
+            sh.adT = S::from_d(ad);
+            sh.prev_ap = ap;
+            sh.prev_ad = ad;
+            ++sh.correctors;
+          }
+        });
+      }
+      if (!sh.mcc_acc) break;
+      // accept: dz += dz~, T += t (the targets from the direction before the sum)
+      for (int64_t q = tid; q < chunk; q += kThreads) {
+        if (!op.valid(q)) continue;
+        const int64_t gi = gb + q;
+        const Q st = S::load(zs, gi);
+        P2 tv;
+        targets(gi, st, tv);
+        P2 x1 = X1[gi], x2 = X2[gi];
+        const P2 xc = Xc[gi];
+        x1.x += xc.x;
+        x1.y += xc.y;
+        x2.x += tv.x;
+        x2.y += tv.y;
+        X1[gi] = x1;
+        X2[gi] = x2;
+      }
+      __syncthreads();
+    }
     // ---- corrector (reading R6)
-    if (sh.corr_next) {
+    if (sh.corr_next && !sh.mcc_on) {
       H zts_t = 0;
       {
         const ScH<H> c = steering(sh, false);  // predictor direction only
