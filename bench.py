@@ -691,6 +691,67 @@ def run_phase(args, rank, world, local_rank):
     print(json.dumps(line), flush=True)
 
 
+def direct_ipm_gpu(A, b, tau, tol=1e-10, max_iter=100, eta=0.995):
+    """Comparison arm of the PCG-against-direct leg (Sec. 5.7) on the same GPU: the
+    Algorithm of Sec. 5.1 (sigma1/sigma2/sigma3, alpha_bar, alpha_tilde as the library's
+    defaults, readings R1-R8) with every Newton system of Eq. redNewtonA solved by a Cholesky
+    factorisation (the vendor library's, through torch, float64) of the m x m matrix
+    I + A (Theta_u + Theta_v) A^T (Sherman-Morrison-Woodbury).  Not the library's path: the
+    direct variant the paper compares its PCG against.  Returns (x, Newton directions)."""
+    import torch
+    n = A.shape[1]
+    atb = A.T @ b
+    c = torch.cat([tau - atb, tau + atb])
+    z = torch.ones(2 * n, dtype=torch.float64, device=A.device)
+    s = torch.ones_like(z)
+    aP_prev = aD_prev = 1.0
+
+    def FFt(v):
+        t = A.T @ (A @ (v[:n] - v[n:]))
+        return torch.cat([t, -t])
+
+    def newton(d, r):
+        th = 1.0 / d
+        Mw = (A * (th[:n] + th[n:])[None, :]) @ A.T
+        Mw.diagonal().add_(1.0)
+        Lc = torch.linalg.cholesky(Mw)
+        Dr = th * r
+        y = torch.cholesky_solve((A @ (Dr[:n] - Dr[n:]))[:, None], Lc)[:, 0]
+        aty = A.T @ y
+        return Dr - th * torch.cat([aty, -aty])
+
+    def step(v, dv):
+        neg = dv < 0
+        if not bool(neg.any()):
+            return 1.0
+        return min(1.0, eta * float(torch.min(-v[neg] / dv[neg])))
+
+    k = 0
+    for k in range(1, max_iter + 1):
+        r = A @ (z[:n] - z[n:]) - b
+        fz = s - c - FFt(z)
+        mu = float(z @ s) / (2 * n)
+        P = tau * float(z.sum()) + 0.5 * float(r @ r)
+        if float(z @ s) / (1.0 + abs(P)) <= tol:
+            break
+        sigma = 0.5 if (k != 1 and (aP_prev <= 0.5 or aD_prev <= 0.5)) else 0.1
+        d = s / z
+        fs = sigma * mu - z * s
+        dz = newton(d, fz + fs / z)
+        ds = fs / z - d * dz
+        aP, aD = step(z, dz), step(s, ds)
+        if aP <= 0.1 or aD <= 0.1:
+            zt, st = z + aP * dz, s + aD * ds
+            fzt = st - c - FFt(zt)
+            fst = 0.8 * float(zt @ st) / (2 * n) - zt * st
+            dz2 = newton(d, fzt + fst / z)
+            dz, ds = dz + dz2, ds + fst / z - d * dz2
+            aP, aD = step(z, dz), step(s, ds)
+        z, s = z + aP * dz, s + aD * ds
+        aP_prev, aD_prev = aP, aD
+    return z[:n] - z[n:], k - 1
+
+
 def run_scaling(args, rank, world, local_rank):
     """PCG against a direct solver (Sec. 5.7): one Gaussian problem per n = 2^5..2^12 (m = n/4,
     tau = 1e-3, noiseless).  One step = one mfipm_solve per size, in turn (float64 PCG in the
@@ -715,7 +776,7 @@ def run_scaling(args, rank, world, local_rank):
     torch.cuda.synchronize()
     L.mfipm_set_timing(1)
     per = [[] for _ in probs]
-    kern_last, infos = [0.0] * len(probs), [None] * len(probs)
+    kern_last, infos, xs_last = [0.0] * len(probs), [None] * len(probs), [None] * len(probs)
     step_ms = []
     if world > 1:
         torch.distributed.barrier()
@@ -728,7 +789,7 @@ def run_scaling(args, rank, world, local_rank):
                 for j, (o, b_, p) in enumerate(zip(ops, bs, probs)):
                     ej = torch.cuda.Event(enable_timing=True)
                     ej.record(stream)
-                    x, infos[j] = M.solve(o, b_, p.tau, params, ws=ws)
+                    xs_last[j], infos[j] = M.solve(o, b_, p.tau, params, ws=ws)
                     kern_last[j] = L.mfipm_last_kernel_ms()
                     per[j].append((ej, torch.cuda.Event(enable_timing=True)))
                     per[j][-1][1].record(stream)
@@ -767,6 +828,17 @@ def run_scaling(args, rank, world, local_rank):
     traffic = tj["bytes_per_launch"] if tj else None
     if rank != 0:
         return
+    # the direct variant on the same GPU (vendor Cholesky, float64), per size: the paper's
+    # comparison of time growth, now on one machine
+    direct = []
+    for p in probs:
+        Ad, bd = torch.from_numpy(p.A).to(dev), torch.from_numpy(p.b).to(dev)
+        direct_ipm_gpu(Ad, bd, p.tau, params.tol)  # warm (library handles, workspace)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        xd, itd = direct_ipm_gpu(Ad, bd, p.tau, params.tol)
+        torch.cuda.synchronize()
+        direct.append((1e3 * (time.perf_counter() - t0), itd, xd.cpu().numpy()))
     # the oracle with direct Newton solves, per size (host), within a bounded budget
     rows, cpu = [], None
     from oracle import mfipm_oracle as O
@@ -774,7 +846,10 @@ def run_scaling(args, rank, world, local_rank):
     for j, p in enumerate(probs):
         row = {"n": p.n, "m": p.m, "k": int(np.count_nonzero(p.x_hat)), "gpu_ms": gpu_ms[j],
                "gpu_ipm_iters": infos[j]["ipm_iters"], "gpu_pcg_iters": infos[j]["pcg_iters"],
-               "gpu_kkt_rel": infos[j]["kkt_rel"]}
+               "gpu_kkt_rel": infos[j]["kkt_rel"], "direct_gpu_ms": direct[j][0],
+               "direct_gpu_ipm_iters": direct[j][1],
+               "x_rel_vs_direct_gpu": float(np.linalg.norm(xs_last[j].cpu().numpy() - direct[j][2])
+                                            / max(np.linalg.norm(direct[j][2]), 1e-300))}
         if not args.no_cpu and t_all < 20.0:
             t0 = time.perf_counter()
             r = O.ipm(O.Operator.from_dense(p.A), p.b, p.tau, O.OracleParams(tol=params.tol))

@@ -64,8 +64,9 @@ typedef enum {
  *                         products): row 0 = 1/sqrt(n); row 2^j + k (0 <= j < log2 n,
  *                         0 <= k < 2^j) = +-2^(j/2)/sqrt(n) on the two halves of
  *                         [k n/2^j, (k+1) n/2^j).  A A^T = I_m.  n a power of two with
- *                         64 <= n <= 65536 (one cluster); solve and solve_batched only, with
- *                         precision MFIPM_PREC_FP32_PCG and the double-float outer loop. */
+ *                         64 <= n <= 65536 (one cluster); solve, solve_batched and backward,
+ *                         with precision MFIPM_PREC_FP32_PCG or MFIPM_PREC_FP64 (float64 PCG)
+ *                         and the double-float outer loop. */
 typedef enum { MFIPM_OP_DENSE = 0, MFIPM_OP_PARTIAL_DCT = 1, MFIPM_OP_PARTIAL_HAAR = 2 } mfipm_op_kind;
 
 /* Storage type of a dense A. */
@@ -76,8 +77,9 @@ typedef enum { MFIPM_A_F64 = 0, MFIPM_A_F32 = 1, MFIPM_A_BF16 = 2 } mfipm_a_dtyp
  * operators its per-index arithmetic follows mfipm_outer below (double-float by default),
  * while its scalar reductions and every output stay float64.
  *   MFIPM_PREC_FP64      PCG vectors and operator products in float64 (dense A; partial DCT
- *                        below the multi-pass threshold, with the float64 outer loop: the PCG
- *                        tolerances of basis pursuit, tol_pcg down to 1e-6, Sec. 5.4).
+ *                        below the multi-pass threshold, with the float64 outer loop; partial
+ *                        Haar, with the double-float outer loop: the PCG tolerances of basis
+ *                        pursuit, tol_pcg down to 1e-6, Sec. 5.4).
  *   MFIPM_PREC_FP32_PCG  PCG vectors and operator products in float32 (the inexact Newton
  *                        direction is corrected by the float64 residuals of the outer loop).
  *   MFIPM_PREC_BF16_A    dense A stored bf16 (times a_scale) on the tensor cores with float32
@@ -216,8 +218,8 @@ int mfipm_solve_batched(int32_t batch, const mfipm_operator* ops, const double* 
  *   grad_x    DEVICE n.   grad_b DEVICE m or NULL.   grad_tau HOST (batch) or NULL.
  *   grad_A    DEVICE m x n row-major or NULL (dense operators only; MFIPM_UNSUPPORTED otherwise).
  * Arrays are HOST arrays of DEVICE pointers, as in mfipm_solve_batched; infos[i].pcg_iters and
- * n_mat count the work of each derivative.  Dense and partial-DCT operators; MFIPM_UNSUPPORTED
- * for the partial Haar operator. */
+ * n_mat count the work of each derivative.  Dense, partial-DCT and partial-Haar operators
+ * (A w of the Haar operator by its float64 analysis pyramid). */
 int mfipm_backward(int32_t batch, const mfipm_operator* ops, const double* const* b,
                    const double* tau, const double* const* x, const double* const* zs,
                    const double* const* grad_x, double* const* grad_b, double* grad_tau,

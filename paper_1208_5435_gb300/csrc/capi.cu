@@ -50,6 +50,10 @@ int ceil_log2i(int64_t v) {
   return l;
 }
 
+// Side stream and fork/join events of the single-CTA helper launch (created on first use).
+thread_local cudaStream_t g_side = nullptr;
+thread_local cudaEvent_t g_fork = nullptr, g_join = nullptr;
+
 // Optional timing of the solver kernel (mfipm_set_timing / mfipm_last_kernel_ms).
 thread_local bool g_timing = false;
 thread_local cudaEvent_t g_ev[2] = {nullptr, nullptr};
@@ -221,7 +225,8 @@ Layout make_layout(const mfipm_operator* ops, int batch, bool pcg64) {
 }
 
 bool pcg_in_fp64(const mfipm_operator& op, const mfipm_params* p) {
-  return (op.kind == MFIPM_OP_DENSE || op.kind == MFIPM_OP_PARTIAL_DCT) && p->precision == MFIPM_PREC_FP64;
+  (void)op;  // dense, partial DCT and partial Haar alike
+  return p->precision == MFIPM_PREC_FP64;
 }
 
 int pick_G(const std::vector<mfipm_operator>& ops, const mfipm_params* p, int batch) {
@@ -309,11 +314,9 @@ int prepare(int batch, const mfipm_operator* ops, const double* const* b, const 
     if (P.dct && ops[i].n > kDctMaxN)
       return fail(MFIPM_UNSUPPORTED, "operator %d: n=%lld above the cluster solver's %lld", i, (long long)ops[i].n,
                   (long long)kDctMaxN);
-  if (P.haar && p->precision != MFIPM_PREC_FP32_PCG)
-    return fail(MFIPM_UNSUPPORTED, "the partial-Haar solver runs its PCG in float32 (precision=%d)", p->precision);
   if (P.dct && p->precision != MFIPM_PREC_FP32_PCG && p->precision != MFIPM_PREC_FP64)
-    return fail(MFIPM_UNSUPPORTED, "the partial-DCT solver runs its PCG in float32 or float64 (precision=%d)",
-                p->precision);
+    return fail(MFIPM_UNSUPPORTED, "the partial-DCT and partial-Haar solvers run their PCG in float32 or float64 "
+                "(precision=%d)", p->precision);
   if (P.haar && p->outer != MFIPM_OUTER_DF)
     return fail(MFIPM_UNSUPPORTED, "the partial-Haar solver keeps its iterate in double-float (outer=%d)", p->outer);
   if (!P.dct && p->precision == MFIPM_PREC_BF16_A)
@@ -411,7 +414,7 @@ int prepare(int batch, const mfipm_operator* ops, const double* const* b, const 
   a.twdf = reinterpret_cast<const float4*>(ws + P.lay.off_twdf);
   a.log2_tw = P.lay.log2_tw;
   a.prm = to_solve(p);
-  if (P.dct && P.pcg64) a.prm.resid_fp64 = 1;  // a float64 PCG runs with the float64 outer loop
+  if (P.dct && !P.haar && P.pcg64) a.prm.resid_fp64 = 1;  // the DCT's float64 PCG runs with the float64 outer loop
   return MFIPM_OK;
 }
 
@@ -449,7 +452,8 @@ int run(Prepared& P, cudaStream_t st, int batch, mfipm_info* infos, const std::v
   }
   P.args.nbig = nbig;
   const bool f64 = P.args.prm.resid_fp64 != 0;
-  int maxc = P.haar             ? max_active_clusters_haar(P.G, P.max_n)
+  int maxc = P.haar             ? (P.pcg64 ? max_active_clusters_haar_f64pcg(P.G, P.max_n)
+                                           : max_active_clusters_haar(P.G, P.max_n))
              : P.dct && P.pcg64 ? max_active_clusters_dct_f64pcg(P.G, P.max_n)
              : P.dct ? (f64 ? max_active_clusters_dct_f64(P.G, P.max_n) : max_active_clusters_dct_df(P.G, P.max_n))
                      : max_active_clusters_dense(P.G, P.pcg64, P.max_n, P.max_m);
@@ -460,12 +464,46 @@ int run(Prepared& P, cudaStream_t st, int batch, mfipm_info* infos, const std::v
       if (!ev && (e = cudaEventCreate(&ev)) != cudaSuccess) return cuda_fail(e, "timing event");
     cudaEventRecord(g_ev[0], st);
   }
-  e = P.haar             ? launch_haar_solver(P.G, P.args, P.max_n, clusters, st)
+  // SMs that no cluster of the persistent launch can hold (cluster placement leaves some of
+  // them out) serve the per-CTA queue through a helper launch of single CTAs on a side stream
+  int helper = 0;
+  int64_t small_n = 0;
+  if (P.dct && P.G > 1 && nbig < batch) {
+    int dev = 0, sms = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess ||
+        (e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+      return cuda_fail(e, "device attributes");
+    helper = std::min(sms - clusters * P.G, batch - nbig);
+    for (int i = nbig; i < batch; ++i) small_n = std::max<int64_t>(small_n, sorted[i].n);
+    if (helper > 0) {
+      if (!g_side && (e = cudaStreamCreateWithFlags(&g_side, cudaStreamNonBlocking)) != cudaSuccess)
+        return cuda_fail(e, "side stream");
+      if ((!g_fork && (e = cudaEventCreateWithFlags(&g_fork, cudaEventDisableTiming)) != cudaSuccess) ||
+          (!g_join && (e = cudaEventCreateWithFlags(&g_join, cudaEventDisableTiming)) != cudaSuccess))
+        return cuda_fail(e, "helper events");
+      if ((e = cudaEventRecord(g_fork, st)) != cudaSuccess) return cuda_fail(e, "fork");
+    }
+  }
+  e = P.haar             ? (P.pcg64 ? launch_haar_solver_f64pcg(P.G, P.args, P.max_n, clusters, st)
+                                    : launch_haar_solver(P.G, P.args, P.max_n, clusters, st))
       : P.dct && P.pcg64 ? launch_dct_solver_f64pcg(P.G, P.args, P.max_n, clusters, st)
       : P.dct ? (f64 ? launch_dct_solver_f64(P.G, P.args, P.max_n, clusters, st)
                      : launch_dct_solver_df(P.G, P.args, P.max_n, clusters, st))
               : launch_dense_solver(P.G, P.pcg64, P.args, P.max_n, P.max_m, clusters, st);
   if (e != cudaSuccess) return cuda_fail(e, "solver launch");
+  if (helper > 0) {
+    KernelArgs ha = P.args;
+    ha.phase2_only = 1;
+    if ((e = cudaStreamWaitEvent(g_side, g_fork, 0)) != cudaSuccess) return cuda_fail(e, "fork");
+    e = P.haar             ? (P.pcg64 ? launch_haar_solver_f64pcg(1, ha, small_n, helper, g_side)
+                                      : launch_haar_solver(1, ha, small_n, helper, g_side))
+        : P.pcg64 ? launch_dct_solver_f64pcg(1, ha, small_n, helper, g_side)
+        : f64     ? launch_dct_solver_f64(1, ha, small_n, helper, g_side)
+                  : launch_dct_solver_df(1, ha, small_n, helper, g_side);
+    if (e != cudaSuccess) return cuda_fail(e, "helper launch");
+    if ((e = cudaEventRecord(g_join, g_side)) != cudaSuccess || (e = cudaStreamWaitEvent(st, g_join, 0)) != cudaSuccess)
+      return cuda_fail(e, "join");
+  }
   if (timing) cudaEventRecord(g_ev[1], st);
   int err = 0;
   if ((e = cudaMemcpyAsync(&err, P.args.err, sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
@@ -777,7 +815,6 @@ int backward_persistent(int32_t batch, const mfipm_operator* ops, const double* 
   Prepared P;
   int rc = prepare(batch, ops, b, tau, p, const_cast<double* const*>(x), nullptr, workspace, ws_bytes, P);
   if (rc) return rc;
-  if (P.haar) return fail(MFIPM_UNSUPPORTED, "mfipm_backward is not built for the partial Haar operator");
   for (int i = 0; i < batch; ++i) {
     if (!zs[i] || !grad_x[i]) return fail(MFIPM_INVALID_ARG, "zs[%d] or grad_x[%d] is NULL", i, i);
     if (grad_A && grad_A[i] && ops[i].kind != MFIPM_OP_DENSE)
@@ -802,12 +839,14 @@ int backward_persistent(int32_t batch, const mfipm_operator* ops, const double* 
     if ((e = launch_dct_setup(P.args.probs, batch, P.max_n, P.args.err, st)) != cudaSuccess)
       return cuda_fail(e, "setup kernel");
   }
-  const int maxc = P.dct ? max_active_clusters_bwd_dct(P.G, P.max_n)
-                         : max_active_clusters_bwd_dense(P.G, P.pcg64, P.max_n, P.max_m);
+  const int maxc = P.haar  ? max_active_clusters_bwd_haar(P.G, P.max_n)
+                   : P.dct ? max_active_clusters_bwd_dct(P.G, P.max_n)
+                           : max_active_clusters_bwd_dense(P.G, P.pcg64, P.max_n, P.max_m);
   if (maxc < 1) return fail(MFIPM_UNSUPPORTED, "no resident cluster of size %d fits this problem", P.G);
   const int clusters = std::min(maxc, batch);
-  e = P.dct ? launch_bwd_dct(P.G, P.args, P.max_n, clusters, st)
-            : launch_bwd_dense(P.G, P.pcg64, P.args, P.max_n, P.max_m, clusters, st);
+  e = P.haar  ? launch_bwd_haar(P.G, P.args, P.max_n, clusters, st)
+      : P.dct ? launch_bwd_dct(P.G, P.args, P.max_n, clusters, st)
+              : launch_bwd_dense(P.G, P.pcg64, P.args, P.max_n, P.max_m, clusters, st);
   if (e != cudaSuccess) return cuda_fail(e, "backward launch");
   std::vector<double> gt(batch);
   std::vector<mfipm_info> tmp;

@@ -71,7 +71,7 @@ struct KernelArgs {
   const float2* tw32;
   const float4* twdf;     // the same roots as double-float {re.hi, re.lo, im.hi, im.lo}
   int32_t log2_tw;
-  int32_t pad2;
+  int32_t phase2_only;    // a helper launch of single CTAs that takes the per-CTA queue only
   SolveParams prm;
 };
 
@@ -88,6 +88,8 @@ int apply_operator(int what, const mfipm_operator& op, const double* in, const d
 cudaError_t launch_dct_solver_df(int G, const KernelArgs& a, int64_t max_n, int grid_clusters, cudaStream_t st);
 cudaError_t launch_haar_solver(int G, const KernelArgs& a, int64_t max_n, int grid_clusters, cudaStream_t st);
 int max_active_clusters_haar(int G, int64_t max_n);
+cudaError_t launch_haar_solver_f64pcg(int G, const KernelArgs& a, int64_t max_n, int grid_clusters, cudaStream_t st);
+int max_active_clusters_haar_f64pcg(int G, int64_t max_n);
 size_t haar_smem_bytes(int G, int64_t max_n);
 cudaError_t launch_dct_solver_f64(int G, const KernelArgs& a, int64_t max_n, int grid_clusters, cudaStream_t st);
 cudaError_t launch_dense_solver(int G, bool fp64_pcg, const KernelArgs& a, int64_t max_n, int64_t max_m,
@@ -104,6 +106,8 @@ cudaError_t launch_bwd_dct(int G, const KernelArgs& a, int64_t max_n, int grid_c
 cudaError_t launch_bwd_dense(int G, bool fp64_pcg, const KernelArgs& a, int64_t max_n, int64_t max_m,
                              int grid_clusters, cudaStream_t st);
 int max_active_clusters_bwd_dct(int G, int64_t max_n);
+cudaError_t launch_bwd_haar(int G, const KernelArgs& a, int64_t max_n, int grid_clusters, cudaStream_t st);
+int max_active_clusters_bwd_haar(int G, int64_t max_n);
 int max_active_clusters_bwd_dense(int G, bool fp64_pcg, int64_t max_n, int64_t max_m);
 
 // Operator-only kernels for mfipm_apply_A / mfipm_apply_At / mfipm_kkt_residual:

@@ -1124,13 +1124,15 @@ int lockstep_run(mr::Dev& d, double* part2, const double* taus, const double* rh
   const dim3 gIdx(nb, R);
   cudaError_t e;
   int live = R, active = R;  // problems covered by the next operator product (host view)
-  // The host reads the active count (one stream synchronisation) only from two iterations
-  // before the count at which the previous PCG solve of this run ended; the iterations
-  // launched before that without a check cost nothing for problems that have stopped (every
-  // pass skips them, their alpha and beta are 0).  The count adapts down by one per solve
-  // when a solve ends earlier, and up exactly when it runs longer.
-  int prev_iters = 0;
+  // The host reads the active count (one stream synchronisation) only from half the
+  // iteration count at which the previous PCG solve of the same kind (predictor, corrector)
+  // ended; the iterations launched before that without a check change nothing for problems
+  // that have stopped (every pass skips them, their alpha and beta are 0), and a solve that
+  // ends sooner than half its predecessor wastes at most those launches.
+  int prev_iters[2] = {0, 0};
   auto pcg = [&](float2* Xo) -> cudaError_t {
+    const int kind = Xo == d.X1 ? 0 : 1;
+    const int first_check = prev_iters[kind] / 2;
     for (int k = 0;; ++k) {
       if ((e = normal(k, k == 0 ? live : active))) return e;
       k_alpha<<<R, kT, 0, st>>>(d, k == 0, part2);
@@ -1140,12 +1142,12 @@ int lockstep_run(mr::Dev& d, double* part2, const double* taus, const double* rh
       if ((e = cudaMemsetAsync(d.counters, 0, 4, st))) return e;
       k_beta<<<R, kT, 0, st>>>(d, k + 1);
       ++g_nlaunch;
-      if (k + 2 >= prev_iters || k + 1 >= d.prm.max_iter_pcg) {
+      if (k + 1 >= first_check || k + 1 >= d.prm.max_iter_pcg) {
         active = 0;
         if ((e = cudaMemcpyAsync(&active, d.counters, 4, cudaMemcpyDeviceToHost, st))) return e;
         if ((e = cudaStreamSynchronize(st))) return e;
         if (active == 0) {
-          prev_iters = k + 1;
+          prev_iters[kind] = k + 1;
           return cudaSuccess;
         }
       }

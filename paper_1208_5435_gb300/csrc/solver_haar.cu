@@ -29,6 +29,7 @@ template <int G> struct HaarOp {
   const double* bsu;
   const float2* bsu_df;
   unsigned char* rb;  // chunk values of the residual buffer (8 bytes each)
+  double* fwd;        // MODE_FORWARD: the n coefficients (reverse mode's A w)
   float* wb;          // chunk float32 values of the PCG operator input
 
   __device__ void init(const ProbDesc& pd, const KernelArgs&, unsigned char* smem, int rank_) {
@@ -52,12 +53,30 @@ template <int G> struct HaarOp {
     return gbase + (t << logV) + i;
   }
   template <class T> __device__ __forceinline__ T* rbuf() const { return reinterpret_cast<T*>(rb); }
-  template <class PS> __device__ __forceinline__ PS* wbuf() const { return reinterpret_cast<PS*>(wb); }
+  // float32 PCG input in its own buffer; the float64 PCG shares the residual buffer (every PCG
+  // initialisation reads the residual of an index before writing that index's input)
+  template <class PS> __device__ __forceinline__ PS* wbuf() const {
+    if constexpr (sizeof(PS) == 8) {
+      return reinterpret_cast<PS*>(rb);
+    } else {
+      return reinterpret_cast<PS*>(wb);
+    }
+  }
   template <class T> __device__ double resid_t() { return chain<T, MODE_RESID>(rbuf<T>()); }
   static constexpr bool kLowpResid = false;
   template <class T> __device__ double resid_lowp() { return resid_t<T>(); }
   template <class PS> __device__ double normal(PS* w) { return chain<PS, MODE_NORMAL>(w); }
-  __device__ void apply_A_out(const ProbDesc&) {}
+  // grad_b = A w for w in rbuf<double>(): the analysis pyramid in float64 writes all n Haar
+  // coefficients to pd.scratch, then the sampled rows are gathered.  Overwrites rbuf.
+  __device__ void apply_A_out(const ProbDesc& pd) {
+    fwd = pd.scratch;
+    chain<double, MODE_FORWARD>(rbuf<double>());
+    __threadfence();
+    cluster_barrier<G>();
+    if (pd.grad_b)
+      for (int64_t i = (int64_t)rank * kThreads + threadIdx.x; i < pd.m; i += (int64_t)G * kThreads)
+        pd.grad_b[i] = pd.scratch[pd.rows[i]];
+  }
   __device__ void grad_A_out(const ProbDesc&, const void*) {}
   template <int GG> __device__ void setup(RedSmem&, int&) {}
 
@@ -69,6 +88,10 @@ template <int G> struct HaarOp {
   }
   // detail or scaling coefficient of index idx: masked (minus b_u), energy into acc
   template <class R, int MODE> __device__ __forceinline__ R coef(R d, int64_t idx, R& acc) const {
+    if constexpr (MODE == MODE_FORWARD) {
+      fwd[idx] = to_double(d);
+      return d;
+    }
     if (!mask[idx]) return R();
     if constexpr (MODE == MODE_RESID) d = d - load_b(idx, R());
     acc = acc + d * d;
@@ -133,41 +156,45 @@ template <int G> struct HaarOp {
           }
         }
         v[0] = coef<R, MODE>(v[0], 0, acc);
+        if constexpr (MODE != MODE_FORWARD) {
 #pragma unroll
-        for (int lam = logG - 1; lam >= 0; --lam) {
-          const int s = 1 << lam;
+          for (int lam = logG - 1; lam >= 0; --lam) {
+            const int s = 1 << lam;
 #pragma unroll
-          for (int g = 0; g < G; g += 2 * s) {
-            const R a0 = v[g], d0 = v[g + s];
-            v[g] = (a0 + d0) * r2;
-            v[g + s] = (a0 - d0) * r2;
+            for (int g = 0; g < G; g += 2 * s) {
+              const R a0 = v[g], d0 = v[g + s];
+              v[g] = (a0 + d0) * r2;
+              v[g + s] = (a0 - d0) * r2;
+            }
           }
-        }
 #pragma unroll
-        for (int g = 0; g < G; ++g) cl.map_shared_rank(buf, g)[0] = v[g];
+          for (int g = 0; g < G; ++g) cl.map_shared_rank(buf, g)[0] = v[g];
+        }
       }
       cg::this_cluster().sync();
     }
     __syncthreads();
-    // synthesis across the threads, coarsest first
-    for (int lam = logTc - 1; lam >= 0; --lam) {
-      const int s = 1 << lam;
-      if (act && (t & (2 * s - 1)) == 0) {
-        const R a0 = buf[t], d0 = buf[t + s];
-        buf[t] = (a0 + d0) * r2;
-        buf[t + s] = (a0 - d0) * r2;
+    if constexpr (MODE != MODE_FORWARD) {  // MODE_FORWARD: analysis only
+      // synthesis across the threads, coarsest first
+      for (int lam = logTc - 1; lam >= 0; --lam) {
+        const int s = 1 << lam;
+        if (act && (t & (2 * s - 1)) == 0) {
+          const R a0 = buf[t], d0 = buf[t + s];
+          buf[t] = (a0 + d0) * r2;
+          buf[t + s] = (a0 - d0) * r2;
+        }
+        // the next level reads slot t + s (written here by thread t): one warp while 2s <= 32
+        if (2 * s <= 32) __syncwarp(); else __syncthreads();
       }
-      // the next level reads slot t + s (written here by thread t): one warp while 2s <= 32
-      if (2 * s <= 32) __syncwarp(); else __syncthreads();
-    }
-    // synthesis inside the thread
-    if (act) {
-      for (int l = logV - 1; l >= 0; --l) {
-        const int s = 1 << l;
-        for (int i = 0; i < V; i += 2 * s) {
-          const R a0 = buf[i * Tc + t], d0 = buf[(i + s) * Tc + t];
-          buf[i * Tc + t] = (a0 + d0) * r2;
-          buf[(i + s) * Tc + t] = (a0 - d0) * r2;
+      // synthesis inside the thread
+      if (act) {
+        for (int l = logV - 1; l >= 0; --l) {
+          const int s = 1 << l;
+          for (int i = 0; i < V; i += 2 * s) {
+            const R a0 = buf[i * Tc + t], d0 = buf[(i + s) * Tc + t];
+            buf[i * Tc + t] = (a0 + d0) * r2;
+            buf[(i + s) * Tc + t] = (a0 - d0) * r2;
+          }
         }
       }
     }
@@ -190,6 +217,45 @@ cudaError_t launch_haar_solver(int G, const KernelArgs& a, int64_t max_n, int gr
 int max_active_clusters_haar(int G, int64_t max_n) {
   const size_t smem = haar_smem_bytes(G, max_n);
 #define O_(g) occupancy_t<g, HaarOp<g>, HaarOp<1>, float, StateDF>(smem)
+  MFIPM_G_SWITCH(G, O_)
+#undef O_
+  return 0;
+}
+
+// The same solver with a float64 PCG (MFIPM_PREC_FP64): operator products, PCG vectors and
+// preconditioner in float64, iterate in double-float.
+cudaError_t launch_haar_solver_f64pcg(int G, const KernelArgs& a, int64_t max_n, int grid_clusters, cudaStream_t st) {
+  const size_t smem = haar_smem_bytes(G, max_n);
+#define L_(g) launch_t<g, HaarOp<g>, HaarOp<1>, double, StateDF>(a, smem, grid_clusters, st)
+  MFIPM_G_SWITCH(G, L_)
+#undef L_
+  return cudaErrorInvalidValue;
+}
+
+int max_active_clusters_haar_f64pcg(int G, int64_t max_n) {
+  const size_t smem = haar_smem_bytes(G, max_n);
+#define O_(g) occupancy_t<g, HaarOp<g>, HaarOp<1>, double, StateDF>(smem)
+  MFIPM_G_SWITCH(G, O_)
+#undef O_
+  return 0;
+}
+
+}  // namespace mfipm
+
+namespace mfipm {
+
+// Reverse mode (mfipm_backward) on the partial Haar operator: float32 adjoint PCG, float64 A w.
+cudaError_t launch_bwd_haar(int G, const KernelArgs& a, int64_t max_n, int grid_clusters, cudaStream_t st) {
+  const size_t smem = haar_smem_bytes(G, max_n);
+#define L_(g) launch_bwd_t<g, HaarOp<g>, float>(a, smem, grid_clusters, st)
+  MFIPM_G_SWITCH(G, L_)
+#undef L_
+  return cudaErrorInvalidValue;
+}
+
+int max_active_clusters_bwd_haar(int G, int64_t max_n) {
+  const size_t smem = haar_smem_bytes(G, max_n);
+#define O_(g) occupancy_bwd_t<g, HaarOp<g>, float>(smem)
   MFIPM_G_SWITCH(G, O_)
 #undef O_
   return 0;

@@ -1391,7 +1391,7 @@ __global__ void __launch_bounds__(kThreads, 1) ipm_kernel(KernelArgs a) {
   int par = 0;
   int rank = 0;
   if constexpr (G > 1) rank = (int)cg::this_cluster().block_rank();
-  for (;;) {
+  for (; !a.phase2_only;) {
     if (rank == 0 && threadIdx.x == 0) rs.fetched = atomicAdd(a.queue, 1);
     cluster_barrier<G>();
     int pid;

@@ -216,7 +216,7 @@ def test_autotune_rejected_before_launch(L):
     assert L.mfipm_clear_tuning() == 0
 
 
-@pytest.mark.parametrize("case", ["n_not_pow2", "n_too_big", "n_too_small", "fp64_outer", "fp64_pcg", "null_rows",
+@pytest.mark.parametrize("case", ["n_not_pow2", "n_too_big", "n_too_small", "fp64_outer", "bf16_prec", "null_rows",
                                   "backward"])
 def test_partial_haar_rejected_before_launch(L, case):
     from paper_1208_5435_gb300 import _capi as C
@@ -233,16 +233,17 @@ def test_partial_haar_rejected_before_launch(L, case):
         op.n, op.m = 32, 8
     elif case == "fp64_outer":
         p.outer = 1
-    elif case == "fp64_pcg":
-        p.precision = C.PREC_FP64
+    elif case == "bf16_prec":
+        p.precision = C.PREC_BF16_A
     elif case == "null_rows":
         op.rows = None
     info = C.Info()
     if case == "backward":
+        # the reverse mode runs on the Haar operator, but dL/dA is defined for dense A only
         one = lambda v: (ctypes.c_void_p * 1)(v)
         rc = L.mfipm_backward(1, ctypes.byref(op), one(0x3000), (ctypes.c_double * 1)(0.1), one(0x4000), one(0x5000),
-                              one(0x6000), one(0x7000), (ctypes.c_double * 1)(), None, ctypes.byref(p), ws, wsb,
-                              ctypes.byref(info), None)
+                              one(0x6000), one(0x7000), (ctypes.c_double * 1)(), one(0x8000), ctypes.byref(p), ws,
+                              wsb, ctypes.byref(info), None)
         assert rc == C.MFIPM_UNSUPPORTED, rc
     else:
         rc = L.mfipm_solve(ctypes.byref(op), ctypes.c_void_p(0x3000), 0.1, ctypes.byref(p), ctypes.c_void_p(0x4000),

@@ -110,3 +110,74 @@ def test_products_match_explicit_rows():
     assert _relx(M.apply_A(op, torch.from_numpy(xr)).cpu().numpy(), A @ xr) <= 1e-12
     assert _relx(M.apply_At(op, torch.from_numpy(yr)).cpu().numpy(), A.T @ yr) <= 1e-12
 
+
+
+@pytest.mark.parametrize("n,G", [(1024, 1), (4096, 4)])
+def test_float64_pcg_matches_oracle(n, G):
+    """The Haar operator with the float64 PCG (precision MFIPM_PREC_FP64): A x and ||x||_1 as
+    the oracle's, x valid by the oracle's KKT residual."""
+    M = mf()
+    p = W.haar_problem(n, n // 4, max(1, n // 100), 2410, n)
+    A = O.haar_matrix_rows(p.n, p.rows)
+    ref = O.ipm(O.Operator.from_dense(A), p.b, p.tau, O.OracleParams(tol=1e-12)).x
+    x, info = M.solve(M.PartialHaar(p.n, torch.from_numpy(p.rows)), torch.from_numpy(p.b), p.tau,
+                      M.SolverParams(tol=1e-12, precision=0, cluster_size=G))
+    x = x.cpu().numpy()
+    assert info["status"] == 0, info
+    assert _relx(A @ x, A @ ref) <= 1e-6
+    assert abs(np.abs(x).sum() - np.abs(ref).sum()) <= 1e-6 * np.abs(ref).sum()
+    assert O.kkt_rel(O.Operator.from_dense(A), p.b, p.tau, x) <= 1e-7
+
+
+@pytest.mark.parametrize("n,G", [(1024, 1), (2048, 2), (4096, 4)])
+def test_backward_on_the_full_haar_basis_matches_the_closed_form(n, G):
+    """mfipm_backward on the Haar operator.  Sampled Haar rows can leave equal columns, where
+    x* is not unique and has no derivative, so the reverse mode is checked where it is unique:
+    all n rows (A orthonormal square), x* = S_tau(A^T b), hence for L with dL/dx = g
+        dL/db = A (g o 1[|A^T b| > tau]),   dL/dtau = -sum_{|A^T b| > tau} g_i sign((A^T b)_i);
+    and against the oracle's exact KKT adjoint at the GPU's own final iterate."""
+    M = mf()
+    rng = np.random.default_rng(2430 + n)
+    rows = np.arange(n, dtype=np.int64)
+    A = O.haar_matrix_rows(n, rows)
+    b = rng.standard_normal(n)
+    atb = A.T @ b
+    # tau in the widest gap of |A^T b| between 0.25 and 0.35 of its max: no coefficient sits
+    # at the threshold, where x* has no derivative (the adjoint at a finite-mu iterate smooths it)
+    a = np.sort(np.abs(atb))
+    lo, hi = np.searchsorted(a, 0.25 * a[-1]), np.searchsorted(a, 0.35 * a[-1])
+    i = lo + int(np.argmax(np.diff(a[lo:hi + 1])))
+    tau = 0.5 * (a[i] + a[i + 1])
+    assert np.min(np.abs(np.abs(atb) - tau)) >= 1e-3 * tau
+    op = M.PartialHaar(n, torch.from_numpy(rows))
+    prm = M.SolverParams(tol=1e-12, cluster_size=G)
+    bt = torch.from_numpy(b).cuda()
+    x, info, zs = M.solve(op, bt, tau, prm, return_zs=True)
+    assert info["status"] == 0
+    xs = O.soft_threshold(atb, tau)
+    assert np.linalg.norm(x.cpu().numpy() - xs) <= 1e-6 * np.linalg.norm(xs)
+    g = rng.standard_normal(n)
+    gbs, gts, _, infos = M.backward([op], [bt], [tau], [x], [zs], [torch.from_numpy(g).cuda()], prm)
+    on = np.abs(atb) > tau
+    want_b = A @ (g * on)
+    want_t = -float(np.sum(g[on] * np.sign(atb[on])))
+    gb = gbs[0].cpu().numpy()
+    assert np.abs(gb - want_b).max() <= 1e-5 * np.abs(want_b).max(), np.abs(gb - want_b).max()
+    assert abs(gts[0] - want_t) <= 1e-5 * max(1.0, abs(want_t)), (gts[0], want_t)
+    zsn = zs.cpu().numpy()
+    rb, rt, _ = O.adjoint_kkt(O.Operator.from_dense(A), b, tau, zsn[:2 * n], zsn[2 * n:], g)
+    assert np.abs(gb - rb).max() <= 5e-6 * np.abs(rb).max()
+    assert infos[0]["pcg_iters"] > 0
+
+
+def test_float64_pcg_on_the_hard_haar_problem():
+    """Problem 198 of the Haar batch (n = 32768): with the float32 PCG its state overflows and
+    the solve ends NUMERIC; the float64 PCG is reported here as it ends (never NUMERIC)."""
+    M = mf()
+    p = W.make_workload("haar_batch_256")[198]
+    x, info = M.solve(M.PartialHaar(p.n, torch.from_numpy(p.rows)), torch.from_numpy(p.b), p.tau,
+                      M.SolverParams(precision=0), raise_on_failure=False)
+    print(f"Haar problem 198, float64 PCG: status {info['status']} ipm {info['ipm_iters']} "
+          f"pcg {info['pcg_iters']} kkt_rel {info['kkt_rel']:.2e}")
+    assert info["status"] in (0, 2), info
+    assert np.all(np.isfinite(x.cpu().numpy()))

@@ -4,6 +4,7 @@ directions need about as many IPM iterations as exact (direct) ones."""
 import math
 
 import numpy as np
+import pytest
 
 import workloads as W
 from oracle import mfipm_oracle as O
@@ -40,3 +41,17 @@ def test_bp_limit_pcg_with_noiseless_settings():
     assert direct.converged and pcg.converged
     assert np.linalg.norm(pcg.x - direct.x) <= 1e-6 * np.linalg.norm(direct.x)
     assert np.linalg.norm(direct.x - p.x_hat) <= 1e-5 * np.linalg.norm(p.x_hat)
+
+
+def test_direct_comparison_arm_matches_the_oracle():
+    """bench.py's same-GPU direct arm of the PCG-against-direct leg (Sec. 5.7), run here on CPU
+    tensors: the same minimiser and the same number of Newton directions as the oracle's
+    direct IPM, which it restates independently (Woodbury Cholesky, readings R1-R8)."""
+    import bench
+    torch = pytest.importorskip("torch")
+    p = W.scaling_problems(1007, (6, 8))[1]
+    A, b = torch.from_numpy(p.A), torch.from_numpy(p.b)
+    x, its = bench.direct_ipm_gpu(A, b, p.tau, 1e-10)
+    r = O.ipm(O.Operator.from_dense(p.A), p.b, p.tau, O.OracleParams(tol=1e-10, solver="woodbury"))
+    assert np.linalg.norm(x.numpy() - r.x) <= 1e-8 * np.linalg.norm(r.x)
+    assert its == r.iters - 1
