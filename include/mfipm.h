@@ -54,11 +54,20 @@ typedef enum {
  *   MFIPM_OP_DENSE        A is an explicit m x n matrix (e.g. the Gaussian ensemble).
  *   MFIPM_OP_PARTIAL_DCT  A = m distinct rows of the orthonormal n x n DCT-II matrix
  *                         C[j,k] = a_j cos(pi*j*(2k+1)/(2n)), a_0 = sqrt(1/n), a_j = sqrt(2/n),
- *                         so that A A^T = I_m (Eq. eq:orthonormality).  n must be a power of
+ *                         so that A A^T = I_m (Eq. eq:orthonormality).  n is a power of
  *                         two with 64 <= n <= 1048576: up to 65536 one thread-block
  *                         cluster holds a problem's FFT in shared memory; from 131072 the
  *                         problems of one length run in lockstep with a three-pass FFT
- *                         through device memory (see mfipm_set_large_dct_threshold).
+ *                         through device memory (see mfipm_set_large_dct_threshold).  Or n
+ *                         is any even length 8 <= n <= 16384 whose half n/2 has no prime
+ *                         factor above 5 (n = 1000 of the phase-transition experiment,
+ *                         Sec. 5.8): a mixed-radix FFT (radices 4, 2, 3, 5) in one CTA's
+ *                         shared memory per problem.  A batch that holds such a length runs
+ *                         every problem of it that way (so all its n <= 16384, cluster_size
+ *                         0 or 1); mfipm_solve, mfipm_solve_batched and mfipm_solve_noalloc
+ *                         take it with either PCG precision and either outer loop;
+ *                         mfipm_backward and the operator products (mfipm_apply_A,
+ *                         mfipm_apply_At, mfipm_kkt_residual) return MFIPM_UNSUPPORTED.
  *   MFIPM_OP_PARTIAL_HAAR: A = the rows `rows` of the orthonormal n x n Haar matrix (Sec. 2
  *                         names Haar wavelets among the orthonormal systems with O(n)
  *                         products): row 0 = 1/sqrt(n); row 2^j + k (0 <= j < log2 n,

@@ -89,7 +89,24 @@ constexpr int64_t kDenseMaxM = 6144;
 // the rest to the cluster-resident persistent kernel (mfipm_set_large_dct_threshold).
 int64_t g_large_dct_min_n = 2 * kDctMaxN;
 bool is_large_dct(const mfipm_operator& o) {
-  return o.kind == MFIPM_OP_PARTIAL_DCT && o.n >= g_large_dct_min_n && o.n >= kLdMinN;
+  return o.kind == MFIPM_OP_PARTIAL_DCT && is_pow2(o.n) && o.n >= g_large_dct_min_n && o.n >= kLdMinN;
+}
+
+// Partial DCT of a general length (the mixed-radix chain, one CTA per problem): n even in
+// [8, 16384] with n/2 free of prime factors above 5.
+constexpr int64_t kGenMinN = 8, kGenMaxN = 16384;
+bool is_gen_dct_n(int64_t n) {
+  if (n < kGenMinN || n > kGenMaxN || (n & 1)) return false;
+  int64_t r = n / 2;
+  for (int f : {2, 3, 5})
+    while (r % f == 0) r /= f;
+  return r == 1;
+}
+// a partial-DCT batch with a length that is not a power of two runs on the mixed-radix chain
+bool needs_gen(const mfipm_operator* ops, int batch) {
+  for (int i = 0; i < batch; ++i)
+    if (ops[i].kind == MFIPM_OP_PARTIAL_DCT && !is_pow2(ops[i].n)) return true;
+  return false;
 }
 
 int validate_op(const mfipm_operator* op, int idx) {
@@ -98,9 +115,13 @@ int validate_op(const mfipm_operator* op, int idx) {
     return fail(MFIPM_INVALID_ARG, "operator %d: need 0 <= m <= n, n > 0 (m=%lld n=%lld)", idx,
                 (long long)op->m, (long long)op->n);
   if (op->kind == MFIPM_OP_PARTIAL_DCT) {
-    if (!is_pow2(op->n) || op->n < kDctMinN || op->n > kLdMaxN)
-      return fail(MFIPM_INVALID_ARG, "operator %d: partial DCT needs n a power of two in [%lld, %lld] (n=%lld)",
-                  idx, (long long)kDctMinN, (long long)kLdMaxN, (long long)op->n);
+    const bool pow2 = is_pow2(op->n) && op->n >= kDctMinN && op->n <= kLdMaxN;
+    if (!pow2 && !is_gen_dct_n(op->n))
+      return fail(MFIPM_INVALID_ARG,
+                  "operator %d: partial DCT needs n a power of two in [%lld, %lld], or an even n in [%lld, %lld] "
+                  "whose half has no prime factor above 5 (n=%lld)",
+                  idx, (long long)kDctMinN, (long long)kLdMaxN, (long long)kGenMinN, (long long)kGenMaxN,
+                  (long long)op->n);
     if (op->m > 0 && !op->rows) return fail(MFIPM_INVALID_ARG, "operator %d: rows is NULL", idx);
     return MFIPM_OK;
   }
@@ -193,8 +214,9 @@ size_t problem_bytes(const mfipm_operator& op, bool pcg64) {
 }
 
 struct Layout {
-  size_t off_hdr, off_tw64, off_tw32, off_twdf, off_desc, off_info, off_gtau, off_probs, total;
+  size_t off_hdr, off_tw64, off_tw32, off_twdf, off_desc, off_info, off_gtau, off_twg, off_probs, total;
   int log2_tw;
+  std::vector<std::pair<int64_t, size_t>> gen_tabs;  // mixed-radix chain: (n, offset of its roots table)
 };
 
 Layout make_layout(const mfipm_operator* ops, int batch, bool pcg64) {
@@ -218,6 +240,17 @@ Layout make_layout(const mfipm_operator* ops, int batch, bool pcg64) {
   o += align256(sizeof(mfipm_info) * (size_t)batch);
   L.off_gtau = o;
   o += align256(sizeof(double) * (size_t)batch);
+  L.off_twg = o;
+  if (needs_gen(ops, batch))
+    for (int i = 0; i < batch; ++i) {
+      const int64_t n = ops[i].n;
+      if (ops[i].kind != MFIPM_OP_PARTIAL_DCT || n > kGenMaxN) continue;
+      bool seen = false;
+      for (auto& t : L.gen_tabs) seen |= t.first == n;
+      if (seen) continue;
+      L.gen_tabs.push_back({n, o});
+      o += align256(gen_tw_bytes(n / 2));
+    }
   L.off_probs = o;
   for (int i = 0; i < batch; ++i) o += problem_bytes(ops[i], pcg64);
   L.total = o;
@@ -284,6 +317,7 @@ struct Prepared {
   KernelArgs args;
   int G;
   bool dct, haar, pcg64;  // dct: a masked orthonormal operator (partial DCT or partial Haar)
+  bool gen;               // partial DCT on the mixed-radix chain (a length not a power of two)
   int64_t max_n, max_m;
   int64_t cta_max_n = 0;  // > 0: largest n solved by a single CTA (tuned), else the default rule
   char* ws;
@@ -310,6 +344,16 @@ int prepare(int batch, const mfipm_operator* ops, const double* const* b, const 
       return fail(MFIPM_UNSUPPORTED, "bf16 A is solved by the shared-A multi-RHS solver (precision MFIPM_PREC_BF16_A)");
   P.haar = kind == MFIPM_OP_PARTIAL_HAAR;
   P.dct = kind == MFIPM_OP_PARTIAL_DCT || P.haar;
+  P.gen = kind == MFIPM_OP_PARTIAL_DCT && needs_gen(ops, batch);
+  if (P.gen) {
+    for (int i = 0; i < batch; ++i)
+      if (ops[i].n > kGenMaxN)
+        return fail(MFIPM_UNSUPPORTED, "operator %d: a batch with a partial DCT whose n is not a power of two runs one "
+                    "CTA per problem, n <= %lld (n=%lld)", i, (long long)kGenMaxN, (long long)ops[i].n);
+    if (p->cluster_size > 1)
+      return fail(MFIPM_INVALID_ARG, "cluster_size %d: the partial DCT of a general length runs one CTA per problem",
+                  p->cluster_size);
+  }
   for (int i = 0; i < batch; ++i)
     if (P.dct && ops[i].n > kDctMaxN)
       return fail(MFIPM_UNSUPPORTED, "operator %d: n=%lld above the cluster solver's %lld", i, (long long)ops[i].n,
@@ -333,8 +377,8 @@ int prepare(int batch, const mfipm_operator* ops, const double* const* b, const 
     P.max_n = std::max<int64_t>(P.max_n, o.n);
     P.max_m = std::max<int64_t>(P.max_m, o.m);
   }
-  P.G = pick_G(vops, p, batch);
-  if (P.dct && !P.haar && p->cluster_size == 0) {
+  P.G = P.gen ? 1 : pick_G(vops, p, batch);
+  if (P.dct && !P.haar && !P.gen && p->cluster_size == 0) {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tune_dct.find({P.max_n, ceil_log2i(batch)});
     if (it != g_tune_dct.end()) {
@@ -392,6 +436,9 @@ int prepare(int batch, const mfipm_operator* ops, const double* const* b, const 
         d.bpk = ws + q;
         q += align256(16 * n);
       }
+      if (P.gen)
+        for (auto& t : P.lay.gen_tabs)
+          if (t.first == op.n) d.twg = ws + t.second;
     }
     d.zs = reinterpret_cast<double*>(ws + q);
     q += align256(32 * n);
@@ -439,6 +486,9 @@ int run(Prepared& P, cudaStream_t st, int batch, mfipm_info* infos, const std::v
         cudaSuccess)
       return cuda_fail(e, "setup kernel");
   }
+  if (P.gen)
+    for (auto& t : P.lay.gen_tabs)
+      if ((e = launch_gen_twiddles(P.ws + t.second, t.first, st)) != cudaSuccess) return cuda_fail(e, "roots table");
   // problems small enough for one CTA's shared memory go to the per-CTA phase of the kernel
   // (the queue order puts every cluster problem before them)
   int nbig = batch;
@@ -452,7 +502,9 @@ int run(Prepared& P, cudaStream_t st, int batch, mfipm_info* infos, const std::v
   }
   P.args.nbig = nbig;
   const bool f64 = P.args.prm.resid_fp64 != 0;
-  int maxc = P.haar             ? (P.pcg64 ? max_active_clusters_haar_f64pcg(P.G, P.max_n)
+  const int gen_variant = P.pcg64 ? kGenF64Pcg : f64 ? kGenF64 : kGenDF;
+  int maxc = P.gen              ? max_active_ctas_dct_gen(gen_variant, P.max_n)
+             : P.haar           ? (P.pcg64 ? max_active_clusters_haar_f64pcg(P.G, P.max_n)
                                            : max_active_clusters_haar(P.G, P.max_n))
              : P.dct && P.pcg64 ? max_active_clusters_dct_f64pcg(P.G, P.max_n)
              : P.dct ? (f64 ? max_active_clusters_dct_f64(P.G, P.max_n) : max_active_clusters_dct_df(P.G, P.max_n))
@@ -484,7 +536,8 @@ int run(Prepared& P, cudaStream_t st, int batch, mfipm_info* infos, const std::v
       if ((e = cudaEventRecord(g_fork, st)) != cudaSuccess) return cuda_fail(e, "fork");
     }
   }
-  e = P.haar             ? (P.pcg64 ? launch_haar_solver_f64pcg(P.G, P.args, P.max_n, clusters, st)
+  e = P.gen              ? launch_dct_gen_solver(gen_variant, P.args, P.max_n, clusters, st)
+      : P.haar           ? (P.pcg64 ? launch_haar_solver_f64pcg(P.G, P.args, P.max_n, clusters, st)
                                     : launch_haar_solver(P.G, P.args, P.max_n, clusters, st))
       : P.dct && P.pcg64 ? launch_dct_solver_f64pcg(P.G, P.args, P.max_n, clusters, st)
       : P.dct ? (f64 ? launch_dct_solver_f64(P.G, P.args, P.max_n, clusters, st)
@@ -812,6 +865,9 @@ int backward_persistent(int32_t batch, const mfipm_operator* ops, const double* 
                    const double* const* x, const double* const* zs, const double* const* grad_x,
                    double* const* grad_b, double* grad_tau, double* const* grad_A, const mfipm_params* p,
                    void* workspace, size_t ws_bytes, mfipm_info* infos, void* stream) {
+  if (needs_gen(ops, batch))
+    return fail(MFIPM_UNSUPPORTED, "mfipm_backward: the partial DCT of a length that is not a power of two has no "
+                "adjoint solver");
   Prepared P;
   int rc = prepare(batch, ops, b, tau, p, const_cast<double* const*>(x), nullptr, workspace, ws_bytes, P);
   if (rc) return rc;
@@ -874,6 +930,9 @@ int apply_checked(int what, const mfipm_operator* op, const double* in, const do
   g_err.clear();
   int rc = validate_op(op, 0);
   if (rc) return rc;
+  if (needs_gen(op, 1))
+    return fail(MFIPM_UNSUPPORTED, "the operator products are built for power-of-two partial-DCT lengths (n=%lld)",
+                (long long)op->n);
   if (!in || (what < 2 && !out) || (what == 2 && (!kkt || (op->m > 0 && !b))))
     return fail(MFIPM_INVALID_ARG, "NULL vector argument");
   if (what == 2 && !(tau > 0.0 && isfinite(tau))) return fail(MFIPM_INVALID_ARG, "tau must be positive and finite");
@@ -1245,7 +1304,7 @@ int mfipm_autotune(int32_t batch, const mfipm_operator* ops, const double* const
     return solve_shared_bf16(batch, ops, b, tau, p, x, nullptr, workspace, ws_bytes, infos, stream);
   }
   const Split sp = split_batch(ops, batch);
-  if (ops[0].kind != MFIPM_OP_PARTIAL_DCT || sp.any_large() || p->cluster_size != 0)
+  if (ops[0].kind != MFIPM_OP_PARTIAL_DCT || sp.any_large() || p->cluster_size != 0 || needs_gen(ops, batch))
     return mfipm_solve_batched(batch, ops, b, tau, p, x, nullptr, workspace, ws_bytes, infos, stream);
   return tune_dct(batch, ops, b, tau, p, x, workspace, ws_bytes, infos, st, tuning);
 }

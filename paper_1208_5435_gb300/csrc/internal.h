@@ -41,6 +41,9 @@ struct ProbDesc {
   // four values); the exchange step reads one code and at most one record per frequency
   uint8_t* mcode;         // DEVICE n/2 or null
   void* bpk;              // DEVICE n/2 records of 32 bytes or null
+  // partial DCT of a general even length (mixed-radix chain): the roots table of this n
+  // (gen_tw_bytes(n/2) bytes, shared by the problems of equal n), else null
+  const void* twg;
   // dense
   const void* A;
   int32_t a_dtype;
@@ -74,6 +77,22 @@ struct KernelArgs {
   int32_t phase2_only;    // a helper launch of single CTAs that takes the per-CTA queue only
   SolveParams prm;
 };
+
+// Roots table of the general-length partial DCT (L = n/2): three runs of L roots
+// (exp(-2 pi i e / L), exp(-2 pi i k / n), exp(-i pi k / (2n))) in float64 pairs, then the
+// same in float32 pairs, then in double-float quadruples, then the L int32 positions of the
+// frequencies after the forward FFT; each part 256-byte aligned.
+__host__ __device__ inline size_t gen_tw_al(size_t x) { return (x + 255) & ~(size_t)255; }
+__host__ __device__ inline size_t gen_tw_off32(int64_t L) { return gen_tw_al((size_t)3 * L * 16); }
+__host__ __device__ inline size_t gen_tw_offdf(int64_t L) { return gen_tw_off32(L) + gen_tw_al((size_t)3 * L * 8); }
+__host__ __device__ inline size_t gen_tw_offpos(int64_t L) { return gen_tw_offdf(L) + gen_tw_al((size_t)3 * L * 16); }
+__host__ __device__ inline size_t gen_tw_bytes(int64_t L) { return gen_tw_offpos(L) + gen_tw_al((size_t)L * 4); }
+// Variants of the general-length partial-DCT kernel: float32 PCG with the double-float or
+// the float64 iterate, and the float64 PCG.
+enum { kGenDF = 0, kGenF64 = 1, kGenF64Pcg = 2 };
+cudaError_t launch_gen_twiddles(void* base, int64_t n, cudaStream_t st);
+cudaError_t launch_dct_gen_solver(int variant, const KernelArgs& a, int64_t max_n, int ctas, cudaStream_t st);
+int max_active_ctas_dct_gen(int variant, int64_t max_n);
 
 // Launchers implemented in solver.cu.  Return cudaError_t of the launch.
 cudaError_t launch_twiddles(double2* tw64, float2* tw32, float4* twdf, int log2_tw, cudaStream_t st);

@@ -140,6 +140,11 @@ template <class R> struct PwConst {
         a2_j(pow2<R>(1 - geo.logN)),
         rs2(rsqrt2<R>()),
         zero() {}
+  // any even N (the mixed-radix chain): 1/L = 2/N, 1/N and 2/N, computed once per problem in
+  // float64 and rounded to the chain's arithmetic
+  __device__ PwConst(double inv_n)
+      : half(pow2<R>(-1)), invL(cst<R>(2.0 * inv_n)), a2_0(cst<R>(inv_n)), a2_j(cst<R>(2.0 * inv_n)),
+        rs2(rsqrt2<R>()), zero() {}
 };
 __device__ __forceinline__ float load_bsu(const DctGeom& g, int64_t i, float) { return g.bsu_df[i].x; }
 __device__ __forceinline__ double load_bsu(const DctGeom& g, int64_t i, double) { return g.bsu[i]; }
@@ -159,7 +164,7 @@ __device__ __forceinline__ df load_bsu(const DctGeom& g, int64_t i, df) {
 template <class C, int MODE, class R = decltype(C().x)>
 __device__ __forceinline__ C dct_pointwise_w(int64_t k, C a, C b, C wN, C eps, unsigned mb, const DctGeom& geo,
                                              const PwConst<R>& pc, bool valid, R& acc, double* fwd_out) {
-  const int64_t L = (int64_t)1 << geo.logL, N = geo.N;
+  const int64_t N = geo.N, L = N >> 1;
   const C c45 = mk(pc.rs2, -pc.rs2);  // exp(-i pi/4)
   const C E = cscale(cadd(a, cconj(b)), pc.half);
   const C O = cscale(cmul_mi(csub(a, cconj(b))), pc.half);

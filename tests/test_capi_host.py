@@ -78,7 +78,7 @@ def test_workspace_size_grows_with_batch(L):
     assert sizes[0] >= 4096 * 80 and sizes[0] < sizes[1] < sizes[2]
 
 
-@pytest.mark.parametrize("case", ["n_not_pow2", "m_gt_n", "n_too_big", "tau_nonpositive", "null_ws", "small_ws",
+@pytest.mark.parametrize("case", ["n_bad_length", "n_odd", "m_gt_n", "n_too_big", "tau_nonpositive", "null_ws", "small_ws",
                                   "bad_cluster", "bad_eta", "dense_bf16_here", "dct_bf16_prec"])
 def test_invalid_arguments_rejected_before_launch(L, case):
     from paper_1208_5435_gb300 import _capi as C
@@ -87,8 +87,10 @@ def test_invalid_arguments_rejected_before_launch(L, case):
     op = _dct_op(C, 4096, 1024)
     tau = 0.1
     ws, wsb = ctypes.c_void_p(0x10000), 1 << 40
-    if case == "n_not_pow2":
-        op.n = 3000
+    if case == "n_bad_length":
+        op.n = 1400  # n/2 = 700 has the prime factor 7
+    elif case == "n_odd":
+        op.n = 3001
     elif case == "m_gt_n":
         op.m = 5000
     elif case == "n_too_big":
@@ -266,3 +268,56 @@ def test_partial_haar_workspace_matches_dct(L):
         assert L.mfipm_workspace_size(ctypes.byref(op), 1, ctypes.byref(p), ctypes.byref(nb)) == 0
         sizes[kind] = nb.value
     assert 97 * 8192 <= sizes[C.OP_PARTIAL_HAAR] < sizes[C.OP_PARTIAL_DCT]
+
+
+def test_general_length_dct_workspace(L):
+    """Lengths that are not powers of two (n/2 with prime factors 2, 3, 5 only) are sized like
+    the others plus one roots table per distinct n, shared by the problems of that n."""
+    from paper_1208_5435_gb300 import _capi as C
+    p = C.Params()
+    L.mfipm_params_default(ctypes.byref(p))
+
+    def size(ns):
+        ops = (C.Operator * len(ns))(*[_dct_op(C, n, n // 4) for n in ns])
+        nb = ctypes.c_size_t()
+        assert L.mfipm_workspace_size(ops, len(ns), ctypes.byref(p), ctypes.byref(nb)) == 0, L.mfipm_last_error()
+        return nb.value
+
+    one = size([1000])
+    same = size([1000, 1000]) - one     # a second problem of the same n: no second table
+    other = size([1000, 960]) - one     # a smaller n with a table of its own (3 x 480 roots x 40 B)
+    assert other > same and other - same >= 3 * 480 * 40 - 2 * 40 * 1000
+    for n in (8, 96, 250, 1000, 6000, 16200):
+        assert size([n]) > 0
+
+
+@pytest.mark.parametrize("case", ["too_long", "factor_7", "cluster", "backward", "apply", "batch_too_long"])
+def test_general_length_dct_rejected_before_launch(L, case):
+    from paper_1208_5435_gb300 import _capi as C
+    p = C.Params()
+    L.mfipm_params_default(ctypes.byref(p))
+    ws, wsb = ctypes.c_void_p(0x10000), 1 << 40
+    info = C.Info()
+    P = ctypes.c_void_p
+    ops = [_dct_op(C, 1000, 250)]
+    if case == "too_long":
+        ops = [_dct_op(C, 20000, 5000)]   # n/2 = 2^4 5^4, above one CTA's 16384
+    elif case == "factor_7":
+        ops = [_dct_op(C, 1400, 300)]
+    elif case == "cluster":
+        p.cluster_size = 4
+    elif case == "batch_too_long":
+        ops = [_dct_op(C, 1000, 250), _dct_op(C, 32768, 8192)]
+    arr = (C.Operator * len(ops))(*ops)
+    ptrs = (P * len(ops))(*[P(0x3000)] * len(ops))
+    taus = (ctypes.c_double * len(ops))(*[0.1] * len(ops))
+    if case == "backward":
+        rc = L.mfipm_backward(1, arr, ptrs, taus, ptrs, ptrs, ptrs, None, None, None, ctypes.byref(p), ws, wsb,
+                              ctypes.byref(info), None)
+    elif case == "apply":
+        rc = L.mfipm_apply_A(ctypes.byref(arr[0]), P(0x3000), P(0x4000), ws, wsb, None)
+    else:
+        infos = (C.Info * len(ops))()
+        rc = L.mfipm_solve_batched(len(ops), arr, ptrs, taus, ctypes.byref(p), ptrs, None, ws, wsb, infos, None)
+    assert rc in (C.MFIPM_INVALID_ARG, C.MFIPM_UNSUPPORTED), (case, rc)
+    assert len(L.mfipm_last_error()) > 5

@@ -24,20 +24,22 @@ def _lib():
     built_lib()
 
 
-def _sample():
+def _sample(name):
     cells = W.phase_cells()
-    probs = W.make_workload("phase_transition_1024")
+    probs = W.make_workload(name)
     pick = [j for j, (m, k) in enumerate(cells)
             if m in (100, 500, 900) and k in (1, max(1, m // 10), m // 4, m // 2, m)]
     return [probs[j] for j in pick]
 
 
-def test_phase_cells_match_oracle():
+@pytest.mark.parametrize("name", ["phase_transition_1000", "phase_transition_1024"])
+def test_phase_cells_match_oracle(name):
+    """n = 1000 (the paper's length, mixed-radix chain) and n = 1024 (power-of-two chain)."""
     import paper_1208_5435_gb300 as M
-    probs = _sample()
+    probs = _sample(name)
     ops = [M.PartialDCT(p.n, torch.from_numpy(p.rows)) for p in probs]
     xs, infos = M.solve_batched(ops, [torch.from_numpy(p.b) for p in probs], [p.tau for p in probs],
-                                M.SolverParams(tol=W.WORKLOADS["phase_transition_1024"]["tol"]))
+                                M.SolverParams(tol=W.WORKLOADS[name]["tol"]))
     for p, x, info in zip(probs, xs, infos):
         op = O.Operator.from_dct_rows(p.n, p.rows)
         ref = O.ipm(op, p.b, p.tau, O.OracleParams(tol=1e-12)).x

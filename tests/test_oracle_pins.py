@@ -285,8 +285,10 @@ def pin_certificate_chain_violation(seed=29, n=40):
 
 
 # ---------------------------------------------------------------- tests
-def test_dct_rows_orthonormal_and_match_library():
-    n = 256
+@pytest.mark.parametrize("n", [256, 1000, 250])
+def test_dct_rows_orthonormal_and_match_library(n):
+    """The DCT rows from their definition at a power of two and at the general lengths of the
+    mixed-radix chain (n = 1000 of Sec. 5.8; n/2 = 125 odd)."""
     rows = np.sort(_rng(1).choice(n, 64, replace=False))
     A = O.dct_matrix_rows(n, rows)
     assert np.abs(A @ A.T - np.eye(64)).max() < 1e-12          # Eq. eq:orthonormality
@@ -299,10 +301,10 @@ def test_dct_rows_orthonormal_and_match_library():
     assert np.abs(full.T @ full - np.eye(n)).max() < 1e-12
 
 
-def test_closed_form_orthonormal_square():
+@pytest.mark.parametrize("n", [64, 60])
+def test_closed_form_orthonormal_square(n):
     assert pin_closed_form_error() < 1e-9
-    # full DCT (m = n) as well
-    n = 64
+    # full DCT (m = n) as well, at a power of two and at n = 60 (n/2 = 2^2 3 5)
     op = O.Operator.from_dct_rows(n, np.arange(n))
     b = _rng(4).standard_normal(n)
     tau = 0.3 * np.abs(op.rmv(b)).max()

@@ -189,12 +189,14 @@ WORKLOADS = {
     # 32 partial-DCT problems n=2^20, m=2^18, k=n/100 N(0,1)
     "dct_adjoint_32x1M": dict(kind="dct", n=1 << 20, m=1 << 18, k=(1 << 20) // 100, values="normal",
                               seed=1005, count=32),
-    # the empirical phase transition of Sec. 5.8: noiseless partial DCT, m = 100..900 step 100,
-    # k = 1..m step 1, +-1 spikes; one problem per (m, k) cell per trial (4500 per trial), n =
-    # 1024 in place of the paper's 1000 (a power of two for the radix-2 DCT), tau = 1e-6
+    # the empirical phase transition of Sec. 5.8: noiseless partial DCT of the paper's n = 1000
+    # (the mixed-radix chain: n/2 = 2^2 5^3), m = 100..900 step 100, k = 1..m step 1, +-1
+    # spikes; one problem per (m, k) cell per trial (4500 per trial), tau = 1e-6
     # ||A^T b||_inf (the paper states no tau for this experiment; see phase_problems); solver
     # tolerance 1e-12: with objectives near tau ||x_hat||_1 ~ 1e-5, a relative gap of 1e-10
     # against 1 + |P| leaves x errors close to the 1e-5 success radius
+    "phase_transition_1000": dict(kind="phase", n=1000, seed=1006, trials=100, tau_frac=1e-6, tol=1e-12),
+    # the same grid at n = 1024 (the power-of-two chain of the persistent kernel's clusters)
     "phase_transition_1024": dict(kind="phase", n=1024, seed=1006, trials=100, tau_frac=1e-6, tol=1e-12),
     # the uneven batch of dct_batch_256 (same sizes and spikes) on partial Haar rows (Sec. 2)
     "haar_batch_256": dict(kind="haar_batch", count=256, seed=1003),
