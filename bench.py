@@ -666,7 +666,7 @@ def run_phase(args, rank, world, local_rank):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32 PCG / f64 IPM", "data": "synthetic",
+        "vs_baseline": None, "dtype": "f32 PCG / double-float outer (~48-bit)", "data": "synthetic",
         "config": {"workload": args.workload, "problems": len(cells), "n": w["n"],
                    "cells": "m = 100..900 step 100, k = 1..m", "tau": "1e-6 ||A^T b||_inf, noiseless b",
                    "trials": args.steps * world, "tol": params.tol,
@@ -1087,7 +1087,7 @@ def run_bf16(args, rank, world, local_rank, probs):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "bf16 A / f32 PCG / f64 IPM", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None, "dtype": "bf16 A / f32 PCG / double-float outer (~48-bit)", "data": "synthetic",
         "config": {"workload": args.workload, "m": m, "n": n, "rhs": R, "l2": "flushed (512 MiB write) before each step",
                    "solved_at_kkt_1e-6": ok,
                    "tuned": {"splits1": tuning["splits1"], "splits2": tuning["splits2"],
@@ -1228,7 +1228,7 @@ def run_adjoint(args, rank, world, local_rank, probs):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32 PCG / f64 IPM", "data": "synthetic",
+        "vs_baseline": None, "dtype": "f32 PCG / double-float outer (~48-bit)", "data": "synthetic",
         "config": {"workload": args.workload, "problems": len(probs), "n": probs[0].n, "m": probs[0].m,
                    "solve": "forward solve + adjoint (mfipm_backward) per problem",
                    "tol": params.tol, "tol_pcg": params.tol_pcg,

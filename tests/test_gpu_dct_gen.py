@@ -127,3 +127,33 @@ def test_zs_out_is_in_natural_order():
     atb = op.rmv(p.b)
     cn = np.sqrt(2 * n * p.tau ** 2 + 2 * atb @ atb)
     assert abs(np.linalg.norm(fz) / (1 + cn) - info["dual_res"]) <= 1e-2 * info["dual_res"] + 1e-12, info
+
+
+@pytest.mark.parametrize("n", [8, 12, 20, 30, 90])
+def test_smallest_lengths(n):
+    """The shortest transforms (n/2 = 4, 6, 10, 15, 45: a lone radix-4 stage, radix 2 after 3,
+    odd halves) against the oracle, every row sampled but one."""
+    M = mf()
+    p = W.dct_problem(n, n - 1, 2, seed=338, j=n)
+    x, info = M.solve(M.PartialDCT(p.n, torch.from_numpy(p.rows)), torch.from_numpy(p.b), p.tau,
+                      M.SolverParams(tol=1e-12))
+    assert info["status"] == 0, (n, info)
+    assert relx(x.cpu().numpy(), oracle_x(p).x) <= RELX_TOL, (n, info)
+
+
+def test_full_basis_is_the_soft_threshold():
+    """m = n = 1000 (A orthonormal and square): the minimiser is S_tau(A^T b) in closed form."""
+    M = mf()
+    p = W.dct_problem(1000, 1000, 20, seed=339)
+    x, info = M.solve(M.PartialDCT(p.n, torch.from_numpy(p.rows)), torch.from_numpy(p.b), p.tau,
+                      M.SolverParams(tol=1e-12))
+    atb = O.Operator.from_dct_rows(p.n, p.rows).rmv(p.b)
+    assert info["status"] == 0 and relx(x.cpu().numpy(), O.soft_threshold(atb, p.tau)) <= RELX_TOL, info
+
+
+def test_no_measurements_gives_zero():
+    """m = 0: the objective is tau ||x||_1, minimised by x = 0."""
+    M = mf()
+    op = M.PartialDCT(1000, torch.zeros(0, dtype=torch.int64))
+    x, info = M.solve(op, torch.zeros(0, dtype=torch.float64), 0.1, M.SolverParams(tol=1e-12))
+    assert info["status"] == 0 and float(x.abs().max()) <= 1e-8 and info["kkt_rel"] <= 1e-8
