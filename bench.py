@@ -398,6 +398,7 @@ def run_ours(args, rank, world, local_rank):
             step_ms.append(e0.elapsed_time(e1))
             kern_ms.append(L.mfipm_last_kernel_ms())
     torch.cuda.synchronize()
+    launches_per_step = last_call_launches(L)
     if world > 1:
         torch.distributed.barrier()
     L.mfipm_set_timing(0)
@@ -535,7 +536,7 @@ def run_ours(args, rank, world, local_rank):
         "batched_over_plain": (value / world / plain["value"]) if plain else None,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "cpu_baseline": cpu,
-        "gpu_launches": 5 * args.steps,  # twiddles, row setup, scatter, per-frequency packing, solver
+        "gpu_launches": launches_per_step * args.steps,  # counted by the library per solve call
         "clocks": clk.summary(),
         "iterations": {"ipm_mean": statistics.mean(i["ipm_iters"] for i in infos),
                        "pcg_mean": statistics.mean(i["pcg_iters"] for i in infos),
@@ -605,6 +606,7 @@ def run_phase(args, rank, world, local_rank):
             kern_ms.append(L.mfipm_last_kernel_ms())
             results.append((xs, infos))
     torch.cuda.synchronize()
+    launches_per_step = last_call_launches(L)
     if world > 1:
         torch.distributed.barrier()
     L.mfipm_set_timing(0)
@@ -682,7 +684,7 @@ def run_phase(args, rank, world, local_rank):
                              "processed_per_s": len(cells) * world / (ms_per_step / 1e3)},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "cpu_baseline": cpu,
-        "gpu_launches": 5 * args.steps,  # twiddles, row setup, scatter, per-frequency packing, solver
+        "gpu_launches": launches_per_step * args.steps,  # counted by the library per solve call
         "clocks": clk.summary(),
         "iterations": {"ipm_mean": statistics.mean(i["ipm_iters"] for i in infos_last),
                        "pcg_mean": statistics.mean(i["pcg_iters"] for i in infos_last),
@@ -1011,7 +1013,7 @@ def run_bf16(args, rank, world, local_rank, probs):
     ms_per_step = total_ms / args.steps
     ms_, by_, pr_, la_ = ctypes.c_double(), ctypes.c_double(), ctypes.c_int64(), ctypes.c_int64()
     assert L.mfipm_last_operator_stats(ctypes.byref(ms_), ctypes.byref(by_), ctypes.byref(pr_), ctypes.byref(la_)) == 0
-    launches = int(la_.value) + 1  # the lockstep solve's kernels + the norm of A before it
+    launches = int(la_.value)  # the kernels of the last solve call (lockstep solve and the norm of A)
 
     # e2e: A and the right-hand sides from pinned host memory, x read back, every step
     hA = torch.from_numpy(probs[0].a_bf16.view(np.int16)).pin_memory()
@@ -1261,6 +1263,13 @@ def kernel_hash(files=None):
     for f in sorted(files or os.listdir(d)):
         h.update(open(os.path.join(d, f), "rb").read())
     return h.hexdigest()[:12]
+
+
+def last_call_launches(L):
+    """Kernels of ours the last solve, batched solve or backward call launched (library count)."""
+    ms_, by_, pr_, la_ = ctypes.c_double(), ctypes.c_double(), ctypes.c_int64(), ctypes.c_int64()
+    assert L.mfipm_last_operator_stats(ctypes.byref(ms_), ctypes.byref(by_), ctypes.byref(pr_), ctypes.byref(la_)) == 0
+    return int(la_.value)
 
 
 def load_traffic(workload):

@@ -267,8 +267,9 @@ double mfipm_last_kernel_ms(void);
  * y = A^T A w of its PCG (the three FFT passes, Sec. 4's only use of A).  For the last such
  * solve or backward on this thread: *ms = their summed device time (-1 if none),
  * *bytes = their algorithmic bytes (w read and y written: 8 bytes per index of every problem
- * the product covers), *products = how many products, *launches = how many kernels the
- * whole call launched.  Not in the paper. */
+ * the product covers), *products = how many products.  *launches = how many kernels the last
+ * mfipm_solve, mfipm_solve_batched or mfipm_backward call on this thread launched, on any
+ * solver path (with timing on or off).  Not in the paper. */
 int mfipm_last_operator_stats(double* ms, double* bytes, int64_t* products, int64_t* launches);
 
 /* Measured float32 FMA throughput of the current device, in TFLOP/s (*tflops, HOST): the

@@ -19,6 +19,14 @@
 #include "large_dct.h"
 #include "mrhs.h"
 
+namespace mfipm {
+// Kernels launched by the current public call on this thread (kept in mrhs.cu, where the
+// lockstep solvers count theirs): cleared when a solve, batched solve or backward call
+// starts; the persistent path adds its launches.
+void lockstep_stats_reset();
+void note_launches(int64_t n);
+}  // namespace mfipm
+
 using namespace mfipm;
 
 namespace {
@@ -558,6 +566,9 @@ int run(Prepared& P, cudaStream_t st, int batch, mfipm_info* infos, const std::v
       return cuda_fail(e, "join");
   }
   if (timing) cudaEventRecord(g_ev[1], st);
+  // twiddles, mask/b setup, scatter, per-frequency packing, the roots tables of general
+  // lengths, the solver and its helper launch
+  note_launches((P.dct ? 4 + (int64_t)P.lay.gen_tabs.size() : 0) + 1 + (helper > 0 ? 1 : 0));
   int err = 0;
   if ((e = cudaMemcpyAsync(&err, P.args.err, sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
     return cuda_fail(e, "read error word");
@@ -904,6 +915,7 @@ int backward_persistent(int32_t batch, const mfipm_operator* ops, const double* 
       : P.dct ? launch_bwd_dct(P.G, P.args, P.max_n, clusters, st)
               : launch_bwd_dense(P.G, P.pcg64, P.args, P.max_n, P.max_m, clusters, st);
   if (e != cudaSuccess) return cuda_fail(e, "backward launch");
+  note_launches((P.dct ? 4 : 0) + 1);
   std::vector<double> gt(batch);
   std::vector<mfipm_info> tmp;
   if (!infos) {
@@ -1136,6 +1148,7 @@ int mfipm_workspace_size(const mfipm_operator* ops, int32_t batch, const mfipm_p
 int mfipm_solve(const mfipm_operator* op, const double* b, double tau, const mfipm_params* p, double* x,
                 double* zs_out, void* workspace, size_t ws_bytes, mfipm_info* info, void* stream) {
   g_err.clear();
+  lockstep_stats_reset();
   const double* bb[1] = {b};
   double* xx[1] = {x};
   double* zz[1] = {zs_out};
@@ -1180,6 +1193,7 @@ int mfipm_solve_batched(int32_t batch, const mfipm_operator* ops, const double* 
                         const mfipm_params* p, double* const* x, double* const* zs_out, void* workspace,
                         size_t ws_bytes, mfipm_info* infos, void* stream) {
   g_err.clear();
+  lockstep_stats_reset();
   {
     int rc = validate_params(p);
     if (rc) return rc;
@@ -1209,6 +1223,7 @@ int mfipm_backward(int32_t batch, const mfipm_operator* ops, const double* const
                    double* const* grad_b, double* grad_tau, double* const* grad_A, const mfipm_params* p,
                    void* workspace, size_t ws_bytes, mfipm_info* infos, void* stream) {
   g_err.clear();
+  lockstep_stats_reset();
   if (!zs || !grad_x) return fail(MFIPM_INVALID_ARG, "zs and grad_x are required");
   if (batch < 1 || !ops || !b || !tau || !x) return fail(MFIPM_INVALID_ARG, "NULL argument array or batch < 1");
   int rc = validate_params(p);

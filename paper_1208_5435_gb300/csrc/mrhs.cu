@@ -1213,7 +1213,6 @@ int lockstep_run(mr::Dev& d, double* part2, const double* taus, const double* rh
 
 int mrhs_solve(const MrhsCall& call, std::string* msg) {
   using namespace mr;
-  g_nlaunch = 0;
   const int64_t m = call.m, n = call.n;
   const int R = call.R;
   cudaStream_t st = call.stream;
@@ -1550,7 +1549,6 @@ struct LdState {
 // carve the workspace, upload per-problem arguments, build mask / b_u and the twiddles
 int ld_setup(const LdCall& call, LdState& S, std::string* msg) {
   using namespace mr;
-  g_nlaunch = 0;
   const int64_t n = call.n;
   const int R = call.R;
   cudaStream_t st = call.stream;
@@ -1802,6 +1800,12 @@ void large_dct_set_timing(bool on) {
   g_optimer.on = on;
   g_optimer.reset();
 }
+void lockstep_stats_reset() {
+  g_nlaunch = 0;
+  g_optimer.reset();
+}
+void note_launches(int64_t n) { g_nlaunch += n; }
+
 void large_dct_timing(double* ms, double* bytes, int64_t* products, int64_t* launches) {
   *ms = g_optimer.ms;
   *bytes = g_optimer.bytes;
@@ -1825,6 +1829,7 @@ cudaError_t bf16_fro2(const void* A, int64_t m, int64_t n, int64_t lda, double* 
   cudaError_t e = cudaMemsetAsync(out, 0, 8, st);
   if (e) return e;
   mr::k_fro2<<<1024, 256, 0, st>>>(static_cast<const __nv_bfloat16*>(A), m, n, lda, out);
+  ++g_nlaunch;
   return cudaGetLastError();
 }
 
