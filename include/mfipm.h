@@ -65,9 +65,10 @@ typedef enum {
  *                         shared memory per problem.  A batch that holds such a length runs
  *                         every problem of it that way (so all its n <= 16384, cluster_size
  *                         0 or 1); mfipm_solve, mfipm_solve_batched and mfipm_solve_noalloc
- *                         take it with either PCG precision and either outer loop;
- *                         mfipm_backward and the operator products (mfipm_apply_A,
- *                         mfipm_apply_At, mfipm_kkt_residual) return MFIPM_UNSUPPORTED.
+ *                         take it with either PCG precision and either outer loop,
+ *                         mfipm_backward with the float32 adjoint PCG; the operator products
+ *                         (mfipm_apply_A, mfipm_apply_At, mfipm_kkt_residual) evaluate such
+ *                         rows from the definition (direct sums, O(m n)).
  *   MFIPM_OP_PARTIAL_HAAR: A = the rows `rows` of the orthonormal n x n Haar matrix (Sec. 2
  *                         names Haar wavelets among the orthonormal systems with O(n)
  *                         products): row 0 = 1/sqrt(n); row 2^j + k (0 <= j < log2 n,

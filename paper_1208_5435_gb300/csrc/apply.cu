@@ -214,7 +214,7 @@ size_t apply_workspace_bytes(const mfipm_operator& op) {
   c.take(256);                                  // error word, kkt result
   c.take((size_t)8 * n);                        // g (float64)
   c.take((size_t)8 * (m > n ? m : n));          // A x (float64)
-  if (op.kind == MFIPM_OP_PARTIAL_DCT && n >= kLdMinN) {
+  if (op.kind == MFIPM_OP_PARTIAL_DCT && n >= kLdMinN && (n & (n - 1)) == 0) {
     const LdShape s = ld_shape(n);
     const size_t tw = (size_t)2 << (s.logN + 2);
     c.take(sizeof(ProbDesc));
@@ -248,7 +248,7 @@ int apply_operator(int what, const mfipm_operator& op, const double* in, const d
   cudaError_t e;
   if ((e = cudaMemsetAsync(err, 0, 4, st))) return cu_fail(e, msg, "clear error word");
   const bool dct = op.kind == MFIPM_OP_PARTIAL_DCT, haar = op.kind == MFIPM_OP_PARTIAL_HAAR;
-  if (dct && n >= kLdMinN) {
+  if (dct && n >= kLdMinN && (n & (n - 1)) == 0) {  // powers of two: the multi-pass chain
     const LdShape s = ld_shape(n);
     const int log2_tw = s.logN + 2;
     const size_t tw = (size_t)2 << log2_tw;

@@ -14,6 +14,7 @@
 #include <string>
 #include <vector>
 
+#include "dct_gen.h"
 #include "device_common.cuh"
 #include "internal.h"
 #include "large_dct.h"
@@ -876,9 +877,6 @@ int backward_persistent(int32_t batch, const mfipm_operator* ops, const double* 
                    const double* const* x, const double* const* zs, const double* const* grad_x,
                    double* const* grad_b, double* grad_tau, double* const* grad_A, const mfipm_params* p,
                    void* workspace, size_t ws_bytes, mfipm_info* infos, void* stream) {
-  if (needs_gen(ops, batch))
-    return fail(MFIPM_UNSUPPORTED, "mfipm_backward: the partial DCT of a length that is not a power of two has no "
-                "adjoint solver");
   Prepared P;
   int rc = prepare(batch, ops, b, tau, p, const_cast<double* const*>(x), nullptr, workspace, ws_bytes, P);
   if (rc) return rc;
@@ -906,16 +904,21 @@ int backward_persistent(int32_t batch, const mfipm_operator* ops, const double* 
     if ((e = launch_dct_setup(P.args.probs, batch, P.max_n, P.args.err, st)) != cudaSuccess)
       return cuda_fail(e, "setup kernel");
   }
-  const int maxc = P.haar  ? max_active_clusters_bwd_haar(P.G, P.max_n)
+  if (P.gen)
+    for (auto& t : P.lay.gen_tabs)
+      if ((e = launch_gen_twiddles(P.ws + t.second, t.first, st)) != cudaSuccess) return cuda_fail(e, "roots table");
+  const int maxc = P.gen    ? max_active_ctas_bwd_dct_gen(P.max_n)
+                   : P.haar ? max_active_clusters_bwd_haar(P.G, P.max_n)
                    : P.dct ? max_active_clusters_bwd_dct(P.G, P.max_n)
                            : max_active_clusters_bwd_dense(P.G, P.pcg64, P.max_n, P.max_m);
   if (maxc < 1) return fail(MFIPM_UNSUPPORTED, "no resident cluster of size %d fits this problem", P.G);
   const int clusters = std::min(maxc, batch);
-  e = P.haar  ? launch_bwd_haar(P.G, P.args, P.max_n, clusters, st)
+  e = P.gen    ? launch_bwd_dct_gen(P.args, P.max_n, clusters, st)
+      : P.haar ? launch_bwd_haar(P.G, P.args, P.max_n, clusters, st)
       : P.dct ? launch_bwd_dct(P.G, P.args, P.max_n, clusters, st)
               : launch_bwd_dense(P.G, P.pcg64, P.args, P.max_n, P.max_m, clusters, st);
   if (e != cudaSuccess) return cuda_fail(e, "backward launch");
-  note_launches((P.dct ? 4 : 0) + 1);
+  note_launches((P.dct ? 4 + (int64_t)P.lay.gen_tabs.size() : 0) + 1);
   std::vector<double> gt(batch);
   std::vector<mfipm_info> tmp;
   if (!infos) {
@@ -942,9 +945,6 @@ int apply_checked(int what, const mfipm_operator* op, const double* in, const do
   g_err.clear();
   int rc = validate_op(op, 0);
   if (rc) return rc;
-  if (needs_gen(op, 1))
-    return fail(MFIPM_UNSUPPORTED, "the operator products are built for power-of-two partial-DCT lengths (n=%lld)",
-                (long long)op->n);
   if (!in || (what < 2 && !out) || (what == 2 && (!kkt || (op->m > 0 && !b))))
     return fail(MFIPM_INVALID_ARG, "NULL vector argument");
   if (what == 2 && !(tau > 0.0 && isfinite(tau))) return fail(MFIPM_INVALID_ARG, "tau must be positive and finite");

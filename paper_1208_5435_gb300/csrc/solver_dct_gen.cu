@@ -6,6 +6,7 @@
 // FFT done as an in-place mixed-radix transform (radices 4, 2, 3, 5) in one CTA's shared
 // memory.  One CTA per problem (n <= 16384: 24 bytes of shared memory per complex point, as
 // for the power-of-two chain); the IPM around it is the persistent kernel's solve_one.
+#include "dct_gen.h"
 #include "solver_impl.cuh"
 
 namespace mfipm {
@@ -156,10 +157,11 @@ __device__ void gen_fft(C* buf, const GenPlan& pl, const GenTw<C>& tw) {
 
 // The untangling, mask and inverse for every frequency: thread k takes k and its partner
 // L - k (0 and, for even L, L/2 pair with themselves).  Returns this CTA's share of the masked
-// coefficient energy.
+// coefficient energy.  MODE_FORWARD writes the orthonormal DCT-II coefficients to fwd
+// instead (every one of the n exactly once) and leaves buf as it is.
 template <class C, int MODE>
-__device__ double gen_pointwise(C* buf, const DctGeom& geo, const GenPlan& pl, const GenTw<C>& tw, double inv_n) {
-  static_assert(MODE != MODE_FORWARD, "the general-length chain has no forward-only mode");
+__device__ double gen_pointwise(C* buf, const DctGeom& geo, const GenPlan& pl, const GenTw<C>& tw, double inv_n,
+                                double* fwd) {
   using R = decltype(C().x);
   const PwConst<R> pc(inv_n);
   R acc = pc.zero;
@@ -170,23 +172,24 @@ __device__ double gen_pointwise(C* buf, const DctGeom& geo, const GenPlan& pl, c
     const unsigned ma = __ldg(geo.mcode + k), mb = __ldg(geo.mcode + kb);
     const C wa = tw.wN(k), ea = tw.eps(k), wb = tw.wN(kb), eb = tw.eps(kb);
     const C a = buf[pa], b = buf[pb];
-    const C na = dct_pointwise_w<C, MODE, R>(k, a, b, wa, ea, ma, geo, pc, true, acc, nullptr);
+    const C na = dct_pointwise_w<C, MODE, R>(k, a, b, wa, ea, ma, geo, pc, true, acc, fwd);
     if (kb != k) {
-      const C nb = dct_pointwise_w<C, MODE, R>(kb, b, a, wb, eb, mb, geo, pc, true, acc, nullptr);
-      buf[pb] = nb;
+      const C nb = dct_pointwise_w<C, MODE, R>(kb, b, a, wb, eb, mb, geo, pc, true, acc, fwd);
+      if constexpr (MODE != MODE_FORWARD) buf[pb] = nb;
     }
-    buf[pa] = na;
+    if constexpr (MODE != MODE_FORWARD) buf[pa] = na;
   }
   return to_double(acc);
 }
 
 template <class C, int MODE>
-__device__ double gen_chain(C* buf, const DctGeom& geo, const GenPlan& pl, const GenTw<C>& tw, double inv_n) {
+__device__ double gen_chain(C* buf, const DctGeom& geo, const GenPlan& pl, const GenTw<C>& tw, double inv_n,
+                            double* fwd = nullptr) {
   __syncthreads();
   gen_fft<false>(buf, pl, tw);
-  const double acc = gen_pointwise<C, MODE>(buf, geo, pl, tw, inv_n);
+  const double acc = gen_pointwise<C, MODE>(buf, geo, pl, tw, inv_n, fwd);
   __syncthreads();
-  gen_fft<true>(buf, pl, tw);
+  if constexpr (MODE != MODE_FORWARD) gen_fft<true>(buf, pl, tw);
   return acc;
 }
 
@@ -261,6 +264,16 @@ struct DctGenOp {
     __syncthreads();
     return acc;
   }
+  // grad_b = A w for w in rbuf<double>() (float64 chain): all n DCT coefficients go to
+  // pd.scratch, then the sampled rows are gathered.  Overwrites rbuf.
+  __device__ void apply_A_out(const ProbDesc& pd) {
+    gen_chain<double2, MODE_FORWARD>(buf64, geo, pl, tw64, inv_n, pd.scratch);
+    __threadfence();
+    __syncthreads();
+    if (pd.grad_b)
+      for (int64_t i = threadIdx.x; i < pd.m; i += kThreads) pd.grad_b[i] = pd.scratch[pd.rows[i]];
+  }
+  __device__ void grad_A_out(const ProbDesc&, const void*) {}
   __device__ int64_t natural(int64_t q) const { return q < geo.N / 2 ? 2 * q : 2 * geo.N - 1 - 2 * q; }
   template <int GG> __device__ void setup(RedSmem&, int&) {}
 };
@@ -314,6 +327,11 @@ cudaError_t launch_dct_gen_solver(int variant, const KernelArgs& a, int64_t max_
     default: return cudaErrorInvalidValue;
   }
 }
+
+cudaError_t launch_bwd_dct_gen(const KernelArgs& a, int64_t max_n, int ctas, cudaStream_t st) {
+  return launch_bwd_t<1, DctGenOp, float>(a, dct_gen_smem_bytes(max_n), ctas, st);
+}
+int max_active_ctas_bwd_dct_gen(int64_t max_n) { return occupancy_bwd_t<1, DctGenOp, float>(dct_gen_smem_bytes(max_n)); }
 
 int max_active_ctas_dct_gen(int variant, int64_t max_n) {
   const size_t smem = dct_gen_smem_bytes(max_n);

@@ -291,7 +291,7 @@ def test_general_length_dct_workspace(L):
         assert size([n]) > 0
 
 
-@pytest.mark.parametrize("case", ["too_long", "factor_7", "cluster", "backward", "apply", "batch_too_long"])
+@pytest.mark.parametrize("case", ["too_long", "factor_7", "cluster", "batch_too_long"])
 def test_general_length_dct_rejected_before_launch(L, case):
     from paper_1208_5435_gb300 import _capi as C
     p = C.Params()
@@ -311,13 +311,7 @@ def test_general_length_dct_rejected_before_launch(L, case):
     arr = (C.Operator * len(ops))(*ops)
     ptrs = (P * len(ops))(*[P(0x3000)] * len(ops))
     taus = (ctypes.c_double * len(ops))(*[0.1] * len(ops))
-    if case == "backward":
-        rc = L.mfipm_backward(1, arr, ptrs, taus, ptrs, ptrs, ptrs, None, None, None, ctypes.byref(p), ws, wsb,
-                              ctypes.byref(info), None)
-    elif case == "apply":
-        rc = L.mfipm_apply_A(ctypes.byref(arr[0]), P(0x3000), P(0x4000), ws, wsb, None)
-    else:
-        infos = (C.Info * len(ops))()
-        rc = L.mfipm_solve_batched(len(ops), arr, ptrs, taus, ctypes.byref(p), ptrs, None, ws, wsb, infos, None)
+    infos = (C.Info * len(ops))()
+    rc = L.mfipm_solve_batched(len(ops), arr, ptrs, taus, ctypes.byref(p), ptrs, None, ws, wsb, infos, None)
     assert rc in (C.MFIPM_INVALID_ARG, C.MFIPM_UNSUPPORTED), (case, rc)
     assert len(L.mfipm_last_error()) > 5

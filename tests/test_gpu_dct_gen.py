@@ -157,3 +157,93 @@ def test_no_measurements_gives_zero():
     op = M.PartialDCT(1000, torch.zeros(0, dtype=torch.int64))
     x, info = M.solve(op, torch.zeros(0, dtype=torch.float64), 0.1, M.SolverParams(tol=1e-12))
     assert info["status"] == 0 and float(x.abs().max()) <= 1e-8 and info["kkt_rel"] <= 1e-8
+
+
+def test_general_length_beside_the_multi_pass_path():
+    """A batch with n = 1000 and a power of two at or above the multi-pass threshold (lowered
+    to 2048): the general length runs on the mixed-radix persistent kernel, the other in the
+    lockstep multi-pass solver, in one call."""
+    import ctypes
+    M = mf()
+    L = M.lib()
+    assert L.mfipm_set_large_dct_threshold(ctypes.c_int64(2048)) == 0
+    try:
+        probs = [W.dct_problem(1000, 250, 10, seed=340), W.dct_problem(2048, 512, 20, seed=341)]
+        ops = [M.PartialDCT(p.n, torch.from_numpy(p.rows)) for p in probs]
+        xs, infos = M.solve_batched(ops, [torch.from_numpy(p.b) for p in probs], [p.tau for p in probs],
+                                    M.SolverParams(tol=1e-12))
+    finally:
+        assert L.mfipm_set_large_dct_threshold(ctypes.c_int64(1 << 17)) == 0
+    for p, x, info in zip(probs, xs, infos):
+        assert info["status"] == 0, (p.n, info)
+        assert relx(x.cpu().numpy(), oracle_x(p).x) <= RELX_TOL, (p.n, info)
+
+
+def test_fixed_scratch_entry_point_takes_a_general_length():
+    """mfipm_solve_noalloc on n = 1000 (the roots table sits in the fixed scratch too): the
+    same x as mfipm_solve with a workspace, twice in a row."""
+    import ctypes
+    from paper_1208_5435_gb300 import _capi as C
+    M = mf()
+    L = M.lib()
+    p = W.dct_problem(1000, 250, 10, seed=342)
+    rows = torch.from_numpy(p.rows).cuda()
+    b = torch.from_numpy(p.b).cuda()
+    op = C.Operator()
+    op.kind, op.a_dtype, op.m, op.n, op.A, op.a_scale, op.lda, op.rows = C.OP_PARTIAL_DCT, 0, p.m, p.n, None, 1.0, 0, rows.data_ptr()
+    prm = C.Params()
+    L.mfipm_params_default(ctypes.byref(prm))
+    prm.tol = 1e-12
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    nb = ctypes.c_size_t()
+    assert L.mfipm_workspace_size(ctypes.byref(op), 1, ctypes.byref(prm), ctypes.byref(nb)) == 0
+    ws = torch.empty(nb.value, dtype=torch.uint8, device="cuda")
+    x_ref = torch.empty(p.n, dtype=torch.float64, device="cuda")
+    info = C.Info()
+    assert L.mfipm_solve(ctypes.byref(op), b.data_ptr(), p.tau, ctypes.byref(prm), x_ref.data_ptr(), None,
+                         ws.data_ptr(), nb.value, ctypes.byref(info), stream) == 0, L.mfipm_last_error()
+    for _ in range(2):
+        x = torch.full((p.n,), float("nan"), dtype=torch.float64, device="cuda")
+        inf = C.Info()
+        assert L.mfipm_solve_noalloc(ctypes.byref(op), b.data_ptr(), p.tau, ctypes.byref(prm), x.data_ptr(), None,
+                                     ctypes.byref(inf), stream) == 0, L.mfipm_last_error()
+        assert inf.status == 0
+        assert relx(x.cpu().numpy(), x_ref.cpu().numpy()) <= RELX_TOL
+    assert relx(x_ref.cpu().numpy(), oracle_x(p).x) <= RELX_TOL
+
+
+def test_backward_matches_oracle_adjoint():
+    """mfipm_backward at n = 1000 against the oracle's exact KKT adjoint (grad_b = A w with
+    the forward chain of the mixed-radix transform, grad_tau); the float32 adjoint PCG to
+    min(tol_pcg, 1e-6), the bar of the power-of-two chain."""
+    M = mf()
+    p = W.dct_problem(1000, 250, 10, seed=343)
+    gx = np.random.default_rng(3).standard_normal(p.n)
+    prm = M.SolverParams(tol=1e-12)
+    op = M.PartialDCT(p.n, torch.from_numpy(p.rows))
+    b = torch.from_numpy(p.b).cuda()
+    x, info, zs = M.solve(op, b, p.tau, prm, return_zs=True)
+    assert info["status"] == 0
+    gbs, gts, _, infos = M.backward([op], [b], [p.tau], [x], [zs], [torch.from_numpy(gx).cuda()], prm)
+    ref = O.Operator.from_dct_rows(p.n, p.rows)
+    res = O.ipm(ref, p.b, p.tau)
+    rb, rt, _ = O.adjoint_kkt(ref, p.b, p.tau, res.z, res.s, gx)
+    gb = gbs[0].cpu().numpy()
+    assert np.abs(gb - rb).max() <= 5e-6 * np.abs(rb).max(), np.abs(gb - rb).max() / np.abs(rb).max()
+    assert abs(gts[0] - rt) <= 5e-6 * max(1.0, abs(rt))
+
+
+def test_operator_products_and_kkt():
+    """mfipm_apply_A, mfipm_apply_At and mfipm_kkt_residual at n = 1000 against the oracle's
+    DCT rows (direct sums from the definition)."""
+    M = mf()
+    p = W.dct_problem(1000, 250, 10, seed=344)
+    op = M.PartialDCT(p.n, torch.from_numpy(p.rows))
+    ref = O.Operator.from_dct_rows(p.n, p.rows)
+    rng = np.random.default_rng(4)
+    xr, yr = rng.standard_normal(p.n), rng.standard_normal(p.m)
+    ax = M.apply_A(op, torch.from_numpy(xr)).cpu().numpy()
+    aty = M.apply_At(op, torch.from_numpy(yr)).cpu().numpy()
+    assert relx(ax, ref.mv(xr)) <= 1e-12 and relx(aty, ref.rmv(yr)) <= 1e-12
+    k = M.kkt_residual(op, torch.from_numpy(p.b), p.tau, torch.from_numpy(xr))
+    assert abs(k - O.kkt_rel(ref, p.b, p.tau, xr)) <= 1e-12 * max(1.0, k)
