@@ -139,7 +139,7 @@ typedef struct {
                             iteration keeps.  Applied only when tau >= 1e-3 ||A^T b||_inf (the
                             float32 chain errs by ~1e-6 ||A^T b||_inf); smaller tau (basis
                             pursuit, the phase-transition workload) always use the outer
-                            precision.  0 = always the outer precision.  1e-4 */
+                            precision.  0 = always the outer precision.  1e-8 */
   int32_t centrality_correctors;  /* 0 (default): the single conditional corrector of the
                             Algorithm (Sec. 5.1).  K in 1..16: the multiple-centrality-corrector
                             variant that Sec. 5.1 names as the method's origin: after each

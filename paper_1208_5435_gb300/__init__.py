@@ -37,7 +37,7 @@ class SolverParams:
     equal_steps: int = 0
     cluster_size: int = 0
     outer: int = 0                    # partial DCT outer loop: 0 double-float, 1 native float64
-    outer_f32_gap: float = 1e-4       # partial DCT: float32 outer residual while the gap exceeds this
+    outer_f32_gap: float = 1e-8       # partial DCT: float32 outer residual while the gap exceeds this
     centrality_correctors: int = 0    # 0: the single corrector; K: up to K centrality correctors
 
     def to_c(self, default_precision: int) -> C.Params:

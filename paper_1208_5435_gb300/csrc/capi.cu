@@ -1120,7 +1120,7 @@ int mfipm_params_default(mfipm_params* p) {
   p->equal_steps = 0;
   p->cluster_size = 0;
   p->outer = MFIPM_OUTER_DF;
-  p->outer_f32_gap = 1e-4;
+  p->outer_f32_gap = 1e-8;
   return MFIPM_OK;
 }
 

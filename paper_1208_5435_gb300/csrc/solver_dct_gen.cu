@@ -12,7 +12,7 @@
 namespace mfipm {
 
 // Radices of L, first stage first: n4 fours, then n2 (0 or 1) twos, n3 threes and n5 fives
-// (the host admits only L whose other prime factors are none).
+// (the host admits only lengths whose half has no other prime factor).
 struct GenPlan {
   int L, n4, n2, n3, n5;
 };

@@ -48,7 +48,7 @@ def test_python_params_mirror_the_c_defaults(L):
     q = M.SolverParams().to_c(C.PREC_FP32_PCG)
     for name, _ in C.Params._fields_:
         assert getattr(p, name) == getattr(q, name), name
-    assert p.outer_f32_gap == 1e-4
+    assert p.outer_f32_gap == 1e-8
     p.outer_f32_gap = -1.0
     op = _dct_op(C, 1024, 256)
     nb = ctypes.c_size_t()
