@@ -132,14 +132,18 @@ typedef struct {
   int32_t equal_steps;   /* 0: separate primal and dual steps as in Sec. 5.1; 1: common step */
   int32_t cluster_size;  /* CTAs that cooperate on one problem (1,2,4,8,16); 0 = automatic */
   int32_t outer;         /* mfipm_outer; MFIPM_OUTER_DF */
-  double outer_f32_gap;  /* partial DCT: while the relative duality gap exceeds this value the
-                            outer residual A^T(Ax - b) runs through the float32 FFT chain; at the
-                            first iterate at or below it, and before any stop, it is recomputed
-                            in the outer loop's precision (mfipm_outer), which every later
-                            iteration keeps.  Applied only when tau >= 1e-3 ||A^T b||_inf (the
-                            float32 chain errs by ~1e-6 ||A^T b||_inf); smaller tau (basis
-                            pursuit, the phase-transition workload) always use the outer
-                            precision.  0 = always the outer precision.  1e-8 */
+  double outer_f32_gap;  /* partial DCT and shared bf16 A: while the relative duality gap exceeds
+                            this value the outer residual A^T(Ax - b) runs through a float32-grade
+                            chain (the float32 FFT chain; for bf16 A two tensor-core GEMMs with x
+                            and r as three bf16 pieces, in place of the exact digit slices); at
+                            the first iterate at or below it, and before any stop, it is
+                            recomputed in the outer loop's precision, which every later
+                            iteration keeps (for bf16 A: once any right-hand side gets there).
+                            Applied only when tau >= 1e-3 ||A^T b||_inf (every right-hand side
+                            for bf16 A; the float32-grade chains err by ~1e-6 ||A^T b||_inf);
+                            smaller tau (basis pursuit, the phase-transition workload) always use
+                            the outer precision.  Not used by the multi-pass partial DCT.
+                            0 = always the outer precision.  1e-8 */
   int32_t centrality_correctors;  /* 0 (default): the single conditional corrector of the
                             Algorithm (Sec. 5.1).  K in 1..16: the multiple-centrality-corrector
                             variant that Sec. 5.1 names as the method's origin: after each

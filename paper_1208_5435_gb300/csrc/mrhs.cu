@@ -544,6 +544,59 @@ __global__ void k_fin2_tc(const float2* __restrict__ Acc, double scale, float2* 
   }
 }
 
+// The residual of the outer loop's large-gap iterations (reading R17) in float32-grade
+// arithmetic on the tensor cores: a value v as three bf16 pieces v0 + v1 + v2 (24 significant
+// bits; every piece times a bf16 entry of A is exact in float32, the GEMM sums in float32).
+__device__ __forceinline__ void bf16_pieces3(float f, __nv_bfloat16* S, int64_t stride, int64_t at) {
+  const __nv_bfloat16 p0 = __float2bfloat16_rn(f);
+  const float r1 = f - __bfloat162float(p0);
+  const __nv_bfloat16 p1 = __float2bfloat16_rn(r1);
+  S[at] = p0;
+  S[at + stride] = p1;
+  S[at + 2 * stride] = __float2bfloat16_rn(r1 - __bfloat162float(p1));
+}
+// x (R x K, double-float) -> S[piece][j][k]
+__global__ void k_pieces_x(const float2* __restrict__ X, int R, int K, __nv_bfloat16* __restrict__ S) {
+  const int64_t total = (int64_t)R * K;
+  for (int64_t gi = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; gi < total; gi += (int64_t)gridDim.x * blockDim.x) {
+    const float2 v = X[gi];
+    // hi - bf16(hi) is exact in float32; lo lies below hi's last bit
+    const __nv_bfloat16 p0 = __float2bfloat16_rn(v.x);
+    const float r1 = (v.x - __bfloat162float(p0)) + v.y;
+    const __nv_bfloat16 p1 = __float2bfloat16_rn(r1);
+    S[gi] = p0;
+    S[gi + total] = p1;
+    S[gi + 2 * total] = __float2bfloat16_rn(r1 - __bfloat162float(p1));
+  }
+}
+// after T = A x (C: splits x 3R x m): Rr = scale T - b (float64) and the pieces of Rr
+__global__ void k_pieces_mid(const float* __restrict__ C, int splits, int R, int m, const double* __restrict__ Bm,
+                             double scale, double* __restrict__ Rr, __nv_bfloat16* __restrict__ S) {
+  const int64_t total = (int64_t)R * m, N = 3 * (int64_t)R;
+  for (int64_t gi = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; gi < total; gi += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t j = gi / m, i = gi % m;
+    float t = 0.f;
+    for (int sp = 0; sp < splits; ++sp)
+      for (int pc = 0; pc < 3; ++pc) t += C[(sp * N + pc * R + j) * m + i];
+    const double r = scale * (double)t - Bm[gi];
+    Rr[gi] = r;
+    bf16_pieces3((float)r, S, total, gi);
+  }
+}
+// after A^T r (C: splits x 3R x n): Gr = scale sum (double-float)
+__global__ void k_pieces_fin(const float* __restrict__ C, int splits, int R, int n, double scale,
+                             float2* __restrict__ Gr) {
+  const int64_t total = (int64_t)R * n, N = 3 * (int64_t)R;
+  const float sc = (float)scale;
+  for (int64_t gi = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; gi < total; gi += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t j = gi / n, k = gi % n;
+    float t = 0.f;
+    for (int sp = 0; sp < splits; ++sp)
+      for (int pc = 0; pc < 3; ++pc) t += C[(sp * N + pc * R + j) * n + k];
+    Gr[gi] = make_float2(sc * t, 0.f);
+  }
+}
+
 // ------------------------------------------------------------------ per-column state
 struct Dev {
   int m, n, R, nb;                 // nb: blocks per column of the index passes
@@ -685,7 +738,10 @@ __global__ void k_colnorm2(const double* __restrict__ V, int len, double* part, 
 
 // gap test, mu, sigma (one thread per column)
 // one block of kT threads per column
-__global__ void k_stats(Dev d, int it, const double* part2) {
+// lowp: the residual came from the float32-grade chain; a column that would stop, or whose gap
+// has reached prm.f32_gap, is counted in counters[3] instead (the driver then recomputes the
+// residual in full precision and runs this kernel again), so no stop rests on it.
+__global__ void k_stats(Dev d, int it, const double* part2, int lowp) {
   const int j = blockIdx.x;
   Col& c = d.col[j];
   if (c.done) return;
@@ -698,7 +754,9 @@ __global__ void k_stats(Dev d, int it, const double* part2) {
   c.rel_gap = zts / (1.0 + fabs(c.P_obj));
   c.corr = 0;
   c.ipm_iters = it - 1;
-  if (!isfinite(c.rel_gap)) { c.stop = MFIPM_NUMERIC; c.done = 1; }
+  const bool stop_now = !isfinite(c.rel_gap) || c.rel_gap <= d.prm.tol || it > d.prm.max_iter;
+  if (lowp && (stop_now || !(c.rel_gap > d.prm.f32_gap))) atomicAdd(&d.counters[3], 1);
+  else if (!isfinite(c.rel_gap)) { c.stop = MFIPM_NUMERIC; c.done = 1; }
   else if (c.rel_gap <= d.prm.tol) { c.stop = MFIPM_OK; c.done = 1; }
   else if (it > d.prm.max_iter) { c.stop = MFIPM_NOT_CONVERGED; c.done = 1; }
   c.sigma = (it != 1 && (c.prev_ap <= d.prm.alpha_bar || c.prev_ad <= d.prm.alpha_bar)) ? d.prm.sigma2 : d.prm.sigma1;
@@ -992,6 +1050,17 @@ __global__ void k_setup_cols(Dev d, const double* __restrict__ taus, const doubl
   d.col[j] = c;
 }
 
+// the float32-grade residual errs by ~1e-6 ||A^T b||_inf: counters[4] counts the columns
+// with tau < 1e-3 ||A^T b||_inf, for which it must not be used (Gr = -A^T b at this point)
+__global__ void k_lowp_gate(Dev d) {
+  __shared__ float red[33];
+  const int j = blockIdx.x;
+  float mx = 0.f;
+  for (int i = threadIdx.x; i < d.n; i += blockDim.x) mx = fmaxf(mx, fabsf(d.Gr[(int64_t)j * d.n + i].x));
+  mx = block_max(mx, red);
+  if (threadIdx.x == 0 && !(d.col[j].tau >= 1e-3 * (double)mx)) atomicAdd(&d.counters[4], 1);
+}
+
 // outputs in natural order and the float64 certificates (Gr holds the final residual)
 __global__ void k_exit(Dev d, double* const* __restrict__ xout, double* const* __restrict__ zsout) {
   const int j = blockIdx.y, blk = blockIdx.x;
@@ -1113,12 +1182,14 @@ int mr_fail(cudaError_t e, std::string* msg, const char* where) {
 }
 
 // The single-corrector IPM of Sec. 5.1 for all R problems in lockstep, each with its own
-// scalars.  residual(gate) computes Gr = A^T (A X - b) and part2 slot 0 = ||A X - b||^2;
-// normal(k, nprob) computes A^T A (p_u - p_v) for PCG iteration k (nprob: problems it covers) and
-// part2 slot 0 = ||A w||^2.
+// scalars.  residual(gate, lowp) computes Gr = A^T (A X - b) and part2 slot 0 = ||A X - b||^2
+// (lowp: by the float32-grade chain of the large-gap iterations, reading R17, where the
+// operator has one; allow_lowp says so); normal(k, nprob) computes A^T A (p_u - p_v) for PCG
+// iteration k (nprob: problems it covers) and part2 slot 0 = ||A w||^2.
 template <class Resid, class Normal>
 int lockstep_run(mr::Dev& d, double* part2, const double* taus, const double* rhos, Resid& residual, Normal& normal,
-                 double* const* xptr, double* const* zptr, mfipm_info* infos, cudaStream_t st, std::string* msg) {
+                 double* const* xptr, double* const* zptr, mfipm_info* infos, cudaStream_t st, std::string* msg,
+                 bool allow_lowp = false) {
   using namespace mr;
   const int R = d.R, nb = d.nb;
   const dim3 gIdx(nb, R);
@@ -1158,22 +1229,42 @@ int lockstep_run(mr::Dev& d, double* part2, const double* taus, const double* rh
 
   // setup: ||A^T b|| for ||c||
   if ((e = cudaMemsetAsync(d.X, 0, (size_t)R * d.n * 8, st))) return mr_fail(e, msg, "clear x");
-  if ((e = residual(GATE_ALL))) return mr_fail(e, msg, "residual");
+  if ((e = residual(GATE_ALL, false))) return mr_fail(e, msg, "residual");
   k_colnorm2_df<<<gIdx, kT, 0, st>>>(d.Gr, d.n, d.part, nb);
   ++g_nlaunch;
   k_setup_cols<<<R, kT, 0, st>>>(d, taus, rhos);
   ++g_nlaunch;
+  // the float32-grade residual while every problem's gap exceeds f32_gap, if every problem
+  // passes its gate (tau >= 1e-3 ||A^T b||_inf); from the first iterate at or below it, and
+  // before any stop, the residual is recomputed in full precision, which later iterations keep
+  bool lowp = false;
+  if (allow_lowp && d.prm.f32_gap > 0.0) {
+    int failing = 0;
+    if ((e = cudaMemsetAsync(d.counters + 4, 0, 4, st))) return mr_fail(e, msg, "counters");
+    k_lowp_gate<<<R, kT, 0, st>>>(d);
+    ++g_nlaunch;
+    if ((e = cudaMemcpyAsync(&failing, d.counters + 4, 4, cudaMemcpyDeviceToHost, st)) ||
+        (e = cudaStreamSynchronize(st)))
+      return mr_fail(e, msg, "residual gate");
+    lowp = failing == 0;
+  }
   for (int it = 1;; ++it) {
     k_update<<<gIdx, kT, 0, st>>>(d, it == 1);
     ++g_nlaunch;
-    if ((e = residual(GATE_LIVE))) return mr_fail(e, msg, "residual");
-    if ((e = cudaMemsetAsync(d.counters, 0, 16, st))) return mr_fail(e, msg, "counters");
-    k_stats<<<R, kT, 0, st>>>(d, it, part2);
-    ++g_nlaunch;
     int unfinished = 0;
-    if ((e = cudaMemcpyAsync(&unfinished, d.counters + 1, 4, cudaMemcpyDeviceToHost, st)) ||
-        (e = cudaStreamSynchronize(st)))
-      return mr_fail(e, msg, "gap test");
+    for (;;) {
+      if ((e = residual(GATE_LIVE, lowp))) return mr_fail(e, msg, "residual");
+      if ((e = cudaMemsetAsync(d.counters, 0, 16, st))) return mr_fail(e, msg, "counters");
+      k_stats<<<R, kT, 0, st>>>(d, it, part2, lowp ? 1 : 0);
+      ++g_nlaunch;
+      int cnt[3] = {0, 0, 0};  // unfinished, corrector columns, full precision needed
+      if ((e = cudaMemcpyAsync(cnt, d.counters + 1, 12, cudaMemcpyDeviceToHost, st)) ||
+          (e = cudaStreamSynchronize(st)))
+        return mr_fail(e, msg, "gap test");
+      unfinished = cnt[0];
+      if (!(lowp && cnt[2] > 0)) break;
+      lowp = false;  // this iterate's residual again, in full precision
+    }
     if (unfinished == 0) break;
     live = unfinished;
     k_pcg_init<<<gIdx, kT, 0, st>>>(d, 0);
@@ -1192,7 +1283,7 @@ int lockstep_run(mr::Dev& d, double* part2, const double* taus, const double* rh
       ++g_nlaunch;
       k_mu_t<<<R, kT, 0, st>>>(d);
       ++g_nlaunch;
-      if ((e = residual(GATE_LIVE))) return mr_fail(e, msg, "trial residual");
+      if ((e = residual(GATE_LIVE, lowp))) return mr_fail(e, msg, "trial residual");
       k_pcg_init<<<gIdx, kT, 0, st>>>(d, 1);
       ++g_nlaunch;
       if ((e = pcg(d.X2))) return mr_fail(e, msg, "corrector PCG");
@@ -1383,8 +1474,35 @@ int mrhs_solve(const MrhsCall& call, std::string* msg) {
     g_nlaunch += 5;
     return cudaGetLastError();
   };
-  auto resid = [&](int) -> cudaError_t { return rtc ? residual_tc() : residual(); };
-  return lockstep_run(d, part2, taus, nullptr, resid, normal, xptr, zptr, call.infos_dev, st, msg);
+  // the large-gap residual: A x and A^T r with x and r as three bf16 pieces (tensor cores,
+  // float32 sums), split-K capped by the chunk-sum buffer
+  auto residual_lowp = [&]() -> cudaError_t {
+    const size_t cap = tc_resid_cbuf(m, n);
+    auto fit = [&](int sp, int64_t rows) {
+      const int64_t lim = (int64_t)(cap / ((size_t)3 * R * rows * 4));
+      return (int)std::max<int64_t>(1, std::min<int64_t>(sp, lim));
+    };
+    const int sa = fit(d.s1, m), sb = fit(d.s2, n);
+    const unsigned gm = (unsigned)std::min<int64_t>(((int64_t)R * m + 255) / 256, 4096);
+    const unsigned gn = (unsigned)std::min<int64_t>(((int64_t)R * n + 255) / 256, 4096);
+    cudaError_t r;
+    k_pieces_x<<<gn, 256, 0, st>>>(d.X, R, (int)n, XS);
+    if ((r = call.gemm(call.gemm_ctx, d.A, XS, Cb, (int)m, 3 * R, (int)n, sa, st, call.stages1))) return r;
+    k_pieces_mid<<<gm, 256, 0, st>>>(Cb, sa, R, (int)m, d.Bm, d.a_scale, d.Rr, XS);
+    if ((r = call.gemm(call.gemm_ctx, At, XS, Cb, (int)n, 3 * R, (int)m, sb, st, call.stages2))) return r;
+    k_pieces_fin<<<gn, 256, 0, st>>>(Cb, sb, R, (int)n, d.a_scale, d.Gr);
+    k_colnorm2<<<dim3(nb, R), kT, 0, st>>>(d.Rr, (int)m, part2, nb);
+    g_nlaunch += 6;
+    return cudaGetLastError();
+  };
+  // the pieces need the digit-slice buffers and N = 3R <= 256 for one GEMM
+  const bool lowp_ok = rtc && 3 * R <= 256 && tc_gemm_supported((int)m, 3 * R, (int)n) &&
+                       tc_gemm_supported((int)n, 3 * R, (int)m);
+  auto resid = [&](int, bool lowp) -> cudaError_t {
+    if (lowp) return residual_lowp();
+    return rtc ? residual_tc() : residual();
+  };
+  return lockstep_run(d, part2, taus, nullptr, resid, normal, xptr, zptr, call.infos_dev, st, msg, lowp_ok);
 }
 
 // ------------------------------------------------------------------ large partial DCT
@@ -1704,7 +1822,7 @@ int large_dct_solve(const LdCall& call, std::string* msg) {
   if (rc) return rc;
   mr::Dev& d = S.d;
   cudaStream_t st = call.stream;
-  auto residual = [&](int gate) -> cudaError_t {
+  auto residual = [&](int gate, bool) -> cudaError_t {
     LdArgs a = S.base;
     a.gate = gate;
     a.din = d.X;
