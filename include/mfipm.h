@@ -138,12 +138,12 @@ typedef struct {
                             and r as three bf16 pieces, in place of the exact digit slices); at
                             the first iterate at or below it, and before any stop, it is
                             recomputed in the outer loop's precision, which every later
-                            iteration keeps (for bf16 A: once any right-hand side gets there).
-                            Applied only when tau >= 1e-3 ||A^T b||_inf (every right-hand side
-                            for bf16 A; the float32-grade chains err by ~1e-6 ||A^T b||_inf);
-                            smaller tau (basis pursuit, the phase-transition workload) always use
-                            the outer precision.  Not used by the multi-pass partial DCT.
-                            0 = always the outer precision.  1e-8 */
+                            iteration keeps (in the lockstep solvers, multi-pass partial DCT and
+                            bf16 A, once any problem of the group gets there).  Applied only when
+                            tau >= 1e-3 ||A^T b||_inf (for every problem of a lockstep group; the
+                            float32-grade chains err by ~1e-6 ||A^T b||_inf); smaller tau (basis
+                            pursuit, the phase-transition workload) always use the outer
+                            precision.  0 = always the outer precision.  1e-8 */
   int32_t centrality_correctors;  /* 0 (default): the single conditional corrector of the
                             Algorithm (Sec. 5.1).  K in 1..16: the multiple-centrality-corrector
                             variant that Sec. 5.1 names as the method's origin: after each

@@ -144,6 +144,23 @@ template <> struct Io<dfc> {
   static __device__ __forceinline__ dfc* inter(const LdArgs& a) { return reinterpret_cast<dfc*>(a.inter); }
 };
 
+// the outer residual of the large-gap iterations (reading R17) through the float32 chain:
+// x from its double-float pairs rounded to float32, A^T (A x - b) stored as double-float pairs
+struct IoR32 {
+  using R = float;
+  static __device__ __forceinline__ float load(const LdArgs& a, int64_t gi) {
+    const float2 v = a.din[gi];
+    return v.x + v.y;
+  }
+  static __device__ __forceinline__ void store4(const LdArgs& a, int64_t gi, float w0, float w1, float w2, float w3) {
+    float4* o = reinterpret_cast<float4*>(a.dout + gi);
+    o[0] = make_float4(w0, 0.f, w1, 0.f);
+    o[1] = make_float4(w2, 0.f, w3, 0.f);
+  }
+  static __device__ __forceinline__ Twiddle<float2> tw(const LdArgs& a) { return Twiddle<float2>{a.tw32, a.log2_tw}; }
+  static __device__ __forceinline__ float2* inter(const LdArgs& a) { return reinterpret_cast<float2*>(a.inter); }
+};
+
 // column t2 of slot ci of block cb (K columns: h = K/2 slots h cb + ci, then their mirrors
 // N2 - 2h - h cb + ci; slot ci and slot K - 1 - ci hold mirror columns t2 and N2 - 1 - t2)
 template <int K>
@@ -152,7 +169,7 @@ __device__ __forceinline__ int col_of(int ci, int cb, int N2) {
   return ci < h ? h * cb + ci : N2 - 2 * h - h * cb + ci;
 }
 
-template <class C>
+template <class C, class IO = Io<C>>
 __global__ void __launch_bounds__(kThr) pass_a(LdArgs a) {
   constexpr int kCols = ColsOf<C>::v, kLog = kCols == 16 ? 4 : 3;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -161,7 +178,6 @@ __global__ void __launch_bounds__(kThr) pass_a(LdArgs a) {
   if (gated_out(a, j)) return;
   const int N1 = 1 << a.logN1, N2 = 1 << a.logN2, stride = N1 + 1;
   const int64_t n = (int64_t)1 << a.logN, L = n >> 1, base = (int64_t)j * n;
-  using IO = Io<C>;
   // pack: t = N2 t1 + t2 (t1 < N1/2) takes w[4t], w[4t+2]; its mirror L-1-t (row N1-1-t1,
   // slot kCols-1-ci) takes w[4t+3], w[4t+1]
 #pragma unroll 4
@@ -330,14 +346,13 @@ __global__ void __launch_bounds__(kThrB) pass_b(LdArgs a) {
   }
 }
 
-template <class C>
+template <class C, class IO = Io<C>>
 __global__ void __launch_bounds__(kThr) pass_c(LdArgs a) {
   constexpr int kCols = ColsOf<C>::v, kLog = kCols == 16 ? 4 : 3;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* buf = reinterpret_cast<C*>(smem_raw);
   const int j = blockIdx.y, cb = blockIdx.x;
   if (gated_out(a, j)) return;
-  using IO = Io<C>;
   const int N1 = 1 << a.logN1, N2 = 1 << a.logN2, stride = N1 + 1;
   const int64_t n = (int64_t)1 << a.logN, L = n >> 1, base = (int64_t)j * n;
   const Twiddle<C> tw = IO::tw(a);
@@ -423,6 +438,13 @@ cudaError_t ld_resid(const LdArgs& a, int R, cudaStream_t st) {
   if ((e = launch_cols<dfc>(ld::pass_a<dfc>, a, R, st))) return e;
   if ((e = launch_rows<dfc>(ld::pass_b<dfc, MODE_RESID>, a, R, st))) return e;
   return launch_cols<dfc>(ld::pass_c<dfc>, a, R, st);
+}
+// the same residual through the float32 chain (the outer loop's large-gap iterations)
+cudaError_t ld_resid_f32(const LdArgs& a, int R, cudaStream_t st) {
+  cudaError_t e;
+  if ((e = launch_cols<float2>(ld::pass_a<float2, ld::IoR32>, a, R, st))) return e;
+  if ((e = launch_rows<float2>(ld::pass_b<float2, MODE_RESID>, a, R, st))) return e;
+  return launch_cols<float2>(ld::pass_c<float2, ld::IoR32>, a, R, st);
 }
 // fwd = C x, the full orthonormal DCT-II (float64 in and out)
 cudaError_t ld_forward(const LdArgs& a, int R, cudaStream_t st) {

@@ -43,6 +43,7 @@ cudaError_t ld_mask_codes(const LdArgs& a, int R, cudaStream_t st);
 size_t ld_mask_code_bytes(int64_t n, int R);
 cudaError_t ld_normal(const LdArgs& a, int R, cudaStream_t st);
 cudaError_t ld_resid(const LdArgs& a, int R, cudaStream_t st);
+cudaError_t ld_resid_f32(const LdArgs& a, int R, cudaStream_t st);  // float32 chain, same output
 cudaError_t ld_forward(const LdArgs& a, int R, cudaStream_t st);
 
 }  // namespace mfipm

@@ -1822,13 +1822,13 @@ int large_dct_solve(const LdCall& call, std::string* msg) {
   if (rc) return rc;
   mr::Dev& d = S.d;
   cudaStream_t st = call.stream;
-  auto residual = [&](int gate, bool) -> cudaError_t {
+  auto residual = [&](int gate, bool lowp) -> cudaError_t {
     LdArgs a = S.base;
     a.gate = gate;
     a.din = d.X;
     a.dout = d.Gr;
     g_nlaunch += 3;
-    return ld_resid(a, d.R, st);
+    return lowp ? ld_resid_f32(a, d.R, st) : ld_resid(a, d.R, st);
   };
   OpTimer& T = g_optimer;
   T.reset();
@@ -1844,7 +1844,7 @@ int large_dct_solve(const LdCall& call, std::string* msg) {
     g_nlaunch += 3;
     return T.on ? T.end(st, (double)nprob * (double)call.n) : cudaSuccess;
   };
-  rc = lockstep_run(d, S.part2, S.taus, S.rhos, residual, normal, S.xptr, S.zptr, S.infos_dev, st, msg);
+  rc = lockstep_run(d, S.part2, S.taus, S.rhos, residual, normal, S.xptr, S.zptr, S.infos_dev, st, msg, true);
   if (rc) return rc;
   rc = ld_read_infos(call, S, msg);
   T.collect();
