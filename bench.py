@@ -222,6 +222,11 @@ def stratified_oracle(probs, budget_s, tol=1e-10):
     while the budget lasts).  Returns ({n: [seconds]}, {batch index: oracle x})."""
     from oracle import mfipm_oracle as O
     times, xs = {}, {}
+    # one untimed solve of the smallest class first: loading the linear-algebra libraries and
+    # starting their threads is not the oracle's cost per problem
+    j0 = next((j for n in ORACLE_CLASSES for j, p in enumerate(probs) if p.n == n), None)
+    if j0 is not None:
+        O.ipm(oracle_op(probs[j0]), probs[j0].b, probs[j0].tau, O.OracleParams(tol=tol))
     t_start = time.perf_counter()
     for n in ORACLE_CLASSES:
         j = next((j for j, p in enumerate(probs) if p.n == n), None)
